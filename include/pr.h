@@ -1,0 +1,216 @@
+/*
+ * pr.h -- C ABI of the GB300 perceptual-rasterization library (libpr.so).
+ *
+ * Perceptual rasterization (Ritschel, Friston, Steed 2018) draws a frame in
+ * which every pixel has its own time (rolling display, Sec. 3.1.2) and its
+ * own ray through a continuously foveated image (Sec. 3.1.1), by casting
+ * that pixel's ray against each triangle moved to that time (Sec. 3.2,
+ * "Intersection"), but only for the pixels inside a tight space-time-fovea
+ * bound of the triangle (Sec. 4).  This library runs that hot path on one
+ * GPU in five stages: (a) per-triangle bounds, (b) tile binning, (c) the
+ * per-fragment ray test with a 64-bit atomicMin on depth|id, (d) deferred
+ * shading and (e) its adjoint.
+ *
+ * Conventions shared by every entry point:
+ *  - camera space: x right, y down, z forward; a pose is a row-major 4x4
+ *    rigid world->camera transform [R | T]; pose0 holds at t = 0 and pose1
+ *    at t = 1 of the frame interval (the start/end model-view matrices of
+ *    Sec. 3.2, "Bounding").
+ *  - a vertex moves linearly: world position p + t v over the frame; its
+ *    camera-space position is c(t) = (1-t)(R0 p + T0) + t(R1 (p+v) + T1),
+ *    the interpolation of M_s v_s and M_e v_e (Sec. 3.2).
+ *  - pixel (i, j) has the unit framebuffer location u = ((i+.5)/W, (j+.5)/H)
+ *    and the display location x = q(u) when foveated (else x = u), with
+ *    q(u) = x_f + (u - x_f)/|u - x_f| * p(|u - x_f|), p(d) = D (d/D)^alpha,
+ *    D = sqrt(2) (Sec. 3.1.1; power foveation of Sec. 5.1).
+ *  - its time is t = r(x) = x . d when rolling, else 0 (Sec. 3.1.2; the joint
+ *    mode takes the time at the display location, Sec. 3.1.3 / 4.3).
+ *  - its camera-space ray starts at the origin with direction
+ *    ((2 x0 - 1) tanX, (2 x1 - 1) tanY, 1), so the ray parameter of a hit
+ *    equals its camera z, which is the stored depth (Sec. 3.2).
+ *  - the nearest hit with depth > z_near wins; equal depths go to the
+ *    smaller triangle id; edges are inclusive; no back-face culling.
+ *
+ * Memory: every pointer argument may point to device memory or to host
+ * memory; the library detects which (cudaPointerGetAttributes) and stages
+ * host buffers through its own device memory.  Caller-owned buffers are
+ * only read or written during the call.  All work is issued on the caller's
+ * stream (a cudaStream_t passed as void*, NULL = legacy default stream); a
+ * call returns after its status word has been read back from the device,
+ * so its outputs are complete on return.
+ *
+ * Errors: every entry point returns a pr_status; nothing aborts, traps or
+ * throws across the ABI.  pr_status_string() names a status.
+ */
+#ifndef PR_H
+#define PR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PR_OK = 0,
+    PR_ERR_INVALID_ARG = 1, /* a size, mode, pointer or parameter is out of range */
+    PR_ERR_CUDA = 2,        /* a CUDA runtime call failed (no device, launch error, ...) */
+    PR_ERR_OOM = 3,         /* device allocation failed */
+    PR_ERR_OVERFLOW = 4,    /* a device buffer was too small even after regrowing */
+    PR_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    PR_ERR_NONFINITE = 6,   /* an input position/velocity/colour is NaN or Inf */
+    PR_ERR_NO_CUDA = 7      /* no CUDA device is visible */
+} pr_status;
+
+typedef enum {
+    PR_CLASSIC = 0,  /* t = 0, x = u: common rasterization */
+    PR_ROLLING = 1,  /* t = r(u), x = u (Sec. 3.1.2) */
+    PR_FOVEATED = 2, /* t = 0, x = q(u) (Sec. 3.1.1) */
+    PR_BOTH = 3      /* t = r(q(u)), x = q(u) (Sec. 3.1.3) */
+} pr_mode;
+
+/* Bound of the display region a moving triangle can cover (Sec. 4.2).
+ * Every kind is conservative, so the image does not depend on it (Sec. 3.2:
+ * the intersection test is the same whatever bound is used); only the
+ * number of ray tests does. */
+typedef enum {
+    PR_BOUND_ZENON = 0,    /* Sec. 4.2.4: catch-up time interval of the rolling scan, default */
+    PR_BOUND_ADAPTIVE = 1, /* Sec. 4.2.3: interval of r over the projected space-time vertices */
+    PR_BOUND_HULL = 2,     /* Sec. 4.2.2: convex hull of the projected space-time vertices */
+    PR_BOUND_QUAD = 3,     /* Sec. 4.2.1: bounding box of the projected space-time vertices */
+    PR_BOUND_TRIVIAL = 4   /* the whole viewport */
+} pr_bound;
+
+/* One view: the camera, the two poses that bracket the frame, the fovea,
+ * the display's rolling direction and the shading constants. */
+typedef struct {
+    int32_t W, H;         /* framebuffer size in pixels, 1..16384 */
+    int32_t mode;         /* pr_mode */
+    int32_t pad0;
+    float tan_x, tan_y;   /* tangents of the half field of view, > 0 */
+    float z_near;         /* hits need depth > z_near > 0 */
+    float alpha;          /* foveation exponent, 1 <= alpha <= 5 (1 = identity) */
+    float pose0[16];      /* world->camera at t = 0, row-major */
+    float pose1[16];      /* world->camera at t = 1, row-major */
+    float fovea[2];       /* x_f in unit framebuffer coordinates, in [0,1]^2 */
+    float d[2];           /* rolling direction: d0, d1 >= 0 and d0 + d1 <= 1 */
+    float light_w[3];     /* world-space direction towards the light (normalised by the library) */
+    float k_a, k_d;       /* rgb = albedo * (k_a + k_d * max(0, n.l)) */
+} pr_view;
+
+typedef struct {
+    int32_t bound;        /* pr_bound */
+    int32_t tile;         /* bin tile side in pixels: 8, 16 or 32; 0 = library default (16) */
+    int32_t fp64_retest;  /* 1: re-test fragments flagged by the FP32 error bound in FP64 */
+    int32_t seg;          /* triangles per fragment work item; 0 = default */
+} pr_params;
+
+/* Counters of the last rasterize call on a scene or workspace. */
+typedef struct {
+    uint64_t tests;       /* ray-triangle tests executed in stage (c) */
+    uint64_t hits;        /* tests that hit (before depth resolution) */
+    uint64_t pairs;       /* (triangle, tile) bin entries */
+    uint64_t items;       /* fragment work items */
+    uint64_t culled;      /* triangles with an empty bound */
+    uint64_t flagged;     /* pixels re-tested in FP64 (precision form) */
+    uint64_t changed;     /* pixels whose winner the FP64 re-test changed */
+    uint64_t pixels;      /* framebuffer pixels over all views */
+} pr_stats;
+
+typedef struct pr_scene pr_scene;         /* library-owned device copy of a mesh + its scratch */
+typedef struct pr_workspace pr_workspace; /* scratch of the batched entry points */
+
+/* Copies a mesh into library-owned device memory (structure of arrays).
+ * pos, vel, col: float32 [V][3] (world position at t = 0, world
+ * displacement over the frame, RGB albedo); tri: int32 [T][3] vertex
+ * indices in [0, V).  V >= 1 and T >= 0 up to 2^30.  The caller keeps
+ * ownership of its arrays.  Returns PR_ERR_NONFINITE if a position,
+ * velocity or colour is not finite, PR_ERR_INVALID_ARG for an index out of
+ * range.  The mesh is the world-space input of Sec. 3.2 ("Bounding").  */
+pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, const int32_t *tri,
+                          int64_t V, int64_t T, void *stream, pr_scene **out);
+
+/* Replaces the positions, velocities and colours of an uploaded scene
+ * (same V); any pointer may be NULL to keep that array.  Used to step the
+ * scene in optimisation loops without re-uploading the indices. */
+pr_status pr_scene_update(pr_scene *scene, const float *pos, const float *vel, const float *col,
+                          void *stream);
+
+void pr_scene_free(pr_scene *scene);
+
+/* Stages (a)-(c) for one view: writes id_out uint32 [H][W] (0xFFFFFFFF =
+ * background) and depth_out float32 [H][W] (+inf = background); either may
+ * be NULL.  params may be NULL (defaults).  Sec. 3.2 "Bounding" and
+ * "Intersection"; bounds of Sec. 4. */
+pr_status pr_rasterize(pr_scene *scene, const pr_view *view, const pr_params *params, uint32_t *id_out,
+                       float *depth_out, void *stream);
+
+/* Stage (d): deferred Lambert shading with the light interpolated at each
+ * pixel's time (Sec. 3.2, "Shading").  id: uint32 [H][W] from
+ * pr_rasterize; rgb_out: float32 planar [3][H][W] (0 = background). */
+pr_status pr_shade(pr_scene *scene, const pr_view *view, const uint32_t *id, float *rgb_out, void *stream);
+
+/* Stage (e): adjoint of (d) and of the barycentrics of (c) with the
+ * visible ids held fixed.  grad_rgb: float32 planar [3][H][W]; dcol, dpos,
+ * dvel: float32 [V][3], ACCUMULATED (+=) by the call; any may be NULL.
+ * Not in the paper: the differentiable form of the method. */
+pr_status pr_backward(pr_scene *scene, const pr_view *view, const uint32_t *id, const float *grad_rgb,
+                      float *dcol, float *dpos, float *dvel, void *stream);
+
+/* One entry of a batched call: a scene, a view and its outputs. */
+typedef struct {
+    pr_scene *scene;
+    pr_view view;
+    uint32_t *id_out;     /* [H][W] or NULL */
+    float *depth_out;     /* [H][W] or NULL */
+    float *rgb_out;       /* [3][H][W] or NULL: shade in the same call */
+    int32_t tile;         /* 0: params->tile, else 8, 16 or 32 for this view */
+    int32_t pad;
+} pr_batch_view;
+
+pr_status pr_workspace_create(pr_workspace **out);
+void pr_workspace_free(pr_workspace *ws);
+
+/* Stages (a)-(d) for n views of possibly different scenes, sizes and modes
+ * as ONE sequence: one bound launch over all triangles, one binning pass
+ * over all tiles and one persistent fragment launch per tile size over a
+ * global (view, tile) work queue.  Per view, the outputs are bit-identical
+ * to pr_rasterize + pr_shade.  Scratch lives in ws. */
+pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                             void *stream);
+
+/* Captures the same sequence into a CUDA graph (after one eager run that
+ * sizes every buffer) and replays it with pr_graph_launch.  The views and
+ * their buffers must stay valid and unchanged in shape while the graph
+ * lives; their contents may change between launches.  pr_graph_launch
+ * returns after the replay's status has been read. */
+typedef struct pr_graph pr_graph;
+pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n,
+                                 const pr_params *params, void *stream, pr_graph **out);
+pr_status pr_graph_launch(pr_graph *g, void *stream);
+void pr_graph_free(pr_graph *g);
+
+/* Counters of the last rasterize call made with this scene / workspace. */
+pr_status pr_scene_stats(const pr_scene *scene, pr_stats *out);
+pr_status pr_workspace_stats(const pr_workspace *ws, pr_stats *out);
+
+/* Per-triangle bound of the last pr_rasterize call on this scene (stage
+ * (a) output, for tests of conservativeness): pix_box int32 [T][4] =
+ * inclusive framebuffer pixel box (i0, j0, i1, j1), empty when i0 > i1;
+ * t_range float32 [T][2] = [t_min, t_max]. */
+pr_status pr_debug_bounds(const pr_scene *scene, int32_t *pix_box, float *t_range);
+
+/* Host evaluation of the stage (a) catch-up interval for one triangle (the
+ * Zenon bound of Sec. 4.2.4): S, E float [3][3] camera-space vertices at
+ * t = 0 and t = 1; writes [t_min, t_max] and returns 1, or returns 0 when
+ * the rolling scan never meets the triangle.  For unit tests. */
+int32_t pr_debug_catch_interval(const pr_view *view, const float *S, const float *E, float *t_out);
+
+const char *pr_status_string(pr_status s);
+int32_t pr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PR_H */

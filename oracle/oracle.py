@@ -124,12 +124,13 @@ def render(view, pos, vel, col, tri, pix=None, near=False):
 
 
 def evaluate(view, pos, vel, tri, lin: int, tri_id: int):
-    """(b0, b1, b2, s, hit) of one triangle at one pixel, in FP64."""
+    """(b0, b1, b2, s, hit, display edge distance) of one triangle at one
+    pixel, in FP64."""
     L = lib()
     v = make_view(view)
     pos, vel = _d(pos), _d(vel)
     tri = np.ascontiguousarray(tri, dtype=np.int32)
-    out = np.empty(5, np.float64)
+    out = np.empty(6, np.float64)
     L.or_eval(C.byref(v), _ptr(pos), _ptr(vel), _ptr(tri), int(lin), int(tri_id), _ptr(out))
     return out
 

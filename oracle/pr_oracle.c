@@ -352,11 +352,14 @@ void or_render(const or_view *v, int64_t V, int64_t T, const double *pos, const 
 /*
  * Evaluate one (pixel, triangle) pair without the inside test: out[0..2] =
  * barycentrics of the ray point in the plane, out[3] = ray parameter s,
- * out[4] = 1 if it counts as a hit.  Used to excuse GPU/oracle mismatches
- * that sit on an edge or a depth tie.
+ * out[4] = 1 if it counts as a hit, out[5] = distance (unit display
+ * coordinates) from the pixel's display location to the boundary of the
+ * triangle projected at the pixel time (0 if a vertex is not in front of
+ * the camera).  Used to excuse GPU/oracle mismatches that sit on an edge or
+ * a depth tie.
  */
 void or_eval(const or_view *v, const double *pos, const double *vel, const int32_t *tri, int64_t lin,
-             int64_t id, double out[5])
+             int64_t id, double out[6])
 {
     int64_t i = lin % v->W, j = lin / v->W;
     double t, x[2], dir[3], P[3][3], b[3], s;
@@ -368,6 +371,27 @@ void or_eval(const or_view *v, const double *pos, const double *vel, const int32
     out[2] = b[2];
     out[3] = s;
     out[4] = is_hit(reg, b, s, v->z_near);
+    double q[3][2], dmin = INFINITY;
+    int front = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (!(P[k][2] > 0.0))
+            front = 0;
+        q[k][0] = (P[k][0] / (P[k][2] * v->tan_x) + 1.0) / 2.0;
+        q[k][1] = (P[k][1] / (P[k][2] * v->tan_y) + 1.0) / 2.0;
+    }
+    for (int k = 0; k < 3 && front; ++k) {
+        const double *a = q[k], *c = q[(k + 1) % 3];
+        double e0 = c[0] - a[0], e1 = c[1] - a[1];
+        double w0 = x[0] - a[0], w1 = x[1] - a[1];
+        double ee = e0 * e0 + e1 * e1;
+        double f = ee > 0.0 ? (w0 * e0 + w1 * e1) / ee : 0.0;
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        double d0 = w0 - f * e0, d1 = w1 - f * e1;
+        double d = sqrt(d0 * d0 + d1 * d1);
+        if (d < dmin)
+            dmin = d;
+    }
+    out[5] = front ? dmin : 0.0;
 }
 
 /* ---------------------------------------------------------------- gradient */

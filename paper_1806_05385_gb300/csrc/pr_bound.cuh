@@ -1,0 +1,276 @@
+// pr_bound.cuh -- math of stage (a), the per-triangle space-time-fovea bound
+// (Sec. 4).  Host+device so that the catch-up interval can be unit-tested
+// on the CPU through pr_debug_catch_interval.
+#pragma once
+
+#include <math.h>
+
+#include "pr_internal.cuh"
+
+namespace pr {
+
+__host__ __device__ inline float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float cross2(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
+
+// ---------------------------------------------------------------------------
+// Zenon's catch-up interval (Sec. 4.2.4), exact form.
+//
+// The rolling scan shows display location x at time r(x) = d . x.  A point
+// c(t) of the moving triangle is met by the scan when t = r(proj(c(t))).
+// Multiplying by 2 z(t) > 0 turns this into h(t) = 2 t z - kx X - ky Y - ks z
+// = 0 with kx = d0/tanX, ky = d1/tanY, ks = d0 + d1, which is linear in the
+// camera-space point and therefore, for fixed t, linear in the barycentrics:
+// h(t, b) = sum_k b_k h_k(t), where h_k(t) = a t^2 + b t + c is the quadratic
+// of vertex k (the paper's rational catch-up equation of Sec. 4.2.4 with the
+// scan speed and the perspective divide written out).  Some point of the
+// triangle is met at time t exactly when min_k h_k(t) <= 0 <= max_k h_k(t);
+// that set only changes at roots of the h_k, so it is bounded by
+// [t_min, t_max] = hull of {roots in [t_lo, t_hi]} plus the domain ends where
+// the condition already holds.  Unlike the paper's closed form, this needs
+// neither one catch per vertex nor a fixed root branch.
+//
+// S: camera-space vertices at t = 0, D: their motion over the frame (all
+// points must have z > 0 over [t_lo, t_hi]).  Returns false when no point of
+// the triangle is ever met by the scan.  FP32 with explicit tolerances: every
+// root gets a margin of kEpsT, near-double roots contribute their vertex,
+// and the end conditions are tested with an evaluation-error allowance.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline bool catch_interval(const float3 S[3], const float3 D[3], float tan_x, float tan_y,
+                                               float d0, float d1, float t_lo, float t_hi, float &tmin, float &tmax)
+{
+    const float kx = d0 / tan_x, ky = d1 / tan_y, ks = d0 + d1;
+    float lo = INFINITY, hi = -INFINITY;
+    bool lo_le = false, lo_ge = false, hi_le = false, hi_ge = false;
+    bool finite = true;
+    for (int k = 0; k < 3; ++k) {
+        const float a = 2.f * D[k].z;
+        const float b = 2.f * S[k].z - kx * D[k].x - ky * D[k].y - ks * D[k].z;
+        const float c = -(kx * S[k].x + ky * S[k].y + ks * S[k].z);
+        if (!(isfinite(a) && isfinite(b) && isfinite(c)))
+            finite = false;
+        // evaluation-error allowance of h at the domain ends
+        const float m1 = 2.f * fabsf(S[k].z) + kx * fabsf(D[k].x) + ky * fabsf(D[k].y) + ks * fabsf(D[k].z);
+        const float m0 = kx * fabsf(S[k].x) + ky * fabsf(S[k].y) + ks * fabsf(S[k].z);
+        const float ends[2] = {t_lo, t_hi};
+        for (int e = 0; e < 2; ++e) {
+            const float t = ends[e];
+            const float h = fmaf(fmaf(a, t, b), t, c);
+            const float tol = 1e-5f * (fabsf(a) * t * t + m1 * fabsf(t) + m0) + 1e-30f;
+            const bool le = h <= tol, ge = h >= -tol;
+            if (e == 0) {
+                lo_le |= le;
+                lo_ge |= ge;
+            } else {
+                hi_le |= le;
+                hi_ge |= ge;
+            }
+        }
+        // roots
+        float r[2];
+        int nr = 0;
+        const float scale = fabsf(b) + fabsf(c);
+        if (fabsf(a) <= 1e-7f * scale) {
+            if (b != 0.f)
+                r[nr++] = -c / b;
+        } else {
+            const float disc = b * b - 4.f * a * c;
+            const float dtol = 1e-5f * (b * b + 4.f * fabsf(a * c));
+            if (disc < -dtol) {
+            } else if (disc <= dtol) {
+                r[nr++] = -b / (2.f * a);
+            } else {
+                const float q = -0.5f * (b + copysignf(sqrtf(disc), b));
+                r[nr++] = q / a;
+                if (q != 0.f)
+                    r[nr++] = c / q;
+            }
+        }
+        for (int e = 0; e < nr; ++e) {
+            if (r[e] >= t_lo - kEpsT && r[e] <= t_hi + kEpsT) {
+                lo = fminf(lo, r[e] - kEpsT);
+                hi = fmaxf(hi, r[e] + kEpsT);
+            }
+        }
+    }
+    if (!finite) {
+        tmin = t_lo;
+        tmax = t_hi;
+        return true;
+    }
+    if (lo_le && lo_ge)
+        lo = t_lo;
+    if (hi_le && hi_ge)
+        hi = t_hi;
+    lo = fmaxf(lo, t_lo);
+    hi = fminf(hi, t_hi);
+    if (!(lo <= hi))
+        return false;
+    tmin = lo;
+    tmax = hi;
+    return true;
+}
+
+// Convex hull (Andrew's monotone chain) of n <= 16 points; writes the hull
+// counter-clockwise (cross > 0 turns) without repeating the first point and
+// returns its size.  pts is sorted in place.
+__host__ __device__ inline int convex_hull(float2 *pts, int n, float2 *out)
+{
+    for (int i = 1; i < n; ++i) {
+        float2 key = pts[i];
+        int j = i - 1;
+        while (j >= 0 && (pts[j].x > key.x || (pts[j].x == key.x && pts[j].y > key.y))) {
+            pts[j + 1] = pts[j];
+            --j;
+        }
+        pts[j + 1] = key;
+    }
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        while (k >= 2 && cross2(f2sub(out[k - 1], out[k - 2]), f2sub(pts[i], out[k - 2])) <= 0.f)
+            --k;
+        out[k++] = pts[i];
+    }
+    for (int i = n - 2, t = k + 1; i >= 0; --i) {
+        while (k >= t && cross2(f2sub(out[k - 1], out[k - 2]), f2sub(pts[i], out[k - 2])) <= 0.f)
+            --k;
+        out[k++] = pts[i];
+    }
+    return k > 1 ? k - 1 : k;
+}
+
+// Bounding box (x0, x1, y0, y1) of the annular sector around f between the
+// unit directions a (clockwise end) and b (counter-clockwise end, less than
+// half a turn from a) and the radii [rho0, rho1]; full = the whole disc.
+__host__ __device__ inline float4 sector_box(float2 f, float2 a, float2 b, float rho0, float rho1, bool full)
+{
+    if (full)
+        return make_float4(f.x - rho1, f.x + rho1, f.y - rho1, f.y + rho1);
+    float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    const float2 c[4] = {make_float2(f.x + rho0 * a.x, f.y + rho0 * a.y), make_float2(f.x + rho0 * b.x, f.y + rho0 * b.y),
+                         make_float2(f.x + rho1 * a.x, f.y + rho1 * a.y), make_float2(f.x + rho1 * b.x, f.y + rho1 * b.y)};
+    for (int k = 0; k < 4; ++k) {
+        x0 = fminf(x0, c[k].x);
+        x1 = fmaxf(x1, c[k].x);
+        y0 = fminf(y0, c[k].y);
+        y1 = fmaxf(y1, c[k].y);
+    }
+    const float2 ax[4] = {make_float2(1.f, 0.f), make_float2(0.f, 1.f), make_float2(-1.f, 0.f), make_float2(0.f, -1.f)};
+    for (int k = 0; k < 4; ++k) {
+        if (cross2(a, ax[k]) >= 0.f && cross2(ax[k], b) >= 0.f) {
+            x0 = fminf(x0, f.x + rho1 * ax[k].x);
+            x1 = fmaxf(x1, f.x + rho1 * ax[k].x);
+            y0 = fminf(y0, f.y + rho1 * ax[k].y);
+            y1 = fmaxf(y1, f.y + rho1 * ax[k].y);
+        }
+    }
+    return make_float4(x0, x1, y0, y1);
+}
+
+// Distance from f to the segment [p, q].
+__host__ __device__ inline float seg_dist(float2 f, float2 p, float2 q)
+{
+    const float2 e = f2sub(q, p), w = f2sub(f, p);
+    const float ee = e.x * e.x + e.y * e.y;
+    float s = ee > 0.f ? (w.x * e.x + w.y * e.y) / ee : 0.f;
+    s = fminf(fmaxf(s, 0.f), 1.f);
+    const float dx = w.x - s * e.x, dy = w.y - s * e.y;
+    return sqrtf(dx * dx + dy * dy);
+}
+
+// Rotate the unit vector a by the small angle whose sine is sn (positive =
+// counter-clockwise).
+__host__ __device__ inline float2 rot_small(float2 a, float sn)
+{
+    sn = fminf(fmaxf(sn, -1.f), 1.f);
+    const float cs = sqrtf(fmaxf(0.f, 1.f - sn * sn));
+    return make_float2(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
+}
+
+// Framebuffer box (u0, u1, v0, v1) that contains q^-1 of the convex display
+// polygon poly[0..n) grown by eps.  q^-1 is radial about the fovea f with
+// radius map p^-1 (Sec. 3.1.1), so the preimage lies in the annular sector
+// spanned by the polygon's directions and the radii p^-1 of its nearest and
+// farthest distances from f.  inv_alpha = 1/alpha.
+__host__ __device__ inline float4 fov_preimage_box(const float2 *poly, int n, float2 f, float inv_alpha, float eps)
+{
+    float rmax = 0.f, rmin = INFINITY;
+    for (int k = 0; k < n; ++k) {
+        const float2 w = f2sub(poly[k], f);
+        rmax = fmaxf(rmax, sqrtf(w.x * w.x + w.y * w.y));
+    }
+    // is f inside the polygon (within eps)?
+    float area = 0.f;
+    for (int k = 0; k < n; ++k)
+        area += cross2(poly[k], poly[(k + 1) % n]);
+    bool inside = n >= 3 && area != 0.f;
+    for (int k = 0; k < n && inside; ++k) {
+        const float2 p = poly[k], q = poly[(k + 1) % n];
+        const float2 e = f2sub(q, p);
+        const float len = sqrtf(e.x * e.x + e.y * e.y);
+        const float side = (area > 0.f ? 1.f : -1.f) * cross2(e, f2sub(f, p));
+        if (side < -eps * len)
+            inside = false;
+    }
+    if (!inside) {
+        for (int k = 0; k < n; ++k)
+            rmin = fminf(rmin, seg_dist(f, poly[k], poly[(k + 1) % n]));
+        rmin = fmaxf(0.f, rmin - eps);
+    }
+    rmax += eps;
+    const float kD1 = powf(kSqrt2, 1.f - inv_alpha);
+    const float rho1 = kD1 * powf(rmax, inv_alpha) * (1.f + 1e-5f) + 1e-6f;
+    if (inside || rmin <= 0.f)
+        return sector_box(f, make_float2(1.f, 0.f), make_float2(1.f, 0.f), 0.f, rho1, true);
+    const float rho0 = kD1 * powf(rmin, inv_alpha) * (1.f - 1e-5f);
+    float2 a = f2sub(poly[0], f), b = a;
+    for (int k = 1; k < n; ++k) {
+        const float2 w = f2sub(poly[k], f);
+        if (cross2(a, w) < 0.f)
+            a = w;
+        if (cross2(b, w) > 0.f)
+            b = w;
+    }
+    const float la = sqrtf(a.x * a.x + a.y * a.y), lb = sqrtf(b.x * b.x + b.y * b.y);
+    a = make_float2(a.x / la, a.y / la);
+    b = make_float2(b.x / lb, b.y / lb);
+    // the grown polygon spans a little more angle: asin(eps / r)
+    a = rot_small(a, -(eps / fmaxf(la, eps) + 1e-6f));
+    b = rot_small(b, eps / fmaxf(lb, eps) + 1e-6f);
+    if (cross2(a, b) <= 0.f)  // span reached half a turn: give up on angles
+        return sector_box(f, a, b, 0.f, rho1, true);
+    return sector_box(f, a, b, rho0, rho1, false);
+}
+
+// Display box (x0, x1, y0, y1) that contains q of the framebuffer box
+// [u0,u1] x [v0,v1]: the same sector argument with the radius map p.
+__host__ __device__ inline float4 fov_image_box(float u0, float u1, float v0, float v1, float2 f, float alpha)
+{
+    const float2 c[4] = {make_float2(u0, v0), make_float2(u1, v0), make_float2(u1, v1), make_float2(u0, v1)};
+    float rmax = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const float2 w = f2sub(c[k], f);
+        rmax = fmaxf(rmax, sqrtf(w.x * w.x + w.y * w.y));
+    }
+    const float kD1 = powf(kSqrt2, 1.f - alpha);
+    const float rho1 = kD1 * powf(rmax, alpha) * (1.f + 1e-5f) + 1e-7f;
+    const bool inside = f.x >= u0 && f.x <= u1 && f.y >= v0 && f.y <= v1;
+    if (inside)
+        return sector_box(f, make_float2(1.f, 0.f), make_float2(1.f, 0.f), 0.f, rho1, true);
+    const float cx = fminf(fmaxf(f.x, u0), u1), cy = fminf(fmaxf(f.y, v0), v1);
+    const float rmin = sqrtf((cx - f.x) * (cx - f.x) + (cy - f.y) * (cy - f.y));
+    const float rho0 = kD1 * powf(rmin, alpha) * (1.f - 1e-5f);
+    float2 a = f2sub(c[0], f), b = a;
+    for (int k = 1; k < 4; ++k) {
+        const float2 w = f2sub(c[k], f);
+        if (cross2(a, w) < 0.f)
+            a = w;
+        if (cross2(b, w) > 0.f)
+            b = w;
+    }
+    const float la = sqrtf(a.x * a.x + a.y * a.y), lb = sqrtf(b.x * b.x + b.y * b.y);
+    a = rot_small(make_float2(a.x / la, a.y / la), -1e-6f);
+    b = rot_small(make_float2(b.x / lb, b.y / lb), 1e-6f);
+    return sector_box(f, a, b, rho0, rho1, false);
+}
+
+}  // namespace pr

@@ -1,0 +1,922 @@
+// pr_host.cu -- the C ABI of libpr (include/pr.h): scene upload, per-view
+// and batched rasterization, shading, adjoint, graph capture.
+//
+// Orchestration of one (batched) frame, all on the caller's stream:
+//   view table -> tile display boxes -> stage (a) bounds -> stage (b) count
+//   -> scan -> scatter -> work items -> stage (c) persistent fragment kernel
+//   (one launch per tile size) -> resolve -> [stage (d) shade]
+// then one device->host read of the status word.  Bin and item buffers are
+// sized from a capacity; if a frame overflows them, the counts it reported
+// size the buffers and the frame is run again.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pr_bound.cuh"
+#include "pr_launch.h"
+
+using namespace pr;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~DevBuf()
+    {
+        if (p)
+            cudaFree(p);
+    }
+    template <class T>
+    T *as() const
+    {
+        return static_cast<T *>(p);
+    }
+};
+
+// Grows b to hold at least `bytes` (contents are not kept).
+cudaError_t ensure(DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap && b.p)
+        return cudaSuccess;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    const size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = want;
+    return cudaSuccess;
+}
+
+template <class T>
+struct PinnedBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    ~PinnedBuf()
+    {
+        if (p)
+            cudaFreeHost(p);
+    }
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= cap && p)
+            return cudaSuccess;
+        if (p)
+            cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMallocHost((void **)&p, std::max<size_t>(n, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        cap = std::max<size_t>(n, 1);
+        return cudaSuccess;
+    }
+};
+
+bool is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+pr_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return PR_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return PR_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+        return PR_ERR_NO_CUDA;
+    return PR_ERR_CUDA;
+}
+
+#define PR_TRY(expr)                                 \
+    do {                                             \
+        cudaError_t _e = (expr);                     \
+        if (_e != cudaSuccess)                       \
+            return from_cuda(_e);                    \
+    } while (0)
+
+constexpr int kDefaultTile = 16;
+constexpr int kDefaultSeg = 256;
+
+}  // namespace
+
+// Scratch of one batched frame.
+struct pr_workspace {
+    DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, tile_tris, items, keys, counters, heads;
+    DevBuf stage;                  // device copies of host-side outputs
+    long long cap_pairs = 0, cap_items = 0;
+    PinnedBuf<ViewDev> h_views;
+    PinnedBuf<long long> h_offs;
+    PinnedBuf<Counters> h_cnt;
+    pr_stats stats{};
+    long long last_T = 0;          // triangles of the last frame (debug bounds)
+};
+
+struct pr_scene {
+    long long V = 0, T = 0;
+    DevBuf soa;   // 9 V floats: px py pz vx vy vz cr cg cb
+    DevBuf idx;   // 3 T ints: i0 i1 i2
+    DevBuf stage; // host input staging
+    pr_workspace ws;
+};
+
+struct pr_graph {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    pr_workspace *ws = nullptr;
+    long long npix = 0;
+};
+
+namespace {
+
+// Host-side derivation of a view's device constants.
+pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int bound, int fp64, ViewDev &v)
+{
+    if (in.W < 1 || in.H < 1 || in.W > 16384 || in.H > 16384)
+        return PR_ERR_INVALID_ARG;
+    if (in.mode < PR_CLASSIC || in.mode > PR_BOTH)
+        return PR_ERR_INVALID_ARG;
+    if (!(in.tan_x > 0.f) || !(in.tan_y > 0.f) || !(in.z_near > 0.f) || !std::isfinite(in.tan_x) ||
+        !std::isfinite(in.tan_y))
+        return PR_ERR_INVALID_ARG;
+    if (!(in.alpha >= 1.f && in.alpha <= 5.f))
+        return PR_ERR_INVALID_ARG;
+    if (!(in.d[0] >= 0.f && in.d[1] >= 0.f && in.d[0] + in.d[1] <= 1.f + 1e-6f) ||
+        ((in.mode == PR_ROLLING || in.mode == PR_BOTH) && in.d[0] + in.d[1] <= 0.f))
+        return PR_ERR_INVALID_ARG;
+    if (!(in.fovea[0] >= 0.f && in.fovea[0] <= 1.f && in.fovea[1] >= 0.f && in.fovea[1] <= 1.f))
+        return PR_ERR_INVALID_ARG;
+    if (tile != 8 && tile != 16 && tile != 32)
+        return PR_ERR_INVALID_ARG;
+    if (bound < PR_BOUND_ZENON || bound > PR_BOUND_TRIVIAL)
+        return PR_ERR_INVALID_ARG;
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(in.pose0[k]) || !std::isfinite(in.pose1[k]))
+            return PR_ERR_INVALID_ARG;
+    std::memset(&v, 0, sizeof v);
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) {
+            v.R0[3 * r + c] = in.pose0[4 * r + c];
+            v.R1[3 * r + c] = in.pose1[4 * r + c];
+        }
+        v.T0[r] = in.pose0[4 * r + 3];
+        v.T1[r] = in.pose1[4 * r + 3];
+    }
+    v.tan_x = in.tan_x;
+    v.tan_y = in.tan_y;
+    v.z_near = in.z_near;
+    v.fx = in.fovea[0];
+    v.fy = in.fovea[1];
+    v.alpha = in.alpha;
+    v.inv_alpha = 1.f / in.alpha;
+    v.d0 = in.d[0];
+    v.d1 = in.d[1];
+    v.t_lo = 0.f;
+    v.t_hi = std::min(1.f, in.d[0] + in.d[1]);
+    double lw[3] = {in.light_w[0], in.light_w[1], in.light_w[2]};
+    double ln = std::sqrt(lw[0] * lw[0] + lw[1] * lw[1] + lw[2] * lw[2]);
+    if (!(ln > 0.0) || !std::isfinite(ln))
+        return PR_ERR_INVALID_ARG;
+    for (int r = 0; r < 3; ++r) {
+        double a = 0, b = 0;
+        for (int c = 0; c < 3; ++c) {
+            a += (double)in.pose0[4 * r + c] * lw[c] / ln;
+            b += (double)in.pose1[4 * r + c] * lw[c] / ln;
+        }
+        v.l0[r] = (float)a;
+        v.l1[r] = (float)b;
+    }
+    v.k_a = in.k_a;
+    v.k_d = in.k_d;
+    v.W = in.W;
+    v.H = in.H;
+    v.mode = in.mode;
+    v.S = tile;
+    v.tiles_x = (in.W + tile - 1) / tile;
+    v.tiles_y = (in.H + tile - 1) / tile;
+    v.bound = bound;
+    v.fp64 = fp64;
+    v.T = (int)sc->T;
+    v.V = (int)sc->V;
+    const float *s = sc->soa.as<float>();
+    const long long V = sc->V;
+    v.px = s;
+    v.py = s + V;
+    v.pz = s + 2 * V;
+    v.vx = s + 3 * V;
+    v.vy = s + 4 * V;
+    v.vz = s + 5 * V;
+    v.cr = s + 6 * V;
+    v.cg = s + 7 * V;
+    v.cb = s + 8 * V;
+    const int *ix = sc->idx.as<int>();
+    v.i0 = ix;
+    v.i1 = ix + sc->T;
+    v.i2 = ix + 2 * sc->T;
+    return PR_OK;
+}
+
+pr_params default_params(const pr_params *p)
+{
+    pr_params d{PR_BOUND_ZENON, kDefaultTile, 0, kDefaultSeg};
+    if (p) {
+        d = *p;
+        if (d.tile == 0)
+            d.tile = kDefaultTile;
+        if (d.seg <= 0)
+            d.seg = kDefaultSeg;
+    }
+    return d;
+}
+
+struct BatchPlan {
+    std::vector<int> order;           // views sorted by tile size
+    std::vector<ViewDev> vd;          // in `order`
+    std::vector<long long> tri_off, tile_off, pix_off;
+    long long ttot = 0, ntiles = 0, npix = 0;
+    struct Cls {
+        int S;
+        long long tile_lo, tile_hi;
+    };
+    std::vector<Cls> classes;
+    // output staging: per view (in order) device pointers used by kernels
+    struct Out {
+        uint32_t *id_user;
+        float *depth_user, *rgb_user;
+        bool id_host, depth_host, rgb_host;
+        long long id_off, depth_off, rgb_off;  // byte offsets in ws->stage, -1 = none
+    };
+    std::vector<Out> out;
+    size_t stage_bytes = 0;
+};
+
+pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, BatchPlan &P)
+{
+    if (n < 1 || !views)
+        return PR_ERR_INVALID_ARG;
+    std::vector<int> tiles(n);
+    for (int k = 0; k < n; ++k) {
+        tiles[k] = views[k].tile ? views[k].tile : prm.tile;
+        if (!views[k].scene)
+            return PR_ERR_INVALID_ARG;
+    }
+    P.order.resize(n);
+    for (int k = 0; k < n; ++k)
+        P.order[k] = k;
+    std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) { return tiles[a] < tiles[b]; });
+    P.vd.resize(n);
+    P.out.resize(n);
+    P.tri_off.assign(n + 1, 0);
+    P.tile_off.assign(n + 1, 0);
+    P.pix_off.assign(n + 1, 0);
+    size_t stage = 0;
+    auto take = [&](size_t bytes) {
+        long long off = (long long)stage;
+        stage += (bytes + 255) & ~(size_t)255;
+        return off;
+    };
+    for (int q = 0; q < n; ++q) {
+        const pr_batch_view &bv = views[P.order[q]];
+        pr_status s = make_viewdev(bv.view, bv.scene, tiles[P.order[q]], prm.bound, prm.fp64_retest, P.vd[q]);
+        if (s != PR_OK)
+            return s;
+        ViewDev &v = P.vd[q];
+        v.tri_off = P.tri_off[q];
+        v.tile_off = P.tile_off[q];
+        v.pix_off = P.pix_off[q];
+        P.tri_off[q + 1] = P.tri_off[q] + bv.scene->T;
+        P.tile_off[q + 1] = P.tile_off[q] + (long long)v.tiles_x * v.tiles_y;
+        P.pix_off[q + 1] = P.pix_off[q] + (long long)v.W * v.H;
+        const long long np = (long long)v.W * v.H;
+        BatchPlan::Out &o = P.out[q];
+        o.id_user = bv.id_out;
+        o.depth_user = bv.depth_out;
+        o.rgb_user = bv.rgb_out;
+        o.id_host = bv.id_out && !is_device_ptr(bv.id_out);
+        o.depth_host = bv.depth_out && !is_device_ptr(bv.depth_out);
+        o.rgb_host = bv.rgb_out && !is_device_ptr(bv.rgb_out);
+        // ids are staged when the caller's buffer is on the host or absent
+        // but shading needs them
+        o.id_off = (o.id_host || (!bv.id_out && bv.rgb_out)) ? take(np * 4) : -1;
+        o.depth_off = o.depth_host ? take(np * 4) : -1;
+        o.rgb_off = o.rgb_host ? take(np * 12) : -1;
+    }
+    P.ttot = P.tri_off[n];
+    P.ntiles = P.tile_off[n];
+    P.npix = P.pix_off[n];
+    P.stage_bytes = stage;
+    if (P.ttot >= (1ll << 32) - 1)
+        return PR_ERR_INVALID_ARG;
+    for (int q = 0; q < n; ++q) {
+        const int S = P.vd[q].S;
+        if (P.classes.empty() || P.classes.back().S != S)
+            P.classes.push_back({S, P.tile_off[q], P.tile_off[q + 1]});
+        else
+            P.classes.back().tile_hi = P.tile_off[q + 1];
+    }
+    return PR_OK;
+}
+
+// Sizes every buffer of the workspace for the plan (eager calls only).
+pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
+{
+    const int n = (int)P.vd.size();
+    PR_TRY(ensure(ws->views, sizeof(ViewDev) * n));
+    PR_TRY(ensure(ws->offs, sizeof(long long) * 3 * (n + 1)));
+    PR_TRY(ensure(ws->rec, sizeof(float4) * kRecF4 * std::max(P.ttot, 1ll)));
+    PR_TRY(ensure(ws->hp, sizeof(float4) * kMaxHp * std::max(P.ttot, 1ll)));
+    PR_TRY(ensure(ws->tbox, sizeof(int4) * std::max(P.ttot, 1ll)));
+    PR_TRY(ensure(ws->tile_box, sizeof(float4) * std::max(P.ntiles, 1ll)));
+    PR_TRY(ensure(ws->tile_cnt, sizeof(unsigned long long) * std::max(P.ntiles, 1ll)));
+    PR_TRY(ensure(ws->scan, sizeof(unsigned long long) * (P.ntiles + 1)));
+    PR_TRY(ensure(ws->fill, sizeof(unsigned) * std::max(P.ntiles, 1ll)));
+    PR_TRY(ensure(ws->sums, sizeof(unsigned long long) * scan_block_sums_needed(P.ntiles)));
+    PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
+    PR_TRY(ensure(ws->counters, sizeof(Counters)));
+    PR_TRY(ensure(ws->heads, sizeof(int) * 8));
+    PR_TRY(ensure(ws->stage, std::max<size_t>(P.stage_bytes, 256)));
+    const long long want_pairs = std::max(ws->cap_pairs, 2 * P.ttot + P.ntiles + 1024);
+    if ((size_t)want_pairs * sizeof(unsigned) > ws->tile_tris.cap || !ws->tile_tris.p) {
+        PR_TRY(ensure(ws->tile_tris, sizeof(unsigned) * want_pairs));
+    }
+    ws->cap_pairs = (long long)(ws->tile_tris.cap / sizeof(unsigned));
+    const long long want_items = std::max(ws->cap_items, ws->cap_pairs / seg + P.ntiles + 1024);
+    if ((size_t)want_items * sizeof(int4) > ws->items.cap || !ws->items.p) {
+        PR_TRY(ensure(ws->items, sizeof(int4) * want_items));
+    }
+    ws->cap_items = (long long)(ws->items.cap / sizeof(int4));
+    PR_TRY(ws->h_views.ensure(n));
+    PR_TRY(ws->h_offs.ensure(3 * (n + 1)));
+    PR_TRY(ws->h_cnt.ensure(1));
+    return PR_OK;
+}
+
+// Enqueues one frame (no host synchronisation).  shade: also run stage (d)
+// for views with an rgb output.
+pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cudaStream_t st)
+{
+    const int n = (int)P.vd.size();
+    char *stage = ws->stage.as<char>();
+    for (int q = 0; q < n; ++q) {
+        ViewDev &v = P.vd[q];
+        const BatchPlan::Out &o = P.out[q];
+        v.id_out = o.id_off >= 0 ? (uint32_t *)(stage + o.id_off) : o.id_user;
+        v.depth_out = o.depth_off >= 0 ? (float *)(stage + o.depth_off) : o.depth_user;
+        v.id_in = v.id_out;
+        v.rgb_out = shade ? (o.rgb_off >= 0 ? (float *)(stage + o.rgb_off) : o.rgb_user) : nullptr;
+        ws->h_views.p[q] = v;
+    }
+    long long *ho = ws->h_offs.p;
+    for (int q = 0; q <= n; ++q) {
+        ho[q] = P.tri_off[q];
+        ho[n + 1 + q] = P.tile_off[q];
+        ho[2 * (n + 1) + q] = P.pix_off[q];
+    }
+    const ViewDev *dv = ws->views.as<ViewDev>();
+    const long long *tri_offs = ws->offs.as<long long>(), *tile_offs = tri_offs + n + 1, *pix_offs = tile_offs + n + 1;
+    Counters *cnt = ws->counters.as<Counters>();
+    PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
+    PR_TRY(cudaMemcpyAsync(ws->offs.p, ho, sizeof(long long) * 3 * (n + 1), cudaMemcpyHostToDevice, st));
+    PR_TRY(cudaMemsetAsync(ws->counters.p, 0, sizeof(Counters), st));
+    PR_TRY(cudaMemsetAsync(ws->heads.p, 0, sizeof(int) * 8, st));
+    PR_TRY(cudaMemsetAsync(ws->tile_cnt.p, 0, sizeof(unsigned long long) * std::max(P.ntiles, 1ll), st));
+    PR_TRY(cudaMemsetAsync(ws->fill.p, 0, sizeof(unsigned) * std::max(P.ntiles, 1ll), st));
+    PR_TRY(cudaMemsetAsync(ws->keys.p, 0xFF, sizeof(unsigned long long) * std::max(P.npix, 1ll), st));
+
+    float4 *rec = ws->rec.as<float4>(), *hp = ws->hp.as<float4>(), *tile_box = ws->tile_box.as<float4>();
+    int4 *tbox = ws->tbox.as<int4>();
+    unsigned long long *tile_cnt = ws->tile_cnt.as<unsigned long long>(), *scan = ws->scan.as<unsigned long long>();
+    PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
+    PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cnt, st));
+    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, rec, hp, tbox, tile_box, tile_cnt, st));
+    PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, st));
+    PR_TRY(launch_bin_scatter(dv, n, tri_offs, P.ttot, rec, hp, tbox, tile_box, scan, ws->fill.as<unsigned>(),
+                              ws->tile_tris.as<unsigned>(), ws->cap_pairs, cnt, st));
+    PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items, ws->cap_pairs, seg, cnt, st));
+    int *heads = ws->heads.as<int>();
+    for (size_t c = 0; c < P.classes.size(); ++c) {
+        const auto &cl = P.classes[c];
+        PR_TRY(launch_fragment(cl.S, dv, ws->items.as<int4>(), scan, cl.tile_lo, cl.tile_hi, ws->cap_items,
+                               heads + c, ws->tile_tris.as<unsigned>(), rec, ws->keys.as<unsigned long long>(),
+                               nullptr, 0, cnt, fragment_grid(cl.S), st));
+    }
+    PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
+    if (shade)
+        PR_TRY(launch_shade(dv, n, pix_offs, P.npix, st));
+    // host-side outputs
+    for (int q = 0; q < n; ++q) {
+        const BatchPlan::Out &o = P.out[q];
+        const long long np = (long long)P.vd[q].W * P.vd[q].H;
+        if (o.id_host)
+            PR_TRY(cudaMemcpyAsync(o.id_user, stage + o.id_off, np * 4, cudaMemcpyDeviceToHost, st));
+        if (o.depth_host)
+            PR_TRY(cudaMemcpyAsync(o.depth_user, stage + o.depth_off, np * 4, cudaMemcpyDeviceToHost, st));
+        if (shade && o.rgb_host)
+            PR_TRY(cudaMemcpyAsync(o.rgb_user, stage + o.rgb_off, np * 12, cudaMemcpyDeviceToHost, st));
+    }
+    PR_TRY(cudaMemcpyAsync(ws->h_cnt.p, ws->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    return PR_OK;
+}
+
+pr_status finish_stats(pr_workspace *ws, const BatchPlan &P)
+{
+    const Counters &c = *ws->h_cnt.p;
+    ws->stats.tests = c.tests;
+    ws->stats.hits = c.hits;
+    ws->stats.pairs = c.pairs_total;
+    ws->stats.items = c.items_total;
+    ws->stats.culled = c.culled;
+    ws->stats.flagged = c.flagged;
+    ws->stats.changed = c.changed;
+    ws->stats.pixels = (uint64_t)P.npix;
+    ws->last_T = P.ttot;
+    if (c.status & ST_TIMEOUT)
+        return PR_ERR_TIMEOUT;
+    if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
+        return PR_ERR_OVERFLOW;
+    return PR_OK;
+}
+
+// Eager frame: enqueue, read the status, regrow and rerun on overflow.
+pr_status run_batch(pr_workspace *ws, const pr_batch_view *views, int n, const pr_params *params, bool shade,
+                    cudaStream_t st)
+{
+    pr_params prm = default_params(params);
+    BatchPlan P;
+    pr_status s = plan_batch(views, n, prm, P);
+    if (s != PR_OK)
+        return s;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        s = size_workspace(ws, P, prm.seg);
+        if (s != PR_OK)
+            return s;
+        s = enqueue_batch(ws, P, prm.seg, shade, st);
+        if (s != PR_OK)
+            return s;
+        PR_TRY(cudaStreamSynchronize(st));
+        s = finish_stats(ws, P);
+        if (s != PR_ERR_OVERFLOW)
+            return s;
+        const Counters &c = *ws->h_cnt.p;
+        ws->cap_pairs = std::max<long long>(ws->cap_pairs, (long long)c.pairs_total + 1024);
+        ws->cap_items = std::max<long long>(ws->cap_items, (long long)c.items_total + 1024);
+        ws->cap_pairs += ws->cap_pairs / 4;
+        ws->cap_items += ws->cap_items / 4;  // size_workspace grows both buffers to these
+    }
+    return PR_ERR_OVERFLOW;
+}
+
+pr_status single_view(pr_scene *sc, const pr_view *view, const pr_params *params, uint32_t *id_out,
+                      float *depth_out, float *rgb_out, cudaStream_t st)
+{
+    if (!sc || !view)
+        return PR_ERR_INVALID_ARG;
+    pr_batch_view bv;
+    std::memset(&bv, 0, sizeof bv);
+    bv.scene = sc;
+    bv.view = *view;
+    bv.id_out = id_out;
+    bv.depth_out = depth_out;
+    bv.rgb_out = rgb_out;
+    return run_batch(&sc->ws, &bv, 1, params, rgb_out != nullptr, st);
+}
+
+// One-view table for stages (d)/(e) called on their own.
+pr_status upload_single(pr_scene *sc, const ViewDev &v, cudaStream_t st)
+{
+    pr_workspace *ws = &sc->ws;
+    PR_TRY(ensure(ws->views, sizeof(ViewDev)));
+    PR_TRY(ensure(ws->offs, sizeof(long long) * 6));
+    PR_TRY(ws->h_views.ensure(1));
+    PR_TRY(ws->h_offs.ensure(6));
+    ws->h_views.p[0] = v;
+    long long *o = ws->h_offs.p;
+    o[0] = 0;
+    o[1] = (long long)v.W * v.H;
+    o[2] = o[3] = o[4] = o[5] = 0;
+    PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev), cudaMemcpyHostToDevice, st));
+    PR_TRY(cudaMemcpyAsync(ws->offs.p, o, sizeof(long long) * 2, cudaMemcpyHostToDevice, st));
+    return PR_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+
+extern "C" {
+
+int32_t pr_version(void) { return 1; }
+
+const char *pr_status_string(pr_status s)
+{
+    switch (s) {
+    case PR_OK: return "ok";
+    case PR_ERR_INVALID_ARG: return "invalid argument";
+    case PR_ERR_CUDA: return "CUDA error";
+    case PR_ERR_OOM: return "out of device memory";
+    case PR_ERR_OVERFLOW: return "device buffer overflow";
+    case PR_ERR_TIMEOUT: return "device wait timed out";
+    case PR_ERR_NONFINITE: return "non-finite input";
+    case PR_ERR_NO_CUDA: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+static pr_status copy_in(const void *src, size_t bytes, DevBuf &stage, const void **dev, cudaStream_t st)
+{
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return PR_OK;
+    }
+    PR_TRY(ensure(stage, bytes));
+    PR_TRY(cudaMemcpyAsync(stage.p, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = stage.p;
+    return PR_OK;
+}
+
+static pr_status check_scene_status(pr_scene *sc, cudaStream_t st)
+{
+    pr_workspace *ws = &sc->ws;
+    PR_TRY(ws->h_cnt.ensure(1));
+    PR_TRY(cudaMemcpyAsync(ws->h_cnt.p, ws->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    PR_TRY(cudaStreamSynchronize(st));
+    const unsigned s = ws->h_cnt.p->status;
+    if (s & ST_NONFINITE)
+        return PR_ERR_NONFINITE;
+    if (s & ST_BAD_INDEX)
+        return PR_ERR_INVALID_ARG;
+    return PR_OK;
+}
+
+pr_status pr_scene_update(pr_scene *sc, const float *pos, const float *vel, const float *col, void *stream)
+{
+    if (!sc)
+        return PR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long V = sc->V;
+    float *soa = sc->soa.as<float>();
+    PR_TRY(ensure(sc->ws.counters, sizeof(Counters)));
+    PR_TRY(cudaMemsetAsync(sc->ws.counters.p, 0, sizeof(Counters), st));
+    // scatter each given [V][3] array into its three planes
+    const float *arrs[3] = {pos, vel, col};
+    for (int a = 0; a < 3; ++a) {
+        if (!arrs[a])
+            continue;
+        const void *d = nullptr;
+        pr_status s = copy_in(arrs[a], sizeof(float) * 3 * V, sc->stage, &d, st);
+        if (s != PR_OK)
+            return s;
+        PR_TRY(launch_planes3((const float *)d, V, soa + 3 * a * V, st));
+    }
+    PR_TRY(launch_scene_check(soa, V, sc->ws.counters.as<Counters>(), st));
+    return check_scene_status(sc, st);
+}
+
+pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, const int32_t *tri, int64_t V,
+                          int64_t T, void *stream, pr_scene **out)
+{
+    if (!out || !pos || !vel || !col || (T > 0 && !tri) || V < 1 || T < 0 || V > (1ll << 30) || T > (1ll << 30))
+        return PR_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return PR_ERR_NO_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    pr_scene *sc = new (std::nothrow) pr_scene;
+    if (!sc)
+        return PR_ERR_OOM;
+    sc->V = V;
+    sc->T = T;
+    pr_status s = from_cuda(ensure(sc->soa, sizeof(float) * 9 * V));
+    if (s == PR_OK)
+        s = from_cuda(ensure(sc->idx, sizeof(int) * 3 * std::max<int64_t>(T, 1)));
+    if (s == PR_OK)
+        s = from_cuda(ensure(sc->ws.counters, sizeof(Counters)));
+    if (s == PR_OK)
+        s = from_cuda(cudaMemsetAsync(sc->ws.counters.p, 0, sizeof(Counters), st));
+    // stage the three [V][3] arrays and the index array
+    DevBuf sp, sv, scol, stri;
+    const void *dp = nullptr, *dvel = nullptr, *dc = nullptr, *dt = nullptr;
+    if (s == PR_OK)
+        s = copy_in(pos, sizeof(float) * 3 * V, sp, &dp, st);
+    if (s == PR_OK)
+        s = copy_in(vel, sizeof(float) * 3 * V, sv, &dvel, st);
+    if (s == PR_OK)
+        s = copy_in(col, sizeof(float) * 3 * V, scol, &dc, st);
+    if (s == PR_OK && T > 0)
+        s = copy_in(tri, sizeof(int) * 3 * T, stri, &dt, st);
+    if (s == PR_OK)
+        s = from_cuda(launch_scene_soa((const float *)dp, (const float *)dvel, (const float *)dc, V,
+                                       sc->soa.as<float>(), st));
+    if (s == PR_OK && T > 0)
+        s = from_cuda(launch_scene_idx((const int *)dt, T, V, sc->idx.as<int>(), sc->ws.counters.as<Counters>(), st));
+    if (s == PR_OK)
+        s = from_cuda(launch_scene_check(sc->soa.as<float>(), V, sc->ws.counters.as<Counters>(), st));
+    if (s == PR_OK)
+        s = check_scene_status(sc, st);  // synchronises: staging buffers may be released
+    if (s != PR_OK) {
+        cudaStreamSynchronize(st);
+        delete sc;
+        return s;
+    }
+    *out = sc;
+    return PR_OK;
+}
+
+void pr_scene_free(pr_scene *sc)
+{
+    if (sc) {
+        cudaDeviceSynchronize();
+        delete sc;
+    }
+}
+
+pr_status pr_rasterize(pr_scene *sc, const pr_view *view, const pr_params *params, uint32_t *id_out, float *depth_out,
+                       void *stream)
+{
+    return single_view(sc, view, params, id_out, depth_out, nullptr, (cudaStream_t)stream);
+}
+
+static pr_status stage_in_ids(pr_scene *sc, const uint32_t *id, long long np, const uint32_t **dev, cudaStream_t st)
+{
+    return copy_in(id, sizeof(uint32_t) * np, sc->stage, (const void **)dev, st);
+}
+
+pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float *rgb_out, void *stream)
+{
+    if (!sc || !view || !id || !rgb_out)
+        return PR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ViewDev v;
+    pr_status s = make_viewdev(*view, sc, kDefaultTile, PR_BOUND_ZENON, 0, v);
+    if (s != PR_OK)
+        return s;
+    const long long np = (long long)view->W * view->H;
+    const uint32_t *did = nullptr;
+    s = stage_in_ids(sc, id, np, &did, st);
+    if (s != PR_OK)
+        return s;
+    const bool host_out = !is_device_ptr(rgb_out);
+    DevBuf *ob = &sc->ws.stage;
+    if (host_out)
+        PR_TRY(ensure(*ob, sizeof(float) * 3 * np));
+    v.id_in = did;
+    v.rgb_out = host_out ? ob->as<float>() : rgb_out;
+    s = upload_single(sc, v, st);
+    if (s != PR_OK)
+        return s;
+    PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(), np, st));
+    if (host_out)
+        PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
+    PR_TRY(cudaStreamSynchronize(st));
+    return PR_OK;
+}
+
+pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, const float *grad_rgb, float *dcol,
+                      float *dpos, float *dvel, void *stream)
+{
+    if (!sc || !view || !id || !grad_rgb)
+        return PR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ViewDev v;
+    pr_status s = make_viewdev(*view, sc, kDefaultTile, PR_BOUND_ZENON, 0, v);
+    if (s != PR_OK)
+        return s;
+    const long long np = (long long)view->W * view->H;
+    const long long V = sc->V;
+    // inputs: ids and gradient (staged if on the host)
+    DevBuf gstage, ostage;
+    const uint32_t *did = nullptr;
+    const void *dg = nullptr;
+    s = stage_in_ids(sc, id, np, &did, st);
+    if (s == PR_OK)
+        s = copy_in(grad_rgb, sizeof(float) * 3 * np, gstage, &dg, st);
+    if (s != PR_OK)
+        return s;
+    // outputs: accumulate in place when on the device, else through staging
+    float *outs[3] = {dcol, dpos, dvel};
+    float *douts[3] = {nullptr, nullptr, nullptr};
+    bool host[3] = {false, false, false};
+    PR_TRY(ensure(ostage, sizeof(float) * 9 * V));
+    for (int a = 0; a < 3; ++a) {
+        if (!outs[a])
+            continue;
+        host[a] = !is_device_ptr(outs[a]);
+        if (host[a]) {
+            douts[a] = ostage.as<float>() + 3 * a * V;
+            PR_TRY(cudaMemcpyAsync(douts[a], outs[a], sizeof(float) * 3 * V, cudaMemcpyHostToDevice, st));
+        } else {
+            douts[a] = outs[a];
+        }
+    }
+    v.id_in = did;
+    v.grad_in = (const float *)dg;
+    v.dcol = douts[0];
+    v.dpos = douts[1];
+    v.dvel = douts[2];
+    s = upload_single(sc, v, st);
+    if (s != PR_OK)
+        return s;
+    PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(), np, st));
+    for (int a = 0; a < 3; ++a)
+        if (host[a])
+            PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
+    PR_TRY(cudaStreamSynchronize(st));
+    return PR_OK;
+}
+
+pr_status pr_workspace_create(pr_workspace **out)
+{
+    if (!out)
+        return PR_ERR_INVALID_ARG;
+    *out = new (std::nothrow) pr_workspace;
+    return *out ? PR_OK : PR_ERR_OOM;
+}
+
+void pr_workspace_free(pr_workspace *ws)
+{
+    if (ws) {
+        cudaDeviceSynchronize();
+        delete ws;
+    }
+}
+
+pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                             void *stream)
+{
+    if (!ws)
+        return PR_ERR_INVALID_ARG;
+    return run_batch(ws, views, n, params, true, (cudaStream_t)stream);
+}
+
+pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                                 void *stream, pr_graph **out)
+{
+    if (!ws || !out)
+        return PR_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!st)
+        return PR_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+    // eager run: sizes every buffer and warms up the kernels
+    pr_status s = run_batch(ws, views, n, params, true, st);
+    if (s != PR_OK)
+        return s;
+    pr_params prm = default_params(params);
+    BatchPlan P;
+    s = plan_batch(views, n, prm, P);
+    if (s != PR_OK)
+        return s;
+    for (const auto &o : P.out)
+        if (o.id_host || o.depth_host || o.rgb_host)
+            return PR_ERR_INVALID_ARG;  // graphs need device outputs
+    pr_graph *g = new (std::nothrow) pr_graph;
+    if (!g)
+        return PR_ERR_OOM;
+    g->ws = ws;
+    g->npix = P.npix;
+    PR_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    s = enqueue_batch(ws, P, prm.seg, true, st);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != PR_OK || e != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        delete g;
+        cudaGetLastError();
+        return s != PR_OK ? s : from_cuda(e);
+    }
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete g;
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    *out = g;
+    return PR_OK;
+}
+
+pr_status pr_graph_launch(pr_graph *g, void *stream)
+{
+    if (!g)
+        return PR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    PR_TRY(cudaGraphLaunch(g->exec, st));
+    PR_TRY(cudaStreamSynchronize(st));
+    pr_workspace *ws = g->ws;
+    const Counters &c = *ws->h_cnt.p;
+    ws->stats.tests = c.tests;
+    ws->stats.hits = c.hits;
+    ws->stats.pairs = c.pairs_total;
+    ws->stats.items = c.items_total;
+    ws->stats.culled = c.culled;
+    ws->stats.flagged = c.flagged;
+    ws->stats.changed = c.changed;
+    ws->stats.pixels = (uint64_t)g->npix;
+    if (c.status & ST_TIMEOUT)
+        return PR_ERR_TIMEOUT;
+    if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
+        return PR_ERR_OVERFLOW;
+    return PR_OK;
+}
+
+void pr_graph_free(pr_graph *g)
+{
+    if (g) {
+        if (g->exec)
+            cudaGraphExecDestroy(g->exec);
+        if (g->graph)
+            cudaGraphDestroy(g->graph);
+        delete g;
+    }
+}
+
+pr_status pr_scene_stats(const pr_scene *sc, pr_stats *out)
+{
+    if (!sc || !out)
+        return PR_ERR_INVALID_ARG;
+    *out = sc->ws.stats;
+    return PR_OK;
+}
+
+pr_status pr_workspace_stats(const pr_workspace *ws, pr_stats *out)
+{
+    if (!ws || !out)
+        return PR_ERR_INVALID_ARG;
+    *out = ws->stats;
+    return PR_OK;
+}
+
+pr_status pr_debug_bounds(const pr_scene *sc, int32_t *pix_box, float *t_range)
+{
+    if (!sc || !pix_box || !t_range)
+        return PR_ERR_INVALID_ARG;
+    const pr_workspace &ws = sc->ws;
+    const long long T = ws.last_T;
+    if (T != sc->T || !ws.tbox.p)
+        return PR_ERR_INVALID_ARG;
+    std::vector<int4> tb(T);
+    std::vector<float4> rec(T * kRecF4);
+    PR_TRY(cudaDeviceSynchronize());
+    PR_TRY(cudaMemcpy(tb.data(), ws.tbox.p, sizeof(int4) * T, cudaMemcpyDeviceToHost));
+    PR_TRY(cudaMemcpy(rec.data(), ws.rec.p, sizeof(float4) * kRecF4 * T, cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < T; ++k) {
+        const int4 b = tb[k];
+        pix_box[4 * k + 0] = b.x & 0xffff;
+        pix_box[4 * k + 1] = b.y & 0xffff;
+        pix_box[4 * k + 2] = (b.x >> 16) & 0xffff;
+        pix_box[4 * k + 3] = (b.y >> 16) & 0xffff;
+        if (b.w) {
+            pix_box[4 * k + 0] = 1;
+            pix_box[4 * k + 2] = 0;
+        }
+        t_range[2 * k + 0] = rec[k * kRecF4 + 5].x;
+        t_range[2 * k + 1] = rec[k * kRecF4 + 5].y;
+    }
+    return PR_OK;
+}
+
+int32_t pr_debug_catch_interval(const pr_view *view, const float *S, const float *E, float *t_out)
+{
+    if (!view || !S || !E || !t_out)
+        return -1;
+    float3 s3[3], d3[3];
+    for (int k = 0; k < 3; ++k) {
+        s3[k] = make_float3(S[3 * k], S[3 * k + 1], S[3 * k + 2]);
+        d3[k] = make_float3(E[3 * k] - S[3 * k], E[3 * k + 1] - S[3 * k + 1], E[3 * k + 2] - S[3 * k + 2]);
+    }
+    const float t_hi = std::min(1.f, view->d[0] + view->d[1]);
+    float lo = 0.f, hi = 0.f;
+    const bool ok = catch_interval(s3, d3, view->tan_x, view->tan_y, view->d[0], view->d[1], 0.f, t_hi, lo, hi);
+    t_out[0] = lo;
+    t_out[1] = hi;
+    return ok ? 1 : 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// pr_internal.cuh -- device-side records and math shared by the kernels of
+// libpr (stages (a)-(e) of the perceptual-rasterization hot path).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pr.h"
+
+namespace pr {
+
+constexpr float kSqrt2 = 1.41421356237309504880f;  // D, the extent of the foveation domain (Sec. 3.1.1)
+constexpr float kEpsDisp = 1e-5f;                  // display-space safety margin of every bound (unit coords)
+constexpr float kEpsT = 1e-4f;                     // time margin of every catch-up interval
+constexpr int kMaxHp = 8;                          // half-planes per bound: <= 6 hull edges + 2 time-strip edges
+constexpr int kRecF4 = 6;                          // float4 per fragment record
+
+// Device status bits (Counters::status).
+enum : uint32_t {
+    ST_OVERFLOW_PAIRS = 1u,
+    ST_OVERFLOW_ITEMS = 2u,
+    ST_TIMEOUT = 4u,
+    ST_NONFINITE = 8u,
+    ST_BAD_INDEX = 16u,
+    ST_OVERFLOW_FLAGS = 32u,
+};
+
+// Per-view constants, derived on the host from pr_view (see pr_host.cu).
+struct ViewDev {
+    float R0[9], T0[3], R1[9], T1[3];  // pose0 / pose1 as rotation + translation
+    float tan_x, tan_y, z_near;
+    float fx, fy;                      // fovea x_f (unit framebuffer coordinates)
+    float alpha, inv_alpha;            // p(d) = D (d/D)^alpha
+    float d0, d1;                      // rolling direction, r(x) = x . d
+    float t_lo, t_hi;                  // range of pixel times over the viewport
+    float l0[3], l1[3];                // camera-space light direction at t = 0 and t = 1
+    float k_a, k_d;
+    int W, H, mode, S;                 // framebuffer, pr_mode, bin tile side
+    int tiles_x, tiles_y, bound, fp64;
+    long long tri_off, tile_off, pix_off;  // offsets of this view in the batch-wide arrays
+    int T, V;
+    const float *px, *py, *pz, *vx, *vy, *vz, *cr, *cg, *cb;  // scene, structure of arrays
+    const int *i0, *i1, *i2;
+    uint32_t *id_out;                  // resolved outputs (device)
+    float *depth_out;
+    const uint32_t *id_in;             // ids read by shading / adjoint
+    float *rgb_out;
+    const float *grad_in;              // adjoint input [3][H][W]
+    float *dcol, *dpos, *dvel;         // adjoint outputs [V][3]
+};
+
+struct Counters {
+    unsigned long long tests, hits, culled, flagged, changed;
+    unsigned long long pairs_total, items_total;  // copied from the scan for the host
+    unsigned int status;
+    unsigned int pad;
+};
+
+__device__ __forceinline__ bool is_rolling(int mode) { return mode == PR_ROLLING || mode == PR_BOTH; }
+__device__ __forceinline__ bool is_foveated(int mode) { return mode == PR_FOVEATED || mode == PR_BOTH; }
+
+// Index of the view that owns element g, given the batch offsets off[0..n]
+// (off[0] = 0, ascending).
+__device__ __forceinline__ int find_view(const long long *off, int n, long long g)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Camera-space start and end positions of vertex k: S = R0 p + T0 and
+// E = R1 (p + v) + T1 (Sec. 3.2, "Bounding": M_s v_s and M_e v_e).  Every
+// kernel that needs a vertex calls this one function, so the bits agree.
+__device__ __forceinline__ void vertex_start_end(const ViewDev &v, int k, float3 &S, float3 &E)
+{
+    const float x = v.px[k], y = v.py[k], z = v.pz[k];
+    const float ex = x + v.vx[k], ey = y + v.vy[k], ez = z + v.vz[k];
+    S.x = fmaf(v.R0[0], x, fmaf(v.R0[1], y, fmaf(v.R0[2], z, v.T0[0])));
+    S.y = fmaf(v.R0[3], x, fmaf(v.R0[4], y, fmaf(v.R0[5], z, v.T0[1])));
+    S.z = fmaf(v.R0[6], x, fmaf(v.R0[7], y, fmaf(v.R0[8], z, v.T0[2])));
+    E.x = fmaf(v.R1[0], ex, fmaf(v.R1[1], ey, fmaf(v.R1[2], ez, v.T1[0])));
+    E.y = fmaf(v.R1[3], ex, fmaf(v.R1[4], ey, fmaf(v.R1[5], ez, v.T1[1])));
+    E.z = fmaf(v.R1[6], ex, fmaf(v.R1[7], ey, fmaf(v.R1[8], ez, v.T1[2])));
+}
+
+// Foveation q (framebuffer -> display) of a point at offset e from the
+// fovea: the offset is scaled by p(|e|)/|e| = (|e|/D)^(alpha-1).
+__device__ __forceinline__ float fov_scale(float r, float alpha)
+{
+    return r > 0.f ? __powf(r * (1.0f / kSqrt2), alpha - 1.0f) : 0.f;
+}
+
+// Pixel (i, j) -> its display location x, its time t and its ray direction
+// (dx, dy, 1) (conventions of pr.h).  FP32; the same code in every stage.
+__device__ __forceinline__ void pixel_ray(const ViewDev &v, int i, int j, float &x0, float &x1, float &t, float &dx,
+                                          float &dy)
+{
+    float u0 = __fdiv_rn((float)i + 0.5f, (float)v.W);
+    float u1 = __fdiv_rn((float)j + 0.5f, (float)v.H);
+    if (is_foveated(v.mode)) {
+        float e0 = u0 - v.fx, e1 = u1 - v.fy;
+        float r = sqrtf(fmaf(e0, e0, e1 * e1));
+        float s = fov_scale(r, v.alpha);
+        x0 = fmaf(e0, s, v.fx);
+        x1 = fmaf(e1, s, v.fy);
+    } else {
+        x0 = u0;
+        x1 = u1;
+    }
+    t = is_rolling(v.mode) ? fmaf(x0, v.d0, x1 * v.d1) : 0.f;
+    dx = fmaf(2.f, x0, -1.f) * v.tan_x;
+    dy = fmaf(2.f, x1, -1.f) * v.tan_y;
+}
+
+// Display location (unit coordinates) of a camera-space point with z > 0.
+__device__ __forceinline__ float2 project(const ViewDev &v, float3 p)
+{
+    float iz = 1.0f / p.z;
+    return make_float2(fmaf(0.5f * p.x * iz, 1.0f / v.tan_x, 0.5f), fmaf(0.5f * p.y * iz, 1.0f / v.tan_y, 0.5f));
+}
+
+// Packed visibility key: FP32 depth bits (positive floats order as their
+// bits) above the triangle id, so a 64-bit min picks the nearest hit and,
+// on equal depth, the smaller id.
+__device__ __forceinline__ unsigned long long pack_key(float depth, uint32_t id)
+{
+    return ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)id;
+}
+
+}  // namespace pr

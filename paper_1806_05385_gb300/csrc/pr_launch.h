@@ -1,0 +1,57 @@
+// pr_launch.h -- host-side launchers of the libpr kernels (one per stage).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pr_internal.cuh"
+
+namespace pr {
+
+// scene upload: [V][3] AoS -> SoA, finiteness and index checks
+cudaError_t launch_scene_soa(const float *pos, const float *vel, const float *col, long long V, float *soa,
+                             cudaStream_t st);
+cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int *idx, Counters *cnt, cudaStream_t st);
+cudaError_t launch_planes3(const float *src, long long V, float *dst, cudaStream_t st);
+cudaError_t launch_scene_check(const float *soa, long long V, Counters *cnt, cudaStream_t st);
+
+// stage (a): display boxes of the framebuffer tiles, per-triangle bounds
+cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
+                              float4 *tile_box, cudaStream_t st);
+cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
+                         float4 *hp, int4 *tbox, Counters *cnt, cudaStream_t st);
+
+// stage (b): tile binning
+cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
+                             const float4 *rec, const float4 *hp, const int4 *tbox, const float4 *tile_box,
+                             unsigned long long *tile_cnt, cudaStream_t st);
+cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *block_sums,
+                        long long n, int seg, cudaStream_t st);
+size_t scan_block_sums_needed(long long n);
+cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
+                               const float4 *rec, const float4 *hp, const int4 *tbox, const float4 *tile_box,
+                               const unsigned long long *scan, unsigned int *fill, unsigned int *tile_tris,
+                               long long cap_pairs, Counters *cnt, cudaStream_t st);
+cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
+                         const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
+                         long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);
+
+// stage (c): per-fragment ray casting, FP64 re-test, resolve
+cudaError_t launch_fragment(int S, const ViewDev *views, const int4 *items, const unsigned long long *scan,
+                            long long tile_lo, long long tile_hi, long long cap_items, int *head,
+                            const unsigned int *tile_tris, const float4 *rec, unsigned long long *keys,
+                            unsigned int *flags, long long cap_flags, Counters *cnt, int grid, cudaStream_t st);
+int fragment_grid(int S);
+cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix_offs, const int4 *items,
+                          const unsigned long long *scan, const long long *tile_offs, const unsigned int *tile_tris,
+                          unsigned int *flags, long long cap_flags, unsigned long long *keys, Counters *cnt,
+                          int grid, cudaStream_t st);
+cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
+                           const unsigned long long *keys, cudaStream_t st);
+
+// stages (d) and (e)
+cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
+                         cudaStream_t st);
+cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
+                            cudaStream_t st);
+
+}  // namespace pr

@@ -1,0 +1,659 @@
+// pr_stage_ab.cu -- scene upload, stage (a) bounds and stage (b) tile binning.
+//
+// Stage (a) follows Sec. 3.2 ("Bounding") and Sec. 4: each triangle becomes
+// a "space-time triangle" of six camera-space vertices (start and end of the
+// frame), and a 2D region is found that holds every display location the
+// triangle can cover at the time the rolling scan shows that location.  The
+// region is kept in display coordinates (convex hull half-planes plus the
+// time strip of the catch-up interval), where it is exact and convex; the
+// foveation warp is applied to the framebuffer tiles instead (their display
+// images), and to the region only to find the range of framebuffer pixels.
+#include "pr_bound.cuh"
+#include "pr_launch.h"
+
+namespace pr {
+
+// ---------------------------------------------------------------- scene
+
+__global__ void k_scene_soa(const float *__restrict__ pos, const float *__restrict__ vel, const float *__restrict__ col,
+                            long long V, float *__restrict__ soa)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= V)
+        return;
+    for (int c = 0; c < 3; ++c) {
+        soa[(0 + c) * V + k] = pos[3 * k + c];
+        soa[(3 + c) * V + k] = vel[3 * k + c];
+        soa[(6 + c) * V + k] = col[3 * k + c];
+    }
+}
+
+__global__ void k_planes3(const float *__restrict__ src, long long V, float *__restrict__ dst)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= V)
+        return;
+    for (int c = 0; c < 3; ++c)
+        dst[c * V + k] = src[3 * k + c];
+}
+
+cudaError_t launch_planes3(const float *src, long long V, float *dst, cudaStream_t st)
+{
+    if (V > 0)
+        k_planes3<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(src, V, dst);
+    return cudaGetLastError();
+}
+
+__global__ void k_scene_check(const float *__restrict__ soa, long long V, Counters *cnt)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= V)
+        return;
+    bool ok = true;
+    for (int c = 0; c < 9; ++c)
+        ok &= isfinite(soa[c * V + k]);
+    if (!ok)
+        atomicOr(&cnt->status, ST_NONFINITE);
+}
+
+__global__ void k_scene_idx(const int *__restrict__ tri, long long T, long long V, int *__restrict__ idx, Counters *cnt)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= T)
+        return;
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        const int a = tri[3 * k + c];
+        ok &= a >= 0 && a < V;
+        idx[c * T + k] = a;
+    }
+    if (!ok)
+        atomicOr(&cnt->status, ST_BAD_INDEX);
+}
+
+cudaError_t launch_scene_soa(const float *pos, const float *vel, const float *col, long long V, float *soa,
+                             cudaStream_t st)
+{
+    if (V > 0)
+        k_scene_soa<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(pos, vel, col, V, soa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scene_check(const float *soa, long long V, Counters *cnt, cudaStream_t st)
+{
+    if (V > 0)
+        k_scene_check<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(soa, V, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int *idx, Counters *cnt, cudaStream_t st)
+{
+    if (T > 0)
+        k_scene_idx<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(tri, T, V, idx, cnt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tiles
+
+// Pixel-centre box of tile lt of view v in unit framebuffer coordinates,
+// computed with the same rounding as pixel_ray.
+__device__ __forceinline__ void tile_pixel_box(const ViewDev &v, long long lt, float &u0, float &u1, float &w0,
+                                               float &w1)
+{
+    const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
+    const int i0 = tx * v.S, i1 = min(v.W, i0 + v.S) - 1;
+    const int j0 = ty * v.S, j1 = min(v.H, j0 + v.S) - 1;
+    u0 = __fdiv_rn((float)i0 + 0.5f, (float)v.W);
+    u1 = __fdiv_rn((float)i1 + 0.5f, (float)v.W);
+    w0 = __fdiv_rn((float)j0 + 0.5f, (float)v.H);
+    w1 = __fdiv_rn((float)j1 + 0.5f, (float)v.H);
+}
+
+// Display box of every framebuffer tile: the box of its pixel centres, or
+// for foveated views the box of their image under q.
+__global__ void k_tile_boxes(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ tile_offs,
+                             long long ntiles, float4 *__restrict__ tile_box)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ntiles)
+        return;
+    const ViewDev &v = views[find_view(tile_offs, nviews, g)];
+    float u0, u1, w0, w1;
+    tile_pixel_box(v, g - v.tile_off, u0, u1, w0, w1);
+    float4 b;
+    if (is_foveated(v.mode))
+        b = fov_image_box(u0, u1, w0, w1, make_float2(v.fx, v.fy), v.alpha);
+    else
+        b = make_float4(u0, u1, w0, w1);
+    const float e = kEpsDisp;
+    tile_box[g] = make_float4(b.x - e, b.y + e, b.z - e, b.w + e);
+}
+
+cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
+                              float4 *tile_box, cudaStream_t st)
+{
+    if (ntiles > 0)
+        k_tile_boxes<<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(views, nviews, tile_offs, ntiles, tile_box);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bound
+
+// Result of stage (a) for one triangle.
+struct Bound {
+    float xmin, xmax, ymin, ymax;  // display box
+    float tmin, tmax;              // catch-up interval (0, 0 when not rolling)
+    float4 hp[kMaxHp];             // outside iff a x + b y + c > 0
+    int nhp;
+    int i0, i1, j0, j1;            // framebuffer pixel box (inclusive)
+    bool culled;
+};
+
+__device__ __forceinline__ float3 lerp_pt(float3 S, float3 D, float t)
+{
+    return make_float3(fmaf(t, D.x, S.x), fmaf(t, D.y, S.y), fmaf(t, D.z, S.z));
+}
+
+// Half-plane through p -> q (counter-clockwise hull) with outward unit
+// normal, grown outward by eps.
+__device__ __forceinline__ float4 edge_halfplane(float2 p, float2 q, float eps)
+{
+    const float ex = q.x - p.x, ey = q.y - p.y;
+    const float len = sqrtf(ex * ex + ey * ey);
+    const float a = ey / len, b = -ex / len;
+    return make_float4(a, b, -(a * p.x + b * p.y) - eps, 0.f);
+}
+
+__device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 D[3], Bound &B)
+{
+    const bool rolling = is_rolling(v.mode), fov = is_foveated(v.mode);
+    const float eps = kEpsDisp;
+    B.nhp = 0;
+    B.culled = false;
+    B.tmin = rolling ? v.t_lo : 0.f;
+    B.tmax = rolling ? v.t_hi : 0.f;
+
+    // the relevant space-time points: the triangle at the ends of the time domain
+    float3 P[6];
+    int np = 3;
+    for (int k = 0; k < 3; ++k)
+        P[k] = lerp_pt(S[k], D[k], B.tmin);
+    if (rolling && B.tmax != B.tmin) {
+        for (int k = 0; k < 3; ++k)
+            P[3 + k] = lerp_pt(S[k], D[k], B.tmax);
+        np = 6;
+    }
+    // frustum culling against the near plane and the four side planes
+    bool all_near = true, all_l = true, all_r = true, all_t = true, all_b = true, any_near = false;
+    for (int k = 0; k < np; ++k) {
+        const float3 p = P[k];
+        const float mx = 1e-6f * (fabsf(p.x) + v.tan_x * fabsf(p.z)) + 1e-30f;
+        const float my = 1e-6f * (fabsf(p.y) + v.tan_y * fabsf(p.z)) + 1e-30f;
+        all_near &= p.z < v.z_near;
+        any_near |= p.z < v.z_near * (1.f + 1e-6f);
+        all_l &= p.x + v.tan_x * p.z < -mx;
+        all_r &= v.tan_x * p.z - p.x < -mx;
+        all_t &= p.y + v.tan_y * p.z < -my;
+        all_b &= v.tan_y * p.z - p.y < -my;
+    }
+    if (all_near || all_l || all_r || all_t || all_b) {
+        B.culled = true;
+        return;
+    }
+
+    float2 Q[16];
+    int nq = 0;
+    bool use_hull = v.bound != PR_BOUND_QUAD && v.bound != PR_BOUND_TRIVIAL;
+    bool strip = false;
+    if (any_near) {
+        // split by the near plane (Sec. 4.2.2): keep the points in front of it
+        // and the crossings of all segments between the space-time vertices
+        for (int k = 0; k < np; ++k)
+            if (P[k].z >= v.z_near)
+                Q[nq++] = project(v, P[k]);
+        for (int a = 0; a < np; ++a)
+            for (int b = a + 1; b < np; ++b) {
+                const float za = P[a].z - v.z_near, zb = P[b].z - v.z_near;
+                if ((za < 0.f) != (zb < 0.f) && nq < 16) {
+                    const float s = za / (za - zb);
+                    float3 x = make_float3(fmaf(s, P[b].x - P[a].x, P[a].x), fmaf(s, P[b].y - P[a].y, P[a].y), v.z_near);
+                    Q[nq++] = project(v, x);
+                }
+            }
+        use_hull = false;
+    } else {
+        if (rolling) {
+            float tmin = v.t_lo, tmax = v.t_hi;
+            if (v.bound == PR_BOUND_ZENON) {
+                if (!catch_interval(S, D, v.tan_x, v.tan_y, v.d0, v.d1, v.t_lo, v.t_hi, tmin, tmax)) {
+                    B.culled = true;
+                    return;
+                }
+                strip = true;
+            } else if (v.bound == PR_BOUND_ADAPTIVE) {
+                // Sec. 4.2.3: the times at which the projected space-time
+                // vertices are shown bound the times of every covered pixel
+                float lo = INFINITY, hi = -INFINITY;
+                for (int k = 0; k < np; ++k) {
+                    const float2 x = project(v, P[k]);
+                    const float r = fmaf(x.x, v.d0, x.y * v.d1);
+                    lo = fminf(lo, r);
+                    hi = fmaxf(hi, r);
+                }
+                tmin = fmaxf(v.t_lo, lo - kEpsT);
+                tmax = fminf(v.t_hi, hi + kEpsT);
+                if (!(tmin <= tmax)) {
+                    B.culled = true;
+                    return;
+                }
+                strip = true;
+            }
+            B.tmin = tmin;
+            B.tmax = tmax;
+            for (int k = 0; k < 3; ++k)
+                Q[nq++] = project(v, lerp_pt(S[k], D[k], tmin));
+            if (tmax != tmin)
+                for (int k = 0; k < 3; ++k)
+                    Q[nq++] = project(v, lerp_pt(S[k], D[k], tmax));
+        } else {
+            for (int k = 0; k < 3; ++k)
+                Q[nq++] = project(v, S[k]);
+        }
+    }
+
+    float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+    for (int k = 0; k < nq; ++k) {
+        xmin = fminf(xmin, Q[k].x);
+        xmax = fmaxf(xmax, Q[k].x);
+        ymin = fminf(ymin, Q[k].y);
+        ymax = fmaxf(ymax, Q[k].y);
+    }
+    const float mx = eps * fmaxf(1.f, fmaxf(fabsf(xmin), fabsf(xmax)));
+    const float my = eps * fmaxf(1.f, fmaxf(fabsf(ymin), fabsf(ymax)));
+    xmin -= mx;
+    xmax += mx;
+    ymin -= my;
+    ymax += my;
+    if (v.bound == PR_BOUND_TRIVIAL) {
+        xmin = ymin = -eps;
+        xmax = ymax = 1.f + eps;
+    }
+    if (strip) {
+        // the time strip t_min <= d . x <= t_max (covered pixels satisfy t = r(x))
+        const float dn = sqrtf(v.d0 * v.d0 + v.d1 * v.d1);
+        if (v.d1 == 0.f) {
+            xmin = fmaxf(xmin, (B.tmin - kEpsT) / v.d0);
+            xmax = fminf(xmax, (B.tmax + kEpsT) / v.d0);
+        } else if (v.d0 == 0.f) {
+            ymin = fmaxf(ymin, (B.tmin - kEpsT) / v.d1);
+            ymax = fminf(ymax, (B.tmax + kEpsT) / v.d1);
+        }
+        B.hp[B.nhp++] = make_float4(-v.d0 / dn, -v.d1 / dn, (B.tmin - kEpsT) / dn, 0.f);
+        B.hp[B.nhp++] = make_float4(v.d0 / dn, v.d1 / dn, -(B.tmax + kEpsT) / dn, 0.f);
+    }
+    // clip to the viewport (every ray's display location lies in [0,1]^2)
+    xmin = fmaxf(xmin, -eps);
+    ymin = fmaxf(ymin, -eps);
+    xmax = fminf(xmax, 1.f + eps);
+    ymax = fminf(ymax, 1.f + eps);
+    if (!(xmin <= xmax && ymin <= ymax)) {
+        B.culled = true;
+        return;
+    }
+    B.xmin = xmin;
+    B.xmax = xmax;
+    B.ymin = ymin;
+    B.ymax = ymax;
+
+    // convex hull (Sec. 4.2.2) -> half-planes
+    float2 H[16];
+    int nh = 0;
+    if (use_hull) {
+        float2 tmp[32];
+        nh = convex_hull(Q, nq, tmp);
+        for (int k = 0; k < nh; ++k)
+            H[k] = tmp[k];
+        if (nh >= 3) {
+            const float gm = eps * fmaxf(1.f, fmaxf(fmaxf(fabsf(xmin), fabsf(xmax)), fmaxf(fabsf(ymin), fabsf(ymax))));
+            for (int k = 0; k < nh && B.nhp < kMaxHp; ++k) {
+                const float2 p = H[k], q = H[(k + 1) % nh];
+                if (p.x != q.x || p.y != q.y)
+                    B.hp[B.nhp++] = edge_halfplane(p, q, gm);
+            }
+        }
+    }
+
+    // framebuffer pixel box
+    float u0, u1, w0, w1;
+    if (fov) {
+        float2 poly[16];
+        int n;
+        if (use_hull && nh >= 3) {
+            for (int k = 0; k < nh; ++k)
+                poly[k] = H[k];
+            n = nh;
+        } else {
+            poly[0] = make_float2(xmin, ymin);
+            poly[1] = make_float2(xmax, ymin);
+            poly[2] = make_float2(xmax, ymax);
+            poly[3] = make_float2(xmin, ymax);
+            n = 4;
+        }
+        const float4 fb = fov_preimage_box(poly, n, make_float2(v.fx, v.fy), v.inv_alpha, 2.f * eps);
+        u0 = fb.x;
+        u1 = fb.y;
+        w0 = fb.z;
+        w1 = fb.w;
+    } else {
+        u0 = xmin;
+        u1 = xmax;
+        w0 = ymin;
+        w1 = ymax;
+    }
+    // pixel centres (i + .5)/W inside [u0, u1], one pixel of slack each side
+    const float fi0 = ceilf(u0 * v.W - 0.5f) - 1.f, fi1 = floorf(u1 * v.W - 0.5f) + 1.f;
+    const float fj0 = ceilf(w0 * v.H - 0.5f) - 1.f, fj1 = floorf(w1 * v.H - 0.5f) + 1.f;
+    B.i0 = (int)fmaxf(fi0, 0.f);
+    B.i1 = (int)fminf(fi1, (float)(v.W - 1));
+    B.j0 = (int)fmaxf(fj0, 0.f);
+    B.j1 = (int)fminf(fj1, (float)(v.H - 1));
+    if (B.i0 > B.i1 || B.j0 > B.j1)
+        B.culled = true;
+}
+
+// Fragment record layout (6 x float4 per triangle):
+//   [0] S0.x S0.y S0.z S1.x   [1] S1.y S1.z S2.x S2.y   [2] S2.z D0.x D0.y D0.z
+//   [3] D1.x D1.y D1.z D2.x   [4] xmin xmax ymin ymax   [5] tmin tmax D2.y D2.z
+// S = camera-space vertex at t = 0, D = its motion over the frame, the box
+// and interval of stage (a).  tbox = (i0 | i1 << 16, j0 | j1 << 16, nhp, culled).
+__global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views, int nviews,
+                                               const long long *__restrict__ tri_offs, long long ttot,
+                                               float4 *__restrict__ rec, float4 *__restrict__ hp,
+                                               int4 *__restrict__ tbox, Counters *cnt)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ttot)
+        return;
+    const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+    const int k = (int)(g - v.tri_off);
+    const int ia = v.i0[k], ib = v.i1[k], ic = v.i2[k];
+    float3 S[3], E[3], D[3];
+    vertex_start_end(v, ia, S[0], E[0]);
+    vertex_start_end(v, ib, S[1], E[1]);
+    vertex_start_end(v, ic, S[2], E[2]);
+    for (int q = 0; q < 3; ++q)
+        D[q] = make_float3(E[q].x - S[q].x, E[q].y - S[q].y, E[q].z - S[q].z);
+    Bound B;
+    compute_bound(v, S, D, B);
+    float4 *r = rec + g * kRecF4;
+    r[0] = make_float4(S[0].x, S[0].y, S[0].z, S[1].x);
+    r[1] = make_float4(S[1].y, S[1].z, S[2].x, S[2].y);
+    r[2] = make_float4(S[2].z, D[0].x, D[0].y, D[0].z);
+    r[3] = make_float4(D[1].x, D[1].y, D[1].z, D[2].x);
+    if (B.culled) {
+        r[4] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+        r[5] = make_float4(INFINITY, -INFINITY, D[2].y, D[2].z);
+        tbox[g] = make_int4(1, 1, 0, 1);
+        atomicAdd(&cnt->culled, 1ull);
+        return;
+    }
+    r[4] = make_float4(B.xmin, B.xmax, B.ymin, B.ymax);
+    r[5] = make_float4(B.tmin - kEpsT, B.tmax + kEpsT, D[2].y, D[2].z);
+    for (int h = 0; h < B.nhp; ++h)
+        hp[g * kMaxHp + h] = B.hp[h];
+    tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), B.nhp, 0);
+}
+
+cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
+                         float4 *hp, int4 *tbox, Counters *cnt, cudaStream_t st)
+{
+    if (ttot > 0)
+        k_bound<<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox, cnt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- binning
+
+// Does the display region of a triangle meet the display box of a tile?
+// Box overlap, then every half-plane against the box corner that lies
+// deepest inside it.
+__device__ __forceinline__ bool tile_meets(const float4 tb, const float4 bb, const float4 *h, int nh)
+{
+    if (bb.x > tb.y || bb.y < tb.x || bb.z > tb.w || bb.w < tb.z)
+        return false;
+    for (int k = 0; k < nh; ++k) {
+        const float4 p = h[k];
+        const float m = fmaf(p.x, p.x > 0.f ? tb.x : tb.y, fmaf(p.y, p.y > 0.f ? tb.z : tb.w, p.z));
+        if (m > 0.f)
+            return false;
+    }
+    return true;
+}
+
+// Bins: tile_cnt[tile] (low 40 bits) = number of triangles whose region
+// meets the tile; warp-aggregated appends (lanes that hit the same tile in
+// the same step share one atomic).
+template <bool kScatter>
+__global__ void __launch_bounds__(128) k_bin(const ViewDev *__restrict__ views, int nviews,
+                                             const long long *__restrict__ tri_offs, long long ttot,
+                                             const float4 *__restrict__ rec, const float4 *__restrict__ hp,
+                                             const int4 *__restrict__ tbox, const float4 *__restrict__ tile_box,
+                                             unsigned long long *__restrict__ tile_cnt,
+                                             const unsigned long long *__restrict__ scan, unsigned int *__restrict__ fill,
+                                             unsigned int *__restrict__ tile_tris, long long cap_pairs, Counters *cnt)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ttot)
+        return;
+    const int4 tb = tbox[g];
+    if (tb.w)
+        return;
+    const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+    const int lane = threadIdx.x & 31;
+    const int tx0 = (tb.x & 0xffff) / v.S, tx1 = (tb.x >> 16) / v.S;
+    const int ty0 = (tb.y & 0xffff) / v.S, ty1 = (tb.y >> 16) / v.S;
+    const float4 bb = rec[g * kRecF4 + 4];
+    float4 h[kMaxHp];
+    int nh = 0;
+    if (tx0 != tx1 || ty0 != ty1) {
+        nh = tb.z;
+        for (int k = 0; k < nh; ++k)
+            h[k] = hp[g * kMaxHp + k];
+    }
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const long long tile = v.tile_off + (long long)ty * v.tiles_x + tx;
+            if (!tile_meets(tile_box[tile], bb, h, nh))
+                continue;
+            const unsigned mask = __activemask();
+            const unsigned peers = __match_any_sync(mask, (unsigned long long)tile);
+            const int leader = __ffs(peers) - 1;
+            if (!kScatter) {
+                if (lane == leader)
+                    atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
+            } else {
+                unsigned base = 0;
+                if (lane == leader)
+                    base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+                const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
+                if (pos < cap_pairs)
+                    tile_tris[pos] = (unsigned)g;
+                else
+                    atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+            }
+        }
+}
+
+cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
+                             const float4 *rec, const float4 *hp, const int4 *tbox, const float4 *tile_box,
+                             unsigned long long *tile_cnt, cudaStream_t st)
+{
+    if (ttot > 0)
+        k_bin<false><<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox,
+                                                                     tile_box, tile_cnt, nullptr, nullptr, nullptr,
+                                                                     0, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
+                               const float4 *rec, const float4 *hp, const int4 *tbox, const float4 *tile_box,
+                               const unsigned long long *scan, unsigned int *fill, unsigned int *tile_tris,
+                               long long cap_pairs, Counters *cnt, cudaStream_t st)
+{
+    if (ttot > 0)
+        k_bin<true><<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox,
+                                                                    tile_box, nullptr, scan, fill, tile_tris,
+                                                                    cap_pairs, cnt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scan
+
+// Exclusive prefix sum of the packed per-tile words: low 40 bits = bin
+// entries, high 24 bits = work items (ceil(entries / seg)).  Three passes:
+// per-block scan, scan of the block sums, add.
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ unsigned long long pack_items(unsigned long long c, int seg)
+{
+    const unsigned long long n = c & 0xFFFFFFFFFFull;
+    return n | (((n + seg - 1) / seg) << 40);
+}
+
+__device__ unsigned long long block_exclusive_scan(unsigned long long x, unsigned long long *total)
+{
+    __shared__ unsigned long long warp_sums[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += y;
+    }
+    if (lane == 31)
+        warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long before = w > 0 ? warp_sums[w - 1] : 0ull;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + inc - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(const unsigned long long *__restrict__ in,
+                                                            unsigned long long *__restrict__ out,
+                                                            unsigned long long *__restrict__ sums, long long n, int seg)
+{
+    const long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
+    unsigned long long v[kScanPer], s = 0;
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < n ? (seg > 0 ? pack_items(in[base + k], seg) : in[base + k]) : 0ull;
+        s += v[k];
+    }
+    unsigned long long total;
+    unsigned long long run = block_exclusive_scan(s, &total);
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n)
+            out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0)
+        sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(unsigned long long *__restrict__ out,
+                                                          const unsigned long long *__restrict__ sums, long long n,
+                                                          unsigned long long *__restrict__ total_out, long long nblocks)
+{
+    const long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
+    const unsigned long long add = sums[blockIdx.x];
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < n)
+            out[base + k] += add;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *total_out = sums[nblocks];
+}
+
+size_t scan_block_sums_needed(long long n)
+{
+    const long long nb = (n + kScanBlock - 1) / kScanBlock;
+    return (size_t)(nb + 1) * 2 + 64;
+}
+
+cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *block_sums,
+                        long long n, int seg, cudaStream_t st)
+{
+    const long long nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb == 0) {
+        cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+        return cudaGetLastError();
+    }
+    if (nb > kScanBlock)
+        return cudaErrorInvalidValue;
+    unsigned long long *sums = block_sums, *sums_out = block_sums + nb + 1;
+    k_scan_local<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, sums, n, seg);
+    // block sums -> exclusive offsets (nb is small: one block of the same scan)
+    k_scan_local<<<1, kScanThreads, 0, st>>>(sums, sums_out, sums_out + nb, nb, 0);
+    // sums_out[nb] holds the grand total after the second pass
+    k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, sums_out, n, out + n, nb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- items
+
+// Work items of the persistent fragment kernel: each non-empty tile's bin
+// cut into runs of at most seg triangles; item = (view, tile in view,
+// first entry, end entry).
+__global__ void k_items(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ tile_offs,
+                        long long ntiles, const unsigned long long *__restrict__ tile_cnt,
+                        const unsigned long long *__restrict__ scan, int4 *__restrict__ items, long long cap_items,
+                        long long cap_pairs, int seg, Counters *cnt)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) {
+        cnt->pairs_total = scan[ntiles] & 0xFFFFFFFFFFull;
+        cnt->items_total = scan[ntiles] >> 40;
+    }
+    if (g >= ntiles)
+        return;
+    const long long n = (long long)(tile_cnt[g] & 0xFFFFFFFFFFull);
+    if (n == 0)
+        return;
+    const int vi = find_view(tile_offs, nviews, g);
+    const long long lt = g - views[vi].tile_off;
+    const long long off = (long long)(scan[g] & 0xFFFFFFFFFFull);
+    const long long ioff = (long long)(scan[g] >> 40);
+    const long long nit = (n + seg - 1) / seg;
+    for (long long q = 0; q < nit; ++q) {
+        // runs past the bin buffer (its scatter overflowed) are clamped to
+        // it, so the frame stays in bounds; the overflow status reruns it
+        const long long b0 = min(off + q * seg, cap_pairs), b1 = min(off + min(n, (q + 1) * seg), cap_pairs);
+        if (ioff + q < cap_items)
+            items[ioff + q] = make_int4(vi, (int)lt, (int)b0, (int)b1);
+        else
+            atomicOr(&cnt->status, ST_OVERFLOW_ITEMS);
+    }
+}
+
+cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
+                         const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
+                         long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st)
+{
+    const long long n = ntiles > 0 ? ntiles : 1;
+    k_items<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, tile_offs, ntiles, tile_cnt, scan, items,
+                                                         cap_items, cap_pairs, seg, cnt);
+    return cudaGetLastError();
+}
+
+}  // namespace pr

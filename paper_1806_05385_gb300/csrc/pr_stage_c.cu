@@ -1,0 +1,230 @@
+// pr_stage_c.cu -- stage (c): per-fragment ray casting (Sec. 3.2,
+// "Intersection") inside the tile bins of stage (b), and the resolve of the
+// packed depth|id keys into the id and depth buffers.
+//
+// Work decomposition: a persistent grid pulls (view, tile, bin run) items
+// from a global atomic queue.  One CTA covers one S x S tile; each warp owns
+// an 8 x 8 pixel block and each lane two pixels of one column (rows r and
+// r + 4), so under a horizontal rolling scan both pixels share one time.
+// The CTA stages the records of a run of binned triangles in shared memory;
+// every warp first tests the triangle's display box and time interval
+// against its block (warp-uniform skip), then each lane runs the watertight
+// test for its pixels.  Per pixel the nearest key is kept in a register and
+// merged into the frame with one 64-bit atomicMin per item.
+#include "pr_launch.h"
+
+namespace pr {
+
+// One watertight ray/triangle test (Woop, Benthin and Wald, "Watertight
+// Ray/Triangle Intersection", JCGT 2013) of the ray from the origin along
+// (dx, dy, 1) against the triangle moved to time t.  With dz = 1 the
+// shear/scale constants are Sx = dx, Sy = dy, Sz = 1.  The edge-function
+// products are rounded separately (no contraction) so that a shared edge
+// yields exactly opposite values in its two triangles.
+__device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const float4 r2, const float4 r3,
+                                         const float d2y, const float d2z, const float t, const float dx,
+                                         const float dy, const float zn, const uint32_t id, unsigned long long &best,
+                                         unsigned &hits)
+{
+    // vertices at time t: c = S + t D
+    const float Az = fmaf(t, r2.w, r0.z), Bz = fmaf(t, r3.z, r1.y), Cz = fmaf(t, d2z, r2.x);
+    const float ax = fmaf(-dx, Az, fmaf(t, r2.y, r0.x)), ay = fmaf(-dy, Az, fmaf(t, r2.z, r0.y));
+    const float bx = fmaf(-dx, Bz, fmaf(t, r3.x, r0.w)), by = fmaf(-dy, Bz, fmaf(t, r3.y, r1.x));
+    const float cx = fmaf(-dx, Cz, fmaf(t, r3.w, r1.z)), cy = fmaf(-dy, Cz, fmaf(t, d2y, r1.w));
+    const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f))
+        return;
+    const float det = U + V + W;
+    if (det == 0.f)
+        return;
+    const float T = fmaf(U, Az, fmaf(V, Bz, W * Cz));
+    const float depth = __fdiv_rn(T, det);
+    if (!(depth > zn))
+        return;
+    ++hits;
+    const unsigned long long key = pack_key(depth, id);
+    best = key < best ? key : best;
+}
+
+template <int S>
+__global__ void __launch_bounds__(S *S / 2) k_fragment(const ViewDev *__restrict__ views, const int4 *__restrict__ items,
+                                                      const unsigned long long *__restrict__ scan, long long tile_lo,
+                                                      long long tile_hi, long long cap_items, int *__restrict__ head,
+                                                      const unsigned int *__restrict__ tile_tris,
+                                                      const float4 *__restrict__ rec,
+                                                      unsigned long long *__restrict__ keys, Counters *cnt)
+{
+    constexpr int NT = S * S / 2;  // threads: two pixels each
+    constexpr int WPR = S / 8;     // 8x8 warp blocks per tile row
+    constexpr int CH = NT < 256 ? NT : 256;  // triangles staged per chunk
+    __shared__ float4 s_rec[CH * kRecF4];
+    __shared__ unsigned s_id[CH];
+    __shared__ long long s_item;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ci = (warp % WPR) * 8 + (lane & 7);
+    const int cj0 = (warp / WPR) * 8 + (lane >> 3), cj1 = cj0 + 4;
+    const long long it_lo = (long long)(scan[tile_lo] >> 40);
+    const long long it_hi = min((long long)(scan[tile_hi] >> 40), cap_items);
+    unsigned long long n_tests = 0, n_hits = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = it_lo + atomicAdd(head, 1);
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= it_hi)
+            break;
+        const int4 item = items[it];
+        const ViewDev &v = views[item.x];
+        const int tx = item.y % v.tiles_x, ty = item.y / v.tiles_x;
+        const int i = tx * S + ci, j0 = ty * S + cj0, j1 = ty * S + cj1;
+        const bool ok0 = i < v.W && j0 < v.H, ok1 = i < v.W && j1 < v.H;
+        float x00, x01, t0, dx0, dy0, x10, x11, t1, dx1, dy1;
+        pixel_ray(v, min(i, v.W - 1), min(j0, v.H - 1), x00, x01, t0, dx0, dy0);
+        pixel_ray(v, min(i, v.W - 1), min(j1, v.H - 1), x10, x11, t1, dx1, dy1);
+        // the warp's block in display space and time (valid pixels only)
+        float wx0 = INFINITY, wx1 = -INFINITY, wy0 = INFINITY, wy1 = -INFINITY, wt0 = INFINITY, wt1 = -INFINITY;
+        if (ok0) {
+            wx0 = x00; wx1 = x00; wy0 = x01; wy1 = x01; wt0 = t0; wt1 = t0;
+        }
+        if (ok1) {
+            wx0 = fminf(wx0, x10); wx1 = fmaxf(wx1, x10); wy0 = fminf(wy0, x11); wy1 = fmaxf(wy1, x11);
+            wt0 = fminf(wt0, t1); wt1 = fmaxf(wt1, t1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
+            wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
+            wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
+            wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
+            wt0 = fminf(wt0, __shfl_xor_sync(0xffffffffu, wt0, o));
+            wt1 = fmaxf(wt1, __shfl_xor_sync(0xffffffffu, wt1, o));
+        }
+        const float zn = v.z_near;
+        const unsigned id_base = (unsigned)v.tri_off;
+        unsigned long long best0 = ~0ull, best1 = ~0ull;
+        unsigned hits = 0, tested = 0;
+        for (int base = item.z; base < item.w; base += CH) {
+            const int n = min(CH, item.w - base);
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += NT)
+                s_id[q] = tile_tris[base + q];
+            __syncthreads();
+            for (int q = threadIdx.x; q < n * kRecF4; q += NT) {
+                const int k = q / kRecF4, f = q - k * kRecF4;
+                s_rec[q] = __ldg(&rec[(size_t)s_id[k] * kRecF4 + f]);
+            }
+            __syncthreads();
+            for (int k = 0; k < n; ++k) {
+                const float4 bb = s_rec[k * kRecF4 + 4];
+                const float4 tb = s_rec[k * kRecF4 + 5];
+                if (bb.x > wx1 || bb.y < wx0 || bb.z > wy1 || bb.w < wy0 || tb.x > wt1 || tb.y < wt0)
+                    continue;
+                const float4 r0 = s_rec[k * kRecF4 + 0], r1 = s_rec[k * kRecF4 + 1];
+                const float4 r2 = s_rec[k * kRecF4 + 2], r3 = s_rec[k * kRecF4 + 3];
+                const unsigned id = s_id[k] - id_base;
+                ++tested;
+                ray_test(r0, r1, r2, r3, tb.z, tb.w, t0, dx0, dy0, zn, id, best0, hits);
+                ray_test(r0, r1, r2, r3, tb.z, tb.w, t1, dx1, dy1, zn, id, best1, hits);
+            }
+        }
+        n_tests += (unsigned long long)tested * (unsigned)(ok0 + ok1);
+        n_hits += hits;
+        if (ok0 && best0 != ~0ull)
+            atomicMin(&keys[v.pix_off + (long long)j0 * v.W + i], best0);
+        if (ok1 && best1 != ~0ull)
+            atomicMin(&keys[v.pix_off + (long long)j1 * v.W + i], best1);
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_tests += __shfl_xor_sync(0xffffffffu, n_tests, o);
+        n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&cnt->tests, n_tests);
+        atomicAdd(&cnt->hits, n_hits);
+    }
+}
+
+template <int S>
+static int grid_for()
+{
+    static int g = 0;
+    if (g == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fragment<S>, S * S / 2, 0);
+        g = sms * (per > 0 ? per : 1);
+    }
+    return g;
+}
+
+int fragment_grid(int S)
+{
+    switch (S) {
+    case 8: return grid_for<8>();
+    case 16: return grid_for<16>();
+    default: return grid_for<32>();
+    }
+}
+
+cudaError_t launch_fragment(int S, const ViewDev *views, const int4 *items, const unsigned long long *scan,
+                            long long tile_lo, long long tile_hi, long long cap_items, int *head,
+                            const unsigned int *tile_tris, const float4 *rec, unsigned long long *keys,
+                            unsigned int *flags, long long cap_flags, Counters *cnt, int grid, cudaStream_t st)
+{
+    (void)flags;
+    (void)cap_flags;
+    switch (S) {
+    case 8:
+        k_fragment<8><<<grid, 32, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head, tile_tris, rec, keys, cnt);
+        break;
+    case 16:
+        k_fragment<16><<<grid, 128, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head, tile_tris, rec, keys, cnt);
+        break;
+    case 32:
+        k_fragment<32><<<grid, 512, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head, tile_tris, rec, keys, cnt);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_retest(const ViewDev *, int, const long long *, const int4 *, const unsigned long long *,
+                          const long long *, const unsigned int *, unsigned int *, long long, unsigned long long *,
+                          Counters *, int, cudaStream_t)
+{
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- resolve
+
+__global__ void k_resolve(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ pix_offs,
+                          long long npix, const unsigned long long *__restrict__ keys)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npix)
+        return;
+    const ViewDev &v = views[find_view(pix_offs, nviews, g)];
+    const long long lin = g - v.pix_off;
+    const unsigned long long key = keys[g];
+    const bool bg = key == ~0ull;
+    if (v.id_out)
+        v.id_out[lin] = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
+    if (v.depth_out)
+        v.depth_out[lin] = bg ? INFINITY : __uint_as_float((unsigned)(key >> 32));
+}
+
+cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
+                           const unsigned long long *keys, cudaStream_t st)
+{
+    if (npix > 0)
+        k_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix, keys);
+    return cudaGetLastError();
+}
+
+}  // namespace pr

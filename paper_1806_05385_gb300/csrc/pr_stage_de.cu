@@ -1,0 +1,230 @@
+// pr_stage_de.cu -- stage (d): deferred shading at the pixel time (Sec. 3.2,
+// "Shading"), and stage (e): its adjoint with respect to the vertex colours,
+// positions and velocities, with the visible triangle of every pixel held
+// fixed.  Both recompute the pixel's time, ray, moved triangle and
+// barycentrics from the id buffer instead of storing them.
+#include "pr_launch.h"
+
+namespace pr {
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 scale3(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+
+// Everything shading needs about the visible triangle at one pixel.
+struct PixelHit {
+    int ia, ib, ic;     // vertex indices
+    float t;            // pixel time
+    float3 dir;         // ray direction
+    float3 A, B, C;     // triangle moved to t (camera space)
+    float b0, b1, b2;   // barycentrics of the ray point
+    float det;          // U + V + W of the watertight test
+    float3 n;           // unit normal facing the viewer
+    float nlen, flip;   // |(B-A) x (C-A)| and the sign applied
+    float3 l;           // unit light direction at t
+    float ndl, sigma;   // n.l and k_a + k_d max(0, n.l)
+};
+
+__device__ __forceinline__ void pixel_hit(const ViewDev &v, long long lin, unsigned id, PixelHit &h)
+{
+    const int i = (int)(lin % v.W), j = (int)(lin / v.W);
+    float x0, x1, dx, dy;
+    pixel_ray(v, i, j, x0, x1, h.t, dx, dy);
+    h.dir = make_float3(dx, dy, 1.f);
+    h.ia = v.i0[id];
+    h.ib = v.i1[id];
+    h.ic = v.i2[id];
+    float3 S, E;
+    const float t = h.t;
+    vertex_start_end(v, h.ia, S, E);
+    h.A = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+    vertex_start_end(v, h.ib, S, E);
+    h.B = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+    vertex_start_end(v, h.ic, S, E);
+    h.C = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+    // barycentrics from the sheared edge functions of the watertight test
+    const float ax = fmaf(-dx, h.A.z, h.A.x), ay = fmaf(-dy, h.A.z, h.A.y);
+    const float bx = fmaf(-dx, h.B.z, h.B.x), by = fmaf(-dy, h.B.z, h.B.y);
+    const float cx = fmaf(-dx, h.C.z, h.C.x), cy = fmaf(-dy, h.C.z, h.C.y);
+    const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    h.det = U + V + W;
+    const float inv = h.det != 0.f ? 1.f / h.det : 0.f;
+    h.b0 = U * inv;
+    h.b1 = V * inv;
+    h.b2 = W * inv;
+    float3 n = cross3(sub3(h.B, h.A), sub3(h.C, h.A));
+    h.flip = dot3(n, h.dir) > 0.f ? -1.f : 1.f;
+    h.nlen = sqrtf(dot3(n, n));
+    const float in = h.nlen > 0.f ? h.flip / h.nlen : 0.f;
+    h.n = scale3(n, in);
+    float3 l = make_float3(fmaf(t, v.l1[0] - v.l0[0], v.l0[0]), fmaf(t, v.l1[1] - v.l0[1], v.l0[1]),
+                           fmaf(t, v.l1[2] - v.l0[2], v.l0[2]));
+    h.l = scale3(l, rsqrtf(dot3(l, l)));
+    h.ndl = dot3(h.n, h.l);
+    h.sigma = v.k_a + v.k_d * fmaxf(h.ndl, 0.f);
+}
+
+__global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ pix_offs,
+                        long long npix)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npix)
+        return;
+    const ViewDev &v = views[find_view(pix_offs, nviews, g)];
+    if (!v.rgb_out)
+        return;
+    const long long lin = g - v.pix_off;
+    const long long plane = (long long)v.W * v.H;
+    const unsigned id = v.id_in[lin];
+    if (id >= (unsigned)v.T) {
+        v.rgb_out[lin] = 0.f;
+        v.rgb_out[plane + lin] = 0.f;
+        v.rgb_out[2 * plane + lin] = 0.f;
+        return;
+    }
+    PixelHit h;
+    pixel_hit(v, lin, id, h);
+    const float r = fmaf(h.b0, v.cr[h.ia], fmaf(h.b1, v.cr[h.ib], h.b2 * v.cr[h.ic]));
+    const float gg = fmaf(h.b0, v.cg[h.ia], fmaf(h.b1, v.cg[h.ib], h.b2 * v.cg[h.ic]));
+    const float b = fmaf(h.b0, v.cb[h.ia], fmaf(h.b1, v.cb[h.ib], h.b2 * v.cb[h.ic]));
+    v.rgb_out[lin] = r * h.sigma;
+    v.rgb_out[plane + lin] = gg * h.sigma;
+    v.rgb_out[2 * plane + lin] = b * h.sigma;
+}
+
+cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *pix_offs, long long npix, cudaStream_t st)
+{
+    if (npix > 0)
+        k_shade<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix);
+    return cudaGetLastError();
+}
+
+// Sum x over the 32 lanes of a fully converged warp.
+__device__ __forceinline__ float warp_sum(float x)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Adjoint of rgb = a sigma, a = sum_k b_k col_k, sigma = k_a + k_d max(0, n.l):
+//  - d/dcol_k = g b_k sigma
+//  - barycentrics b_k = w_k / sum w with w_0 = dir.(B x C), w_1 = dir.(C x A),
+//    w_2 = dir.(A x B) (the watertight U, V, W are -w), so
+//    d sum/dw_j = (gb_j - sum_k gb_k b_k) / sum w and dw_j/dA etc. are
+//    cross products with dir;
+//  - the unit normal n = flip (B-A)x(C-A) / |.|: dn gets (I - n n^T)/|.|;
+//  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1:
+//    dc/dp = (1-t) R0 + t R1, dc/dv = t R1.
+// Contributions are summed over the warp when every lane sees the same
+// triangle, else added per lane.
+__global__ void k_backward(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ pix_offs,
+                           long long npix)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npix)
+        return;
+    const ViewDev &v = views[find_view(pix_offs, nviews, g)];
+    const long long lin = g - v.pix_off;
+    const long long plane = (long long)v.W * v.H;
+    const unsigned id = v.id_in[lin];
+    const bool valid = id < (unsigned)v.T;
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, valid ? id : 0xFFFFFFFFu);
+    if (!valid)
+        return;
+    PixelHit h;
+    pixel_hit(v, lin, id, h);
+    const float g0 = v.grad_in[lin], g1 = v.grad_in[plane + lin], g2 = v.grad_in[2 * plane + lin];
+    const int vid[3] = {h.ia, h.ib, h.ic};
+    const float b[3] = {h.b0, h.b1, h.b2};
+    float col[3][3];
+    for (int k = 0; k < 3; ++k) {
+        col[k][0] = v.cr[vid[k]];
+        col[k][1] = v.cg[vid[k]];
+        col[k][2] = v.cb[vid[k]];
+    }
+    float a[3];
+    for (int c = 0; c < 3; ++c)
+        a[c] = b[0] * col[0][c] + b[1] * col[1][c] + b[2] * col[2][c];
+    float gc[3][3], gb[3];
+    const float gv[3] = {g0, g1, g2};
+    for (int k = 0; k < 3; ++k) {
+        gb[k] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            gc[k][c] = gv[c] * b[k] * h.sigma;
+            gb[k] += gv[c] * col[k][c];
+        }
+        gb[k] *= h.sigma;
+    }
+    const float gsig = g0 * a[0] + g1 * a[1] + g2 * a[2];
+    // barycentrics -> moved vertices
+    const float sw = -h.det;
+    const float gdotb = gb[0] * b[0] + gb[1] * b[1] + gb[2] * b[2];
+    const float isw = sw != 0.f ? 1.f / sw : 0.f;
+    const float gw0 = (gb[0] - gdotb) * isw, gw1 = (gb[1] - gdotb) * isw, gw2 = (gb[2] - gdotb) * isw;
+    const float3 D = h.dir;
+    float3 gA = add3(scale3(cross3(D, h.C), gw1), scale3(cross3(h.B, D), gw2));
+    float3 gB = add3(scale3(cross3(h.C, D), gw0), scale3(cross3(D, h.A), gw2));
+    float3 gC = add3(scale3(cross3(D, h.B), gw0), scale3(cross3(h.A, D), gw1));
+    // normal -> moved vertices
+    if (h.ndl > 0.f && h.nlen > 0.f) {
+        const float3 gnh = scale3(h.l, gsig * v.k_d);
+        const float pr = dot3(h.n, gnh);
+        const float3 gnn = scale3(sub3(gnh, scale3(h.n, pr)), h.flip / h.nlen);
+        gA = add3(gA, cross3(sub3(h.B, h.C), gnn));
+        gB = add3(gB, cross3(sub3(h.C, h.A), gnn));
+        gC = add3(gC, cross3(sub3(h.A, h.B), gnn));
+    }
+    // moved vertices -> positions and velocities
+    const float3 gk[3] = {gA, gB, gC};
+    const float t = h.t, omt = 1.f - t;
+    float gp[3][3], gvel[3][3];
+    for (int k = 0; k < 3; ++k) {
+        for (int c = 0; c < 3; ++c) {
+            const float m0 = v.R0[c], m1 = v.R0[3 + c], m2 = v.R0[6 + c];
+            const float n0 = v.R1[c], n1 = v.R1[3 + c], n2 = v.R1[6 + c];
+            const float e1 = n0 * gk[k].x + n1 * gk[k].y + n2 * gk[k].z;
+            gp[k][c] = omt * (m0 * gk[k].x + m1 * gk[k].y + m2 * gk[k].z) + t * e1;
+            gvel[k][c] = t * e1;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    if (peers == 0xffffffffu) {
+        // the whole warp sees one triangle: reduce first, then one lane adds
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) {
+                gc[k][c] = warp_sum(gc[k][c]);
+                gp[k][c] = warp_sum(gp[k][c]);
+                gvel[k][c] = warp_sum(gvel[k][c]);
+            }
+        if (lane != 0)
+            return;
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) {
+            if (v.dcol)
+                atomicAdd(&v.dcol[3 * vid[k] + c], gc[k][c]);
+            if (v.dpos)
+                atomicAdd(&v.dpos[3 * vid[k] + c], gp[k][c]);
+            if (v.dvel)
+                atomicAdd(&v.dvel[3 * vid[k] + c], gvel[k][c]);
+        }
+}
+
+cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
+                            cudaStream_t st)
+{
+    if (npix > 0)
+        k_backward<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix);
+    return cudaGetLastError();
+}
+
+}  // namespace pr
