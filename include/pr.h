@@ -115,6 +115,10 @@ typedef struct {
     uint64_t flagged;     /* pixels re-tested in FP64 (precision form) */
     uint64_t changed;     /* pixels whose winner the FP64 re-test changed */
     uint64_t pixels;      /* framebuffer pixels over all views */
+    float stage_ms[8];    /* device time of the last frame's stages, from CUDA events on the
+                             caller's stream: [0] (a) tile boxes + bounds, [1] (b) binning
+                             (count, scan, scatter, items), [2] (c) fragment kernel(s),
+                             [3] FP64 re-test, [4] resolve, [5] (d) shading, [6]-[7] unused */
 } pr_stats;
 
 typedef struct pr_scene pr_scene;         /* library-owned device copy of a mesh + its scratch */

@@ -49,10 +49,12 @@ class PrParams(C.Structure):
 
 class PrStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("tests", "hits", "pairs", "items", "culled", "flagged", "changed",
-                                          "pixels")]
+                                          "pixels")] + [("stage_ms", C.c_float * 8)]
 
     def as_dict(self):
-        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "stage_ms"}
+        d["stage_ms"] = [float(x) for x in self.stage_ms]
+        return d
 
 
 class PrBatchView(C.Structure):

@@ -110,11 +110,15 @@ pr_status from_cuda(cudaError_t e)
     return PR_ERR_CUDA;
 }
 
+// On failure: clear the runtime's last error (so the caller's later CUDA
+// calls do not see it) and return the mapped status.
 #define PR_TRY(expr)                                 \
     do {                                             \
         cudaError_t _e = (expr);                     \
-        if (_e != cudaSuccess)                       \
+        if (_e != cudaSuccess) {                     \
+            cudaGetLastError();                      \
             return from_cuda(_e);                    \
+        }                                            \
     } while (0)
 
 constexpr int kDefaultTile = 16;
@@ -125,6 +129,7 @@ constexpr int kDefaultSeg = 256;
 // Scratch of one batched frame.
 struct pr_workspace {
     DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, tile_tris, items, keys, counters, heads;
+    DevBuf cand, cand_off;         // candidate tiles per triangle and their prefix sum
     DevBuf stage;                  // device copies of host-side outputs
     long long cap_pairs = 0, cap_items = 0;
     PinnedBuf<ViewDev> h_views;
@@ -132,6 +137,43 @@ struct pr_workspace {
     PinnedBuf<Counters> h_cnt;
     pr_stats stats{};
     long long last_T = 0;          // triangles of the last frame (debug bounds)
+    static constexpr int kEv = 7;  // stage boundaries of one frame
+    cudaEvent_t ev[kEv] = {};
+    bool ev_ok = false;
+    ~pr_workspace()
+    {
+        for (int k = 0; k < kEv; ++k)
+            if (ev[k])
+                cudaEventDestroy(ev[k]);
+    }
+    cudaError_t events()
+    {
+        if (ev_ok)
+            return cudaSuccess;
+        for (int k = 0; k < kEv; ++k)
+            if (!ev[k]) {
+                cudaError_t e = cudaEventCreate(&ev[k]);
+                if (e != cudaSuccess)
+                    return e;
+            }
+        ev_ok = true;
+        return cudaSuccess;
+    }
+    // stage times of the last completed frame (events already complete)
+    void read_stage_times()
+    {
+        for (int k = 0; k < 8; ++k)
+            stats.stage_ms[k] = 0.f;
+        if (!ev_ok)
+            return;
+        for (int k = 0; k + 1 < kEv; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess)
+                stats.stage_ms[k] = ms;
+            else
+                cudaGetLastError();
+        }
+    }
 };
 
 struct pr_scene {
@@ -254,8 +296,8 @@ pr_params default_params(const pr_params *p)
 struct BatchPlan {
     std::vector<int> order;           // views sorted by tile size
     std::vector<ViewDev> vd;          // in `order`
-    std::vector<long long> tri_off, tile_off, pix_off;
-    long long ttot = 0, ntiles = 0, npix = 0;
+    std::vector<long long> tri_off, tile_off, pix_off, blk_off;
+    long long ttot = 0, ntiles = 0, npix = 0, nblk = 0;
     struct Cls {
         int S;
         long long tile_lo, tile_hi;
@@ -291,6 +333,7 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
     P.tri_off.assign(n + 1, 0);
     P.tile_off.assign(n + 1, 0);
     P.pix_off.assign(n + 1, 0);
+    P.blk_off.assign(n + 1, 0);
     size_t stage = 0;
     auto take = [&](size_t bytes) {
         long long off = (long long)stage;
@@ -306,6 +349,8 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
         v.tri_off = P.tri_off[q];
         v.tile_off = P.tile_off[q];
         v.pix_off = P.pix_off[q];
+        v.blk_off = P.blk_off[q];
+        P.blk_off[q + 1] = P.blk_off[q] + (long long)((v.W + 7) / 8) * ((v.H + 3) / 4);
         P.tri_off[q + 1] = P.tri_off[q] + bv.scene->T;
         P.tile_off[q + 1] = P.tile_off[q] + (long long)v.tiles_x * v.tiles_y;
         P.pix_off[q + 1] = P.pix_off[q] + (long long)v.W * v.H;
@@ -326,6 +371,7 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
     P.ttot = P.tri_off[n];
     P.ntiles = P.tile_off[n];
     P.npix = P.pix_off[n];
+    P.nblk = P.blk_off[n];
     P.stage_bytes = stage;
     if (P.ttot >= (1ll << 32) - 1)
         return PR_ERR_INVALID_ARG;
@@ -344,7 +390,7 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
 {
     const int n = (int)P.vd.size();
     PR_TRY(ensure(ws->views, sizeof(ViewDev) * n));
-    PR_TRY(ensure(ws->offs, sizeof(long long) * 3 * (n + 1)));
+    PR_TRY(ensure(ws->offs, sizeof(long long) * 4 * (n + 1)));
     PR_TRY(ensure(ws->rec, sizeof(float4) * kRecF4 * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->hp, sizeof(float4) * kMaxHp * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->tbox, sizeof(int4) * std::max(P.ttot, 1ll)));
@@ -352,7 +398,10 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->tile_cnt, sizeof(unsigned long long) * std::max(P.ntiles, 1ll)));
     PR_TRY(ensure(ws->scan, sizeof(unsigned long long) * (P.ntiles + 1)));
     PR_TRY(ensure(ws->fill, sizeof(unsigned) * std::max(P.ntiles, 1ll)));
-    PR_TRY(ensure(ws->sums, sizeof(unsigned long long) * scan_block_sums_needed(P.ntiles)));
+    PR_TRY(ensure(ws->sums,
+                  sizeof(unsigned long long) * std::max(scan_block_sums_needed(P.ntiles), scan_block_sums_needed(P.ttot))));
+    PR_TRY(ensure(ws->cand, sizeof(unsigned long long) * std::max(P.ttot, 1ll)));
+    PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
     PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
     PR_TRY(ensure(ws->counters, sizeof(Counters)));
     PR_TRY(ensure(ws->heads, sizeof(int) * 8));
@@ -368,7 +417,7 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     }
     ws->cap_items = (long long)(ws->items.cap / sizeof(int4));
     PR_TRY(ws->h_views.ensure(n));
-    PR_TRY(ws->h_offs.ensure(3 * (n + 1)));
+    PR_TRY(ws->h_offs.ensure(4 * (n + 1)));
     PR_TRY(ws->h_cnt.ensure(1));
     return PR_OK;
 }
@@ -393,12 +442,14 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
         ho[q] = P.tri_off[q];
         ho[n + 1 + q] = P.tile_off[q];
         ho[2 * (n + 1) + q] = P.pix_off[q];
+        ho[3 * (n + 1) + q] = P.blk_off[q];
     }
     const ViewDev *dv = ws->views.as<ViewDev>();
     const long long *tri_offs = ws->offs.as<long long>(), *tile_offs = tri_offs + n + 1, *pix_offs = tile_offs + n + 1;
+    const long long *blk_offs = pix_offs + n + 1;
     Counters *cnt = ws->counters.as<Counters>();
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
-    PR_TRY(cudaMemcpyAsync(ws->offs.p, ho, sizeof(long long) * 3 * (n + 1), cudaMemcpyHostToDevice, st));
+    PR_TRY(cudaMemcpyAsync(ws->offs.p, ho, sizeof(long long) * 4 * (n + 1), cudaMemcpyHostToDevice, st));
     PR_TRY(cudaMemsetAsync(ws->counters.p, 0, sizeof(Counters), st));
     PR_TRY(cudaMemsetAsync(ws->heads.p, 0, sizeof(int) * 8, st));
     PR_TRY(cudaMemsetAsync(ws->tile_cnt.p, 0, sizeof(unsigned long long) * std::max(P.ntiles, 1ll), st));
@@ -408,13 +459,26 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     float4 *rec = ws->rec.as<float4>(), *hp = ws->hp.as<float4>(), *tile_box = ws->tile_box.as<float4>();
     int4 *tbox = ws->tbox.as<int4>();
     unsigned long long *tile_cnt = ws->tile_cnt.as<unsigned long long>(), *scan = ws->scan.as<unsigned long long>();
+    PR_TRY(ws->events());
+    cudaEvent_t *ev = ws->ev;
+    // while capturing, external records keep the events as graph nodes
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    PR_TRY(cudaStreamIsCapturing(st, &cs));
+    const unsigned ev_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    auto mark = [&](int k) { return cudaEventRecordWithFlags(ev[k], st, ev_flags); };
+    unsigned long long *cand = ws->cand.as<unsigned long long>(), *cand_off = ws->cand_off.as<unsigned long long>();
+    PR_TRY(mark(0));
     PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
-    PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cnt, st));
-    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, rec, hp, tbox, tile_box, tile_cnt, st));
+    PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, cnt, st));
+    PR_TRY(mark(1));
+    PR_TRY(launch_scan(cand, cand_off, ws->sums.as<unsigned long long>(), P.ttot, 0, st));
+    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
     PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, st));
-    PR_TRY(launch_bin_scatter(dv, n, tri_offs, P.ttot, rec, hp, tbox, tile_box, scan, ws->fill.as<unsigned>(),
-                              ws->tile_tris.as<unsigned>(), ws->cap_pairs, cnt, st));
-    PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items, ws->cap_pairs, seg, cnt, st));
+    PR_TRY(launch_bin_scatter(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, scan,
+                              ws->fill.as<unsigned>(), ws->tile_tris.as<unsigned>(), ws->cap_pairs, cnt, st));
+    PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,
+                        ws->cap_pairs, seg, cnt, st));
+    PR_TRY(mark(2));
     int *heads = ws->heads.as<int>();
     for (size_t c = 0; c < P.classes.size(); ++c) {
         const auto &cl = P.classes[c];
@@ -422,9 +486,13 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
                                heads + c, ws->tile_tris.as<unsigned>(), rec, ws->keys.as<unsigned long long>(),
                                nullptr, 0, cnt, fragment_grid(cl.S), st));
     }
+    PR_TRY(mark(3));
+    PR_TRY(mark(4));
     PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
+    PR_TRY(mark(5));
     if (shade)
-        PR_TRY(launch_shade(dv, n, pix_offs, P.npix, st));
+        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, st));
+    PR_TRY(mark(6));
     // host-side outputs
     for (int q = 0; q < n; ++q) {
         const BatchPlan::Out &o = P.out[q];
@@ -452,6 +520,7 @@ pr_status finish_stats(pr_workspace *ws, const BatchPlan &P)
     ws->stats.changed = c.changed;
     ws->stats.pixels = (uint64_t)P.npix;
     ws->last_T = P.ttot;
+    ws->read_stage_times();
     if (c.status & ST_TIMEOUT)
         return PR_ERR_TIMEOUT;
     if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
@@ -514,7 +583,7 @@ pr_status upload_single(pr_scene *sc, const ViewDev &v, cudaStream_t st)
     ws->h_views.p[0] = v;
     long long *o = ws->h_offs.p;
     o[0] = 0;
-    o[1] = (long long)v.W * v.H;
+    o[1] = (long long)((v.W + 7) / 8) * ((v.H + 3) / 4);  // 8x4 blocks
     o[2] = o[3] = o[4] = o[5] = 0;
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev), cudaMemcpyHostToDevice, st));
     PR_TRY(cudaMemcpyAsync(ws->offs.p, o, sizeof(long long) * 2, cudaMemcpyHostToDevice, st));
@@ -689,7 +758,8 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
     s = upload_single(sc, v, st);
     if (s != PR_OK)
         return s;
-    PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(), np, st));
+    PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
+                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), st));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
     PR_TRY(cudaStreamSynchronize(st));
@@ -741,7 +811,8 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     s = upload_single(sc, v, st);
     if (s != PR_OK)
         return s;
-    PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(), np, st));
+    PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
+                           (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), st));
     for (int a = 0; a < 3; ++a)
         if (host[a])
             PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
@@ -839,6 +910,7 @@ pr_status pr_graph_launch(pr_graph *g, void *stream)
     ws->stats.flagged = c.flagged;
     ws->stats.changed = c.changed;
     ws->stats.pixels = (uint64_t)g->npix;
+    ws->read_stage_times();
     if (c.status & ST_TIMEOUT)
         return PR_ERR_TIMEOUT;
     if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))

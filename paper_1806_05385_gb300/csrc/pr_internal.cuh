@@ -38,6 +38,7 @@ struct ViewDev {
     int W, H, mode, S;                 // framebuffer, pr_mode, bin tile side
     int tiles_x, tiles_y, bound, fp64;
     long long tri_off, tile_off, pix_off;  // offsets of this view in the batch-wide arrays
+    long long blk_off;                 // offset of its 8x4 pixel blocks (stages d, e)
     int T, V;
     const float *px, *py, *pz, *vx, *vy, *vz, *cr, *cg, *cb;  // scene, structure of arrays
     const int *i0, *i1, *i2;

@@ -369,7 +369,8 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
 __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views, int nviews,
                                                const long long *__restrict__ tri_offs, long long ttot,
                                                float4 *__restrict__ rec, float4 *__restrict__ hp,
-                                               int4 *__restrict__ tbox, Counters *cnt)
+                                               int4 *__restrict__ tbox, unsigned long long *__restrict__ cand,
+                                               Counters *cnt)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ttot)
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views
         r[4] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
         r[5] = make_float4(INFINITY, -INFINITY, D[2].y, D[2].z);
         tbox[g] = make_int4(1, 1, 0, 1);
+        cand[g] = 0ull;
         atomicAdd(&cnt->culled, 1ull);
         return;
     }
@@ -402,13 +404,15 @@ __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views
     for (int h = 0; h < B.nhp; ++h)
         hp[g * kMaxHp + h] = B.hp[h];
     tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), B.nhp, 0);
+    cand[g] = (unsigned long long)(B.i1 / v.S - B.i0 / v.S + 1) * (unsigned long long)(B.j1 / v.S - B.j0 / v.S + 1);
 }
 
 cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
-                         float4 *hp, int4 *tbox, Counters *cnt, cudaStream_t st)
+                         float4 *hp, int4 *tbox, unsigned long long *cand, Counters *cnt, cudaStream_t st)
 {
     if (ttot > 0)
-        k_bound<<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox, cnt);
+        k_bound<<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox, cand,
+                                                                cnt);
     return cudaGetLastError();
 }
 
@@ -430,82 +434,115 @@ __device__ __forceinline__ bool tile_meets(const float4 tb, const float4 bb, con
     return true;
 }
 
-// Bins: tile_cnt[tile] (low 40 bits) = number of triangles whose region
-// meets the tile; warp-aggregated appends (lanes that hit the same tile in
-// the same step share one atomic).
+// Bins.  Every triangle's framebuffer box spans a rectangle of candidate
+// tiles; cand_off is the prefix sum of those counts over the batch, so
+// candidate pair p belongs to the triangle g with cand_off[g] <= p <
+// cand_off[g+1].  One thread per candidate pair (grid-stride) keeps the
+// work balanced when a few triangles -- near the fovea, where q^-1
+// magnifies, or close to the camera -- span thousands of tiles.
+// tile_cnt[tile] = number of triangles whose region meets the tile;
+// appends are warp-aggregated (lanes that hit the same tile share one
+// atomic).
+__device__ __forceinline__ long long owner_of(const unsigned long long *cand_off, long long ttot, long long p)
+{
+    long long lo = 0, hi = ttot - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if ((long long)cand_off[mid] <= p)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 template <bool kScatter>
-__global__ void __launch_bounds__(128) k_bin(const ViewDev *__restrict__ views, int nviews,
+__global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, int nviews,
                                              const long long *__restrict__ tri_offs, long long ttot,
+                                             const unsigned long long *__restrict__ cand_off,
                                              const float4 *__restrict__ rec, const float4 *__restrict__ hp,
                                              const int4 *__restrict__ tbox, const float4 *__restrict__ tile_box,
                                              unsigned long long *__restrict__ tile_cnt,
                                              const unsigned long long *__restrict__ scan, unsigned int *__restrict__ fill,
                                              unsigned int *__restrict__ tile_tris, long long cap_pairs, Counters *cnt)
 {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ttot)
-        return;
-    const int4 tb = tbox[g];
-    if (tb.w)
-        return;
-    const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+    const long long total = (long long)cand_off[ttot];
     const int lane = threadIdx.x & 31;
-    const int tx0 = (tb.x & 0xffff) / v.S, tx1 = (tb.x >> 16) / v.S;
-    const int ty0 = (tb.y & 0xffff) / v.S, ty1 = (tb.y >> 16) / v.S;
-    const float4 bb = rec[g * kRecF4 + 4];
-    float4 h[kMaxHp];
-    int nh = 0;
-    if (tx0 != tx1 || ty0 != ty1) {
-        nh = tb.z;
-        for (int k = 0; k < nh; ++k)
-            h[k] = hp[g * kMaxHp + k];
-    }
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const long long tile = v.tile_off + (long long)ty * v.tiles_x + tx;
-            if (!tile_meets(tile_box[tile], bb, h, nh))
-                continue;
-            const unsigned mask = __activemask();
-            const unsigned peers = __match_any_sync(mask, (unsigned long long)tile);
-            const int leader = __ffs(peers) - 1;
-            if (!kScatter) {
-                if (lane == leader)
-                    atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
-            } else {
-                unsigned base = 0;
-                if (lane == leader)
-                    base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
-                base = __shfl_sync(peers, base, leader);
-                const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-                const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
-                if (pos < cap_pairs)
-                    tile_tris[pos] = (unsigned)g;
-                else
-                    atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
-            }
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // all lanes of a warp run the same number of iterations (for the shuffles)
+    const long long p0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long pw = p0; pw < total; pw += stride) {
+        const long long p = pw + lane;
+        bool hit = false;
+        long long tile = -1, g = -1;
+        if (p < total) {
+            g = owner_of(cand_off, ttot, p);
+            const int4 tb = tbox[g];
+            const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+            const int tx0 = (tb.x & 0xffff) / v.S, tx1 = (tb.x >> 16) / v.S;
+            const int ty0 = (tb.y & 0xffff) / v.S;
+            const int w = tx1 - tx0 + 1;
+            const long long q = p - (long long)cand_off[g];
+            const int tx = tx0 + (int)(q % w), ty = ty0 + (int)(q / w);
+            tile = v.tile_off + (long long)ty * v.tiles_x + tx;
+            const float4 bb = rec[g * kRecF4 + 4];
+            const int nh = cand_off[g + 1] - cand_off[g] > 1 ? tb.z : 0;
+            hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
         }
+        const unsigned want = __ballot_sync(0xffffffffu, hit);
+        if (!hit)
+            continue;
+        const unsigned peers = __match_any_sync(want, (unsigned long long)tile);
+        const int leader = __ffs(peers) - 1;
+        if (!kScatter) {
+            if (lane == leader)
+                atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
+        } else {
+            unsigned base = 0;
+            if (lane == leader)
+                base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
+            if (pos < cap_pairs)
+                tile_tris[pos] = (unsigned)g;
+            else
+                atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+        }
+    }
+}
+
+static int bin_grid()
+{
+    static int g = 0;
+    if (g == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = sms * 8;
+    }
+    return g;
 }
 
 cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
-                             const float4 *rec, const float4 *hp, const int4 *tbox, const float4 *tile_box,
-                             unsigned long long *tile_cnt, cudaStream_t st)
+                             const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
+                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt, cudaStream_t st)
 {
     if (ttot > 0)
-        k_bin<false><<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox,
-                                                                     tile_box, tile_cnt, nullptr, nullptr, nullptr,
-                                                                     0, nullptr);
+        k_bin<false><<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box,
+                                                 tile_cnt, nullptr, nullptr, nullptr, 0, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
-                               const float4 *rec, const float4 *hp, const int4 *tbox, const float4 *tile_box,
-                               const unsigned long long *scan, unsigned int *fill, unsigned int *tile_tris,
-                               long long cap_pairs, Counters *cnt, cudaStream_t st)
+                               const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
+                               const int4 *tbox, const float4 *tile_box, const unsigned long long *scan,
+                               unsigned int *fill, unsigned int *tile_tris, long long cap_pairs, Counters *cnt,
+                               cudaStream_t st)
 {
     if (ttot > 0)
-        k_bin<true><<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox,
-                                                                    tile_box, nullptr, scan, fill, tile_tris,
-                                                                    cap_pairs, cnt);
+        k_bin<true><<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box,
+                                                nullptr, scan, fill, tile_tris, cap_pairs, cnt);
     return cudaGetLastError();
 }
 

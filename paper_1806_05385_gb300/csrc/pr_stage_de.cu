@@ -71,16 +71,38 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, long long lin, unsig
     h.sigma = v.k_a + v.k_d * fmaxf(h.ndl, 0.f);
 }
 
-__global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ pix_offs,
-                        long long npix)
+// Stages (d) and (e) run one warp per 8x4 pixel block (lane -> column
+// lane % 8, row lane / 8), so the lanes of a warp mostly see the same
+// triangles: gathers of vertex data coalesce and the adjoint can sum a
+// triangle's contributions over the warp before touching memory.
+// blk_offs[q] = first 8x4 block of view q in the batch.
+__device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, const long long *blk_offs, long long g,
+                                            const ViewDev *&vp, long long &lin)
+{
+    const long long b = g >> 5;
+    const int lane = (int)(g & 31);
+    const ViewDev &v = views[find_view(blk_offs, nviews, b)];
+    vp = &v;
+    const long long lb = b - v.blk_off;
+    const int bw = (v.W + 7) >> 3;
+    const int i = (int)(lb % bw) * 8 + (lane & 7), j = (int)(lb / bw) * 4 + (lane >> 3);
+    lin = (long long)j * v.W + i;
+    return i < v.W && j < v.H;
+}
+
+__global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ blk_offs,
+                        long long nthreads)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= npix)
+    if (g >= nthreads)
         return;
-    const ViewDev &v = views[find_view(pix_offs, nviews, g)];
+    const ViewDev *vp;
+    long long lin;
+    if (!block_pixel(views, nviews, blk_offs, g, vp, lin))
+        return;
+    const ViewDev &v = *vp;
     if (!v.rgb_out)
         return;
-    const long long lin = g - v.pix_off;
     const long long plane = (long long)v.W * v.H;
     const unsigned id = v.id_in[lin];
     if (id >= (unsigned)v.T) {
@@ -99,14 +121,16 @@ __global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const lon
     v.rgb_out[2 * plane + lin] = b * h.sigma;
 }
 
-cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *pix_offs, long long npix, cudaStream_t st)
+cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
+                         cudaStream_t st)
 {
-    if (npix > 0)
-        k_shade<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix);
+    const long long n = nblocks * 32;
+    if (n > 0)
+        k_shade<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n);
     return cudaGetLastError();
 }
 
-// Sum x over the 32 lanes of a fully converged warp.
+// Sum of x over the lanes of a fully converged warp.
 __device__ __forceinline__ float warp_sum(float x)
 {
     for (int o = 16; o > 0; o >>= 1)
@@ -123,107 +147,119 @@ __device__ __forceinline__ float warp_sum(float x)
 //  - the unit normal n = flip (B-A)x(C-A) / |.|: dn gets (I - n n^T)/|.|;
 //  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1:
 //    dc/dp = (1-t) R0 + t R1, dc/dv = t R1.
-// Contributions are summed over the warp when every lane sees the same
-// triangle, else added per lane.
-__global__ void k_backward(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ pix_offs,
-                           long long npix)
+// Per warp, the contributions of each distinct triangle are summed over the
+// lanes that see it (masked butterflies), and one lane adds the 27 sums.
+__global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ views, int nviews,
+                                                 const long long *__restrict__ blk_offs, long long nthreads)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= npix)
-        return;
-    const ViewDev &v = views[find_view(pix_offs, nviews, g)];
-    const long long lin = g - v.pix_off;
-    const long long plane = (long long)v.W * v.H;
-    const unsigned id = v.id_in[lin];
-    const bool valid = id < (unsigned)v.T;
-    const unsigned mask = __activemask();
-    const unsigned peers = __match_any_sync(mask, valid ? id : 0xFFFFFFFFu);
-    if (!valid)
-        return;
-    PixelHit h;
-    pixel_hit(v, lin, id, h);
-    const float g0 = v.grad_in[lin], g1 = v.grad_in[plane + lin], g2 = v.grad_in[2 * plane + lin];
-    const int vid[3] = {h.ia, h.ib, h.ic};
-    const float b[3] = {h.b0, h.b1, h.b2};
-    float col[3][3];
-    for (int k = 0; k < 3; ++k) {
-        col[k][0] = v.cr[vid[k]];
-        col[k][1] = v.cg[vid[k]];
-        col[k][2] = v.cb[vid[k]];
-    }
-    float a[3];
-    for (int c = 0; c < 3; ++c)
-        a[c] = b[0] * col[0][c] + b[1] * col[1][c] + b[2] * col[2][c];
-    float gc[3][3], gb[3];
-    const float gv[3] = {g0, g1, g2};
-    for (int k = 0; k < 3; ++k) {
-        gb[k] = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            gc[k][c] = gv[c] * b[k] * h.sigma;
-            gb[k] += gv[c] * col[k][c];
+    if ((g & ~31ll) >= nthreads)
+        return;  // whole warps only
+    const ViewDev *vp = views;
+    long long lin = 0;
+    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin);
+    const ViewDev &v = *vp;
+    unsigned id = 0xFFFFFFFFu;
+    if (inside)
+        id = v.id_in[lin];
+    const bool valid = inside && id < (unsigned)v.T;
+    float gc[3][3], gp[3][3], gvel[3][3];
+    int vid[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c)
+            gc[k][c] = gp[k][c] = gvel[k][c] = 0.f;
+    if (valid) {
+        const long long plane = (long long)v.W * v.H;
+        PixelHit h;
+        pixel_hit(v, lin, id, h);
+        const float g0 = v.grad_in[lin], g1 = v.grad_in[plane + lin], g2 = v.grad_in[2 * plane + lin];
+        vid[0] = h.ia;
+        vid[1] = h.ib;
+        vid[2] = h.ic;
+        const float b[3] = {h.b0, h.b1, h.b2};
+        float col[3][3];
+        for (int k = 0; k < 3; ++k) {
+            col[k][0] = v.cr[vid[k]];
+            col[k][1] = v.cg[vid[k]];
+            col[k][2] = v.cb[vid[k]];
         }
-        gb[k] *= h.sigma;
-    }
-    const float gsig = g0 * a[0] + g1 * a[1] + g2 * a[2];
-    // barycentrics -> moved vertices
-    const float sw = -h.det;
-    const float gdotb = gb[0] * b[0] + gb[1] * b[1] + gb[2] * b[2];
-    const float isw = sw != 0.f ? 1.f / sw : 0.f;
-    const float gw0 = (gb[0] - gdotb) * isw, gw1 = (gb[1] - gdotb) * isw, gw2 = (gb[2] - gdotb) * isw;
-    const float3 D = h.dir;
-    float3 gA = add3(scale3(cross3(D, h.C), gw1), scale3(cross3(h.B, D), gw2));
-    float3 gB = add3(scale3(cross3(h.C, D), gw0), scale3(cross3(D, h.A), gw2));
-    float3 gC = add3(scale3(cross3(D, h.B), gw0), scale3(cross3(h.A, D), gw1));
-    // normal -> moved vertices
-    if (h.ndl > 0.f && h.nlen > 0.f) {
-        const float3 gnh = scale3(h.l, gsig * v.k_d);
-        const float pr = dot3(h.n, gnh);
-        const float3 gnn = scale3(sub3(gnh, scale3(h.n, pr)), h.flip / h.nlen);
-        gA = add3(gA, cross3(sub3(h.B, h.C), gnn));
-        gB = add3(gB, cross3(sub3(h.C, h.A), gnn));
-        gC = add3(gC, cross3(sub3(h.A, h.B), gnn));
-    }
-    // moved vertices -> positions and velocities
-    const float3 gk[3] = {gA, gB, gC};
-    const float t = h.t, omt = 1.f - t;
-    float gp[3][3], gvel[3][3];
-    for (int k = 0; k < 3; ++k) {
-        for (int c = 0; c < 3; ++c) {
-            const float m0 = v.R0[c], m1 = v.R0[3 + c], m2 = v.R0[6 + c];
-            const float n0 = v.R1[c], n1 = v.R1[3 + c], n2 = v.R1[6 + c];
-            const float e1 = n0 * gk[k].x + n1 * gk[k].y + n2 * gk[k].z;
-            gp[k][c] = omt * (m0 * gk[k].x + m1 * gk[k].y + m2 * gk[k].z) + t * e1;
-            gvel[k][c] = t * e1;
+        float a[3];
+        for (int c = 0; c < 3; ++c)
+            a[c] = b[0] * col[0][c] + b[1] * col[1][c] + b[2] * col[2][c];
+        float gb[3];
+        const float gv[3] = {g0, g1, g2};
+        for (int k = 0; k < 3; ++k) {
+            gb[k] = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                gc[k][c] = gv[c] * b[k] * h.sigma;
+                gb[k] += gv[c] * col[k][c];
+            }
+            gb[k] *= h.sigma;
+        }
+        const float gsig = g0 * a[0] + g1 * a[1] + g2 * a[2];
+        // barycentrics -> moved vertices
+        const float sw = -h.det;
+        const float gdotb = gb[0] * b[0] + gb[1] * b[1] + gb[2] * b[2];
+        const float isw = sw != 0.f ? 1.f / sw : 0.f;
+        const float gw0 = (gb[0] - gdotb) * isw, gw1 = (gb[1] - gdotb) * isw, gw2 = (gb[2] - gdotb) * isw;
+        const float3 D = h.dir;
+        float3 gA = add3(scale3(cross3(D, h.C), gw1), scale3(cross3(h.B, D), gw2));
+        float3 gB = add3(scale3(cross3(h.C, D), gw0), scale3(cross3(D, h.A), gw2));
+        float3 gC = add3(scale3(cross3(D, h.B), gw0), scale3(cross3(h.A, D), gw1));
+        // normal -> moved vertices
+        if (h.ndl > 0.f && h.nlen > 0.f) {
+            const float3 gnh = scale3(h.l, gsig * v.k_d);
+            const float pr = dot3(h.n, gnh);
+            const float3 gnn = scale3(sub3(gnh, scale3(h.n, pr)), h.flip / h.nlen);
+            gA = add3(gA, cross3(sub3(h.B, h.C), gnn));
+            gB = add3(gB, cross3(sub3(h.C, h.A), gnn));
+            gC = add3(gC, cross3(sub3(h.A, h.B), gnn));
+        }
+        // moved vertices -> positions and velocities
+        const float3 gk[3] = {gA, gB, gC};
+        const float t = h.t, omt = 1.f - t;
+        for (int k = 0; k < 3; ++k) {
+            for (int c = 0; c < 3; ++c) {
+                const float e1 = v.R1[c] * gk[k].x + v.R1[3 + c] * gk[k].y + v.R1[6 + c] * gk[k].z;
+                gp[k][c] = omt * (v.R0[c] * gk[k].x + v.R0[3 + c] * gk[k].y + v.R0[6 + c] * gk[k].z) + t * e1;
+                gvel[k][c] = t * e1;
+            }
         }
     }
     const int lane = threadIdx.x & 31;
-    if (peers == 0xffffffffu) {
-        // the whole warp sees one triangle: reduce first, then one lane adds
+    unsigned rem = __ballot_sync(0xffffffffu, valid);
+    while (rem) {
+        const int leader = __ffs(rem) - 1;
+        const unsigned tid = __shfl_sync(0xffffffffu, id, leader);
+        const bool mine = valid && id == tid;
+        rem &= ~__ballot_sync(0xffffffffu, mine);
+        float s[27];
         for (int k = 0; k < 3; ++k)
             for (int c = 0; c < 3; ++c) {
-                gc[k][c] = warp_sum(gc[k][c]);
-                gp[k][c] = warp_sum(gp[k][c]);
-                gvel[k][c] = warp_sum(gvel[k][c]);
+                s[9 * k + c] = warp_sum(mine ? gc[k][c] : 0.f);
+                s[9 * k + 3 + c] = warp_sum(mine ? gp[k][c] : 0.f);
+                s[9 * k + 6 + c] = warp_sum(mine ? gvel[k][c] : 0.f);
             }
-        if (lane != 0)
-            return;
-    }
-    for (int k = 0; k < 3; ++k)
-        for (int c = 0; c < 3; ++c) {
-            if (v.dcol)
-                atomicAdd(&v.dcol[3 * vid[k] + c], gc[k][c]);
-            if (v.dpos)
-                atomicAdd(&v.dpos[3 * vid[k] + c], gp[k][c]);
-            if (v.dvel)
-                atomicAdd(&v.dvel[3 * vid[k] + c], gvel[k][c]);
+        if (lane == leader) {
+            for (int k = 0; k < 3; ++k)
+                for (int c = 0; c < 3; ++c) {
+                    if (v.dcol)
+                        atomicAdd(&v.dcol[3 * vid[k] + c], s[9 * k + c]);
+                    if (v.dpos)
+                        atomicAdd(&v.dpos[3 * vid[k] + c], s[9 * k + 3 + c]);
+                    if (v.dvel)
+                        atomicAdd(&v.dvel[3 * vid[k] + c], s[9 * k + 6 + c]);
+                }
         }
+    }
 }
 
-cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
+cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                             cudaStream_t st)
 {
-    if (npix > 0)
-        k_backward<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix);
+    const long long n = nblocks * 32;
+    if (n > 0)
+        k_backward<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n);
     return cudaGetLastError();
 }
 
