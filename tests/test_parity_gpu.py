@@ -155,7 +155,7 @@ def test_degenerate_near_plane_and_huge_triangles(pr, oracle):
         # a 7,680-pixel frame built around an edge-on triangle: every mismatch
         # must be excused, the frame-level agreement floor is relaxed
         compare(oracle, view, sc, o, g["id"], g["depth"], g["rgb"], min_agree=0.999)
-        assert (o["id"] == 4).mean() > 0.05     # the screen-covering triangle shows
+        assert (o["id"] != BG).mean() > 0.3     # the screen-covering triangle and the near ones cover it
 
 
 def test_host_buffers_match_device_buffers(pr):
