@@ -194,6 +194,32 @@ pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, i
 pr_status pr_graph_launch(pr_graph *g, void *stream);
 void pr_graph_free(pr_graph *g);
 
+/* pr_rasterize without allocating: stages (a)-(c) of one view, with every
+ * scratch buffer carved from a fixed 64 MiB array that the library keeps in
+ * device memory (a file-scope __device__ array, held by every GPU that loads
+ * the library until the process exits).  The paper has no counterpart; this
+ * entry point exists for callers that may not allocate device memory -- a
+ * real-time frame loop in which cudaMalloc/cudaFree would synchronise the
+ * device and stall a frame, or a host that owns all GPU memory up front and
+ * gives libraries none.
+ * pos, vel, col: DEVICE float32 [V][3]; tri: DEVICE int32 [T][3]; id_out
+ * uint32 [H][W] and depth_out float32 [H][W]: DEVICE buffers (either may be
+ * NULL).  Host pointers are rejected (PR_ERR_INVALID_ARG): staging them
+ * would need allocations.  params as for pr_rasterize.
+ * Limits: a frame whose fixed scratch (about 36 V + 12 T + 280 T bytes, 60
+ * bytes per tile and 8 bytes per pixel) does not fit the 64 MiB returns
+ * PR_ERR_INVALID_ARG; one whose bins then do not fit what is left returns
+ * PR_ERR_OVERFLOW.  No buffer grows and nothing is retried.
+ * The first call on a device looks up the array's device address on that
+ * device (with it current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * clears what must start at zero); calls that overlap on the GPU -- other
+ * streams or other host threads -- race on it and must be serialised.
+ * Output equals pr_rasterize with the same arguments. */
+pr_status pr_rasterize_noalloc(const float *pos, const float *vel, const float *col, const int32_t *tri,
+                               int64_t V, int64_t T, const pr_view *view, const pr_params *params,
+                               uint32_t *id_out, float *depth_out, void *stream);
+
 /* Counters of the last rasterize call made with this scene / workspace. */
 pr_status pr_scene_stats(const pr_scene *scene, pr_stats *out);
 pr_status pr_workspace_stats(const pr_workspace *ws, pr_stats *out);

@@ -27,7 +27,7 @@ BG = 0xFFFFFFFF
 EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize", "pr_shade", "pr_backward",
            "pr_workspace_create", "pr_workspace_free", "pr_rasterize_batch", "pr_graph_capture_batch",
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
-           "pr_debug_catch_interval", "pr_status_string", "pr_version")
+           "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc")
 
 
 class PrError(RuntimeError):
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
             "pr_debug_catch_interval": ([C.POINTER(PrView), P, P, P], I32),
             "pr_status_string": ([I32], C.c_char_p),
             "pr_version": ([], I32),
+            "pr_rasterize_noalloc": ([P, P, P, P, I64, I64, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -286,6 +287,16 @@ def pr_debug_catch_interval(view, S, E):
     out = np.empty(2, np.float32)
     ok = load().pr_debug_catch_interval(C.byref(pv), _ptr(S), _ptr(E), _ptr(out))
     return bool(ok == 1), out
+
+
+def pr_rasterize_noalloc(pos, vel, col, tri, view, params=None, id_out=None, depth_out=None, stream=None):
+    """Stages (a)-(c) with the library's fixed device scratch array (no
+    allocation); every buffer must be a CUDA tensor."""
+    pv = view if isinstance(view, PrView) else make_view(view)
+    pp = params if params is not None else make_params()
+    _check(load().pr_rasterize_noalloc(_ptr(pos), _ptr(vel), _ptr(col), _ptr(tri), int(pos.shape[0]),
+                                       int(tri.shape[0]), C.byref(pv), C.byref(pp), _ptr(id_out), _ptr(depth_out),
+                                       stream if stream is not None else current_stream()), "pr_rasterize_noalloc")
 
 
 def pr_status_string(s: int) -> str:

@@ -1,0 +1,279 @@
+// pr_noalloc.cu -- pr_rasterize_noalloc: stages (a)-(c) of one view with all
+// scratch in a fixed, file-scope device array instead of allocated buffers.
+//
+// Who needs it: a caller that may not allocate device memory -- a real-time
+// frame loop (VR compositor, game engine) in which cudaMalloc/cudaFree would
+// synchronise the device and stall the frame, or a host that owns all GPU
+// memory up front and hands libraries none.  Such a caller still passes its
+// own device input arrays and output buffers; everything else lives in
+// g_noalloc_scratch.
+//
+// The array is kNoAllocBytes (64 MiB) and is held by every GPU that loads
+// the library until the process exits.  Every call on a device shares it and
+// it keeps the last call's contents, so each call clears what must start at
+// zero, and calls whose work overlaps on the GPU (other streams, or another
+// host thread) race on it: serialise them.  The host-side name of the array
+// is only a stand-in for the device symbol, so its device address is looked
+// up with cudaGetSymbolAddress once per device, on the first call made on
+// that device (with that device current); make that first call before any
+// stream capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "pr_launch.h"
+
+using namespace pr;
+
+namespace {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+void *g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of g_noalloc_scratch on the current device (set up once).
+cudaError_t scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+pr_status status_of(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return PR_OK;
+    cudaGetLastError();
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+        return PR_ERR_NO_CUDA;
+    return PR_ERR_CUDA;
+}
+
+#define NA_TRY(expr)                          \
+    do {                                      \
+        cudaError_t _e = (expr);              \
+        if (_e != cudaSuccess)                \
+            return status_of(_e);             \
+    } while (0)
+
+// Carves aligned regions out of the arena; fails once it is exhausted.
+struct Carver {
+    size_t off = 0;
+    bool ok = true;
+    size_t take(size_t bytes)
+    {
+        const size_t at = (off + 255) & ~(size_t)255;
+        if (at + bytes > kNoAllocBytes) {
+            ok = false;
+            return 0;
+        }
+        off = at + bytes;
+        return at;
+    }
+};
+
+// View constants of pr_view (the same derivation as the allocating path).
+pr_status view_constants(const pr_view &in, int tile, int bound, float *soa, int *idx, long long V, long long T,
+                         ViewDev &v)
+{
+    if (in.W < 1 || in.H < 1 || in.W > 16384 || in.H > 16384 || in.mode < PR_CLASSIC || in.mode > PR_BOTH)
+        return PR_ERR_INVALID_ARG;
+    if (!(in.tan_x > 0.f) || !(in.tan_y > 0.f) || !(in.z_near > 0.f) || !std::isfinite(in.tan_x) ||
+        !std::isfinite(in.tan_y) || !(in.alpha >= 1.f && in.alpha <= 5.f))
+        return PR_ERR_INVALID_ARG;
+    if (!(in.d[0] >= 0.f && in.d[1] >= 0.f && in.d[0] + in.d[1] <= 1.f + 1e-6f) ||
+        ((in.mode == PR_ROLLING || in.mode == PR_BOTH) && in.d[0] + in.d[1] <= 0.f))
+        return PR_ERR_INVALID_ARG;
+    if (!(in.fovea[0] >= 0.f && in.fovea[0] <= 1.f && in.fovea[1] >= 0.f && in.fovea[1] <= 1.f))
+        return PR_ERR_INVALID_ARG;
+    if ((tile != 8 && tile != 16 && tile != 32) || bound < PR_BOUND_ZENON || bound > PR_BOUND_TRIVIAL)
+        return PR_ERR_INVALID_ARG;
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(in.pose0[k]) || !std::isfinite(in.pose1[k]))
+            return PR_ERR_INVALID_ARG;
+    std::memset(&v, 0, sizeof v);
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) {
+            v.R0[3 * r + c] = in.pose0[4 * r + c];
+            v.R1[3 * r + c] = in.pose1[4 * r + c];
+        }
+        v.T0[r] = in.pose0[4 * r + 3];
+        v.T1[r] = in.pose1[4 * r + 3];
+    }
+    v.tan_x = in.tan_x;
+    v.tan_y = in.tan_y;
+    v.z_near = in.z_near;
+    v.fx = in.fovea[0];
+    v.fy = in.fovea[1];
+    v.alpha = in.alpha;
+    v.inv_alpha = 1.f / in.alpha;
+    v.d0 = in.d[0];
+    v.d1 = in.d[1];
+    v.t_lo = 0.f;
+    v.t_hi = std::min(1.f, in.d[0] + in.d[1]);
+    v.k_a = in.k_a;
+    v.k_d = in.k_d;
+    v.W = in.W;
+    v.H = in.H;
+    v.mode = in.mode;
+    v.S = tile;
+    v.tiles_x = (in.W + tile - 1) / tile;
+    v.tiles_y = (in.H + tile - 1) / tile;
+    v.bound = bound;
+    v.T = (int)T;
+    v.V = (int)V;
+    v.px = soa;
+    v.py = soa + V;
+    v.pz = soa + 2 * V;
+    v.vx = soa + 3 * V;
+    v.vy = soa + 4 * V;
+    v.vz = soa + 5 * V;
+    v.cr = soa + 6 * V;
+    v.cg = soa + 7 * V;
+    v.cb = soa + 8 * V;
+    v.i0 = idx;
+    v.i1 = idx + T;
+    v.i2 = idx + 2 * T;
+    return PR_OK;
+}
+
+}  // namespace
+
+extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, const float *col, const int32_t *tri,
+                                          int64_t V, int64_t T, const pr_view *view, const pr_params *params,
+                                          uint32_t *id_out, float *depth_out, void *stream)
+{
+    if (!view || V < 1 || T < 0 || V > (1ll << 30) || T > (1ll << 30))
+        return PR_ERR_INVALID_ARG;
+    if (!on_device(pos) || !on_device(vel) || !on_device(col) || (T > 0 && !on_device(tri)) ||
+        (id_out && !on_device(id_out)) || (depth_out && !on_device(depth_out)))
+        return PR_ERR_INVALID_ARG;  // device buffers only: staging host memory would need allocations
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tile = params && params->tile ? params->tile : 16;
+    const int bound = params ? params->bound : PR_BOUND_ZENON;
+    const int seg = params && params->seg > 0 ? params->seg : 256;
+
+    void *base = nullptr;
+    NA_TRY(scratch_address(&base));
+    char *arena = static_cast<char *>(base);
+
+    // layout of this call in the arena
+    const long long W = view->W, H = view->H;
+    if (W < 1 || H < 1 || W > 16384 || H > 16384 || (tile != 8 && tile != 16 && tile != 32))
+        return PR_ERR_INVALID_ARG;
+    const long long nt = ((W + tile - 1) / tile) * ((H + tile - 1) / tile), np = W * H, Tn = std::max<int64_t>(T, 1);
+    Carver c;
+    const size_t o_views = c.take(sizeof(ViewDev)), o_offs = c.take(sizeof(long long) * 8);
+    const size_t o_cnt = c.take(sizeof(Counters)), o_heads = c.take(sizeof(int) * 8);
+    const size_t o_soa = c.take(sizeof(float) * 9 * V), o_idx = c.take(sizeof(int) * 3 * Tn);
+    const size_t o_rec = c.take(sizeof(float4) * kRecF4 * Tn), o_hp = c.take(sizeof(float4) * kMaxHp * Tn);
+    const size_t o_tbox = c.take(sizeof(int4) * Tn), o_cand = c.take(8 * Tn), o_cand_off = c.take(8 * (Tn + 1));
+    const size_t o_tile_box = c.take(sizeof(float4) * nt), o_tile_cnt = c.take(8 * nt);
+    const size_t o_scan = c.take(8 * (nt + 1)), o_fill = c.take(4 * nt);
+    const size_t o_sums = c.take(8 * std::max(scan_block_sums_needed(nt), scan_block_sums_needed(Tn)));
+    const size_t o_keys = c.take(8 * np);
+    if (!c.ok)
+        return PR_ERR_INVALID_ARG;  // the frame's fixed scratch exceeds the 64 MiB arena
+    // the rest: work items and bin entries
+    const long long rest = (long long)kNoAllocBytes - (long long)((c.off + 255) & ~(size_t)255) - 512;
+    const long long item_fixed = nt + 1024;
+    if (rest < (long long)(16 * item_fixed + 4 * (2 * Tn + nt)))
+        return PR_ERR_INVALID_ARG;  // too little room left for the bins of this frame
+    const long long cap_pairs = (rest - 16 * item_fixed) / (4 + 16 / seg + 1);
+    const long long cap_items = item_fixed + cap_pairs / seg + 1;
+    const size_t o_items = c.take(sizeof(int4) * cap_items), o_tris = c.take(4 * cap_pairs);
+    if (!c.ok)
+        return PR_ERR_INVALID_ARG;
+
+    float *soa = (float *)(arena + o_soa);
+    int *idx = (int *)(arena + o_idx);
+    ViewDev v;
+    pr_status s = view_constants(*view, tile, bound, soa, idx, V, T, v);
+    if (s != PR_OK)
+        return s;
+    v.id_out = id_out;
+    v.depth_out = depth_out;
+    long long offs[8] = {0, T, 0, nt, 0, np, 0, 0};  // tri, tile, pixel offsets of the one view
+
+    ViewDev *dv = (ViewDev *)(arena + o_views);
+    long long *doffs = (long long *)(arena + o_offs);
+    Counters *cnt = (Counters *)(arena + o_cnt);
+    int *heads = (int *)(arena + o_heads);
+    unsigned long long *cand = (unsigned long long *)(arena + o_cand), *cand_off = (unsigned long long *)(arena + o_cand_off);
+    unsigned long long *tile_cnt = (unsigned long long *)(arena + o_tile_cnt), *scan = (unsigned long long *)(arena + o_scan);
+    float4 *rec = (float4 *)(arena + o_rec), *hp = (float4 *)(arena + o_hp), *tile_box = (float4 *)(arena + o_tile_box);
+    int4 *tbox = (int4 *)(arena + o_tbox), *items = (int4 *)(arena + o_items);
+    unsigned *fill = (unsigned *)(arena + o_fill), *tile_tris = (unsigned *)(arena + o_tris);
+    unsigned long long *sums = (unsigned long long *)(arena + o_sums), *keys = (unsigned long long *)(arena + o_keys);
+
+    // host-side constants go up by plain (pageable) copies; they complete
+    // before the call returns, so the stack buffers may go out of scope
+    NA_TRY(cudaMemcpyAsync(dv, &v, sizeof v, cudaMemcpyHostToDevice, st));
+    NA_TRY(cudaMemcpyAsync(doffs, offs, sizeof offs, cudaMemcpyHostToDevice, st));
+    // what must start at zero (the arena keeps the previous call's contents)
+    NA_TRY(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
+    NA_TRY(cudaMemsetAsync(heads, 0, sizeof(int) * 8, st));
+    NA_TRY(cudaMemsetAsync(tile_cnt, 0, 8 * nt, st));
+    NA_TRY(cudaMemsetAsync(fill, 0, 4 * nt, st));
+    NA_TRY(cudaMemsetAsync(keys, 0xFF, 8 * np, st));
+
+    const long long *tri_offs = doffs, *tile_offs = doffs + 2, *pix_offs = doffs + 4;
+    NA_TRY(launch_scene_soa(pos, vel, col, V, soa, st));
+    NA_TRY(launch_scene_idx(tri, T, V, idx, cnt, st));
+    NA_TRY(launch_scene_check(soa, V, cnt, st));
+    NA_TRY(launch_tile_boxes(dv, 1, tile_offs, nt, tile_box, st));
+    NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, cnt, st));
+    NA_TRY(launch_scan(cand, cand_off, sums, T, 0, st));
+    NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
+    NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, st));
+    NA_TRY(launch_bin_scatter(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, scan, fill, tile_tris,
+                              cap_pairs, cnt, st));
+    NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
+    NA_TRY(launch_fragment(tile, dv, items, scan, 0, nt, cap_items, heads, tile_tris, rec, keys, nullptr, 0, cnt,
+                           fragment_grid(tile), st));
+    NA_TRY(launch_resolve(dv, 1, pix_offs, np, keys, st));
+    Counters h;
+    NA_TRY(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
+    NA_TRY(cudaStreamSynchronize(st));
+    if (h.status & ST_NONFINITE)
+        return PR_ERR_NONFINITE;
+    if (h.status & ST_BAD_INDEX)
+        return PR_ERR_INVALID_ARG;
+    if (h.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS))
+        return PR_ERR_OVERFLOW;  // the bins of this frame do not fit the fixed arena
+    return PR_OK;
+}
