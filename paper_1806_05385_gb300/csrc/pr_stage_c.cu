@@ -20,13 +20,20 @@ namespace pr {
 // (dx, dy, 1) against the triangle moved to time t.  With dz = 1 the
 // shear/scale constants are Sx = dx, Sy = dy, Sz = 1.  The edge-function
 // products are rounded separately (no contraction) so that a shared edge
-// yields exactly opposite values in its two triangles.
+// yields exactly opposite values in its two triangles; zero counts as
+// either sign (inclusive edges).
+//
+// A hit's depth is T / det.  Its key only matters if it can beat the
+// pixel's current best, so the exact depth (IEEE division) is computed only
+// when T / det <= best_depth (1 + 2^-20), tested as a product; the margin
+// keeps every candidate that could win or tie, so the result is the exact
+// minimum key whatever the order of the triangles.
 __device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const float4 r2, const float4 r3,
                                          const float d2y, const float d2z, const float t, const float dx,
                                          const float dy, const float zn, const uint32_t id, unsigned long long &best,
-                                         unsigned &hits)
+                                         float &best_depth, unsigned &hits)
 {
-    // vertices at time t: c = S + t D
+    // vertices at time t (c = S + t D), sheared so the ray is the z axis
     const float Az = fmaf(t, r2.w, r0.z), Bz = fmaf(t, r3.z, r1.y), Cz = fmaf(t, d2z, r2.x);
     const float ax = fmaf(-dx, Az, fmaf(t, r2.y, r0.x)), ay = fmaf(-dy, Az, fmaf(t, r2.z, r0.y));
     const float bx = fmaf(-dx, Bz, fmaf(t, r3.x, r0.w)), by = fmaf(-dy, Bz, fmaf(t, r3.y, r1.x));
@@ -34,22 +41,40 @@ __device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const
     const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
     const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
     const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
-    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f))
+    if (fminf(U, fminf(V, W)) < 0.f && fmaxf(U, fmaxf(V, W)) > 0.f)
         return;
     const float det = U + V + W;
-    if (det == 0.f)
-        return;
     const float T = fmaf(U, Az, fmaf(V, Bz, W * Cz));
+    const float adet = fabsf(det), aT = det < 0.f ? -T : T;   // depth = aT / adet
+    if (!(adet > 0.f) || !(aT > zn * adet))
+        return;
+    ++hits;
+    if (aT > best_depth * 1.00000095f * adet)
+        return;  // behind the current best: cannot win
     const float depth = __fdiv_rn(T, det);
     if (!(depth > zn))
         return;
-    ++hits;
     const unsigned long long key = pack_key(depth, id);
-    best = key < best ? key : best;
+    if (key < best) {
+        best = key;
+        best_depth = depth;
+    }
 }
 
+// Build-time knobs of the fragment kernel: the occupancy it is compiled for
+// (resident warps per SM, which caps registers) and the unroll of its
+// triangle loop.
+#ifndef PR_FRAG_WARPS
+#define PR_FRAG_WARPS 32
+#endif
+#define PR_FRAG_MINB(nt) (PR_FRAG_WARPS > 0 ? (PR_FRAG_WARPS * 32) / (nt) : 1)
+#ifndef PR_FRAG_UNROLL
+#define PR_FRAG_UNROLL 2
+#endif
+constexpr int kFragUnroll = PR_FRAG_UNROLL;
+
 template <int S>
-__global__ void __launch_bounds__(S *S / 2) k_fragment(const ViewDev *__restrict__ views, const int4 *__restrict__ items,
+__global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2)) k_fragment(const ViewDev *__restrict__ views, const int4 *__restrict__ items,
                                                       const unsigned long long *__restrict__ scan, long long tile_lo,
                                                       long long tile_hi, long long cap_items, int *__restrict__ head,
                                                       const unsigned int *__restrict__ tile_tris,
@@ -57,8 +82,10 @@ __global__ void __launch_bounds__(S *S / 2) k_fragment(const ViewDev *__restrict
                                                       unsigned long long *__restrict__ keys, Counters *cnt)
 {
     constexpr int NT = S * S / 2;  // threads: two pixels each
+    constexpr int NW = NT / 32;    // warps
     constexpr int WPR = S / 8;     // 8x8 warp blocks per tile row
-    constexpr int CH = NT < 256 ? NT : 256;  // triangles staged per chunk
+    constexpr int CH = NT < 256 ? (NT < 128 ? 128 : NT) : 256;  // triangles staged per chunk
+    constexpr int PER_WARP = CH / NW;  // triangles each warp gathers (multiple of 32)
     __shared__ float4 s_rec[CH * kRecF4];
     __shared__ unsigned s_id[CH];
     __shared__ long long s_item;
@@ -102,21 +129,39 @@ __global__ void __launch_bounds__(S *S / 2) k_fragment(const ViewDev *__restrict
             wt0 = fminf(wt0, __shfl_xor_sync(0xffffffffu, wt0, o));
             wt1 = fmaxf(wt1, __shfl_xor_sync(0xffffffffu, wt1, o));
         }
+        // with a horizontal scan (d1 = 0) the time strip is already part of
+        // every triangle's display box; otherwise test the interval too
+        const bool test_t = is_rolling(v.mode) && v.d1 != 0.f;
+        if (!test_t) {
+            wt0 = -INFINITY;
+            wt1 = INFINITY;
+        }
         const float zn = v.z_near;
         const unsigned id_base = (unsigned)v.tri_off;
         unsigned long long best0 = ~0ull, best1 = ~0ull;
+        float bd0 = INFINITY, bd1 = INFINITY;
         unsigned hits = 0, tested = 0;
         for (int base = item.z; base < item.w; base += CH) {
             const int n = min(CH, item.w - base);
-            __syncthreads();
-            for (int q = threadIdx.x; q < n; q += NT)
-                s_id[q] = tile_tris[base + q];
-            __syncthreads();
-            for (int q = threadIdx.x; q < n * kRecF4; q += NT) {
-                const int k = q / kRecF4, f = q - k * kRecF4;
-                s_rec[q] = __ldg(&rec[(size_t)s_id[k] * kRecF4 + f]);
+            __syncthreads();  // the previous chunk is no longer read
+            // each warp gathers PER_WARP records: ids coalesced, then the
+            // 6 float4 of 32 records at a time with consecutive lanes on
+            // consecutive float4s
+            for (int w0 = warp * PER_WARP; w0 < (warp + 1) * PER_WARP; w0 += 32) {
+                const int q = w0 + lane;
+                const unsigned gid = q < n ? tile_tris[base + q] : 0u;
+                if (q < n)
+                    s_id[q] = gid;
+#pragma unroll
+                for (int f = 0; f < kRecF4; ++f) {
+                    const int idx = lane + 32 * f, r = idx / kRecF4, fld = idx - r * kRecF4;
+                    const unsigned g = __shfl_sync(0xffffffffu, gid, r);
+                    if (w0 + r < n)
+                        s_rec[(w0 + r) * kRecF4 + fld] = __ldg(&rec[(size_t)g * kRecF4 + fld]);
+                }
             }
             __syncthreads();
+#pragma unroll kFragUnroll
             for (int k = 0; k < n; ++k) {
                 const float4 bb = s_rec[k * kRecF4 + 4];
                 const float4 tb = s_rec[k * kRecF4 + 5];
@@ -126,8 +171,8 @@ __global__ void __launch_bounds__(S *S / 2) k_fragment(const ViewDev *__restrict
                 const float4 r2 = s_rec[k * kRecF4 + 2], r3 = s_rec[k * kRecF4 + 3];
                 const unsigned id = s_id[k] - id_base;
                 ++tested;
-                ray_test(r0, r1, r2, r3, tb.z, tb.w, t0, dx0, dy0, zn, id, best0, hits);
-                ray_test(r0, r1, r2, r3, tb.z, tb.w, t1, dx1, dy1, zn, id, best1, hits);
+                ray_test(r0, r1, r2, r3, tb.z, tb.w, t0, dx0, dy0, zn, id, best0, bd0, hits);
+                ray_test(r0, r1, r2, r3, tb.z, tb.w, t1, dx1, dy1, zn, id, best1, bd1, hits);
             }
         }
         n_tests += (unsigned long long)tested * (unsigned)(ok0 + ok1);

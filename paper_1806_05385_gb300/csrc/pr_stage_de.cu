@@ -233,23 +233,44 @@ __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ vi
         const unsigned tid = __shfl_sync(0xffffffffu, id, leader);
         const bool mine = valid && id == tid;
         rem &= ~__ballot_sync(0xffffffffu, mine);
-        float s[27];
+        // the 27 contributions of this triangle (value 9k + c: colour,
+        // 9k + 3 + c: position, 9k + 6 + c: velocity of vertex k), zero for
+        // lanes that see another triangle, padded to 32
+        float s[32];
+#pragma unroll
         for (int k = 0; k < 3; ++k)
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                s[9 * k + c] = warp_sum(mine ? gc[k][c] : 0.f);
-                s[9 * k + 3 + c] = warp_sum(mine ? gp[k][c] : 0.f);
-                s[9 * k + 6 + c] = warp_sum(mine ? gvel[k][c] : 0.f);
+                s[9 * k + c] = mine ? gc[k][c] : 0.f;
+                s[9 * k + 3 + c] = mine ? gp[k][c] : 0.f;
+                s[9 * k + 6 + c] = mine ? gvel[k][c] : 0.f;
             }
-        if (lane == leader) {
-            for (int k = 0; k < 3; ++k)
-                for (int c = 0; c < 3; ++c) {
-                    if (v.dcol)
-                        atomicAdd(&v.dcol[3 * vid[k] + c], s[9 * k + c]);
-                    if (v.dpos)
-                        atomicAdd(&v.dpos[3 * vid[k] + c], s[9 * k + 3 + c]);
-                    if (v.dvel)
-                        atomicAdd(&v.dvel[3 * vid[k] + c], s[9 * k + 6 + c]);
-                }
+#pragma unroll
+        for (int e = 27; e < 32; ++e)
+            s[e] = 0.f;
+        // reduce-scatter over the warp: at each step a lane keeps the half
+        // of its values selected by its lane bit and adds its partner's
+        // copy of that half; after five steps lane l holds the warp sum of
+        // value l (31 shuffles instead of 27 full butterflies)
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int half = 16 >> step;
+            const bool upper = (lane & half) != 0;
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const float send = upper ? s[k] : s[k + half];
+                const float keep = upper ? s[k + half] : s[k];
+                s[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+            }
+        }
+        const int k = lane / 9, r = lane - 9 * (lane / 9);
+        const int v0 = __shfl_sync(0xffffffffu, vid[0], leader), v1 = __shfl_sync(0xffffffffu, vid[1], leader),
+                  v2 = __shfl_sync(0xffffffffu, vid[2], leader);
+        if (lane < 27) {
+            const int vk = k == 0 ? v0 : (k == 1 ? v1 : v2);
+            float *dst = r < 3 ? v.dcol : (r < 6 ? v.dpos : v.dvel);
+            if (dst)
+                atomicAdd(&dst[3 * vk + (r % 3)], s[0]);
         }
     }
 }
