@@ -67,23 +67,29 @@ def lib():
     return _lib
 
 
+def _f32(x) -> float:
+    return float(np.float32(x))
+
+
 def make_view(view) -> OrView:
     """Widen a ``scenes.View``-like object (any object with the same fields)
-    into the oracle's FP64 view record."""
+    into the oracle's FP64 view record.  The method's inputs are the FP32
+    values the library takes (camera, poses, fovea, scan direction), so each
+    field is rounded to FP32 first and then widened exactly."""
     v = OrView()
     v.W, v.H, v.mode = int(view.W), int(view.H), int(view.mode)
-    v.tan_x, v.tan_y, v.z_near = float(view.tan_x), float(view.tan_y), float(view.z_near)
-    p0 = np.asarray(view.pose0, dtype=np.float64).reshape(16)
-    p1 = np.asarray(view.pose1, dtype=np.float64).reshape(16)
+    v.tan_x, v.tan_y, v.z_near = _f32(view.tan_x), _f32(view.tan_y), _f32(view.z_near)
+    p0 = np.asarray(view.pose0, dtype=np.float32).astype(np.float64).reshape(16)
+    p1 = np.asarray(view.pose1, dtype=np.float32).astype(np.float64).reshape(16)
     for k in range(16):
         v.pose0[k] = p0[k]
         v.pose1[k] = p1[k]
-    v.fovea[0], v.fovea[1] = float(view.fovea[0]), float(view.fovea[1])
-    v.alpha = float(view.alpha)
-    v.d[0], v.d[1] = float(view.d[0]), float(view.d[1])
+    v.fovea[0], v.fovea[1] = _f32(view.fovea[0]), _f32(view.fovea[1])
+    v.alpha = _f32(view.alpha)
+    v.d[0], v.d[1] = _f32(view.d[0]), _f32(view.d[1])
     for k in range(3):
-        v.light_w[k] = float(view.light_w[k])
-    v.k_a, v.k_d = float(view.k_a), float(view.k_d)
+        v.light_w[k] = _f32(view.light_w[k])
+    v.k_a, v.k_d = _f32(view.k_a), _f32(view.k_d)
     return v
 
 

@@ -18,12 +18,20 @@ from paper_1806_05385_gb300 import scenes as S
 BG = 0xFFFFFFFF
 
 
+def _f32(x):
+    return float(np.float32(x))
+
+
 def mkview(W=16, H=12, mode=S.MODE_CLASSIC, tan=(0.5, 0.5), pose0=None, pose1=None, fovea=(0.5, 0.5),
            alpha=2.0, d=(1.0, 0.0), light=(0.0, 0.0, -1.0), k_a=0.1, k_d=0.9):
+    """A view whose parameters are FP32 values (the method's inputs are the
+    FP32 values of the library's ABI; the oracle widens them exactly), so the
+    independent computations below see exactly what the oracle sees."""
     I = np.eye(4, dtype=np.float32)
-    return S.View(W=W, H=H, tan_x=tan[0], tan_y=tan[1], pose0=I if pose0 is None else pose0,
-                  pose1=(I if pose0 is None else pose0) if pose1 is None else pose1, mode=mode, fovea=fovea,
-                  alpha=alpha, d=d, light_w=light, k_a=k_a, k_d=k_d)
+    return S.View(W=W, H=H, tan_x=_f32(tan[0]), tan_y=_f32(tan[1]), pose0=I if pose0 is None else pose0,
+                  pose1=(I if pose0 is None else pose0) if pose1 is None else pose1, mode=mode,
+                  fovea=(_f32(fovea[0]), _f32(fovea[1])), alpha=_f32(alpha), d=(_f32(d[0]), _f32(d[1])),
+                  light_w=tuple(_f32(x) for x in light), k_a=_f32(k_a), k_d=_f32(k_d))
 
 
 # --------------------------------------------------------------------------
@@ -33,7 +41,7 @@ def mkview(W=16, H=12, mode=S.MODE_CLASSIC, tan=(0.5, 0.5), pose0=None, pose1=No
 def test_warp_fixed_point_inverse_radial(oracle):
     rng = np.random.default_rng(1)
     for _ in range(200):
-        f = rng.uniform(0.05, 0.95, 2)
+        f = rng.uniform(0.05, 0.95, 2).astype(np.float32).astype(np.float64)
         v = mkview(fovea=tuple(f), alpha=float(rng.uniform(1.0, 4.0)))
         assert np.array_equal(oracle.q(v, f), f)            # the fovea is a fixed point
         x = rng.uniform(0, 1, 2)
