@@ -49,11 +49,13 @@ class PrParams(C.Structure):
 
 class PrStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("tests", "hits", "pairs", "items", "culled", "flagged", "changed",
-                                          "pixels")] + [("stage_ms", C.c_float * 8)]
+                                          "pixels")] + [("stage_ms", C.c_float * 8), ("fp64_depth_err", C.c_float),
+                                                        ("pad_stats", C.c_float)]
 
     def as_dict(self):
-        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "stage_ms"}
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n not in ("stage_ms", "fp64_depth_err", "pad_stats")}
         d["stage_ms"] = [float(x) for x in self.stage_ms]
+        d["fp64_depth_err"] = float(self.fp64_depth_err)
         return d
 
 

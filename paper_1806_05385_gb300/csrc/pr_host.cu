@@ -130,6 +130,7 @@ constexpr int kDefaultSeg = 256;
 struct pr_workspace {
     DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, tile_tris, items, keys, counters, heads;
     DevBuf cand, cand_off;         // candidate tiles per triangle and their prefix sum
+    DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
     DevBuf stage;                  // device copies of host-side outputs
     long long cap_pairs = 0, cap_items = 0;
     PinnedBuf<ViewDev> h_views;
@@ -300,8 +301,10 @@ struct BatchPlan {
     long long ttot = 0, ntiles = 0, npix = 0, nblk = 0;
     struct Cls {
         int S;
+        bool fp64;
         long long tile_lo, tile_hi;
     };
+    bool any_fp64 = false;
     std::vector<Cls> classes;
     // output staging: per view (in order) device pointers used by kernels
     struct Out {
@@ -327,6 +330,7 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
     P.order.resize(n);
     for (int k = 0; k < n; ++k)
         P.order[k] = k;
+    // views of one tile size and one precision form run in one fragment launch
     std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) { return tiles[a] < tiles[b]; });
     P.vd.resize(n);
     P.out.resize(n);
@@ -377,8 +381,10 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
         return PR_ERR_INVALID_ARG;
     for (int q = 0; q < n; ++q) {
         const int S = P.vd[q].S;
-        if (P.classes.empty() || P.classes.back().S != S)
-            P.classes.push_back({S, P.tile_off[q], P.tile_off[q + 1]});
+        const bool f = P.vd[q].fp64 != 0;
+        P.any_fp64 |= f;
+        if (P.classes.empty() || P.classes.back().S != S || P.classes.back().fp64 != f)
+            P.classes.push_back({S, f, P.tile_off[q], P.tile_off[q + 1]});
         else
             P.classes.back().tile_hi = P.tile_off[q + 1];
     }
@@ -403,6 +409,10 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->cand, sizeof(unsigned long long) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
     PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
+    if (P.any_fp64) {
+        PR_TRY(ensure(ws->flag_bits, sizeof(unsigned) * ((P.npix + 31) / 32 + 1)));
+        PR_TRY(ensure(ws->flag_list, sizeof(long long) * std::max(P.npix, 1ll)));
+    }
     PR_TRY(ensure(ws->counters, sizeof(Counters)));
     PR_TRY(ensure(ws->heads, sizeof(int) * 8));
     PR_TRY(ensure(ws->stage, std::max<size_t>(P.stage_bytes, 256)));
@@ -455,6 +465,8 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(cudaMemsetAsync(ws->tile_cnt.p, 0, sizeof(unsigned long long) * std::max(P.ntiles, 1ll), st));
     PR_TRY(cudaMemsetAsync(ws->fill.p, 0, sizeof(unsigned) * std::max(P.ntiles, 1ll), st));
     PR_TRY(cudaMemsetAsync(ws->keys.p, 0xFF, sizeof(unsigned long long) * std::max(P.npix, 1ll), st));
+    if (P.any_fp64)
+        PR_TRY(cudaMemsetAsync(ws->flag_bits.p, 0, sizeof(unsigned) * ((P.npix + 31) / 32 + 1), st));
 
     float4 *rec = ws->rec.as<float4>(), *hp = ws->hp.as<float4>(), *tile_box = ws->tile_box.as<float4>();
     int4 *tbox = ws->tbox.as<int4>();
@@ -482,11 +494,15 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     int *heads = ws->heads.as<int>();
     for (size_t c = 0; c < P.classes.size(); ++c) {
         const auto &cl = P.classes[c];
-        PR_TRY(launch_fragment(cl.S, dv, ws->items.as<int4>(), scan, cl.tile_lo, cl.tile_hi, ws->cap_items,
+        PR_TRY(launch_fragment(cl.S, cl.fp64, dv, ws->items.as<int4>(), scan, cl.tile_lo, cl.tile_hi, ws->cap_items,
                                heads + c, ws->tile_tris.as<unsigned>(), rec, ws->keys.as<unsigned long long>(),
-                               nullptr, 0, cnt, fragment_grid(cl.S), st));
+                               ws->flag_bits.as<unsigned>(), ws->flag_list.as<long long>(), cnt,
+                               fragment_grid(cl.S, cl.fp64), st));
     }
     PR_TRY(mark(3));
+    if (P.any_fp64)
+        PR_TRY(launch_retest(dv, n, pix_offs, scan, tile_cnt, ws->tile_tris.as<unsigned>(), rec,
+                             ws->flag_list.as<long long>(), ws->keys.as<unsigned long long>(), cnt, st));
     PR_TRY(mark(4));
     PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
     PR_TRY(mark(5));
@@ -518,6 +534,12 @@ pr_status finish_stats(pr_workspace *ws, const BatchPlan &P)
     ws->stats.culled = c.culled;
     ws->stats.flagged = c.flagged;
     ws->stats.changed = c.changed;
+    {
+        unsigned b = c.depth_err_bits;
+        float e;
+        std::memcpy(&e, &b, sizeof e);
+        ws->stats.fp64_depth_err = e;
+    }
     ws->stats.pixels = (uint64_t)P.npix;
     ws->last_T = P.ttot;
     ws->read_stage_times();
@@ -909,6 +931,12 @@ pr_status pr_graph_launch(pr_graph *g, void *stream)
     ws->stats.culled = c.culled;
     ws->stats.flagged = c.flagged;
     ws->stats.changed = c.changed;
+    {
+        unsigned b = c.depth_err_bits;
+        float e;
+        std::memcpy(&e, &b, sizeof e);
+        ws->stats.fp64_depth_err = e;
+    }
     ws->stats.pixels = (uint64_t)g->npix;
     ws->read_stage_times();
     if (c.status & ST_TIMEOUT)

@@ -54,7 +54,7 @@ struct Counters {
     unsigned long long tests, hits, culled, flagged, changed;
     unsigned long long pairs_total, items_total;  // copied from the scan for the host
     unsigned int status;
-    unsigned int pad;
+    unsigned int depth_err_bits;  // bits of the largest FP32-vs-FP64 relative depth error (re-test)
 };
 
 __device__ __forceinline__ bool is_rolling(int mode) { return mode == PR_ROLLING || mode == PR_BOTH; }

@@ -37,15 +37,14 @@ cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile
                          long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);
 
 // stage (c): per-fragment ray casting, FP64 re-test, resolve
-cudaError_t launch_fragment(int S, const ViewDev *views, const int4 *items, const unsigned long long *scan,
+cudaError_t launch_fragment(int S, bool flag, const ViewDev *views, const int4 *items, const unsigned long long *scan,
                             long long tile_lo, long long tile_hi, long long cap_items, int *head,
                             const unsigned int *tile_tris, const float4 *rec, unsigned long long *keys,
-                            unsigned int *flags, long long cap_flags, Counters *cnt, int grid, cudaStream_t st);
-int fragment_grid(int S);
-cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix_offs, const int4 *items,
-                          const unsigned long long *scan, const long long *tile_offs, const unsigned int *tile_tris,
-                          unsigned int *flags, long long cap_flags, unsigned long long *keys, Counters *cnt,
-                          int grid, cudaStream_t st);
+                            unsigned *flag_bits, long long *flag_list, Counters *cnt, int grid, cudaStream_t st);
+int fragment_grid(int S, bool flag);
+cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix_offs, const unsigned long long *scan,
+                          const unsigned long long *tile_cnt, const unsigned *tile_tris, const float4 *rec,
+                          const long long *flag_list, unsigned long long *keys, Counters *cnt, cudaStream_t st);
 cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
                            const unsigned long long *keys, cudaStream_t st);
 

@@ -189,3 +189,13 @@ def test_full_size_hmd_frame_sampled(pr, oracle):
 def test_large_frame_sampled(pr, oracle):
     sc, views = S.config_large(seed=3)
     _sampled(pr, oracle, sc, views, n_uniform=300, win=12, seed=200, tile=32)
+
+
+def test_full_size_hmd_frame_fp64_retest_strict(pr, oracle):
+    sc, views = S.config_hmd(seed=2)
+    v = views[0]
+    g = gpu_frame(pr, sc, v, fp64=1)
+    pix = S.sample_pixels(v.W, v.H, 1500, 1, 24, 300)
+    o = oracle.render(v, sc.pos, sc.vel, sc.col, sc.tri, pix=pix)
+    compare(oracle, v, sc, o, g["id"], g["depth"], g["rgb"], pix=pix, fp64=True)
+    assert g["stats"]["flagged"] > 0
