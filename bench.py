@@ -1,16 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the perceptual-rasterization hot path on GB300.
 
-One step = one stereo HMD frame through every stage of the path: the
+One step = one frame of the workload through every stage of the path: the
 batched, graph-captured forward (a) bounds -> (b) binning -> (c) per-fragment
-ray casting -> (d) shading for both eyes, then (e) the adjoint of the shaded
-image for both eyes.  value = framebuffer pixels / step time (Mpix/s).
+ray casting -> (d) shading for all views, then (e) the adjoint of the shaded
+image for every view.  value = framebuffer pixels / step time (Mpix/s).
 
 Prints ONE JSON line (rank 0).  Default workload: 1440x1600 per eye x 2
 eyes, 266k triangles (200 subdivision-3 icospheres + a 10k ground plane),
 joint foveated + rolling, seeded synthetic scene already resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload hmd|large|batched|diff]
 """
 from __future__ import annotations
 
@@ -48,14 +49,40 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["hmd", "large", "batched", "diff"], default="hmd",
+                    help="hmd: stereo 1440x1600, 266k tris (default); large: stereo 2160^2, 1M tris, FP64 "
+                         "re-test; batched: 64 views of 1k-500k tris; diff: 512^2, 10k tris")
     return ap.parse_args()
 
 
-def workload():
-    sc, views = S.config_hmd(seed=2)
-    name = (f"hmd-stereo {views[0].W}x{views[0].H}x2 eyes, {sc.T} tris (200 ico-sub3 + 10k ground), "
-            f"foveated+rolling (alpha 2, d=(1,0)), yaw 3deg pitch 1deg, zenon bound, tile 16")
-    return sc, views, name
+class Workload:
+    """Scenes, views (each naming its scene), the FP64 re-test switch and a name."""
+
+    def __init__(self, scenes, views, scene_of, fp64, name):
+        self.scenes, self.views, self.scene_of, self.fp64, self.name = scenes, views, scene_of, fp64, name
+
+
+def workload(kind: str = "hmd") -> Workload:
+    if kind == "hmd":
+        sc, views = S.config_hmd(seed=2)
+        name = (f"hmd-stereo {views[0].W}x{views[0].H}x2 eyes, {sc.T} tris (200 ico-sub3 + 10k ground), "
+                f"foveated+rolling (alpha 2, d=(1,0)), yaw 3deg pitch 1deg, zenon bound, tile 16")
+        return Workload([sc], views, [0, 0], 0, name)
+    if kind == "large":
+        sc, views = S.config_large(seed=3)
+        name = (f"large-stereo {views[0].W}x{views[0].H}x2 eyes, {sc.T} tris (ico-sub2/box instances, sizes "
+                f"1e-3..1, half moving), foveated+rolling, FP64 re-test of flagged fragments")
+        return Workload([sc], views, [0, 0], 1, name)
+    if kind == "batched":
+        pairs = S.config_batched(seed=4)
+        scenes = [p[0] for p in pairs]
+        views = [p[1] for p in pairs]
+        name = (f"batched {len(views)} views, {sum(x.T for x in scenes)} tris (1k..500k log-uniform), "
+                f"{sum(v.W * v.H for v in views) / 1e6:.1f} Mpx (512^2..2160^2), mixed modes, autotuned tiles")
+        return Workload(scenes, views, list(range(len(views))), 0, name)
+    sc, view, _ = S.config_diff(seed=5)
+    name = f"diff {view.W}x{view.H}, {sc.T} small tris, foveated+rolling, fwd + bwd (colours, positions, velocities)"
+    return Workload([sc], [view], [0], 0, name)
 
 
 # ---------------------------------------------------------------------- clocks
@@ -116,9 +143,10 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------- reference arm
 
-def cpu_oracle_sample(sc, views, seconds: float, seed: int = 11):
-    """Time the FP64 oracle (forward render + shade + gradient) on a seeded
-    pixel sample of the stereo frame, sized to about `seconds` of work."""
+def cpu_oracle_sample(wl: Workload, seconds: float, seed: int = 11):
+    """Time the FP64 oracle (forward render + shade + gradient, every
+    triangle of the view's scene tested per pixel) on a seeded pixel sample
+    spread over the workload's views, sized to about `seconds` of work."""
     from oracle import oracle as O
     O.build()
     rng = np.random.default_rng(seed)
@@ -126,40 +154,40 @@ def cpu_oracle_sample(sc, views, seconds: float, seed: int = 11):
     def run(n):
         t0 = time.perf_counter()
         tests = 0
-        for v in views:
-            pix = np.sort(rng.choice(v.W * v.H, size=n // len(views), replace=False))
+        per = max(1, n // len(wl.views))
+        for v, si in zip(wl.views, wl.scene_of):
+            sc = wl.scenes[si]
+            pix = np.sort(rng.choice(v.W * v.H, size=min(per, v.W * v.H), replace=False))
             o = O.render(v, sc.pos, sc.vel, sc.col, sc.tri, pix=pix)
-            g = np.ones((pix.size, 3))
-            O.grad(v, sc.pos, sc.vel, sc.col, sc.tri, o["id"], g, pix=pix)
+            O.grad(v, sc.pos, sc.vel, sc.col, sc.tri, o["id"], np.ones((pix.size, 3)), pix=pix)
             tests += pix.size * sc.T
-        return time.perf_counter() - t0, tests
+        return time.perf_counter() - t0, tests, per * len(wl.views)
 
-    dt, _ = run(256)
-    n = int(max(256, min(1 << 16, 256 * seconds / max(dt, 1e-3))))
-    n -= n % len(views)
-    dt, tests = run(n)
+    dt, _, n0 = run(max(64, 4 * len(wl.views)))
+    n = int(max(n0, min(1 << 16, n0 * seconds / max(dt, 1e-3))))
+    dt, tests, n = run(n)
     return {"pixels": n, "seconds": dt, "tests": tests, "cores": O.num_threads()}
 
 
 def reference_arm(args, rank, world):
-    sc, views, name = workload()
+    wl = workload(args.workload)
     if rank != 0:
         return 0
     cpu_s = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_oracle_sample(sc, views, cpu_s / 4)
-    runs = [cpu_oracle_sample(sc, views, cpu_s) for _ in range(args.steps)]
+        cpu_oracle_sample(wl, cpu_s / 4)
+    runs = [cpu_oracle_sample(wl, cpu_s) for _ in range(args.steps)]
     px = sum(r["pixels"] for r in runs)
     sec = sum(r["seconds"] for r in runs)
     val = px / sec / 1e6
-    line = {"metric": "Mpix/s & ray-tri tests/s at 1 GB300 (batched vs plain); fwd+bwd ms/frame",
-            "value": val, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": name, "sample": f"{runs[0]['pixels']} pixels per step, all triangles each"},
+    sample = (f"{runs[0]['pixels']} seeded pixels over the workload's views per step, FP64 forward + gradient, "
+              f"every triangle tested")
+    line = {"metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "sample": sample},
             "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": runs[0]["cores"], "kind": "oracle",
-                             "sample": f"{runs[0]['pixels']} seeded pixels of the stereo frame per step, "
-                                       f"forward + gradient, every triangle tested"},
+                             "sample": sample},
             "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "tests_per_s": sum(r["tests"] for r in runs) / sec}
     print(json.dumps(line), flush=True)
@@ -168,22 +196,40 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------------- our arm
 
+METRIC = "Mpix/s & ray-tri tests/s at 1 GB300 (batched vs plain); fwd+bwd ms/frame"
+
+
 def source_hash():
     p = os.path.join(ROOT, "paper_1806_05385_gb300", "csrc", "pr_stage_c.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def ncu_traffic():
+def ncu_traffic(workload_kind: str):
     """DRAM bytes per fragment launch from the committed ncu summary, only
-    if it was taken on the current fragment-kernel source."""
+    if it was taken on this workload and on the current fragment source."""
     p = os.path.join(ROOT, "profiles", "fragment_traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if d.get("source_sha256_16") != source_hash():
+    if d.get("source_sha256_16") != source_hash() or d.get("workload") != workload_kind:
         return None
     return d.get("dram_bytes_per_launch")
+
+
+def aggregate(local_ms: float, local_pixels: int, dist=None, device="cpu"):
+    """Whole-job throughput of weakly scaled replicas: the pixels all ranks
+    rendered per step over the slowest rank's step time.  Returns (Mpix/s,
+    max ms per step); without a process group, the local values."""
+    if dist is None:
+        return local_pixels / (local_ms * 1e-3) / 1e6, local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    p = torch.tensor([float(local_pixels)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return float(p.item()) / (ms * 1e-3) / 1e6, ms
 
 
 def our_arm(args, rank, world):
@@ -197,11 +243,13 @@ def our_arm(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.load()
-    sc, views, name = workload()
+    wl = workload(args.workload)
+    views = wl.views
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     stream = torch.cuda.Stream()          # a capturable stream for the forward graph
     torch.cuda.set_stream(stream)
-    h = B.pr_scene_upload(dev(sc.pos), dev(sc.vel), dev(sc.col), dev(sc.tri))
+    handles = [B.pr_scene_upload(dev(sc.pos), dev(sc.vel), dev(sc.col), dev(sc.tri)) for sc in wl.scenes]
+    hv = [handles[si] for si in wl.scene_of]
     ws = B.pr_workspace_create()
     npx = [v.W * v.H for v in views]
     ids = [torch.empty(n, dtype=torch.int32, device="cuda") for n in npx]
@@ -209,16 +257,22 @@ def our_arm(args, rank, world):
     rgb = [torch.empty(3 * n, dtype=torch.float32, device="cuda") for n in npx]
     gen = torch.Generator(device="cuda").manual_seed(1234)
     grad = [torch.randn(3 * n, device="cuda", generator=gen) for n in npx]
-    V = sc.V
-    dcol, dpos, dvel = (torch.zeros(3 * V, device="cuda") for _ in range(3))
-    params = B.make_params("zenon", 16, 0, 0)
-    entries = [(h, v, ids[k], depth[k], rgb[k]) for k, v in enumerate(views)]
+    grads = [tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3)) for sc in wl.scenes]
+    if args.workload == "batched":
+        from paper_1806_05385_gb300 import autotune
+        tiles = autotune.tune([(hv[k], v, wl.scenes[wl.scene_of[k]].T) for k, v in enumerate(views)])
+    else:
+        tiles = [16] * len(views)
+    params = B.make_params("zenon", 16, wl.fp64, 0)
+    entries = [(hv[k], v, ids[k], depth[k], rgb[k], tiles[k]) for k, v in enumerate(views)]
     graph = B.pr_graph_capture_batch(ws, entries, params)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
+    bwd_entries = [(hv[k], v, ids[k], grad[k], *grads[wl.scene_of[k]]) for k, v in enumerate(views)]
+    ws_b = B.pr_workspace_create()
+
     def backward():
-        for k, v in enumerate(views):
-            B.pr_backward(h, v, ids[k], grad[k], dcol, dpos, dvel)
+        B.pr_backward_batch(ws_b, bwd_entries)
 
     def step():
         B.pr_graph_launch(graph)
@@ -258,43 +312,41 @@ def our_arm(args, rank, world):
 
     def plain():
         for k, v in enumerate(views):
-            B.pr_rasterize(h, v, params, ids[k], depth[k])
-            B.pr_shade(h, v, ids[k], rgb[k])
-    for _ in range(3):
+            p = B.make_params("zenon", tiles[k], wl.fp64, 0)
+            B.pr_rasterize(hv[k], v, p, ids[k], depth[k])
+            B.pr_shade(hv[k], v, ids[k], rgb[k])
+    for _ in range(2):
         plain()
-    fwd_plain = timed(plain, args.steps)
-    bwd_ms = timed(backward, args.steps)
+    fwd_plain = timed(plain, max(3, args.steps // 2))
+    bwd_ms = timed(backward, max(3, args.steps // 2))
 
-    total_ms = sum(step_ms)
-    mean_ms = total_ms / len(step_ms)
-    if dist:
-        t = torch.tensor([mean_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
     pix = sum(npx)
-    value = world * pix / (mean_ms * 1e-3) / 1e6
+    value, mean_ms = aggregate(sum(step_ms) / len(step_ms), pix, dist, "cuda")
 
     # end to end through the C ABI with host buffers: scene arrays in from
     # pinned host memory, shaded images and gradients back to pinned host
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        hpos, hvel, hcol = pin(sc.pos), pin(sc.vel), pin(sc.col)
+        hsc = [(pin(sc.pos), pin(sc.vel), pin(sc.col)) for sc in wl.scenes]
         hrgb = [torch.empty(3 * n, dtype=torch.float32).pin_memory() for n in npx]
         hg = [g.cpu().pin_memory() for g in grad]
-        hd = [torch.zeros(3 * V).pin_memory() for _ in range(3)]
-        ent_h = [(h, v, ids[k], None, hrgb[k]) for k, v in enumerate(views)]
+        hd = [tuple(torch.zeros(3 * sc.V).pin_memory() for _ in range(3)) for sc in wl.scenes]
+        ent_h = [(hv[k], v, ids[k], None, hrgb[k], tiles[k]) for k, v in enumerate(views)]
 
         def e2e_step():
-            B.pr_scene_update(h, hpos, hvel, hcol)
+            for h, a in zip(handles, hsc):
+                B.pr_scene_update(h, *a)
             B.pr_rasterize_batch(ws, ent_h, params)
             for k, v in enumerate(views):
-                B.pr_backward(h, v, ids[k], hg[k], hd[0], hd[1], hd[2])
+                d = hd[wl.scene_of[k]]
+                B.pr_backward(hv[k], v, ids[k], hg[k], d[0], d[1], d[2])
         for _ in range(2):
             e2e_step()
         ems = timed(e2e_step, max(3, args.steps // 2))
-        h2d = 3 * V * 12 + sum(g.numel() * 4 for g in hg) + 3 * (3 * V * 4)
-        d2h = sum(x.numel() * 4 for x in hrgb) + 3 * (3 * V * 4)
+        sv = sum(sc.V for sc in wl.scenes)
+        h2d = 3 * sv * 12 + sum(g.numel() * 4 for g in hg) + sum(3 * 3 * wl.scenes[si].V * 4 for si in wl.scene_of)
+        d2h = sum(x.numel() * 4 for x in hrgb) + sum(3 * 3 * wl.scenes[si].V * 4 for si in wl.scene_of)
         e2e = {"value": world * pix / (statistics.mean(ems) * 1e-3) / 1e6, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
@@ -303,44 +355,53 @@ def our_arm(args, rank, world):
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     achieved = st["tests"] * FLOP_PER_TEST / (frag_ms * 1e-3) / 1e12 if frag_ms > 0 else 0.0
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": ncu_traffic(),
-            "kernel": "k_fragment<16>", "flop_per_test": FLOP_PER_TEST,
+            "frac": achieved / peak if peak else None, "traffic": ncu_traffic(args.workload),
+            "kernel": "k_fragment", "flop_per_test": FLOP_PER_TEST,
             "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x median SM clock {sm_mhz:.0f} MHz "
-                          f"sampled during the timed region"}
+                          f"sampled during the timed region (no FP32 figure in MEASURED_PEAKS.json)",
+            "achieved_basis": "ray-triangle tests of one forward frame x 39 FLOP / fragment-stage time of that "
+                              "frame (CUDA events on the launching stream, inside the graph replay)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r = cpu_oracle_sample(sc, views, args.cpu_seconds)
+        r = cpu_oracle_sample(wl, args.cpu_seconds)
         cpu = {"value": r["pixels"] / r["seconds"] / 1e6, "unit": "Mpix/s", "cores": r["cores"], "kind": "oracle",
-               "sample": f"{r['pixels']} seeded pixels of the stereo frame, FP64 forward + gradient, "
+               "sample": f"{r['pixels']} seeded pixels over the workload's views, FP64 forward + gradient, "
                          f"every triangle tested ({r['tests']:.3g} tests in {r['seconds']:.1f} s)",
                "tests_per_s": r["tests"] / r["seconds"]}
 
-    kernels_per_step = 11 + len(views)   # forward graph (11 kernels) + one adjoint per eye
+    n_classes = len({(t, wl.fp64) for t in tiles})
+    kernels_fwd = 13 + n_classes + (1 if wl.fp64 else 0)   # tile boxes, bound, 2 scans x3, bins x2, items, resolve, shade
+    kernels_bwd = 1
     line = {
-        "metric": "Mpix/s & ray-tri tests/s at 1 GB300 (batched vs plain); fwd+bwd ms/frame",
-        "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": name, "views": len(views), "pixels_per_step": pix, "triangles": sc.T,
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if not wl.fp64 else "f32+f64-retest", "data": "synthetic",
+        "config": {"workload": wl.name, "views": len(views), "pixels_per_step": pix,
+                   "triangles": sum(sc.T for sc in wl.scenes),
+                   "step": "batched forward graph (bound, bin, fragment, shade) + batched adjoint (one launch)",
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
-        "gpu_launches": kernels_per_step * args.steps,
+        "gpu_launches": (kernels_fwd + kernels_bwd) * args.steps,
         "tests_per_s": st["tests"] / (frag_ms * 1e-3) if frag_ms > 0 else None,
         "ste": st["hits"] / st["tests"] if st["tests"] else None,
-        "stats": {k: st[k] for k in ("tests", "hits", "pairs", "items", "culled", "pixels")},
+        "stats": {k: st[k] for k in ("tests", "hits", "pairs", "items", "culled", "pixels", "flagged", "changed",
+                                     "fp64_depth_err")},
         "stage_ms": {"bound": st["stage_ms"][0], "bin": st["stage_ms"][1], "fragment": frag_ms,
-                     "resolve": st["stage_ms"][4], "shade": st["stage_ms"][5]},
+                     "fp64_retest": st["stage_ms"][3], "resolve": st["stage_ms"][4], "shade": st["stage_ms"][5]},
         "fwd_mpix_s": {"batched_graph": world * pix / (statistics.mean(fwd_batched) * 1e-3) / 1e6,
                        "plain_per_view": world * pix / (statistics.mean(fwd_plain) * 1e-3) / 1e6},
         "fwd_bwd_ms_per_frame": mean_ms, "bwd_ms_per_frame": statistics.mean(bwd_ms),
+        "tiles": sorted(set(tiles)),
     }
     B.pr_graph_free(graph)
     B.pr_workspace_free(ws)
-    B.pr_scene_free(h)
+    B.pr_workspace_free(ws_b)
+    for h in handles:
+        B.pr_scene_free(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -165,6 +165,24 @@ pr_status pr_shade(pr_scene *scene, const pr_view *view, const uint32_t *id, flo
 pr_status pr_backward(pr_scene *scene, const pr_view *view, const uint32_t *id, const float *grad_rgb,
                       float *dcol, float *dpos, float *dvel, void *stream);
 
+/* One entry of a batched adjoint: the scene and view of a rendered frame,
+ * its id buffer, the gradient of the loss w.r.t. its rgb image, and the
+ * per-vertex gradient outputs (accumulated; any may be NULL).  DEVICE
+ * pointers only. */
+typedef struct {
+    pr_scene *scene;
+    pr_view view;
+    const uint32_t *id;        /* [H][W] */
+    const float *grad_rgb;     /* [3][H][W] */
+    float *dcol, *dpos, *dvel; /* [V][3] of the scene, accumulated (+=) */
+} pr_backward_view;
+
+/* Stage (e) for n views in one launch (8x4 pixel blocks of all views in
+ * one grid); equal to n calls of pr_backward up to the order of the float
+ * additions.  Host pointers are rejected (PR_ERR_INVALID_ARG).  Uses ws
+ * only for the view table. */
+pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int32_t n, void *stream);
+
 /* One entry of a batched call: a scene, a view and its outputs. */
 typedef struct {
     pr_scene *scene;

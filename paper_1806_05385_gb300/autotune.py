@@ -1,0 +1,86 @@
+"""Tile-size autotuner of the batched form.
+
+For each view class -- mode, resolution bucket and triangle-count bucket --
+it times the view's frame through the C ABI (pr_rasterize, CUDA events on the
+current stream) for each bin tile size in {8, 16, 32} and keeps the fastest;
+choices are cached in a JSON file so that later runs reuse them.  Bin and
+work-item capacities need no tuning: the library sizes them from the counts
+a frame reports and regrows on overflow.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+from . import binding as B
+
+TILES = (8, 16, 32)
+
+
+def default_cache_path() -> str:
+    base = os.environ.get("PR_AUTOTUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache",
+                                                                 "paper_1806_05385_gb300")
+    return base if base.endswith(".json") else os.path.join(base, "tiles.json")
+
+
+def view_class(view, T: int) -> str:
+    """Views that share mode, resolution bucket (x1.5 steps) and triangle
+    bucket (x4 steps) share a tile size."""
+    px = max(1, int(view.W) * int(view.H))
+    return f"m{int(view.mode)}_p{int(math.log(px, 1.5))}_t{int(math.log(max(T, 1), 4))}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_tile(scene, view, tile: int, reps: int = 5, params=None) -> float:
+    """Median device time (ms) of pr_rasterize for one view at one tile size."""
+    import torch
+    n = int(view.W) * int(view.H)
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = B.make_params(params.bound if params is not None else "zenon", tile,
+                      params.fp64_retest if params is not None else 0, params.seg if params is not None else 0)
+    st = torch.cuda.current_stream()
+    B.pr_rasterize(scene, view, p, ids, None)  # warm-up (sizes the scratch)
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        B.pr_rasterize(scene, view, p, ids, None)
+        e1.record(st)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def tune(cases, cache_path: str | None = None, reps: int = 5, refresh: bool = False):
+    """cases: list of (scene_handle, view, T).  Returns one tile size per
+    case (cached classes are not re-timed unless refresh)."""
+    path = cache_path or default_cache_path()
+    cache = {} if refresh else _load(path)
+    tiles, changed = [], False
+    for scene, view, T in cases:
+        key = view_class(view, T)
+        if key not in cache:
+            times = {t: time_tile(scene, view, t, reps) for t in TILES}
+            cache[key] = {"tile": min(times, key=times.get), "ms": times}
+            changed = True
+        tiles.append(int(cache[key]["tile"]))
+    if changed:
+        _save(path, cache)
+    return tiles

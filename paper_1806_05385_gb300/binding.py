@@ -27,7 +27,8 @@ BG = 0xFFFFFFFF
 EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize", "pr_shade", "pr_backward",
            "pr_workspace_create", "pr_workspace_free", "pr_rasterize_batch", "pr_graph_capture_batch",
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
-           "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc")
+           "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
+           "pr_backward_batch")
 
 
 class PrError(RuntimeError):
@@ -57,6 +58,11 @@ class PrStats(C.Structure):
         d["stage_ms"] = [float(x) for x in self.stage_ms]
         d["fp64_depth_err"] = float(self.fp64_depth_err)
         return d
+
+
+class PrBackwardView(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("view", PrView), ("id", C.c_void_p), ("grad_rgb", C.c_void_p),
+                ("dcol", C.c_void_p), ("dpos", C.c_void_p), ("dvel", C.c_void_p)]
 
 
 class PrBatchView(C.Structure):
@@ -100,6 +106,7 @@ def load(build_if_missing: bool = True):
             "pr_status_string": ([I32], C.c_char_p),
             "pr_version": ([], I32),
             "pr_rasterize_noalloc": ([P, P, P, P, I64, I64, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
+            "pr_backward_batch": ([P, C.POINTER(PrBackwardView), I32, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -206,6 +213,19 @@ def pr_backward(scene, view, ids, grad_rgb, dcol=None, dpos=None, dvel=None, str
     pv = view if isinstance(view, PrView) else make_view(view)
     _check(load().pr_backward(C.c_void_p(scene), C.byref(pv), _ptr(ids), _ptr(grad_rgb), _ptr(dcol), _ptr(dpos),
                               _ptr(dvel), stream if stream is not None else current_stream()), "pr_backward")
+
+
+def pr_backward_batch(ws, entries, stream=None):
+    """entries: list of (scene, view, ids, grad_rgb, dcol, dpos, dvel), CUDA tensors."""
+    arr = (PrBackwardView * len(entries))()
+    for k, (scene, view, ids, g, dc, dp, dv) in enumerate(entries):
+        arr[k].scene = C.c_void_p(scene)
+        arr[k].view = view if isinstance(view, PrView) else make_view(view)
+        for name, buf in (("id", ids), ("grad_rgb", g), ("dcol", dc), ("dpos", dp), ("dvel", dv)):
+            p = _ptr(buf)
+            setattr(arr[k], name, p.value if p is not None else None)
+    _check(load().pr_backward_batch(C.c_void_p(ws), arr, len(entries),
+                                    stream if stream is not None else current_stream()), "pr_backward_batch")
 
 
 def pr_workspace_create() -> int:

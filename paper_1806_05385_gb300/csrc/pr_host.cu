@@ -182,6 +182,7 @@ struct pr_scene {
     DevBuf soa;   // 9 V floats: px py pz vx vy vz cr cg cb
     DevBuf idx;   // 3 T ints: i0 i1 i2
     DevBuf stage; // host input staging
+    DevBuf gstage, ostage;  // adjoint: staged host gradient image / host gradient outputs
     pr_workspace ws;
 };
 
@@ -445,6 +446,7 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
         v.depth_out = o.depth_off >= 0 ? (float *)(stage + o.depth_off) : o.depth_user;
         v.id_in = v.id_out;
         v.rgb_out = shade ? (o.rgb_off >= 0 ? (float *)(stage + o.rgb_off) : o.rgb_user) : nullptr;
+        v.rec = ws->rec.as<float4>();  // shading in the same frame reads its records
         ws->h_views.p[q] = v;
     }
     long long *ho = ws->h_offs.p;
@@ -801,25 +803,24 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     const long long np = (long long)view->W * view->H;
     const long long V = sc->V;
     // inputs: ids and gradient (staged if on the host)
-    DevBuf gstage, ostage;
     const uint32_t *did = nullptr;
     const void *dg = nullptr;
     s = stage_in_ids(sc, id, np, &did, st);
     if (s == PR_OK)
-        s = copy_in(grad_rgb, sizeof(float) * 3 * np, gstage, &dg, st);
+        s = copy_in(grad_rgb, sizeof(float) * 3 * np, sc->gstage, &dg, st);
     if (s != PR_OK)
         return s;
     // outputs: accumulate in place when on the device, else through staging
     float *outs[3] = {dcol, dpos, dvel};
     float *douts[3] = {nullptr, nullptr, nullptr};
     bool host[3] = {false, false, false};
-    PR_TRY(ensure(ostage, sizeof(float) * 9 * V));
     for (int a = 0; a < 3; ++a) {
         if (!outs[a])
             continue;
         host[a] = !is_device_ptr(outs[a]);
         if (host[a]) {
-            douts[a] = ostage.as<float>() + 3 * a * V;
+            PR_TRY(ensure(sc->ostage, sizeof(float) * 9 * V));
+            douts[a] = sc->ostage.as<float>() + 3 * a * V;
             PR_TRY(cudaMemcpyAsync(douts[a], outs[a], sizeof(float) * 3 * V, cudaMemcpyHostToDevice, st));
         } else {
             douts[a] = outs[a];
@@ -838,6 +839,43 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     for (int a = 0; a < 3; ++a)
         if (host[a])
             PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
+    PR_TRY(cudaStreamSynchronize(st));
+    return PR_OK;
+}
+
+pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int32_t n, void *stream)
+{
+    if (!ws || !views || n < 1)
+        return PR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    PR_TRY(ws->h_views.ensure(n));
+    PR_TRY(ws->h_offs.ensure(n + 1));
+    PR_TRY(ensure(ws->views, sizeof(ViewDev) * n));
+    PR_TRY(ensure(ws->offs, sizeof(long long) * (n + 1)));
+    long long *blk = ws->h_offs.p;
+    blk[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        const pr_backward_view &b = views[k];
+        if (!b.scene || !b.id || !b.grad_rgb || !is_device_ptr(b.id) || !is_device_ptr(b.grad_rgb) ||
+            (b.dcol && !is_device_ptr(b.dcol)) || (b.dpos && !is_device_ptr(b.dpos)) ||
+            (b.dvel && !is_device_ptr(b.dvel)))
+            return PR_ERR_INVALID_ARG;
+        ViewDev v;
+        pr_status s = make_viewdev(b.view, b.scene, kDefaultTile, PR_BOUND_ZENON, 0, v);
+        if (s != PR_OK)
+            return s;
+        v.id_in = b.id;
+        v.grad_in = b.grad_rgb;
+        v.dcol = b.dcol;
+        v.dpos = b.dpos;
+        v.dvel = b.dvel;
+        v.blk_off = blk[k];
+        blk[k + 1] = blk[k] + (long long)((v.W + 7) / 8) * ((v.H + 3) / 4);
+        ws->h_views.p[k] = v;
+    }
+    PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
+    PR_TRY(cudaMemcpyAsync(ws->offs.p, blk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
+    PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], st));
     PR_TRY(cudaStreamSynchronize(st));
     return PR_OK;
 }

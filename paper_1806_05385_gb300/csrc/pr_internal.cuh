@@ -48,6 +48,7 @@ struct ViewDev {
     float *rgb_out;
     const float *grad_in;              // adjoint input [3][H][W]
     float *dcol, *dpos, *dvel;         // adjoint outputs [V][3]
+    const float4 *rec;                 // this frame's stage (a) records (batch-wide index), or null
 };
 
 struct Counters {

@@ -39,14 +39,24 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, long long lin, unsig
     h.ia = v.i0[id];
     h.ib = v.i1[id];
     h.ic = v.i2[id];
-    float3 S, E;
     const float t = h.t;
-    vertex_start_end(v, h.ia, S, E);
-    h.A = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
-    vertex_start_end(v, h.ib, S, E);
-    h.B = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
-    vertex_start_end(v, h.ic, S, E);
-    h.C = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+    if (v.rec) {
+        // the frame's own stage (a) record: S and D = E - S, the same bits
+        // vertex_start_end gives, in 64 contiguous bytes
+        const float4 *r = v.rec + ((size_t)v.tri_off + id) * kRecF4;
+        const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r5 = r[5];
+        h.A = make_float3(fmaf(t, r2.y, r0.x), fmaf(t, r2.z, r0.y), fmaf(t, r2.w, r0.z));
+        h.B = make_float3(fmaf(t, r3.x, r0.w), fmaf(t, r3.y, r1.x), fmaf(t, r3.z, r1.y));
+        h.C = make_float3(fmaf(t, r3.w, r1.z), fmaf(t, r5.z, r1.w), fmaf(t, r5.w, r2.x));
+    } else {
+        float3 S, E;
+        vertex_start_end(v, h.ia, S, E);
+        h.A = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+        vertex_start_end(v, h.ib, S, E);
+        h.B = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+        vertex_start_end(v, h.ic, S, E);
+        h.C = make_float3(fmaf(t, E.x - S.x, S.x), fmaf(t, E.y - S.y, S.y), fmaf(t, E.z - S.z, S.z));
+    }
     // barycentrics from the sheared edge functions of the watertight test
     const float ax = fmaf(-dx, h.A.z, h.A.x), ay = fmaf(-dy, h.A.z, h.A.y);
     const float bx = fmaf(-dx, h.B.z, h.B.x), by = fmaf(-dy, h.B.z, h.B.y);
@@ -147,8 +157,9 @@ __device__ __forceinline__ float warp_sum(float x)
 //  - the unit normal n = flip (B-A)x(C-A) / |.|: dn gets (I - n n^T)/|.|;
 //  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1:
 //    dc/dp = (1-t) R0 + t R1, dc/dv = t R1.
-// Per warp, the contributions of each distinct triangle are summed over the
-// lanes that see it (masked butterflies), and one lane adds the 27 sums.
+// Per warp, the 27 contributions of each distinct triangle are summed over
+// the lanes that see it with a reduce-scatter (lane l ends with the sum of
+// value l) and added with one 27-lane atomic instruction.
 __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ views, int nviews,
                                                  const long long *__restrict__ blk_offs, long long nthreads)
 {

@@ -199,3 +199,31 @@ def test_full_size_hmd_frame_fp64_retest_strict(pr, oracle):
     o = oracle.render(v, sc.pos, sc.vel, sc.col, sc.tri, pix=pix)
     compare(oracle, v, sc, o, g["id"], g["depth"], g["rgb"], pix=pix, fp64=True)
     assert g["stats"]["flagged"] > 0
+
+
+def test_backward_batch_equals_per_view(pr):
+    import torch
+    cases = _views_mixed()
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+    ws = pr.pr_workspace_create()
+    try:
+        rng = np.random.default_rng(3)
+        ent, per = [], []
+        for h, (sc, v, tile) in zip(handles, cases):
+            n = v.W * v.H
+            ids = torch.empty(n, dtype=torch.int32, device="cuda")
+            pr.pr_rasterize(h, v, pr.make_params("zenon", tile), ids, None)
+            g = _dev(rng.normal(size=3 * n).astype(np.float32))
+            a = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            b = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            ent.append((h, v, ids, g, *a))
+            pr.pr_backward(h, v, ids, g, *b)
+            per.append(b)
+        pr.pr_backward_batch(ws, ent)
+        for e, b in zip(ent, per):
+            for x, y in zip(e[4:], b):
+                assert torch.allclose(x, y, rtol=1e-4, atol=1e-5 * float(y.abs().max()) + 1e-12)
+    finally:
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)

@@ -1,0 +1,35 @@
+"""The multi-GPU (replica) path of bench.py on CPU: two gloo ranks with
+different step times; the whole-job value is the pixels of both ranks over
+the slower rank's time, identical on every rank."""
+import os
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    local_ms = 2.0 if rank == 0 else 3.0
+    value, ms = bench.aggregate(local_ms, 1_000_000, dist, "cpu")
+    out[rank] = (value, ms)
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregate():
+    port = 29500 + os.getpid() % 1000
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    for r in (0, 1):
+        value, ms = res[r]
+        assert ms == pytest.approx(3.0)
+        assert value == pytest.approx(2_000_000 / 3e-3 / 1e6)
+
+
+def test_single_process_aggregate():
+    import bench
+    assert bench.aggregate(4.0, 2_000_000) == pytest.approx((500.0, 4.0))
