@@ -130,10 +130,13 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
     constexpr int NT = S * S / 2;  // threads: two pixels each
     constexpr int NW = NT / 32;    // warps
     constexpr int WPR = S / 8;     // 8x8 warp blocks per tile row
-    constexpr int CH = NT < 256 ? (NT < 128 ? 128 : NT) : 256;  // triangles staged per chunk
-    constexpr int PER_WARP = CH / NW;  // triangles each warp gathers (multiple of 32)
-    __shared__ float4 s_rec[CH * kRecF4];
+    constexpr int CH = NT >= 128 ? 128 : 64;  // triangles staged per chunk (smaller for one-warp CTAs)
+    __shared__ float4 s_raw[CH * kRecF4];  // records as gathered
+    __shared__ unsigned s_rid[CH];
+    __shared__ float s_rkey[CH];
+    __shared__ float4 s_rec[CH * kRecF4];  // the same records, nearest first
     __shared__ unsigned s_id[CH];
+    __shared__ float s_key[CH];
     __shared__ long long s_item;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -191,25 +194,62 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
         for (int base = item.z; base < item.w; base += CH) {
             const int n = min(CH, item.w - base);
             __syncthreads();  // the previous chunk is no longer read
-            // each warp gathers PER_WARP records: ids coalesced, then the
-            // 6 float4 of 32 records at a time with consecutive lanes on
-            // consecutive float4s
-            for (int w0 = warp * PER_WARP; w0 < (warp + 1) * PER_WARP; w0 += 32) {
+            // warps gather 32 records at a time: ids coalesced, then the 6
+            // float4 of the 32 records with consecutive lanes on consecutive
+            // float4s
+            for (int w0 = warp * 32; w0 < CH; w0 += NW * 32) {
                 const int q = w0 + lane;
                 const unsigned gid = q < n ? tile_tris[base + q] : 0u;
                 if (q < n)
-                    s_id[q] = gid;
+                    s_rid[q] = gid;
 #pragma unroll
                 for (int f = 0; f < kRecF4; ++f) {
                     const int idx = lane + 32 * f, r = idx / kRecF4, fld = idx - r * kRecF4;
                     const unsigned g = __shfl_sync(0xffffffffu, gid, r);
                     if (w0 + r < n)
-                        s_rec[(w0 + r) * kRecF4 + fld] = __ldg(&rec[(size_t)g * kRecF4 + fld]);
+                        s_raw[(w0 + r) * kRecF4 + fld] = __ldg(&rec[(size_t)g * kRecF4 + fld]);
                 }
             }
             __syncthreads();
+            // nearest possible depth of each triangle over the frame: camera
+            // z is linear on the moving triangle, so min_k S_k.z + min(0, D_k.z)
+            for (int q = threadIdx.x; q < n; q += NT) {
+                const float4 *r = s_raw + q * kRecF4;
+                s_rkey[q] = fminf(fminf(r[0].z + fminf(0.f, r[2].w), r[1].y + fminf(0.f, r[3].z)),
+                                  r[2].x + fminf(0.f, r[5].w));
+            }
+            __syncthreads();
+            // rank sort, nearest first (ties by position), into s_rec
+            for (int q = threadIdx.x; q < n; q += NT) {
+                const float kq = s_rkey[q];
+                int rank = 0;
+                for (int j = 0; j < n; ++j) {
+                    const float kj = s_rkey[j];
+                    rank += (kj < kq) || (kj == kq && j < q);
+                }
+#pragma unroll
+                for (int f = 0; f < kRecF4; ++f)
+                    s_rec[rank * kRecF4 + f] = s_raw[q * kRecF4 + f];
+                s_id[rank] = s_rid[q];
+                s_key[rank] = kq;
+            }
+            __syncthreads();
+            // Front-to-back with early exit: once the next triangle cannot
+            // come nearer than every pixel's current best (with a margin for
+            // the FP32 depth; for the precision form also the tie band), no
+            // later one in this chunk can change a pixel of this warp.
+            const float cull = kFlag ? (1.f + 3.f * kTieRel) : 1.f;
+            float wmax = INFINITY;
 #pragma unroll kFragUnroll
             for (int k = 0; k < n; ++k) {
+                if ((k & 7) == 0) {
+                    float m = fmaxf(ok0 ? bd0 : 0.f, ok1 ? bd1 : 0.f);
+                    for (int o = 16; o > 0; o >>= 1)
+                        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    wmax = m * cull;
+                }
+                if (s_key[k] * 0.99999f > wmax)
+                    break;
                 const float4 bb = s_rec[k * kRecF4 + 4];
                 const float4 tb = s_rec[k * kRecF4 + 5];
                 if (bb.x > wx1 || bb.y < wx0 || bb.z > wy1 || bb.w < wy0 || tb.x > wt1 || tb.y < wt0)
