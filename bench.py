@@ -265,7 +265,13 @@ def our_arm(args, rank, world):
         tiles = [16] * len(views)
     params = B.make_params("zenon", 16, wl.fp64, 0)
     entries = [(hv[k], v, ids[k], depth[k], rgb[k], tiles[k]) for k, v in enumerate(views)]
-    graph = B.pr_graph_capture_batch(ws, entries, params)
+    # one training frame = one graph: forward (a)-(d), then the adjoint (e)
+    # of an upstream image gradient, reading the frame's own records
+    fgrads = [dict(grad_rgb=grad[k], dcol=grads[wl.scene_of[k]][0], dpos=grads[wl.scene_of[k]][1],
+                   dvel=grads[wl.scene_of[k]][2]) for k in range(len(views))]
+    graph = B.pr_graph_capture_frame(ws, entries, fgrads, params)
+    ws_f = B.pr_workspace_create()
+    graph_fwd = B.pr_graph_capture_batch(ws_f, entries, params)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
     bwd_entries = [(hv[k], v, ids[k], grad[k], *grads[wl.scene_of[k]]) for k, v in enumerate(views)]
@@ -276,7 +282,6 @@ def our_arm(args, rank, world):
 
     def step():
         B.pr_graph_launch(graph)
-        backward()
 
     def timed(fn, k, flush_l2=True):
         ms = []
@@ -308,7 +313,7 @@ def our_arm(args, rank, world):
     frag_ms = st["stage_ms"][2]
 
     # forward only: batched graph vs plain per-view calls
-    fwd_batched = timed(lambda: B.pr_graph_launch(graph), args.steps)
+    fwd_batched = timed(lambda: B.pr_graph_launch(graph_fwd), args.steps)
 
     def plain():
         for k, v in enumerate(views):
@@ -371,34 +376,37 @@ def our_arm(args, rank, world):
                "tests_per_s": r["tests"] / r["seconds"]}
 
     n_classes = len({(t, wl.fp64) for t in tiles})
-    kernels_fwd = 13 + n_classes + (1 if wl.fp64 else 0)   # tile boxes, bound, 2 scans x3, bins x2, items, resolve, shade
-    kernels_bwd = 1
+    # tile boxes, bound, 2 scans x3, bins x2, items, fragment classes, [FP64 re-test], shade+resolve, adjoint
+    kernels_step = 12 + n_classes + (1 if wl.fp64 else 0) + 1
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if not wl.fp64 else "f32+f64-retest", "data": "synthetic",
         "config": {"workload": wl.name, "views": len(views), "pixels_per_step": pix,
                    "triangles": sum(sc.T for sc in wl.scenes),
-                   "step": "batched forward graph (bound, bin, fragment, shade) + batched adjoint (one launch)",
+                   "step": "one graph per frame: bound, bin, fragment, [FP64 re-test], resolve+shade, adjoint",
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
-        "gpu_launches": (kernels_fwd + kernels_bwd) * args.steps,
+        "gpu_launches": kernels_step * args.steps,
         "tests_per_s": st["tests"] / (frag_ms * 1e-3) if frag_ms > 0 else None,
         "ste": st["hits"] / st["tests"] if st["tests"] else None,
         "stats": {k: st[k] for k in ("tests", "hits", "pairs", "items", "culled", "pixels", "flagged", "changed",
                                      "fp64_depth_err")},
         "stage_ms": {"bound": st["stage_ms"][0], "bin": st["stage_ms"][1], "fragment": frag_ms,
-                     "fp64_retest": st["stage_ms"][3], "resolve": st["stage_ms"][4], "shade": st["stage_ms"][5]},
+                     "fp64_retest": st["stage_ms"][3], "resolve_shade": st["stage_ms"][5],
+                     "adjoint": st["stage_ms"][6]},
         "fwd_mpix_s": {"batched_graph": world * pix / (statistics.mean(fwd_batched) * 1e-3) / 1e6,
                        "plain_per_view": world * pix / (statistics.mean(fwd_plain) * 1e-3) / 1e6},
-        "fwd_bwd_ms_per_frame": mean_ms, "bwd_ms_per_frame": statistics.mean(bwd_ms),
+        "fwd_bwd_ms_per_frame": mean_ms, "bwd_ms_separate_call": statistics.mean(bwd_ms),
         "tiles": sorted(set(tiles)),
     }
     B.pr_graph_free(graph)
+    B.pr_graph_free(graph_fwd)
     B.pr_workspace_free(ws)
+    B.pr_workspace_free(ws_f)
     B.pr_workspace_free(ws_b)
     for h in handles:
         B.pr_scene_free(h)

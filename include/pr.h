@@ -118,7 +118,9 @@ typedef struct {
     float stage_ms[8];    /* device time of the last frame's stages, from CUDA events on the
                              caller's stream: [0] (a) tile boxes + bounds, [1] (b) binning
                              (count, scan, scatter, items), [2] (c) fragment kernel(s),
-                             [3] FP64 re-test, [4] resolve, [5] (d) shading, [6]-[7] unused */
+                             [3] FP64 re-test, [4] resolve (when not shading), [5] (d) shading
+                             (which then also resolves), [6] (e) adjoint of a training frame,
+                             [7] unused */
     float fp64_depth_err; /* precision form: largest |depth_fp32 - depth_fp64| / depth_fp64 over the
                              re-tested pixels whose winner FP64 confirmed (the FP32 error that the
                              re-test removed); 0 without the re-test */
@@ -205,6 +207,28 @@ void pr_workspace_free(pr_workspace *ws);
 pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
                              void *stream);
 
+/* The gradient side of one view of a training frame: either grad_rgb =
+ * dL/drgb [3][H][W], or target_rgb [3][H][W] for the L2 loss
+ * L = sum (rgb - target)^2 (then dL/drgb = 2 (rgb - target) is formed from
+ * the frame's own shaded image inside the adjoint kernel); dcol, dpos, dvel
+ * [V][3] of the view's scene are ACCUMULATED (+=), any may be NULL.  All
+ * DEVICE pointers.  Both NULL: no adjoint for this view. */
+typedef struct {
+    const float *grad_rgb;
+    const float *target_rgb;
+    float *dcol, *dpos, *dvel;
+} pr_frame_grad;
+
+/* A training frame: pr_rasterize_batch (stages (a)-(d)) followed, in the
+ * same sequence and with no host round trip, by stage (e) for every view
+ * with a gradient entry (grads: n entries in view order, or NULL).  The
+ * adjoint reads the frame's own stage (a) records.  Views with a gradient
+ * need a device rgb_out.  When a forward attempt overflows the workspace and
+ * is rerun after regrowth, the adjoint of that attempt does nothing, so the
+ * gradients are accumulated exactly once per call. */
+pr_status pr_frame_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                         const pr_frame_grad *grads, void *stream);
+
 /* Captures the same sequence into a CUDA graph (after one eager run that
  * sizes every buffer) and replays it with pr_graph_launch.  The views and
  * their buffers must stay valid and unchanged in shape while the graph
@@ -213,6 +237,14 @@ pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32
 typedef struct pr_graph pr_graph;
 pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n,
                                  const pr_params *params, void *stream, pr_graph **out);
+/* The same for a training frame (pr_frame_batch): forward, loss gradient and
+ * adjoint replayed as one graph.  Gradient outputs accumulate on every
+ * replay (zero them between replays if a fresh gradient is wanted); a replay
+ * whose forward overflows skips the adjoint and pr_graph_launch returns
+ * PR_ERR_OVERFLOW (recapture after an eager call has regrown the workspace). */
+pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, int32_t n,
+                                 const pr_params *params, const pr_frame_grad *grads, void *stream,
+                                 pr_graph **out);
 pr_status pr_graph_launch(pr_graph *g, void *stream);
 void pr_graph_free(pr_graph *g);
 

@@ -28,7 +28,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_workspace_create", "pr_workspace_free", "pr_rasterize_batch", "pr_graph_capture_batch",
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
-           "pr_backward_batch")
+           "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame")
 
 
 class PrError(RuntimeError):
@@ -63,6 +63,11 @@ class PrStats(C.Structure):
 class PrBackwardView(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("view", PrView), ("id", C.c_void_p), ("grad_rgb", C.c_void_p),
                 ("dcol", C.c_void_p), ("dpos", C.c_void_p), ("dvel", C.c_void_p)]
+
+
+class PrFrameGrad(C.Structure):
+    _fields_ = [("grad_rgb", C.c_void_p), ("target_rgb", C.c_void_p), ("dcol", C.c_void_p), ("dpos", C.c_void_p),
+                ("dvel", C.c_void_p)]
 
 
 class PrBatchView(C.Structure):
@@ -107,6 +112,9 @@ def load(build_if_missing: bool = True):
             "pr_version": ([], I32),
             "pr_rasterize_noalloc": ([P, P, P, P, I64, I64, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
             "pr_backward_batch": ([P, C.POINTER(PrBackwardView), I32, P], I32),
+            "pr_frame_batch": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P], I32),
+            "pr_graph_capture_frame": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P,
+                                        C.POINTER(P)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -270,6 +278,40 @@ def pr_graph_capture_batch(ws, entries, params=None, stream=None) -> int:
     _check(load().pr_graph_capture_batch(C.c_void_p(ws), arr, len(entries), C.byref(pp),
                                          stream if stream is not None else current_stream(), C.byref(h)),
            "pr_graph_capture_batch")
+    return h.value
+
+
+def make_grads(grads):
+    """grads: list (one per view) of None or a dict with any of grad_rgb,
+    target_rgb, dcol, dpos, dvel (CUDA tensors)."""
+    arr = (PrFrameGrad * len(grads))()
+    keep = []
+    for k, g in enumerate(grads):
+        for name, buf in (g or {}).items():
+            p = _ptr(buf)
+            setattr(arr[k], name, p.value if p is not None else None)
+            keep.append(buf)
+    return arr, keep
+
+
+def pr_frame_batch(ws, entries, grads, params=None, stream=None):
+    """A training frame: the batched forward, then the adjoint of every view
+    whose grads entry is given (see make_grads)."""
+    arr, _keep = make_batch(entries)
+    garr, _gkeep = make_grads(grads)
+    pp = params if params is not None else make_params()
+    _check(load().pr_frame_batch(C.c_void_p(ws), arr, len(entries), C.byref(pp), garr,
+                                 stream if stream is not None else current_stream()), "pr_frame_batch")
+
+
+def pr_graph_capture_frame(ws, entries, grads, params=None, stream=None) -> int:
+    arr, _keep = make_batch(entries)
+    garr, _gkeep = make_grads(grads)
+    pp = params if params is not None else make_params()
+    h = C.c_void_p()
+    _check(load().pr_graph_capture_frame(C.c_void_p(ws), arr, len(entries), C.byref(pp), garr,
+                                         stream if stream is not None else current_stream(), C.byref(h)),
+           "pr_graph_capture_frame")
     return h.value
 
 

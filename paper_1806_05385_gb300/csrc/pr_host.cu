@@ -138,7 +138,7 @@ struct pr_workspace {
     PinnedBuf<Counters> h_cnt;
     pr_stats stats{};
     long long last_T = 0;          // triangles of the last frame (debug bounds)
-    static constexpr int kEv = 7;  // stage boundaries of one frame
+    static constexpr int kEv = 8;  // stage boundaries of one frame
     cudaEvent_t ev[kEv] = {};
     bool ev_ok = false;
     ~pr_workspace()
@@ -308,6 +308,7 @@ struct BatchPlan {
     bool any_fp64 = false;
     std::vector<Cls> classes;
     // output staging: per view (in order) device pointers used by kernels
+    std::vector<pr_frame_grad> grads;  // per view (in order); empty: no adjoint
     struct Out {
         uint32_t *id_user;
         float *depth_user, *rgb_user;
@@ -318,7 +319,8 @@ struct BatchPlan {
     size_t stage_bytes = 0;
 };
 
-pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, BatchPlan &P)
+pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, BatchPlan &P,
+                     const pr_frame_grad *grads = nullptr)
 {
     if (n < 1 || !views)
         return PR_ERR_INVALID_ARG;
@@ -372,6 +374,19 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
         o.id_off = (o.id_host || (!bv.id_out && bv.rgb_out)) ? take(np * 4) : -1;
         o.depth_off = o.depth_host ? take(np * 4) : -1;
         o.rgb_off = o.rgb_host ? take(np * 12) : -1;
+    }
+    if (grads) {
+        P.grads.resize(n);
+        for (int q = 0; q < n; ++q) {
+            const pr_frame_grad &g = grads[P.order[q]];
+            const pr_batch_view &bv = views[P.order[q]];
+            const bool any = g.grad_rgb || g.target_rgb;
+            if (any && (!bv.rgb_out || P.out[q].rgb_host || (g.grad_rgb && !is_device_ptr(g.grad_rgb)) ||
+                        (g.target_rgb && !is_device_ptr(g.target_rgb)) || (g.dcol && !is_device_ptr(g.dcol)) ||
+                        (g.dpos && !is_device_ptr(g.dpos)) || (g.dvel && !is_device_ptr(g.dvel))))
+                return PR_ERR_INVALID_ARG;  // the adjoint in a frame needs device buffers and the shaded image
+            P.grads[q] = g;
+        }
     }
     P.ttot = P.tri_off[n];
     P.ntiles = P.tile_off[n];
@@ -447,6 +462,14 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
         v.id_in = v.id_out;
         v.rgb_out = shade ? (o.rgb_off >= 0 ? (float *)(stage + o.rgb_off) : o.rgb_user) : nullptr;
         v.rec = ws->rec.as<float4>();  // shading in the same frame reads its records
+        if (!P.grads.empty()) {
+            const pr_frame_grad &g = P.grads[q];
+            v.grad_in = g.grad_rgb;
+            v.target = g.grad_rgb ? nullptr : g.target_rgb;
+            v.dcol = g.dcol;
+            v.dpos = g.dpos;
+            v.dvel = g.dvel;
+        }
         ws->h_views.p[q] = v;
     }
     long long *ho = ws->h_offs.p;
@@ -506,11 +529,15 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
         PR_TRY(launch_retest(dv, n, pix_offs, scan, tile_cnt, ws->tile_tris.as<unsigned>(), rec,
                              ws->flag_list.as<long long>(), ws->keys.as<unsigned long long>(), cnt, st));
     PR_TRY(mark(4));
-    PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
+    if (!shade)
+        PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
     PR_TRY(mark(5));
-    if (shade)
-        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, st));
+    if (shade)  // resolves the keys too
+        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), st));
     PR_TRY(mark(6));
+    if (!P.grads.empty())
+        PR_TRY(launch_backward(dv, n, blk_offs, P.nblk, cnt, st));
+    PR_TRY(mark(7));
     // host-side outputs
     for (int q = 0; q < n; ++q) {
         const BatchPlan::Out &o = P.out[q];
@@ -554,11 +581,11 @@ pr_status finish_stats(pr_workspace *ws, const BatchPlan &P)
 
 // Eager frame: enqueue, read the status, regrow and rerun on overflow.
 pr_status run_batch(pr_workspace *ws, const pr_batch_view *views, int n, const pr_params *params, bool shade,
-                    cudaStream_t st)
+                    cudaStream_t st, const pr_frame_grad *grads = nullptr)
 {
     pr_params prm = default_params(params);
     BatchPlan P;
-    pr_status s = plan_batch(views, n, prm, P);
+    pr_status s = plan_batch(views, n, prm, P, grads);
     if (s != PR_OK)
         return s;
     for (int attempt = 0; attempt < 3; ++attempt) {
@@ -783,7 +810,7 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
     if (s != PR_OK)
         return s;
     PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), st));
+                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, st));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
     PR_TRY(cudaStreamSynchronize(st));
@@ -835,7 +862,7 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     if (s != PR_OK)
         return s;
     PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                           (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), st));
+                           (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, st));
     for (int a = 0; a < 3; ++a)
         if (host[a])
             PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
@@ -875,7 +902,7 @@ pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int
     }
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
     PR_TRY(cudaMemcpyAsync(ws->offs.p, blk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
-    PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], st));
+    PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], nullptr, st));
     PR_TRY(cudaStreamSynchronize(st));
     return PR_OK;
 }
@@ -904,8 +931,16 @@ pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32
     return run_batch(ws, views, n, params, true, (cudaStream_t)stream);
 }
 
-pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
-                                 void *stream, pr_graph **out)
+pr_status pr_frame_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                         const pr_frame_grad *grads, void *stream)
+{
+    if (!ws)
+        return PR_ERR_INVALID_ARG;
+    return run_batch(ws, views, n, params, true, (cudaStream_t)stream, grads);
+}
+
+pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                                 const pr_frame_grad *grads, void *stream, pr_graph **out)
 {
     if (!ws || !out)
         return PR_ERR_INVALID_ARG;
@@ -914,12 +949,12 @@ pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, i
     if (!st)
         return PR_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
     // eager run: sizes every buffer and warms up the kernels
-    pr_status s = run_batch(ws, views, n, params, true, st);
+    pr_status s = run_batch(ws, views, n, params, true, st, grads);
     if (s != PR_OK)
         return s;
     pr_params prm = default_params(params);
     BatchPlan P;
-    s = plan_batch(views, n, prm, P);
+    s = plan_batch(views, n, prm, P, grads);
     if (s != PR_OK)
         return s;
     for (const auto &o : P.out)
@@ -951,6 +986,12 @@ pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, i
     }
     *out = g;
     return PR_OK;
+}
+
+pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
+                                 void *stream, pr_graph **out)
+{
+    return pr_graph_capture_frame(ws, views, n, params, nullptr, stream, out);
 }
 
 pr_status pr_graph_launch(pr_graph *g, void *stream)

@@ -47,6 +47,7 @@ struct ViewDev {
     const uint32_t *id_in;             // ids read by shading / adjoint
     float *rgb_out;
     const float *grad_in;              // adjoint input [3][H][W]
+    const float *target;               // or: L2 target [3][H][W], gradient 2 (rgb - target) from rgb_out
     float *dcol, *dpos, *dvel;         // adjoint outputs [V][3]
     const float4 *rec;                 // this frame's stage (a) records (batch-wide index), or null
 };

@@ -49,9 +49,11 @@ cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pi
                            const unsigned long long *keys, cudaStream_t st);
 
 // stages (d) and (e)
-cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
-                         cudaStream_t st);
-cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
-                            cudaStream_t st);
+cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
+                         const unsigned long long *keys, cudaStream_t st);
+// frame_cnt: the counters of the frame whose forward ran just before in the
+// same sequence (the adjoint is skipped if it overflowed), or null.
+cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
+                            const Counters *frame_cnt, cudaStream_t st);
 
 }  // namespace pr

@@ -100,8 +100,10 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
     return i < v.W && j < v.H;
 }
 
+// keys != null: the frame's packed depth|id keys are resolved here too
+// (id and depth written, then shaded), saving the separate resolve pass.
 __global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ blk_offs,
-                        long long nthreads)
+                        long long nthreads, const unsigned long long *__restrict__ keys)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nthreads)
@@ -111,10 +113,21 @@ __global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const lon
     if (!block_pixel(views, nviews, blk_offs, g, vp, lin))
         return;
     const ViewDev &v = *vp;
+    unsigned id;
+    if (keys) {
+        const unsigned long long key = keys[v.pix_off + lin];
+        const bool bg = key == ~0ull;
+        id = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
+        if (v.id_out)
+            v.id_out[lin] = id;
+        if (v.depth_out)
+            v.depth_out[lin] = bg ? INFINITY : __uint_as_float((unsigned)(key >> 32));
+    } else {
+        id = v.id_in[lin];
+    }
     if (!v.rgb_out)
         return;
     const long long plane = (long long)v.W * v.H;
-    const unsigned id = v.id_in[lin];
     if (id >= (unsigned)v.T) {
         v.rgb_out[lin] = 0.f;
         v.rgb_out[plane + lin] = 0.f;
@@ -132,11 +145,11 @@ __global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const lon
 }
 
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         cudaStream_t st)
+                         const unsigned long long *keys, cudaStream_t st)
 {
     const long long n = nblocks * 32;
     if (n > 0)
-        k_shade<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n);
+        k_shade<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, keys);
     return cudaGetLastError();
 }
 
@@ -161,19 +174,25 @@ __device__ __forceinline__ float warp_sum(float x)
 // the lanes that see it with a reduce-scatter (lane l ends with the sum of
 // value l) and added with one 27-lane atomic instruction.
 __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ views, int nviews,
-                                                 const long long *__restrict__ blk_offs, long long nthreads)
+                                                 const long long *__restrict__ blk_offs, long long nthreads,
+                                                 const Counters *__restrict__ frame_cnt)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if ((g & ~31ll) >= nthreads)
         return;  // whole warps only
+    // in a training frame: a forward that overflowed is rerun by the host,
+    // so its adjoint must not accumulate
+    if (frame_cnt && (frame_cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS | ST_TIMEOUT)))
+        return;
     const ViewDev *vp = views;
     long long lin = 0;
     const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin);
     const ViewDev &v = *vp;
     unsigned id = 0xFFFFFFFFu;
-    if (inside)
+    const bool wants = v.grad_in || v.target;  // views of a batch without a gradient are skipped
+    if (inside && wants)
         id = v.id_in[lin];
-    const bool valid = inside && id < (unsigned)v.T;
+    const bool valid = inside && wants && id < (unsigned)v.T;
     float gc[3][3], gp[3][3], gvel[3][3];
     int vid[3] = {0, 0, 0};
     for (int k = 0; k < 3; ++k)
@@ -183,7 +202,17 @@ __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ vi
         const long long plane = (long long)v.W * v.H;
         PixelHit h;
         pixel_hit(v, lin, id, h);
-        const float g0 = v.grad_in[lin], g1 = v.grad_in[plane + lin], g2 = v.grad_in[2 * plane + lin];
+        float g0, g1, g2;
+        if (v.target) {
+            // L2 loss sum (rgb - target)^2: its gradient from this frame's image
+            g0 = 2.f * (v.rgb_out[lin] - v.target[lin]);
+            g1 = 2.f * (v.rgb_out[plane + lin] - v.target[plane + lin]);
+            g2 = 2.f * (v.rgb_out[2 * plane + lin] - v.target[2 * plane + lin]);
+        } else {
+            g0 = v.grad_in[lin];
+            g1 = v.grad_in[plane + lin];
+            g2 = v.grad_in[2 * plane + lin];
+        }
         vid[0] = h.ia;
         vid[1] = h.ib;
         vid[2] = h.ic;
@@ -287,11 +316,11 @@ __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ vi
 }
 
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                            cudaStream_t st)
+                            const Counters *frame_cnt, cudaStream_t st)
 {
     const long long n = nblocks * 32;
     if (n > 0)
-        k_backward<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n);
+        k_backward<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, frame_cnt);
     return cudaGetLastError();
 }
 

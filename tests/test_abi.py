@@ -48,9 +48,10 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pr_view), offsetof(pr_view, pose0),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pr_view), offsetof(pr_view, pose0),
          offsetof(pr_view, light_w), sizeof(pr_params), sizeof(pr_stats), sizeof(pr_batch_view),
-         offsetof(pr_batch_view, id_out), offsetof(pr_batch_view, tile));
+         offsetof(pr_batch_view, id_out), offsetof(pr_batch_view, tile), sizeof(pr_frame_grad),
+         offsetof(pr_frame_grad, dvel), sizeof(pr_backward_view), offsetof(pr_backward_view, dvel));
   return 0;
 }}
 """)
@@ -58,7 +59,9 @@ int main(void) {{
     subprocess.run(["gcc", str(prog), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(B.PrView), B.PrView.pose0.offset, B.PrView.light_w.offset, C.sizeof(B.PrParams),
-            C.sizeof(B.PrStats), C.sizeof(B.PrBatchView), B.PrBatchView.id_out.offset, B.PrBatchView.tile.offset]
+            C.sizeof(B.PrStats), C.sizeof(B.PrBatchView), B.PrBatchView.id_out.offset, B.PrBatchView.tile.offset,
+            C.sizeof(B.PrFrameGrad), B.PrFrameGrad.dvel.offset, C.sizeof(B.PrBackwardView),
+            B.PrBackwardView.dvel.offset]
     assert got == want
 
 
@@ -77,6 +80,8 @@ def test_invalid_arguments_are_statuses_not_crashes(lib):
     assert lib.pr_shade(None, None, None, None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_backward(None, None, None, None, None, None, None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_rasterize_batch(None, None, 0, None, None) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_frame_batch(None, None, 0, None, None, None) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_graph_capture_frame(None, None, 0, None, None, None, C.byref(h)) == B.PR_ERR_INVALID_ARG
 
 
 def test_no_device_is_reported(lib):

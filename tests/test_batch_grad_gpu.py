@@ -227,3 +227,127 @@ def test_backward_batch_equals_per_view(pr):
         pr.pr_workspace_free(ws)
         for h in handles:
             pr.pr_scene_free(h)
+
+
+def _frame_setup(pr, cases):
+    import torch
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+    outs, entries = [], []
+    for h, (sc, v, tile) in zip(handles, cases):
+        n = v.W * v.H
+        o = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, device="cuda"),
+             torch.empty(3 * n, device="cuda"))
+        outs.append(o)
+        entries.append((h, v, o[0], o[1], o[2], tile))
+    return handles, outs, entries
+
+
+def test_frame_batch_equals_forward_then_adjoint(pr):
+    """The training frame's forward is the batched forward bit for bit; its
+    adjoint (for the views given a gradient, upstream gradient or L2 target)
+    equals the separate adjoint call up to the order of float atomics."""
+    import torch
+    cases = _views_mixed()
+    handles, outs, entries = _frame_setup(pr, cases)
+    ws, ws2 = pr.pr_workspace_create(), pr.pr_workspace_create()
+    try:
+        rng = np.random.default_rng(11)
+        grads, want = [], []
+        for k, (sc, v, tile) in enumerate(cases):
+            n = v.W * v.H
+            d = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            if k == 1:
+                grads.append(None)            # a view of the batch without a gradient
+            elif k == 3:
+                grads.append(dict(target_rgb=_dev(rng.uniform(size=3 * n).astype(np.float32)), dcol=d[0],
+                                  dpos=d[1], dvel=d[2]))
+            else:
+                grads.append(dict(grad_rgb=_dev(rng.normal(size=3 * n).astype(np.float32)), dcol=d[0], dpos=d[1],
+                                  dvel=d[2]))
+        pr.pr_frame_batch(ws, entries, grads)
+        ref_outs, ref_entries = [], []
+        for h, (sc, v, tile) in zip(handles, cases):
+            n = v.W * v.H
+            o = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, device="cuda"),
+                 torch.empty(3 * n, device="cuda"))
+            ref_outs.append(o)
+            ref_entries.append((h, v, o[0], o[1], o[2], tile))
+        pr.pr_rasterize_batch(ws2, ref_entries)
+        for o, r in zip(outs, ref_outs):
+            assert all(torch.equal(a, b) for a, b in zip(o, r))
+        bwd = []
+        for k, (h, (sc, v, tile), o) in enumerate(zip(handles, cases, ref_outs)):
+            if grads[k] is None:
+                continue
+            g = grads[k]["grad_rgb"] if "grad_rgb" in grads[k] else 2.0 * (o[2] - grads[k]["target_rgb"])
+            d = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            bwd.append((h, v, o[0], g, *d))
+            want.append((k, d))
+        pr.pr_backward_batch(ws2, bwd)
+        for k, d in want:
+            got = (grads[k]["dcol"], grads[k]["dpos"], grads[k]["dvel"])
+            for x, y in zip(got, d):
+                assert torch.allclose(x, y, rtol=1e-4, atol=1e-5 * float(y.abs().max()) + 1e-12)
+            assert float(got[0].abs().sum()) > 0
+    finally:
+        pr.pr_workspace_free(ws)
+        pr.pr_workspace_free(ws2)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
+def test_frame_graph_replays_eager_frame(pr):
+    """forward + L2-loss gradient + adjoint as one graph: a replay with the
+    gradient buffers zeroed reproduces the eager frame."""
+    import torch
+    cases = _views_mixed()[1:4]
+    stream = torch.cuda.Stream()
+    handles, outs, entries = _frame_setup(pr, cases)
+    ws = pr.pr_workspace_create()
+    try:
+        with torch.cuda.stream(stream):
+            rng = np.random.default_rng(5)
+            grads = []
+            for sc, v, _ in cases:
+                d = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+                grads.append(dict(target_rgb=_dev(rng.uniform(size=3 * v.W * v.H).astype(np.float32)), dcol=d[0],
+                                  dpos=d[1], dvel=d[2]))
+            pr.pr_frame_batch(ws, entries, grads)
+            eager_out = [tuple(x.clone() for x in o) for o in outs]
+            eager_d = [tuple(g[n].clone() for n in ("dcol", "dpos", "dvel")) for g in grads]
+            graph = pr.pr_graph_capture_frame(ws, entries, grads)   # runs the frame once more, eagerly
+            for rep in range(2):
+                for g in grads:
+                    for n in ("dcol", "dpos", "dvel"):
+                        g[n].zero_()
+                for o in outs:
+                    for x in o:
+                        x.fill_(3)
+                pr.pr_graph_launch(graph)
+                stream.synchronize()
+                for o, r in zip(outs, eager_out):
+                    assert all(torch.equal(a, b) for a, b in zip(o, r))
+                for g, r in zip(grads, eager_d):
+                    for n, y in zip(("dcol", "dpos", "dvel"), r):
+                        assert torch.allclose(g[n], y, rtol=1e-4, atol=1e-5 * float(y.abs().max()) + 1e-12)
+            pr.pr_graph_free(graph)
+    finally:
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
+def test_frame_gradient_rejects_host_buffers(pr):
+    import torch
+    cases = _views_mixed()[:1]
+    handles, outs, entries = _frame_setup(pr, cases)
+    ws = pr.pr_workspace_create()
+    try:
+        sc, v, _ = cases[0]
+        host_target = torch.zeros(3 * v.W * v.H)
+        with pytest.raises(pr.PrError):
+            pr.pr_frame_batch(ws, entries, [dict(target_rgb=host_target)])
+    finally:
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
