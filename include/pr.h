@@ -102,7 +102,7 @@ typedef struct {
     int32_t bound;        /* pr_bound */
     int32_t tile;         /* bin tile side in pixels: 8, 16 or 32; 0 = library default (16) */
     int32_t fp64_retest;  /* 1: re-test fragments flagged by the FP32 error bound in FP64 */
-    int32_t seg;          /* triangles per fragment work item; 0 = default */
+    int32_t seg;          /* triangles per fragment work item; 0 = default (256), at most 1024 */
 } pr_params;
 
 /* Counters of the last rasterize call on a scene or workspace. */

@@ -128,7 +128,7 @@ constexpr int kDefaultSeg = 256;
 
 // Scratch of one batched frame.
 struct pr_workspace {
-    DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, tile_tris, items, keys, counters, heads;
+    DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, pairs, items, keys, counters, heads;
     DevBuf cand, cand_off;         // candidate tiles per triangle and their prefix sum
     DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
     DevBuf stage;                  // device copies of host-side outputs
@@ -291,6 +291,7 @@ pr_params default_params(const pr_params *p)
             d.tile = kDefaultTile;
         if (d.seg <= 0)
             d.seg = kDefaultSeg;
+        d.seg = std::min(d.seg, kMaxSeg);
     }
     return d;
 }
@@ -433,10 +434,10 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->heads, sizeof(int) * 8));
     PR_TRY(ensure(ws->stage, std::max<size_t>(P.stage_bytes, 256)));
     const long long want_pairs = std::max(ws->cap_pairs, 2 * P.ttot + P.ntiles + 1024);
-    if ((size_t)want_pairs * sizeof(unsigned) > ws->tile_tris.cap || !ws->tile_tris.p) {
-        PR_TRY(ensure(ws->tile_tris, sizeof(unsigned) * want_pairs));
+    if ((size_t)want_pairs * sizeof(unsigned long long) > ws->pairs.cap || !ws->pairs.p) {
+        PR_TRY(ensure(ws->pairs, sizeof(unsigned long long) * want_pairs));
     }
-    ws->cap_pairs = (long long)(ws->tile_tris.cap / sizeof(unsigned));
+    ws->cap_pairs = (long long)(ws->pairs.cap / sizeof(unsigned long long));
     const long long want_items = std::max(ws->cap_items, ws->cap_pairs / seg + P.ntiles + 1024);
     if ((size_t)want_items * sizeof(int4) > ws->items.cap || !ws->items.p) {
         PR_TRY(ensure(ws->items, sizeof(int4) * want_items));
@@ -512,22 +513,24 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
     PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, st));
     PR_TRY(launch_bin_scatter(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, scan,
-                              ws->fill.as<unsigned>(), ws->tile_tris.as<unsigned>(), ws->cap_pairs, cnt, st));
+                              ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,
                         ws->cap_pairs, seg, cnt, st));
+    PR_TRY(launch_sort_items(ws->items.as<int4>(), scan, P.ntiles, ws->cap_items, ws->pairs.as<unsigned long long>(),
+                             st));
     PR_TRY(mark(2));
     int *heads = ws->heads.as<int>();
     for (size_t c = 0; c < P.classes.size(); ++c) {
         const auto &cl = P.classes[c];
         PR_TRY(launch_fragment(cl.S, cl.fp64, dv, ws->items.as<int4>(), scan, cl.tile_lo, cl.tile_hi, ws->cap_items,
-                               heads + c, ws->tile_tris.as<unsigned>(), rec, ws->keys.as<unsigned long long>(),
+                               heads + c, ws->pairs.as<unsigned long long>(), rec, ws->keys.as<unsigned long long>(),
                                ws->flag_bits.as<unsigned>(), ws->flag_list.as<long long>(), cnt,
                                fragment_grid(cl.S, cl.fp64), st));
     }
     PR_TRY(mark(3));
     if (P.any_fp64)
-        PR_TRY(launch_retest(dv, n, pix_offs, scan, tile_cnt, ws->tile_tris.as<unsigned>(), rec,
-                             ws->flag_list.as<long long>(), ws->keys.as<unsigned long long>(), cnt, st));
+        PR_TRY(launch_retest(dv, n, pix_offs, scan, tile_cnt, ws->pairs.as<unsigned long long>(), rec,
+                             ws->flag_list.as<long long>(), ws->keys.as<unsigned long long>(), ws->cap_pairs, cnt, st));
     PR_TRY(mark(4));
     if (!shade)
         PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
@@ -1070,11 +1073,7 @@ pr_status pr_debug_bounds(const pr_scene *sc, int32_t *pix_box, float *t_range)
         pix_box[4 * k + 0] = b.x & 0xffff;
         pix_box[4 * k + 1] = b.y & 0xffff;
         pix_box[4 * k + 2] = (b.x >> 16) & 0xffff;
-        pix_box[4 * k + 3] = (b.y >> 16) & 0xffff;
-        if (b.w) {
-            pix_box[4 * k + 0] = 1;
-            pix_box[4 * k + 2] = 0;
-        }
+        pix_box[4 * k + 3] = (b.y >> 16) & 0xffff;  // a culled triangle has the empty box [1, 0]
         t_range[2 * k + 0] = rec[k * kRecF4 + 5].x;
         t_range[2 * k + 1] = rec[k * kRecF4 + 5].y;
     }

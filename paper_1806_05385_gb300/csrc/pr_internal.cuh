@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/pr.h"
 
@@ -14,6 +15,7 @@ constexpr float kEpsDisp = 1e-5f;                  // display-space safety margi
 constexpr float kEpsT = 1e-4f;                     // time margin of every catch-up interval
 constexpr int kMaxHp = 8;                          // half-planes per bound: <= 6 hull edges + 2 time-strip edges
 constexpr int kRecF4 = 6;                          // float4 per fragment record
+constexpr int kMaxSeg = 1024;                      // longest bin run of one work item (pr_params.seg)
 
 // Device status bits (Counters::status).
 enum : uint32_t {
@@ -126,6 +128,22 @@ __device__ __forceinline__ float2 project(const ViewDev &v, float3 p)
 {
     float iz = 1.0f / p.z;
     return make_float2(fmaf(0.5f * p.x * iz, 1.0f / v.tan_x, 0.5f), fmaf(0.5f * p.y * iz, 1.0f / v.tan_y, 0.5f));
+}
+
+// A float as an unsigned integer of the same order (negative values
+// included), and back: the depth sort key of the bin pairs.
+__host__ __device__ __forceinline__ uint32_t depth_order_key(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u ^ ((u >> 31) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__host__ __device__ __forceinline__ float depth_from_order_key(uint32_t u)
+{
+    u ^= (u >> 31) ? 0x80000000u : 0xFFFFFFFFu;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
 }
 
 // Packed visibility key: FP32 depth bits (positive floats order as their

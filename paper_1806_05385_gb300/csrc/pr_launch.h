@@ -30,21 +30,25 @@ size_t scan_block_sums_needed(long long n);
 cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                                const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
                                const int4 *tbox, const float4 *tile_box, const unsigned long long *scan,
-                               unsigned int *fill, unsigned int *tile_tris, long long cap_pairs, Counters *cnt,
+                               unsigned int *fill, unsigned long long *pairs, long long cap_pairs, Counters *cnt,
                                cudaStream_t st);
 cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
                          const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
                          long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);
+// sorts every item's run of bin entries (nearest first); runs <= kMaxSeg
+cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
+                              unsigned long long *pairs, cudaStream_t st);
 
 // stage (c): per-fragment ray casting, FP64 re-test, resolve
 cudaError_t launch_fragment(int S, bool flag, const ViewDev *views, const int4 *items, const unsigned long long *scan,
                             long long tile_lo, long long tile_hi, long long cap_items, int *head,
-                            const unsigned int *tile_tris, const float4 *rec, unsigned long long *keys,
+                            const unsigned long long *pairs, const float4 *rec, unsigned long long *keys,
                             unsigned *flag_bits, long long *flag_list, Counters *cnt, int grid, cudaStream_t st);
 int fragment_grid(int S, bool flag);
 cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix_offs, const unsigned long long *scan,
-                          const unsigned long long *tile_cnt, const unsigned *tile_tris, const float4 *rec,
-                          const long long *flag_list, unsigned long long *keys, Counters *cnt, cudaStream_t st);
+                          const unsigned long long *tile_cnt, const unsigned long long *pairs, const float4 *rec,
+                          const long long *flag_list, unsigned long long *keys, long long cap_pairs, Counters *cnt,
+                          cudaStream_t st);
 cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
                            const unsigned long long *keys, cudaStream_t st);
 

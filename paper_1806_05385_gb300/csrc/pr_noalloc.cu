@@ -185,7 +185,7 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     cudaStream_t st = (cudaStream_t)stream;
     const int tile = params && params->tile ? params->tile : 16;
     const int bound = params ? params->bound : PR_BOUND_ZENON;
-    const int seg = params && params->seg > 0 ? params->seg : 256;
+    const int seg = std::min(params && params->seg > 0 ? params->seg : 256, kMaxSeg);
 
     void *base = nullptr;
     NA_TRY(scratch_address(&base));
@@ -211,11 +211,11 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     // the rest: work items and bin entries
     const long long rest = (long long)kNoAllocBytes - (long long)((c.off + 255) & ~(size_t)255) - 512;
     const long long item_fixed = nt + 1024;
-    if (rest < (long long)(16 * item_fixed + 4 * (2 * Tn + nt)))
+    if (rest < (long long)(16 * item_fixed + 8 * (2 * Tn + nt)))
         return PR_ERR_INVALID_ARG;  // too little room left for the bins of this frame
-    const long long cap_pairs = (rest - 16 * item_fixed) / (4 + 16 / seg + 1);
+    const long long cap_pairs = (rest - 16 * item_fixed) / (8 + 16 / seg + 1);
     const long long cap_items = item_fixed + cap_pairs / seg + 1;
-    const size_t o_items = c.take(sizeof(int4) * cap_items), o_tris = c.take(4 * cap_pairs);
+    const size_t o_items = c.take(sizeof(int4) * cap_items), o_tris = c.take(8 * cap_pairs);
     if (!c.ok)
         return PR_ERR_INVALID_ARG;
 
@@ -237,7 +237,8 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     unsigned long long *tile_cnt = (unsigned long long *)(arena + o_tile_cnt), *scan = (unsigned long long *)(arena + o_scan);
     float4 *rec = (float4 *)(arena + o_rec), *hp = (float4 *)(arena + o_hp), *tile_box = (float4 *)(arena + o_tile_box);
     int4 *tbox = (int4 *)(arena + o_tbox), *items = (int4 *)(arena + o_items);
-    unsigned *fill = (unsigned *)(arena + o_fill), *tile_tris = (unsigned *)(arena + o_tris);
+    unsigned *fill = (unsigned *)(arena + o_fill);
+    unsigned long long *pairs = (unsigned long long *)(arena + o_tris);
     unsigned long long *sums = (unsigned long long *)(arena + o_sums), *keys = (unsigned long long *)(arena + o_keys);
 
     // host-side constants go up by plain (pageable) copies; they complete
@@ -260,10 +261,11 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_scan(cand, cand_off, sums, T, 0, st));
     NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
     NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, st));
-    NA_TRY(launch_bin_scatter(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, scan, fill, tile_tris,
+    NA_TRY(launch_bin_scatter(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, scan, fill, pairs,
                               cap_pairs, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
-    NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, tile_tris, rec, keys, nullptr,
+    NA_TRY(launch_sort_items(items, scan, nt, cap_items, pairs, st));
+    NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, pairs, rec, keys, nullptr,
                            nullptr, cnt, fragment_grid(tile, false), st));
     NA_TRY(launch_resolve(dv, 1, pix_offs, np, keys, st));
     Counters h;

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views
     if (B.culled) {
         r[4] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
         r[5] = make_float4(INFINITY, -INFINITY, D[2].y, D[2].z);
-        tbox[g] = make_int4(1, 1, 0, 1);
+        tbox[g] = make_int4(1, 1, 0, 0);  // the empty box [1, 0] x [1, 0]
         cand[g] = 0ull;
         atomicAdd(&cnt->culled, 1ull);
         return;
@@ -403,7 +403,11 @@ __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views
     r[5] = make_float4(B.tmin - kEpsT, B.tmax + kEpsT, D[2].y, D[2].z);
     for (int h = 0; h < B.nhp; ++h)
         hp[g * kMaxHp + h] = B.hp[h];
-    tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), B.nhp, 0);
+    // nearest camera depth the moving triangle reaches (z is linear in t on
+    // every vertex): min_k S_k.z + min(0, D_k.z), the sort key of its pairs
+    const float near = fminf(fminf(S[0].z + fminf(0.f, D[0].z), S[1].z + fminf(0.f, D[1].z)),
+                             S[2].z + fminf(0.f, D[2].z));
+    tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), B.nhp, (int)depth_order_key(near));
     cand[g] = (unsigned long long)(B.i1 / v.S - B.i0 / v.S + 1) * (unsigned long long)(B.j1 / v.S - B.j0 / v.S + 1);
 }
 
@@ -442,7 +446,8 @@ __device__ __forceinline__ bool tile_meets(const float4 tb, const float4 bb, con
 // magnifies, or close to the camera -- span thousands of tiles.
 // tile_cnt[tile] = number of triangles whose region meets the tile;
 // appends are warp-aggregated (lanes that hit the same tile share one
-// atomic).
+// atomic).  A bin entry is (depth order key of the triangle << 32) | its
+// batch-wide index, so that sorting entries sorts by nearest depth.
 __device__ __forceinline__ long long owner_of(const unsigned long long *cand_off, long long ttot, long long p)
 {
     long long lo = 0, hi = ttot - 1;
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                                              const int4 *__restrict__ tbox, const float4 *__restrict__ tile_box,
                                              unsigned long long *__restrict__ tile_cnt,
                                              const unsigned long long *__restrict__ scan, unsigned int *__restrict__ fill,
-                                             unsigned int *__restrict__ tile_tris, long long cap_pairs, Counters *cnt)
+                                             unsigned long long *__restrict__ pairs, long long cap_pairs, Counters *cnt)
 {
     const long long total = (long long)cand_off[ttot];
     const int lane = threadIdx.x & 31;
@@ -475,9 +480,11 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
         const long long p = pw + lane;
         bool hit = false;
         long long tile = -1, g = -1;
+        unsigned key = 0u;
         if (p < total) {
             g = owner_of(cand_off, ttot, p);
             const int4 tb = tbox[g];
+            key = (unsigned)tb.w;
             const ViewDev &v = views[find_view(tri_offs, nviews, g)];
             const int tx0 = (tb.x & 0xffff) / v.S, tx1 = (tb.x >> 16) / v.S;
             const int ty0 = (tb.y & 0xffff) / v.S;
@@ -505,7 +512,7 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
             const unsigned rank = __popc(peers & ((1u << lane) - 1u));
             const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
             if (pos < cap_pairs)
-                tile_tris[pos] = (unsigned)g;
+                pairs[pos] = ((unsigned long long)key << 32) | (unsigned long long)g;
             else
                 atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
         }
@@ -537,12 +544,12 @@ cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *
 cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                                const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
                                const int4 *tbox, const float4 *tile_box, const unsigned long long *scan,
-                               unsigned int *fill, unsigned int *tile_tris, long long cap_pairs, Counters *cnt,
+                               unsigned int *fill, unsigned long long *pairs, long long cap_pairs, Counters *cnt,
                                cudaStream_t st)
 {
     if (ttot > 0)
         k_bin<true><<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box,
-                                                nullptr, scan, fill, tile_tris, cap_pairs, cnt);
+                                                nullptr, scan, fill, pairs, cap_pairs, cnt);
     return cudaGetLastError();
 }
 
@@ -681,6 +688,83 @@ __global__ void k_items(const ViewDev *__restrict__ views, int nviews, const lon
         else
             atomicOr(&cnt->status, ST_OVERFLOW_ITEMS);
     }
+}
+
+// Sorts the bin run of every work item (at most kMaxSeg entries) by its
+// entries, i.e. nearest triangle first, so the fragment stage can stop a
+// run at the first triangle that lies behind every pixel of its block.
+// One warp per item: a run of up to 32 entries is sorted in registers with
+// a bitonic network over the lanes; a longer one in the warp's shared
+// memory, padded to a power of two.
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__restrict__ items,
+                                                                const unsigned long long *__restrict__ scan,
+                                                                long long ntiles, long long cap_items,
+                                                                unsigned long long *__restrict__ pairs)
+{
+    __shared__ unsigned long long s_run[kSortWarps][kMaxSeg];
+    const long long nitems = min((long long)(scan[ntiles] >> 40), cap_items);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long *run = s_run[w];
+    const long long nwarps = (long long)gridDim.x * kSortWarps;
+    for (long long it = (long long)blockIdx.x * kSortWarps + w; it < nitems; it += nwarps) {
+        const int4 item = items[it];
+        const int n = item.w - item.z;
+        unsigned long long *e = pairs + item.z;
+        if (n <= 1)
+            continue;
+        if (n <= 32) {
+            unsigned long long x = lane < n ? e[lane] : ~0ull;
+            for (int k = 2; k <= 32; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+                    // the lower lane of a pair keeps the smaller value in an
+                    // ascending block, the larger in a descending one
+                    const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+                    x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+                }
+            if (lane < n)
+                e[lane] = x;
+            continue;
+        }
+        int P = 64;
+        while (P < n)
+            P <<= 1;
+        for (int q = lane; q < P; q += 32)
+            run[q] = q < n ? e[q] : ~0ull;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int q = lane; q < P / 2; q += 32) {
+                    // q-th compare-exchange pair of this step: (i, i + j)
+                    const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                    const unsigned long long a = run[i], b = run[i + j];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        run[i] = b;
+                        run[i + j] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        for (int q = lane; q < n; q += 32)
+            e[q] = run[q];
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
+                              unsigned long long *pairs, cudaStream_t st)
+{
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = sms * 8;
+    }
+    k_sort_items<<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,

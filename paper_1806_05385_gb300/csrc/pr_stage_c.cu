@@ -6,11 +6,13 @@
 // from a global atomic queue.  One CTA covers one S x S tile; each warp owns
 // an 8 x 8 pixel block and each lane two pixels of one column (rows r and
 // r + 4), so under a horizontal rolling scan both pixels share one time.
-// The CTA stages the records of a run of binned triangles in shared memory;
-// every warp first tests the triangle's display box and time interval
-// against its block (warp-uniform skip), then each lane runs the watertight
-// test for its pixels.  Per pixel the nearest key is kept in a register and
-// merged into the frame with one 64-bit atomicMin per item.
+// The bin run of an item comes sorted by nearest depth (stage b).  Every
+// warp walks it on its own, 32 entries at a time: the lanes screen the
+// entries against the block (depth cut, display box, time interval) while
+// the records stream into the warp's shared memory, then the warp runs the
+// watertight test for the survivors, each lane for its two pixels.  Per
+// pixel the nearest key is kept in a register and merged into the frame
+// with one 64-bit atomicMin per item.
 #include "pr_launch.h"
 
 namespace pr {
@@ -96,17 +98,12 @@ __device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const
     }
 }
 
-// Build-time knobs of the fragment kernel: the occupancy it is compiled for
-// (resident warps per SM, which caps registers) and the unroll of its
-// triangle loop.
+// Build-time knob of the fragment kernel: the occupancy it is compiled for
+// (resident warps per SM, which caps registers).
 #ifndef PR_FRAG_WARPS
 #define PR_FRAG_WARPS 32
 #endif
 #define PR_FRAG_MINB(nt) (PR_FRAG_WARPS > 0 ? (PR_FRAG_WARPS * 32) / (nt) : 1)
-#ifndef PR_FRAG_UNROLL
-#define PR_FRAG_UNROLL 2
-#endif
-constexpr int kFragUnroll = PR_FRAG_UNROLL;
 
 // Marks pixel g for the FP64 re-test (once: a bitmap de-duplicates the
 // pixels that several items flag) and appends it to the flag list.
@@ -119,40 +116,64 @@ __device__ __forceinline__ void flag_pixel(long long g, unsigned *flag_bits, lon
     }
 }
 
+// Order-preserving int image of a float (and back), for warp min/max
+// reductions of float values with the integer redux instruction.
+__device__ __forceinline__ int fkey(float f)
+{
+    const int i = __float_as_int(f);
+    return i ^ ((i >> 31) & 0x7FFFFFFF);
+}
+__device__ __forceinline__ float funkey(int i) { return __int_as_float(i ^ ((i >> 31) & 0x7FFFFFFF)); }
+__device__ __forceinline__ float warp_minf(float x) { return funkey(__reduce_min_sync(0xffffffffu, fkey(x))); }
+__device__ __forceinline__ float warp_maxf(float x) { return funkey(__reduce_max_sync(0xffffffffu, fkey(x))); }
+
+// 16-byte asynchronous global -> shared copy (L1-cached), and the wait for
+// all of this thread's copies.
+__device__ __forceinline__ void copy16_async(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Records staged per warp and triangle: S and D of the three vertices
+// (float4 0-3 of the record) and the time interval / D2yz float4 (5).
+constexpr int kStageF4 = 5;
+
 template <int S, bool kFlag>
 __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
     k_fragment(const ViewDev *__restrict__ views, const int4 *__restrict__ items,
                const unsigned long long *__restrict__ scan, long long tile_lo, long long tile_hi, long long cap_items,
-               int *__restrict__ head, const unsigned int *__restrict__ tile_tris, const float4 *__restrict__ rec,
+               int *__restrict__ head, const unsigned long long *__restrict__ pairs, const float4 *__restrict__ rec,
                unsigned long long *__restrict__ keys, unsigned *__restrict__ flag_bits,
                long long *__restrict__ flag_list, Counters *cnt)
 {
     constexpr int NT = S * S / 2;  // threads: two pixels each
     constexpr int NW = NT / 32;    // warps
     constexpr int WPR = S / 8;     // 8x8 warp blocks per tile row
-    constexpr int CH = NT >= 128 ? 128 : 64;  // triangles staged per chunk (smaller for one-warp CTAs)
-    __shared__ float4 s_raw[CH * kRecF4];  // records as gathered
-    __shared__ unsigned s_rid[CH];
-    __shared__ float s_rkey[CH];
-    __shared__ float4 s_rec[CH * kRecF4];  // the same records, nearest first
-    __shared__ unsigned s_id[CH];
-    __shared__ float s_key[CH];
-    __shared__ long long s_item;
+    __shared__ float4 s_rec[NW][32 * kStageF4];  // per warp: the records of its current 32 candidates
+    __shared__ long long s_item[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ci = (warp % WPR) * 8 + (lane & 7);
     const int cj0 = (warp / WPR) * 8 + (lane >> 3), cj1 = cj0 + 4;
     const long long it_lo = (long long)(scan[tile_lo] >> 40);
     const long long it_hi = min((long long)(scan[tile_hi] >> 40), cap_items);
+    float4 *wrec = s_rec[warp];
     unsigned long long n_tests = 0, n_hits = 0;
 
-    for (;;) {
-        if (threadIdx.x == 0)
-            s_item = it_lo + atomicAdd(head, 1);
-        __syncthreads();
-        const long long it = s_item;
+    if (threadIdx.x == 0)
+        s_item[0] = it_lo + atomicAdd(head, 1);
+    __syncthreads();
+    for (int par = 0;; par ^= 1) {
+        const long long it = s_item[par];
         if (it >= it_hi)
             break;
+        if (threadIdx.x == 0)  // the next item, fetched while this one runs
+            s_item[par ^ 1] = it_lo + atomicAdd(head, 1);
         const int4 item = items[it];
         const ViewDev &v = views[item.x];
         const int tx = item.y % v.tiles_x, ty = item.y / v.tiles_x;
@@ -162,28 +183,16 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
         pixel_ray(v, min(i, v.W - 1), min(j0, v.H - 1), x00, x01, t0, dx0, dy0);
         pixel_ray(v, min(i, v.W - 1), min(j1, v.H - 1), x10, x11, t1, dx1, dy1);
         // the warp's block in display space and time (valid pixels only)
-        float wx0 = INFINITY, wx1 = -INFINITY, wy0 = INFINITY, wy1 = -INFINITY, wt0 = INFINITY, wt1 = -INFINITY;
-        if (ok0) {
-            wx0 = x00; wx1 = x00; wy0 = x01; wy1 = x01; wt0 = t0; wt1 = t0;
-        }
-        if (ok1) {
-            wx0 = fminf(wx0, x10); wx1 = fmaxf(wx1, x10); wy0 = fminf(wy0, x11); wy1 = fmaxf(wy1, x11);
-            wt0 = fminf(wt0, t1); wt1 = fmaxf(wt1, t1);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
-            wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
-            wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
-            wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
-            wt0 = fminf(wt0, __shfl_xor_sync(0xffffffffu, wt0, o));
-            wt1 = fmaxf(wt1, __shfl_xor_sync(0xffffffffu, wt1, o));
-        }
+        const float wx0 = warp_minf(fminf(ok0 ? x00 : INFINITY, ok1 ? x10 : INFINITY));
+        const float wx1 = warp_maxf(fmaxf(ok0 ? x00 : -INFINITY, ok1 ? x10 : -INFINITY));
+        const float wy0 = warp_minf(fminf(ok0 ? x01 : INFINITY, ok1 ? x11 : INFINITY));
+        const float wy1 = warp_maxf(fmaxf(ok0 ? x01 : -INFINITY, ok1 ? x11 : -INFINITY));
         // with a horizontal scan (d1 = 0) the time strip is already part of
         // every triangle's display box; otherwise test the interval too
-        const bool test_t = is_rolling(v.mode) && v.d1 != 0.f;
-        if (!test_t) {
-            wt0 = -INFINITY;
-            wt1 = INFINITY;
+        float wt0 = -INFINITY, wt1 = INFINITY;
+        if (is_rolling(v.mode) && v.d1 != 0.f) {
+            wt0 = warp_minf(fminf(ok0 ? t0 : INFINITY, ok1 ? t1 : INFINITY));
+            wt1 = warp_maxf(fmaxf(ok0 ? t0 : -INFINITY, ok1 ? t1 : -INFINITY));
         }
         const float zn = v.z_near;
         const unsigned id_base = (unsigned)v.tri_off;
@@ -191,76 +200,62 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
         float bd0 = INFINITY, bd1 = INFINITY;
         unsigned hits = 0, tested = 0;
         bool fl0 = false, fl1 = false;
-        for (int base = item.z; base < item.w; base += CH) {
-            const int n = min(CH, item.w - base);
-            __syncthreads();  // the previous chunk is no longer read
-            // warps gather 32 records at a time: ids coalesced, then the 6
-            // float4 of the 32 records with consecutive lanes on consecutive
-            // float4s
-            for (int w0 = warp * 32; w0 < CH; w0 += NW * 32) {
-                const int q = w0 + lane;
-                const unsigned gid = q < n ? tile_tris[base + q] : 0u;
-                if (q < n)
-                    s_rid[q] = gid;
+        // The run is sorted nearest first (stage b).  Once a triangle cannot
+        // come nearer than every pixel's current best (with a margin for the
+        // FP32 depth; for the precision form also the tie band), no later
+        // one can change a pixel of this warp.  The lanes screen 32 entries
+        // at a time (depth cut, display box, time interval) while their
+        // records stream into the warp's shared memory; the warp then runs
+        // the ray tests for the survivors, in order.
+        const float cull = kFlag ? (1.f + 3.f * kTieRel) : 1.f;
+        for (int k0 = item.z; k0 < item.w; k0 += 32) {
+            float wmax = warp_maxf(fmaxf(ok0 ? bd0 : 0.f, ok1 ? bd1 : 0.f)) * cull;
+            const int kk = k0 + lane;
+            const unsigned long long e = kk < item.w ? pairs[kk] : ~0ull;
+            const float key = depth_from_order_key((unsigned)(e >> 32));
+            const unsigned stopm = __ballot_sync(0xffffffffu, kk >= item.w || key * 0.99999f > wmax);
+            // entries ascend, so every lane from the first stop on stops too
+            const int ncand = stopm ? __ffs(stopm) - 1 : 32;
+            const unsigned gid = (unsigned)e;
+            float d2y = 0.f, d2z = 0.f;
+            bool take = false;
+            if (lane < ncand) {
+                const float4 *r = rec + (size_t)gid * kRecF4;
 #pragma unroll
-                for (int f = 0; f < kRecF4; ++f) {
-                    const int idx = lane + 32 * f, r = idx / kRecF4, fld = idx - r * kRecF4;
-                    const unsigned g = __shfl_sync(0xffffffffu, gid, r);
-                    if (w0 + r < n)
-                        s_raw[(w0 + r) * kRecF4 + fld] = __ldg(&rec[(size_t)g * kRecF4 + fld]);
-                }
+                for (int f = 0; f < 4; ++f)
+                    copy16_async(wrec + lane * kStageF4 + f, r + f);
+                const float4 bb = __ldg(r + 4), tb = __ldg(r + 5);
+                d2y = tb.z;
+                d2z = tb.w;
+                take = !(bb.x > wx1 || bb.y < wx0 || bb.z > wy1 || bb.w < wy0 || tb.x > wt1 || tb.y < wt0);
             }
-            __syncthreads();
-            // nearest possible depth of each triangle over the frame: camera
-            // z is linear on the moving triangle, so min_k S_k.z + min(0, D_k.z)
-            for (int q = threadIdx.x; q < n; q += NT) {
-                const float4 *r = s_raw + q * kRecF4;
-                s_rkey[q] = fminf(fminf(r[0].z + fminf(0.f, r[2].w), r[1].y + fminf(0.f, r[3].z)),
-                                  r[2].x + fminf(0.f, r[5].w));
-            }
-            __syncthreads();
-            // rank sort, nearest first (ties by position), into s_rec
-            for (int q = threadIdx.x; q < n; q += NT) {
-                const float kq = s_rkey[q];
-                int rank = 0;
-                for (int j = 0; j < n; ++j) {
-                    const float kj = s_rkey[j];
-                    rank += (kj < kq) || (kj == kq && j < q);
+            copy_async_wait_all();
+            __syncwarp();
+            unsigned live = __ballot_sync(0xffffffffu, take);
+            bool stop = stopm != 0u;
+            int since = 0;
+            while (live) {
+                const int k = __ffs(live) - 1;
+                live &= live - 1u;
+                if (++since == 8) {  // the bests have moved on: re-check the cut
+                    since = 0;
+                    wmax = warp_maxf(fmaxf(ok0 ? bd0 : 0.f, ok1 ? bd1 : 0.f)) * cull;
+                    if (__shfl_sync(0xffffffffu, key, k) * 0.99999f > wmax) {
+                        stop = true;
+                        break;
+                    }
                 }
-#pragma unroll
-                for (int f = 0; f < kRecF4; ++f)
-                    s_rec[rank * kRecF4 + f] = s_raw[q * kRecF4 + f];
-                s_id[rank] = s_rid[q];
-                s_key[rank] = kq;
-            }
-            __syncthreads();
-            // Front-to-back with early exit: once the next triangle cannot
-            // come nearer than every pixel's current best (with a margin for
-            // the FP32 depth; for the precision form also the tie band), no
-            // later one in this chunk can change a pixel of this warp.
-            const float cull = kFlag ? (1.f + 3.f * kTieRel) : 1.f;
-            float wmax = INFINITY;
-#pragma unroll kFragUnroll
-            for (int k = 0; k < n; ++k) {
-                if ((k & 7) == 0) {
-                    float m = fmaxf(ok0 ? bd0 : 0.f, ok1 ? bd1 : 0.f);
-                    for (int o = 16; o > 0; o >>= 1)
-                        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                    wmax = m * cull;
-                }
-                if (s_key[k] * 0.99999f > wmax)
-                    break;
-                const float4 bb = s_rec[k * kRecF4 + 4];
-                const float4 tb = s_rec[k * kRecF4 + 5];
-                if (bb.x > wx1 || bb.y < wx0 || bb.z > wy1 || bb.w < wy0 || tb.x > wt1 || tb.y < wt0)
-                    continue;
-                const float4 r0 = s_rec[k * kRecF4 + 0], r1 = s_rec[k * kRecF4 + 1];
-                const float4 r2 = s_rec[k * kRecF4 + 2], r3 = s_rec[k * kRecF4 + 3];
-                const unsigned id = s_id[k] - id_base;
+                const float4 r0 = wrec[k * kStageF4 + 0], r1 = wrec[k * kStageF4 + 1];
+                const float4 r2 = wrec[k * kStageF4 + 2], r3 = wrec[k * kStageF4 + 3];
+                const float ky = __shfl_sync(0xffffffffu, d2y, k), kz = __shfl_sync(0xffffffffu, d2z, k);
+                const unsigned id = __shfl_sync(0xffffffffu, gid, k) - id_base;
                 ++tested;
-                ray_test<kFlag>(r0, r1, r2, r3, tb.z, tb.w, t0, dx0, dy0, zn, id, best0, bd0, hits, fl0);
-                ray_test<kFlag>(r0, r1, r2, r3, tb.z, tb.w, t1, dx1, dy1, zn, id, best1, bd1, hits, fl1);
+                ray_test<kFlag>(r0, r1, r2, r3, ky, kz, t0, dx0, dy0, zn, id, best0, bd0, hits, fl0);
+                ray_test<kFlag>(r0, r1, r2, r3, ky, kz, t1, dx1, dy1, zn, id, best1, bd1, hits, fl1);
             }
+            if (stop)
+                break;
+            __syncwarp();  // the staged records are no longer read
         }
         n_tests += (unsigned long long)tested * (unsigned)(ok0 + ok1);
         n_hits += hits;
@@ -275,7 +270,7 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
             if (ok1 && fl1)
                 flag_pixel(g1, flag_bits, flag_list, cnt);
         }
-        __syncthreads();
+        __syncthreads();  // s_item[par ^ 1] is written; s_item[par] may be reused
     }
     for (int o = 16; o > 0; o >>= 1) {
         n_tests += __shfl_xor_sync(0xffffffffu, n_tests, o);
@@ -311,22 +306,22 @@ int fragment_grid(int S, bool flag)
 template <bool kFlag>
 static cudaError_t launch_fragment_t(int S, const ViewDev *views, const int4 *items, const unsigned long long *scan,
                                      long long tile_lo, long long tile_hi, long long cap_items, int *head,
-                                     const unsigned int *tile_tris, const float4 *rec, unsigned long long *keys,
+                                     const unsigned long long *pairs, const float4 *rec, unsigned long long *keys,
                                      unsigned *flag_bits, long long *flag_list, Counters *cnt, int grid,
                                      cudaStream_t st)
 {
     switch (S) {
     case 8:
-        k_fragment<8, kFlag><<<grid, 32, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head, tile_tris,
+        k_fragment<8, kFlag><<<grid, 32, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head, pairs,
                                                   rec, keys, flag_bits, flag_list, cnt);
         break;
     case 16:
         k_fragment<16, kFlag><<<grid, 128, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head,
-                                                    tile_tris, rec, keys, flag_bits, flag_list, cnt);
+                                                    pairs, rec, keys, flag_bits, flag_list, cnt);
         break;
     case 32:
         k_fragment<32, kFlag><<<grid, 512, 0, st>>>(views, items, scan, tile_lo, tile_hi, cap_items, head,
-                                                    tile_tris, rec, keys, flag_bits, flag_list, cnt);
+                                                    pairs, rec, keys, flag_bits, flag_list, cnt);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -336,13 +331,13 @@ static cudaError_t launch_fragment_t(int S, const ViewDev *views, const int4 *it
 
 cudaError_t launch_fragment(int S, bool flag, const ViewDev *views, const int4 *items, const unsigned long long *scan,
                             long long tile_lo, long long tile_hi, long long cap_items, int *head,
-                            const unsigned int *tile_tris, const float4 *rec, unsigned long long *keys,
+                            const unsigned long long *pairs, const float4 *rec, unsigned long long *keys,
                             unsigned *flag_bits, long long *flag_list, Counters *cnt, int grid, cudaStream_t st)
 {
     if (flag)
-        return launch_fragment_t<true>(S, views, items, scan, tile_lo, tile_hi, cap_items, head, tile_tris, rec,
+        return launch_fragment_t<true>(S, views, items, scan, tile_lo, tile_hi, cap_items, head, pairs, rec,
                                        keys, flag_bits, flag_list, cnt, grid, st);
-    return launch_fragment_t<false>(S, views, items, scan, tile_lo, tile_hi, cap_items, head, tile_tris, rec, keys,
+    return launch_fragment_t<false>(S, views, items, scan, tile_lo, tile_hi, cap_items, head, pairs, rec, keys,
                                     flag_bits, flag_list, cnt, grid, st);
 }
 
@@ -421,10 +416,14 @@ __global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ view
                                                const long long *__restrict__ pix_offs,
                                                const unsigned long long *__restrict__ scan,
                                                const unsigned long long *__restrict__ tile_cnt,
-                                               const unsigned *__restrict__ tile_tris, const float4 *__restrict__ rec,
+                                               const unsigned long long *__restrict__ pairs, const float4 *__restrict__ rec,
                                                const long long *__restrict__ flag_list,
-                                               unsigned long long *__restrict__ keys, Counters *cnt)
+                                               unsigned long long *__restrict__ keys, long long cap_pairs, Counters *cnt)
 {
+    // an attempt whose bins overflowed is rerun by the host; its bin counts
+    // reach past the entries that were written
+    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
+        return;
     const long long nflag = (long long)cnt->flagged;
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -434,7 +433,8 @@ __global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ view
         const long long lin = g - v.pix_off;
         const int i = (int)(lin % v.W), j = (int)(lin / v.W);
         const long long tile = v.tile_off + (long long)(j / v.S) * v.tiles_x + i / v.S;
-        const long long off = (long long)(scan[tile] & 0xFFFFFFFFFFull), n = (long long)(tile_cnt[tile] & 0xFFFFFFFFFFull);
+        const long long off = (long long)(scan[tile] & 0xFFFFFFFFFFull);
+        const long long n = min((long long)(tile_cnt[tile] & 0xFFFFFFFFFFull), max(cap_pairs - off, 0ll));
         float x0, x1, t, dx, dy;
         pixel_ray(v, i, j, x0, x1, t, dx, dy);
         const float zn = v.z_near;
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ view
         // sweep 1: nearest settled hit
         float rb = INFINITY;
         for (long long k = lane; k < n; k += 32) {
-            const unsigned gid = tile_tris[off + k];
+            const unsigned gid = (unsigned)pairs[off + k];
             const float4 *r = rec + (size_t)gid * kRecF4;
             unsigned long long best = ~0ull;
             float bd = INFINITY;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ view
         double bs = INFINITY;
         unsigned bid = 0xFFFFFFFFu;
         for (long long k = lane; k < n; k += 32) {
-            const unsigned gid = tile_tris[off + k];
+            const unsigned gid = (unsigned)pairs[off + k];
             const float4 *r = rec + (size_t)gid * kRecF4;
             unsigned long long best = ~0ull;
             float bd = lim;  // "best so far" = the limit, so fl marks pairs in front of it
@@ -514,11 +514,12 @@ int retest_grid()
 }
 
 cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix_offs, const unsigned long long *scan,
-                          const unsigned long long *tile_cnt, const unsigned *tile_tris, const float4 *rec,
-                          const long long *flag_list, unsigned long long *keys, Counters *cnt, cudaStream_t st)
+                          const unsigned long long *tile_cnt, const unsigned long long *pairs, const float4 *rec,
+                          const long long *flag_list, unsigned long long *keys, long long cap_pairs, Counters *cnt,
+                          cudaStream_t st)
 {
-    k_retest<<<retest_grid(), 256, 0, st>>>(views, nviews, pix_offs, scan, tile_cnt, tile_tris, rec, flag_list, keys,
-                                            cnt);
+    k_retest<<<retest_grid(), 256, 0, st>>>(views, nviews, pix_offs, scan, tile_cnt, pairs, rec, flag_list, keys,
+                                            cap_pairs, cnt);
     return cudaGetLastError();
 }
 
