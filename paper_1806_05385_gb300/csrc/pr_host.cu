@@ -516,8 +516,8 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
                               ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,
                         ws->cap_pairs, seg, cnt, st));
-    PR_TRY(launch_sort_items(ws->items.as<int4>(), scan, P.ntiles, ws->cap_items, ws->pairs.as<unsigned long long>(),
-                             st));
+    PR_TRY(launch_sort_items(ws->items.as<int4>(), scan, P.ntiles, ws->cap_items, seg,
+                             ws->pairs.as<unsigned long long>(), st));
     PR_TRY(mark(2));
     int *heads = ws->heads.as<int>();
     for (size_t c = 0; c < P.classes.size(); ++c) {

@@ -37,7 +37,7 @@ cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile
                          long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);
 // sorts every item's run of bin entries (nearest first); runs <= kMaxSeg
 cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
-                              unsigned long long *pairs, cudaStream_t st);
+                              int seg, unsigned long long *pairs, cudaStream_t st);
 
 // stage (c): per-fragment ray casting, FP64 re-test, resolve
 cudaError_t launch_fragment(int S, bool flag, const ViewDev *views, const int4 *items, const unsigned long long *scan,

@@ -264,7 +264,7 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_bin_scatter(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, scan, fill, pairs,
                               cap_pairs, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
-    NA_TRY(launch_sort_items(items, scan, nt, cap_items, pairs, st));
+    NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, st));
     NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, pairs, rec, keys, nullptr,
                            nullptr, cnt, fragment_grid(tile, false), st));
     NA_TRY(launch_resolve(dv, 1, pix_offs, np, keys, st));

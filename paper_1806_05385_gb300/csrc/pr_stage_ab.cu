@@ -100,7 +100,7 @@ cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int *idx,
 __device__ __forceinline__ void tile_pixel_box(const ViewDev &v, long long lt, float &u0, float &u1, float &w0,
                                                float &w1)
 {
-    const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
+    const int ty = (int)lt / v.tiles_x, tx = (int)lt - ty * v.tiles_x;
     const int i0 = tx * v.S, i1 = min(v.W, i0 + v.S) - 1;
     const int j0 = ty * v.S, j1 = min(v.H, j0 + v.S) - 1;
     u0 = __fdiv_rn((float)i0 + 0.5f, (float)v.W);
@@ -365,7 +365,8 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
 //   [0] S0.x S0.y S0.z S1.x   [1] S1.y S1.z S2.x S2.y   [2] S2.z D0.x D0.y D0.z
 //   [3] D1.x D1.y D1.z D2.x   [4] xmin xmax ymin ymax   [5] tmin tmax D2.y D2.z
 // S = camera-space vertex at t = 0, D = its motion over the frame, the box
-// and interval of stage (a).  tbox = (i0 | i1 << 16, j0 | j1 << 16, nhp, culled).
+// and interval of stage (a).  tbox = (i0 | i1 << 16, j0 | j1 << 16, nhp, depth order
+// key of the nearest depth the triangle reaches).
 __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views, int nviews,
                                                const long long *__restrict__ tri_offs, long long ttot,
                                                float4 *__restrict__ rec, float4 *__restrict__ hp,
@@ -489,8 +490,9 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
             const int tx0 = (tb.x & 0xffff) / v.S, tx1 = (tb.x >> 16) / v.S;
             const int ty0 = (tb.y & 0xffff) / v.S;
             const int w = tx1 - tx0 + 1;
-            const long long q = p - (long long)cand_off[g];
-            const int tx = tx0 + (int)(q % w), ty = ty0 + (int)(q / w);
+            const int q = (int)(p - (long long)cand_off[g]);  // < tiles of one view
+            const int qy = q / w;
+            const int tx = tx0 + (q - qy * w), ty = ty0 + qy;
             tile = v.tile_off + (long long)ty * v.tiles_x + tx;
             const float4 bb = rec[g * kRecF4 + 4];
             const int nh = cand_off[g + 1] - cand_off[g] > 1 ? tb.z : 0;
@@ -690,19 +692,86 @@ __global__ void k_items(const ViewDev *__restrict__ views, int nviews, const lon
     }
 }
 
-// Sorts the bin run of every work item (at most kMaxSeg entries) by its
-// entries, i.e. nearest triangle first, so the fragment stage can stop a
-// run at the first triangle that lies behind every pixel of its block.
-// One warp per item: a run of up to 32 entries is sorted in registers with
-// a bitonic network over the lanes; a longer one in the warp's shared
-// memory, padded to a power of two.
+// Sorts the bin run of every work item by depth key, nearest first, so the
+// fragment stage can stop a run at the first triangle that lies behind
+// every pixel of its block.  One warp per item.  A run of up to 256 entries
+// is sorted in registers (R = 1, 2, 4 or 8 per lane) by a bitonic network
+// over 32-bit words: the depth order key with its low 8 bits replaced by
+// the entry's position in the run.  The entry is written back with that
+// truncated key -- a lower bound of the true one, so every cut the fragment
+// stage takes on it stays conservative -- and its triangle index.  Longer
+// runs (pr_params.seg above 256) are sorted in the warp's shared memory on
+// the full 64-bit entries.
 constexpr int kSortWarps = 4;
+constexpr int kSortRegMax = 256;
+
+template <int R>
+__device__ __forceinline__ void warp_bitonic(unsigned (&x)[R], int lane)
+{
+    // element m of a lane sits at position 32 m + lane
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const int m2 = m ^ (j >> 5);
+                    if (m2 > m) {
+                        const bool up = ((32 * m) & k) == 0;
+                        const unsigned lo = min(x[m], x[m2]), hi = max(x[m], x[m2]);
+                        x[m] = up ? lo : hi;
+                        x[m2] = up ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const unsigned y = __shfl_xor_sync(0xffffffffu, x[m], j);
+                    // the lower position of a pair keeps the smaller word in
+                    // an ascending block, the larger in a descending one
+                    const bool lower = (lane & j) == 0, up = ((32 * m + lane) & k) == 0;
+                    x[m] = (lower == up) ? min(x[m], y) : max(x[m], y);
+                }
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void sort_run_regs(unsigned long long *e, int n, int lane, unsigned *s_gid)
+{
+    unsigned x[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const int q = 32 * m + lane;
+        if (q < n) {
+            const unsigned long long v = e[q];
+            x[m] = ((unsigned)(v >> 32) & ~0xFFu) | (unsigned)q;
+            s_gid[q] = (unsigned)v;
+        } else {
+            x[m] = 0xFFFFFFFFu;  // above every real word (keys are finite or +-inf)
+        }
+    }
+    __syncwarp();
+    warp_bitonic<R>(x, lane);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const int q = 32 * m + lane;
+        if (q < n)
+            e[q] = ((unsigned long long)(x[m] & ~0xFFu) << 32) | s_gid[x[m] & 0xFFu];
+    }
+    __syncwarp();
+}
+
+template <bool kLong>
 __global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__restrict__ items,
                                                                 const unsigned long long *__restrict__ scan,
                                                                 long long ntiles, long long cap_items,
                                                                 unsigned long long *__restrict__ pairs)
 {
-    __shared__ unsigned long long s_run[kSortWarps][kMaxSeg];
+    __shared__ unsigned s_gid[kSortWarps][kSortRegMax];
+    __shared__ unsigned long long s_run[kSortWarps][kLong ? kMaxSeg : 1];
     const long long nitems = min((long long)(scan[ntiles] >> 40), cap_items);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long *run = s_run[w];
@@ -714,20 +783,22 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__re
         if (n <= 1)
             continue;
         if (n <= 32) {
-            unsigned long long x = lane < n ? e[lane] : ~0ull;
-            for (int k = 2; k <= 32; k <<= 1)
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
-                    // the lower lane of a pair keeps the smaller value in an
-                    // ascending block, the larger in a descending one
-                    const bool lower = (lane & j) == 0, up = (lane & k) == 0;
-                    x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
-                }
-            if (lane < n)
-                e[lane] = x;
+            sort_run_regs<1>(e, n, lane, s_gid[w]);
             continue;
         }
-        int P = 64;
+        if (n <= 64) {
+            sort_run_regs<2>(e, n, lane, s_gid[w]);
+            continue;
+        }
+        if (n <= 128) {
+            sort_run_regs<4>(e, n, lane, s_gid[w]);
+            continue;
+        }
+        if (n <= kSortRegMax || !kLong) {  // without kLong, runs are at most kSortRegMax long
+            sort_run_regs<8>(e, n, lane, s_gid[w]);
+            continue;
+        }
+        int P = 512;
         while (P < n)
             P <<= 1;
         for (int q = lane; q < P; q += 32)
@@ -754,7 +825,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__re
 }
 
 cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
-                              unsigned long long *pairs, cudaStream_t st)
+                              int seg, unsigned long long *pairs, cudaStream_t st)
 {
     static int grid = 0;
     if (grid == 0) {
@@ -763,7 +834,10 @@ cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms * 8;
     }
-    k_sort_items<<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs);
+    if (seg > kSortRegMax)
+        k_sort_items<true><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs);
+    else
+        k_sort_items<false><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs);
     return cudaGetLastError();
 }
 

@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ view
         const long long g = flag_list[f];
         const ViewDev &v = views[find_view(pix_offs, nviews, g)];
         const long long lin = g - v.pix_off;
-        const int i = (int)(lin % v.W), j = (int)(lin / v.W);
+        const int j = (int)lin / v.W, i = (int)lin - j * v.W;  // lin < 2^28
         const long long tile = v.tile_off + (long long)(j / v.S) * v.tiles_x + i / v.S;
         const long long off = (long long)(scan[tile] & 0xFFFFFFFFFFull);
         const long long n = min((long long)(tile_cnt[tile] & 0xFFFFFFFFFFull), max(cap_pairs - off, 0ll));

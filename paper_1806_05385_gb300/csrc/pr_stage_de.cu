@@ -30,9 +30,8 @@ struct PixelHit {
     float ndl, sigma;   // n.l and k_a + k_d max(0, n.l)
 };
 
-__device__ __forceinline__ void pixel_hit(const ViewDev &v, long long lin, unsigned id, PixelHit &h)
+__device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsigned id, PixelHit &h)
 {
-    const int i = (int)(lin % v.W), j = (int)(lin / v.W);
     float x0, x1, dx, dy;
     pixel_ray(v, i, j, x0, x1, h.t, dx, dy);
     h.dir = make_float3(dx, dy, 1.f);
@@ -87,15 +86,17 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, long long lin, unsig
 // triangle's contributions over the warp before touching memory.
 // blk_offs[q] = first 8x4 block of view q in the batch.
 __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, const long long *blk_offs, long long g,
-                                            const ViewDev *&vp, long long &lin)
+                                            const ViewDev *&vp, long long &lin, int &i, int &j)
 {
     const long long b = g >> 5;
     const int lane = (int)(g & 31);
     const ViewDev &v = views[find_view(blk_offs, nviews, b)];
     vp = &v;
-    const long long lb = b - v.blk_off;
+    const int lb = (int)(b - v.blk_off);  // < 2^23 blocks per view: 32-bit division
     const int bw = (v.W + 7) >> 3;
-    const int i = (int)(lb % bw) * 8 + (lane & 7), j = (int)(lb / bw) * 4 + (lane >> 3);
+    const int by = lb / bw;
+    i = (lb - by * bw) * 8 + (lane & 7);
+    j = by * 4 + (lane >> 3);
     lin = (long long)j * v.W + i;
     return i < v.W && j < v.H;
 }
@@ -110,7 +111,8 @@ __global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const lon
         return;
     const ViewDev *vp;
     long long lin;
-    if (!block_pixel(views, nviews, blk_offs, g, vp, lin))
+    int pi, pj;
+    if (!block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj))
         return;
     const ViewDev &v = *vp;
     unsigned id;
@@ -135,7 +137,7 @@ __global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const lon
         return;
     }
     PixelHit h;
-    pixel_hit(v, lin, id, h);
+    pixel_hit(v, pi, pj, id, h);
     const float r = fmaf(h.b0, v.cr[h.ia], fmaf(h.b1, v.cr[h.ib], h.b2 * v.cr[h.ic]));
     const float gg = fmaf(h.b0, v.cg[h.ia], fmaf(h.b1, v.cg[h.ib], h.b2 * v.cg[h.ic]));
     const float b = fmaf(h.b0, v.cb[h.ia], fmaf(h.b1, v.cb[h.ib], h.b2 * v.cb[h.ic]));
@@ -186,7 +188,8 @@ __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ vi
         return;
     const ViewDev *vp = views;
     long long lin = 0;
-    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin);
+    int pi = 0, pj = 0;
+    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj);
     const ViewDev &v = *vp;
     unsigned id = 0xFFFFFFFFu;
     const bool wants = v.grad_in || v.target;  // views of a batch without a gradient are skipped
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ vi
     if (valid) {
         const long long plane = (long long)v.W * v.H;
         PixelHit h;
-        pixel_hit(v, lin, id, h);
+        pixel_hit(v, pi, pj, id, h);
         float g0, g1, g2;
         if (v.target) {
             // L2 loss sum (rgb - target)^2: its gradient from this frame's image

@@ -74,6 +74,20 @@ def test_tile_sizes_agree(pr, oracle, mode, tile):
         compare(oracle, view, sc, o, g["id"], g["depth"], g["rgb"])
 
 
+@pytest.mark.parametrize("seg", [1, 5, 32, 33, 100, 256, 257, 700, 1024, 5000])
+def test_work_item_runs_give_identical_images(pr, seg):
+    """Splitting a tile's bin into work items of any run length (and the
+    depth sort of each run, in registers up to 256 entries and in shared
+    memory beyond) changes only the order of the tests, never the result."""
+    sc = S.random_triangles(4000, 21, offset=0.25)
+    p0, p1 = S.head_poses(2.0, 0.5)
+    view = S.View(W=120, H=88, tan_x=0.5, tan_y=0.5, pose0=p0, pose1=p1, mode=S.MODE_BOTH, fovea=(0.45, 0.55))
+    g = gpu_frame(pr, sc, view, tile=32, seg=seg, shade=False)
+    ref = gpu_frame(pr, sc, view, tile=32, shade=False)
+    assert ref["stats"]["pairs"] / 12 > 300   # 12 tiles: bins longer than 256 entries exist
+    assert np.array_equal(g["id"], ref["id"]) and np.array_equal(g["depth"], ref["depth"])
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_bound_kinds_give_identical_images(pr, mode):
     """Sec. 3.2: the intersection test is the same whatever bound is used,
