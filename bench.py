@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the perceptual-rasterization hot path on GB300.
 
-One step = one frame of the workload through every stage of the path: the
-batched, graph-captured forward (a) bounds -> (b) binning -> (c) per-fragment
-ray casting -> (d) shading for all views, then (e) the adjoint of the shaded
-image for every view.  value = framebuffer pixels / step time (Mpix/s).
+One step = one training frame of the workload through every stage of the
+path, captured as one CUDA graph: (a) bounds -> (b) binning and the depth
+sort of every work item's run -> (c) per-fragment ray casting -> (d)
+shading for all views, with (e) the adjoint of an upstream image gradient
+for every view in the same kernel.  value = framebuffer pixels / step time
+(Mpix/s).
 
 Prints ONE JSON line (rank 0).  Default workload: 1440x1600 per eye x 2
 eyes, 266k triangles (200 subdivision-3 icospheres + a 10k ground plane),
@@ -265,7 +267,7 @@ def our_arm(args, rank, world):
         tiles = [16] * len(views)
     params = B.make_params("zenon", 16, wl.fp64, 0)
     entries = [(hv[k], v, ids[k], depth[k], rgb[k], tiles[k]) for k, v in enumerate(views)]
-    # one training frame = one graph: forward (a)-(d), then the adjoint (e)
+    # one training frame = one graph: forward (a)-(d) with the adjoint (e)
     # of an upstream image gradient, reading the frame's own records
     fgrads = [dict(grad_rgb=grad[k], dcol=grads[wl.scene_of[k]][0], dpos=grads[wl.scene_of[k]][1],
                    dvel=grads[wl.scene_of[k]][2]) for k in range(len(views))]
@@ -376,15 +378,17 @@ def our_arm(args, rank, world):
                "tests_per_s": r["tests"] / r["seconds"]}
 
     n_classes = len({(t, wl.fp64) for t in tiles})
-    # tile boxes, bound, 2 scans x3, bins x2, items, fragment classes, [FP64 re-test], shade+resolve, adjoint
-    kernels_step = 12 + n_classes + (1 if wl.fp64 else 0) + 1
+    # tile boxes, bound, 2 scans x3, bins x2, items, run sort, fragment classes, [FP64 re-test],
+    # resolve + shade + adjoint
+    kernels_step = 13 + n_classes + (1 if wl.fp64 else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if not wl.fp64 else "f32+f64-retest", "data": "synthetic",
         "config": {"workload": wl.name, "views": len(views), "pixels_per_step": pix,
                    "triangles": sum(sc.T for sc in wl.scenes),
-                   "step": "one graph per frame: bound, bin, fragment, [FP64 re-test], resolve+shade, adjoint",
+                   "step": "one graph per frame: bound, bin, run sort, fragment, [FP64 re-test], "
+                           "resolve + shade + adjoint (one kernel)",
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -396,8 +400,7 @@ def our_arm(args, rank, world):
         "stats": {k: st[k] for k in ("tests", "hits", "pairs", "items", "culled", "pixels", "flagged", "changed",
                                      "fp64_depth_err")},
         "stage_ms": {"bound": st["stage_ms"][0], "bin": st["stage_ms"][1], "fragment": frag_ms,
-                     "fp64_retest": st["stage_ms"][3], "resolve_shade": st["stage_ms"][5],
-                     "adjoint": st["stage_ms"][6]},
+                     "fp64_retest": st["stage_ms"][3], "resolve_shade_adjoint": st["stage_ms"][5]},
         "fwd_mpix_s": {"batched_graph": world * pix / (statistics.mean(fwd_batched) * 1e-3) / 1e6,
                        "plain_per_view": world * pix / (statistics.mean(fwd_plain) * 1e-3) / 1e6},
         "fwd_bwd_ms_per_frame": mean_ms, "bwd_ms_separate_call": statistics.mean(bwd_ms),

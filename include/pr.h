@@ -119,8 +119,8 @@ typedef struct {
                              caller's stream: [0] (a) tile boxes + bounds, [1] (b) binning
                              (count, scan, scatter, items), [2] (c) fragment kernel(s),
                              [3] FP64 re-test, [4] resolve (when not shading), [5] (d) shading
-                             (which then also resolves), [6] (e) adjoint of a training frame,
-                             [7] unused */
+                             (which then also resolves and, in a training frame, runs the
+                             (e) adjoint), [6]-[7] unused */
     float fp64_depth_err; /* precision form: largest |depth_fp32 - depth_fp64| / depth_fp64 over the
                              re-tested pixels whose winner FP64 confirmed (the FP32 error that the
                              re-test removed); 0 without the re-test */

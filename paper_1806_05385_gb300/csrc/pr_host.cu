@@ -138,7 +138,7 @@ struct pr_workspace {
     PinnedBuf<Counters> h_cnt;
     pr_stats stats{};
     long long last_T = 0;          // triangles of the last frame (debug bounds)
-    static constexpr int kEv = 8;  // stage boundaries of one frame
+    static constexpr int kEv = 7;  // stage boundaries of one frame
     cudaEvent_t ev[kEv] = {};
     bool ev_ok = false;
     ~pr_workspace()
@@ -535,12 +535,9 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     if (!shade)
         PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
     PR_TRY(mark(5));
-    if (shade)  // resolves the keys too
-        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), st));
+    if (shade)  // resolves the keys too, and in a training frame runs the adjoint
+        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), !P.grads.empty(), cnt, st));
     PR_TRY(mark(6));
-    if (!P.grads.empty())
-        PR_TRY(launch_backward(dv, n, blk_offs, P.nblk, cnt, st));
-    PR_TRY(mark(7));
     // host-side outputs
     for (int q = 0; q < n; ++q) {
         const BatchPlan::Out &o = P.out[q];
@@ -813,7 +810,7 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
     if (s != PR_OK)
         return s;
     PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, st));
+                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, false, nullptr, st));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
     PR_TRY(cudaStreamSynchronize(st));

@@ -101,68 +101,6 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
     return i < v.W && j < v.H;
 }
 
-// keys != null: the frame's packed depth|id keys are resolved here too
-// (id and depth written, then shaded), saving the separate resolve pass.
-__global__ void k_shade(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ blk_offs,
-                        long long nthreads, const unsigned long long *__restrict__ keys)
-{
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= nthreads)
-        return;
-    const ViewDev *vp;
-    long long lin;
-    int pi, pj;
-    if (!block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj))
-        return;
-    const ViewDev &v = *vp;
-    unsigned id;
-    if (keys) {
-        const unsigned long long key = keys[v.pix_off + lin];
-        const bool bg = key == ~0ull;
-        id = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
-        if (v.id_out)
-            v.id_out[lin] = id;
-        if (v.depth_out)
-            v.depth_out[lin] = bg ? INFINITY : __uint_as_float((unsigned)(key >> 32));
-    } else {
-        id = v.id_in[lin];
-    }
-    if (!v.rgb_out)
-        return;
-    const long long plane = (long long)v.W * v.H;
-    if (id >= (unsigned)v.T) {
-        v.rgb_out[lin] = 0.f;
-        v.rgb_out[plane + lin] = 0.f;
-        v.rgb_out[2 * plane + lin] = 0.f;
-        return;
-    }
-    PixelHit h;
-    pixel_hit(v, pi, pj, id, h);
-    const float r = fmaf(h.b0, v.cr[h.ia], fmaf(h.b1, v.cr[h.ib], h.b2 * v.cr[h.ic]));
-    const float gg = fmaf(h.b0, v.cg[h.ia], fmaf(h.b1, v.cg[h.ib], h.b2 * v.cg[h.ic]));
-    const float b = fmaf(h.b0, v.cb[h.ia], fmaf(h.b1, v.cb[h.ib], h.b2 * v.cb[h.ic]));
-    v.rgb_out[lin] = r * h.sigma;
-    v.rgb_out[plane + lin] = gg * h.sigma;
-    v.rgb_out[2 * plane + lin] = b * h.sigma;
-}
-
-cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         const unsigned long long *keys, cudaStream_t st)
-{
-    const long long n = nblocks * 32;
-    if (n > 0)
-        k_shade<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, keys);
-    return cudaGetLastError();
-}
-
-// Sum of x over the lanes of a fully converged warp.
-__device__ __forceinline__ float warp_sum(float x)
-{
-    for (int o = 16; o > 0; o >>= 1)
-        x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 // Adjoint of rgb = a sigma, a = sum_k b_k col_k, sigma = k_a + k_d max(0, n.l):
 //  - d/dcol_k = g b_k sigma
 //  - barycentrics b_k = w_k / sum w with w_0 = dir.(B x C), w_1 = dir.(C x A),
@@ -174,48 +112,17 @@ __device__ __forceinline__ float warp_sum(float x)
 //    dc/dp = (1-t) R0 + t R1, dc/dv = t R1.
 // Per warp, the 27 contributions of each distinct triangle are summed over
 // the lanes that see it with a reduce-scatter (lane l ends with the sum of
-// value l) and added with one 27-lane atomic instruction.
-__global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ views, int nviews,
-                                                 const long long *__restrict__ blk_offs, long long nthreads,
-                                                 const Counters *__restrict__ frame_cnt)
+// value l) and added with one 27-lane atomic instruction.  Called by every
+// lane of a warp; valid = this lane has a pixel with a visible triangle.
+__device__ __forceinline__ void adjoint_pixel(const ViewDev &v, const PixelHit &h, bool valid, unsigned id, float g0,
+                                              float g1, float g2)
 {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((g & ~31ll) >= nthreads)
-        return;  // whole warps only
-    // in a training frame: a forward that overflowed is rerun by the host,
-    // so its adjoint must not accumulate
-    if (frame_cnt && (frame_cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS | ST_TIMEOUT)))
-        return;
-    const ViewDev *vp = views;
-    long long lin = 0;
-    int pi = 0, pj = 0;
-    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj);
-    const ViewDev &v = *vp;
-    unsigned id = 0xFFFFFFFFu;
-    const bool wants = v.grad_in || v.target;  // views of a batch without a gradient are skipped
-    if (inside && wants)
-        id = v.id_in[lin];
-    const bool valid = inside && wants && id < (unsigned)v.T;
     float gc[3][3], gp[3][3], gvel[3][3];
     int vid[3] = {0, 0, 0};
     for (int k = 0; k < 3; ++k)
         for (int c = 0; c < 3; ++c)
             gc[k][c] = gp[k][c] = gvel[k][c] = 0.f;
     if (valid) {
-        const long long plane = (long long)v.W * v.H;
-        PixelHit h;
-        pixel_hit(v, pi, pj, id, h);
-        float g0, g1, g2;
-        if (v.target) {
-            // L2 loss sum (rgb - target)^2: its gradient from this frame's image
-            g0 = 2.f * (v.rgb_out[lin] - v.target[lin]);
-            g1 = 2.f * (v.rgb_out[plane + lin] - v.target[plane + lin]);
-            g2 = 2.f * (v.rgb_out[2 * plane + lin] - v.target[2 * plane + lin]);
-        } else {
-            g0 = v.grad_in[lin];
-            g1 = v.grad_in[plane + lin];
-            g2 = v.grad_in[2 * plane + lin];
-        }
         vid[0] = h.ia;
         vid[1] = h.ib;
         vid[2] = h.ic;
@@ -316,6 +223,141 @@ __global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ vi
                 atomicAdd(&dst[3 * vk + (r % 3)], s[0]);
         }
     }
+}
+
+__device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
+{
+    return frame_cnt && (frame_cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS | ST_TIMEOUT));
+}
+
+// Stage (d).  keys != null: the frame's packed depth|id keys are resolved
+// here too (id and depth written, then shaded), saving a separate resolve
+// pass.  kAdjoint (a training frame): for views with a gradient input, the
+// stage (e) adjoint of the pixel follows from the same PixelHit -- with an
+// L2 target, from the colour just computed -- so the frame needs no
+// separate adjoint pass.  Whole warps run (the adjoint's reductions).
+template <bool kAdjoint>
+__global__ void __launch_bounds__(256) k_shade(const ViewDev *__restrict__ views, int nviews,
+                                              const long long *__restrict__ blk_offs, long long nthreads,
+                                              const unsigned long long *__restrict__ keys,
+                                              const Counters *__restrict__ frame_cnt)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((g & ~31ll) >= nthreads)
+        return;
+    const ViewDev *vp = views;
+    long long lin = 0;
+    int pi = 0, pj = 0;
+    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj);
+    const ViewDev &v = *vp;
+    unsigned id = 0xFFFFFFFFu;
+    if (inside) {
+        if (keys) {
+            const unsigned long long key = keys[v.pix_off + lin];
+            const bool bg = key == ~0ull;
+            id = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
+            if (v.id_out)
+                v.id_out[lin] = id;
+            if (v.depth_out)
+                v.depth_out[lin] = bg ? INFINITY : __uint_as_float((unsigned)(key >> 32));
+        } else {
+            id = v.id_in[lin];
+        }
+    }
+    // a view with neither an image nor a gradient only needs the resolve
+    const bool hit = inside && id < (unsigned)v.T && (v.rgb_out || (kAdjoint && (v.grad_in || v.target)));
+    const long long plane = (long long)v.W * v.H;
+    PixelHit h;
+    float rgb[3] = {0.f, 0.f, 0.f};
+    if (hit) {
+        pixel_hit(v, pi, pj, id, h);
+        const float r = fmaf(h.b0, v.cr[h.ia], fmaf(h.b1, v.cr[h.ib], h.b2 * v.cr[h.ic]));
+        const float gg = fmaf(h.b0, v.cg[h.ia], fmaf(h.b1, v.cg[h.ib], h.b2 * v.cg[h.ic]));
+        const float b = fmaf(h.b0, v.cb[h.ia], fmaf(h.b1, v.cb[h.ib], h.b2 * v.cb[h.ic]));
+        rgb[0] = r * h.sigma;
+        rgb[1] = gg * h.sigma;
+        rgb[2] = b * h.sigma;
+    }
+    if (inside && v.rgb_out) {
+        v.rgb_out[lin] = rgb[0];
+        v.rgb_out[plane + lin] = rgb[1];
+        v.rgb_out[2 * plane + lin] = rgb[2];
+    }
+    if (kAdjoint) {
+        // views of a batch without a gradient skip it (a warp covers one view)
+        if (!(v.grad_in || v.target) || frame_overflowed(frame_cnt))
+            return;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (hit) {
+            if (v.target) {
+                // L2 loss sum (rgb - target)^2: its gradient from this frame's image
+                g0 = 2.f * (rgb[0] - v.target[lin]);
+                g1 = 2.f * (rgb[1] - v.target[plane + lin]);
+                g2 = 2.f * (rgb[2] - v.target[2 * plane + lin]);
+            } else {
+                g0 = v.grad_in[lin];
+                g1 = v.grad_in[plane + lin];
+                g2 = v.grad_in[2 * plane + lin];
+            }
+        }
+        adjoint_pixel(v, h, hit, id, g0, g1, g2);
+    }
+}
+
+cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
+                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, cudaStream_t st)
+{
+    const long long n = nblocks * 32;
+    if (n > 0) {
+        if (adjoint)
+            k_shade<true><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, keys, frame_cnt);
+        else
+            k_shade<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, keys, frame_cnt);
+    }
+    return cudaGetLastError();
+}
+
+// Stage (e) on its own: the adjoint of a shaded frame from its id buffer
+// and an upstream gradient.
+__global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ views, int nviews,
+                                                 const long long *__restrict__ blk_offs, long long nthreads,
+                                                 const Counters *__restrict__ frame_cnt)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((g & ~31ll) >= nthreads)
+        return;  // whole warps only
+    // in a training frame: a forward that overflowed is rerun by the host,
+    // so its adjoint must not accumulate
+    if (frame_overflowed(frame_cnt))
+        return;
+    const ViewDev *vp = views;
+    long long lin = 0;
+    int pi = 0, pj = 0;
+    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj);
+    const ViewDev &v = *vp;
+    if (!(v.grad_in || v.target))
+        return;  // views of a batch without a gradient (a warp covers one view)
+    unsigned id = 0xFFFFFFFFu;
+    if (inside)
+        id = v.id_in[lin];
+    const bool valid = inside && id < (unsigned)v.T;
+    PixelHit h;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (valid) {
+        const long long plane = (long long)v.W * v.H;
+        pixel_hit(v, pi, pj, id, h);
+        if (v.target) {
+            // L2 loss sum (rgb - target)^2: its gradient from this frame's image
+            g0 = 2.f * (v.rgb_out[lin] - v.target[lin]);
+            g1 = 2.f * (v.rgb_out[plane + lin] - v.target[plane + lin]);
+            g2 = 2.f * (v.rgb_out[2 * plane + lin] - v.target[2 * plane + lin]);
+        } else {
+            g0 = v.grad_in[lin];
+            g1 = v.grad_in[plane + lin];
+            g2 = v.grad_in[2 * plane + lin];
+        }
+    }
+    adjoint_pixel(v, h, valid, id, g0, g1, g2);
 }
 
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
