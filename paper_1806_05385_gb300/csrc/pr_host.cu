@@ -509,9 +509,9 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
     PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, cnt, st));
     PR_TRY(mark(1));
-    PR_TRY(launch_scan(cand, cand_off, ws->sums.as<unsigned long long>(), P.ttot, 0, st));
+    PR_TRY(launch_scan(cand, cand_off, ws->sums.as<unsigned long long>(), P.ttot, 0, cnt, st));
     PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
-    PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, st));
+    PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, cnt, st));
     PR_TRY(launch_bin_scatter(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, scan,
                               ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,

@@ -24,8 +24,8 @@ cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_
 cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                              const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
                              const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt, cudaStream_t st);
-cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *block_sums,
-                        long long n, int seg, cudaStream_t st);
+cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
+                        int seg, Counters *cnt, cudaStream_t st);
 size_t scan_block_sums_needed(long long n);
 cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                                const unsigned long long *cand_off, const float4 *rec, const float4 *hp,

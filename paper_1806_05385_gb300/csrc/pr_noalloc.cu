@@ -258,9 +258,9 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_scene_check(soa, V, cnt, st));
     NA_TRY(launch_tile_boxes(dv, 1, tile_offs, nt, tile_box, st));
     NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, cnt, st));
-    NA_TRY(launch_scan(cand, cand_off, sums, T, 0, st));
+    NA_TRY(launch_scan(cand, cand_off, sums, T, 0, cnt, st));
     NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
-    NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, st));
+    NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, cnt, st));
     NA_TRY(launch_bin_scatter(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, scan, fill, pairs,
                               cap_pairs, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));

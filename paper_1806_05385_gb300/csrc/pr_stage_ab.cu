@@ -462,6 +462,8 @@ __device__ __forceinline__ long long owner_of(const unsigned long long *cand_off
     return lo;
 }
 
+constexpr int kBinChunks = 4;
+
 template <bool kScatter>
 __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, int nviews,
                                              const long long *__restrict__ tri_offs, long long ttot,
@@ -474,49 +476,74 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
 {
     const long long total = (long long)cand_off[ttot];
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    // all lanes of a warp run the same number of iterations (for the shuffles)
-    const long long p0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-    for (long long pw = p0; pw < total; pw += stride) {
-        const long long p = pw + lane;
-        bool hit = false;
-        long long tile = -1, g = -1;
-        unsigned key = 0u;
-        if (p < total) {
-            g = owner_of(cand_off, ttot, p);
-            const int4 tb = tbox[g];
-            key = (unsigned)tb.w;
-            const ViewDev &v = views[find_view(tri_offs, nviews, g)];
-            const int tx0 = (tb.x & 0xffff) / v.S, tx1 = (tb.x >> 16) / v.S;
-            const int ty0 = (tb.y & 0xffff) / v.S;
-            const int w = tx1 - tx0 + 1;
-            const int q = (int)(p - (long long)cand_off[g]);  // < tiles of one view
-            const int qy = q / w;
-            const int tx = tx0 + (q - qy * w), ty = ty0 + qy;
-            tile = v.tile_off + (long long)ty * v.tiles_x + tx;
-            const float4 bb = rec[g * kRecF4 + 4];
-            const int nh = cand_off[g + 1] - cand_off[g] > 1 ? tb.z : 0;
-            hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
-        }
-        const unsigned want = __ballot_sync(0xffffffffu, hit);
-        if (!hit)
-            continue;
-        const unsigned peers = __match_any_sync(want, (unsigned long long)tile);
-        const int leader = __ffs(peers) - 1;
-        if (!kScatter) {
-            if (lane == leader)
-                atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
-        } else {
-            unsigned base = 0;
-            if (lane == leader)
-                base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
-            base = __shfl_sync(peers, base, leader);
-            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-            const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
-            if (pos < cap_pairs)
-                pairs[pos] = ((unsigned long long)key << 32) | (unsigned long long)g;
-            else
-                atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    // Each warp takes tasks of kBinChunks x 32 consecutive candidate pairs.
+    // The owner of the task's first pair is found by a binary search over
+    // the triangle offsets (warp-uniform, so one broadcast load per step);
+    // the owners of each chunk's pairs then follow from the offsets of the
+    // next 32 triangles, loaded with one coalesced read and searched with
+    // shuffles.  All lanes run the same iterations (for the shuffles).
+    for (long long pt = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kBinChunks);
+         pt < total; pt += nwarps * (32 * kBinChunks)) {
+        long long g0 = owner_of(cand_off, ttot, pt);
+        for (int c = 0; c < kBinChunks; ++c) {
+            const long long pw = pt + 32 * c;
+            if (pw >= total)
+                break;
+            const long long p = pw + lane;
+            const long long gl = g0 + 1 + lane;
+            const unsigned long long o = gl <= ttot ? cand_off[gl] : ~0ull;
+            // every lane takes part in every shuffle; the fallback search
+            // (no warp operations) runs after them
+            int k = 0;  // offsets of the window at or below p
+            for (int sstep = 16; sstep > 0; sstep >>= 1) {
+                const unsigned long long probe = __shfl_sync(0xffffffffu, o, k + sstep - 1);
+                if (probe <= (unsigned long long)p)
+                    k += sstep;
+            }
+            const bool beyond = __shfl_sync(0xffffffffu, o, 31) <= (unsigned long long)p;
+            // past the window (a run of empty triangles): search all offsets
+            const long long g = beyond ? owner_of(cand_off, ttot, p) : g0 + k;
+            g0 = __shfl_sync(0xffffffffu, g, 31);  // owners ascend with p
+            bool hit = false;
+            long long tile = -1;
+            unsigned key = 0u;
+            if (p < total) {
+                const int4 tb = tbox[g];
+                key = (unsigned)tb.w;
+                const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+                const int sh = __ffs(v.S) - 1;  // S is a power of two
+                const int tx0 = (tb.x & 0xffff) >> sh, tx1 = (tb.x >> 16) >> sh;
+                const int ty0 = (tb.y & 0xffff) >> sh;
+                const int w = tx1 - tx0 + 1;
+                const int q = (int)(p - (long long)cand_off[g]);  // < tiles of one view
+                const int qy = q / w;
+                const int tx = tx0 + (q - qy * w), ty = ty0 + qy;
+                tile = v.tile_off + (long long)ty * v.tiles_x + tx;
+                const float4 bb = rec[g * kRecF4 + 4];
+                const int nh = cand_off[g + 1] - cand_off[g] > 1 ? tb.z : 0;
+                hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
+            }
+            const unsigned want = __ballot_sync(0xffffffffu, hit);
+            if (!hit)
+                continue;
+            const unsigned peers = __match_any_sync(want, (unsigned long long)tile);
+            const int leader = __ffs(peers) - 1;
+            if (!kScatter) {
+                if (lane == leader)
+                    atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
+            } else {
+                unsigned base = 0;
+                if (lane == leader)
+                    base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+                const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
+                if (pos < cap_pairs)
+                    pairs[pos] = ((unsigned long long)key << 32) | (unsigned long long)g;
+                else
+                    atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+            }
         }
     }
 }
@@ -557,10 +584,18 @@ cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long
 
 // ---------------------------------------------------------------- scan
 
-// Exclusive prefix sum of the packed per-tile words: low 40 bits = bin
-// entries, high 24 bits = work items (ceil(entries / seg)).  Three passes:
-// per-block scan, scan of the block sums, add.
-constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
+// Exclusive prefix sum of u64 words in one pass (decoupled look-back,
+// Merrill and Garland 2016): each CTA scans a tile of kScanBlock words,
+// publishes the tile's sum, and warp 0 walks back over its predecessors --
+// 32 at a time, polling their flags -- until it meets a tile whose
+// inclusive prefix is published.  Tiles are numbered by an atomic ticket,
+// so every tile waited on belongs to a CTA that started earlier; each poll
+// is bounded (ST_TIMEOUT if it runs out).  With seg > 0 each input word is
+// first packed as low 40 bits = bin entries, high 24 bits = work items
+// (ceil(entries / seg)).  out[n] = the grand total.
+constexpr int kScanThreads = 512, kScanPer = 8, kScanBlock = kScanThreads * kScanPer;
+constexpr unsigned long long kFlagAgg = 1ull, kFlagPre = 2ull;
+constexpr int kScanSpinLimit = 1 << 22;
 
 __device__ __forceinline__ unsigned long long pack_items(unsigned long long c, int seg)
 {
@@ -597,62 +632,122 @@ __device__ unsigned long long block_exclusive_scan(unsigned long long x, unsigne
     return before + inc - x;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_local(const unsigned long long *__restrict__ in,
-                                                            unsigned long long *__restrict__ out,
-                                                            unsigned long long *__restrict__ sums, long long n, int seg)
+__device__ __forceinline__ unsigned long long load_volatile(const unsigned long long *p)
 {
-    const long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
-    unsigned long long v[kScanPer], s = 0;
-    for (int k = 0; k < kScanPer; ++k) {
-        v[k] = base + k < n ? (seg > 0 ? pack_items(in[base + k], seg) : in[base + k]) : 0ull;
-        s += v[k];
-    }
-    unsigned long long total;
-    unsigned long long run = block_exclusive_scan(s, &total);
-    for (int k = 0; k < kScanPer; ++k) {
-        if (base + k < n)
-            out[base + k] = run;
-        run += v[k];
-    }
-    if (threadIdx.x == 0)
-        sums[blockIdx.x] = total;
+    return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ void store_volatile(unsigned long long *p, unsigned long long v)
+{
+    *(volatile unsigned long long *)p = v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(unsigned long long *__restrict__ out,
-                                                          const unsigned long long *__restrict__ sums, long long n,
-                                                          unsigned long long *__restrict__ total_out, long long nblocks)
+// state: [0] ticket, [1, 1 + nb) flags, then nb tile sums, then nb
+// inclusive prefixes; the ticket and flags start at zero.
+__global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long *__restrict__ in,
+                                                      unsigned long long *__restrict__ out, long long n, int seg,
+                                                      unsigned long long *state, long long nb, Counters *cnt)
 {
-    const long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
-    const unsigned long long add = sums[blockIdx.x];
-    for (int k = 0; k < kScanPer; ++k)
+    unsigned long long *flags = state + 1, *agg = state + 1 + nb, *inc = state + 1 + 2 * nb;
+    __shared__ long long s_tile;
+    __shared__ unsigned long long s_excl;
+    if (threadIdx.x == 0)
+        s_tile = (long long)atomicAdd(&state[0], 1ull);
+    __syncthreads();
+    const long long tile = s_tile;
+    const long long base = tile * kScanBlock + (long long)threadIdx.x * kScanPer;
+    unsigned long long v[kScanPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < n ? (seg > 0 ? pack_items(in[base + k], seg) : in[base + k]) : 0ull;
+        sum += v[k];
+    }
+    unsigned long long total;
+    unsigned long long run = block_exclusive_scan(sum, &total);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            if (lane == 0) {
+                store_volatile(&inc[0], total);
+                __threadfence();
+                store_volatile(&flags[0], kFlagPre);
+            }
+        } else {
+            if (lane == 0) {
+                store_volatile(&agg[tile], total);
+                __threadfence();
+                store_volatile(&flags[tile], kFlagAgg);
+            }
+            bool late = false;
+            for (long long j = tile - 1;; j -= 32) {
+                const long long t = j - lane;
+                unsigned long long f = kFlagPre, val = 0;  // before tile 0: a prefix of 0
+                if (t >= 0) {
+                    int spins = 0;
+                    while ((f = load_volatile(&flags[t])) == 0ull) {
+                        if (++spins > kScanSpinLimit) {
+                            late = true;
+                            f = kFlagPre;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    __threadfence();
+                    if (f == kFlagPre)
+                        val = load_volatile(&inc[t]);
+                    else
+                        val = load_volatile(&agg[t]);
+                }
+                const unsigned pre = __ballot_sync(0xffffffffu, f == kFlagPre);
+                const int first = pre ? __ffs(pre) - 1 : 31;  // nearest tile with a prefix
+                unsigned long long c = lane <= first ? val : 0ull;
+                for (int o = 16; o > 0; o >>= 1)
+                    c += __shfl_xor_sync(0xffffffffu, c, o);
+                excl += c;
+                if (pre)
+                    break;
+            }
+            if (lane == 0) {
+                store_volatile(&inc[tile], excl + total);
+                __threadfence();
+                store_volatile(&flags[tile], kFlagPre);
+            }
+            if (__any_sync(0xffffffffu, late) && lane == 0)
+                atomicOr(&cnt->status, ST_TIMEOUT);
+        }
+        if (lane == 0)
+            s_excl = excl;
+    }
+    __syncthreads();
+    const unsigned long long excl = s_excl;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
         if (base + k < n)
-            out[base + k] += add;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        *total_out = sums[nblocks];
+            out[base + k] = excl + run;
+        run += v[k];
+    }
+    if (tile == nb - 1 && threadIdx.x == 0)
+        out[n] = excl + total;
 }
 
 size_t scan_block_sums_needed(long long n)
 {
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
-    return (size_t)(nb + 1) * 2 + 64;
+    return (size_t)(3 * nb + 2);
 }
 
-cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *block_sums,
-                        long long n, int seg, cudaStream_t st)
+cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
+                        int seg, Counters *cnt, cudaStream_t st)
 {
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) {
         cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
         return cudaGetLastError();
     }
-    if (nb > kScanBlock)
-        return cudaErrorInvalidValue;
-    unsigned long long *sums = block_sums, *sums_out = block_sums + nb + 1;
-    k_scan_local<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, sums, n, seg);
-    // block sums -> exclusive offsets (nb is small: one block of the same scan)
-    k_scan_local<<<1, kScanThreads, 0, st>>>(sums, sums_out, sums_out + nb, nb, 0);
-    // sums_out[nb] holds the grand total after the second pass
-    k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, sums_out, n, out + n, nb);
+    cudaError_t e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (nb + 1), st);
+    if (e != cudaSuccess)
+        return e;
+    k_scan<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, seg, state, nb, cnt);
     return cudaGetLastError();
 }
 
