@@ -129,6 +129,7 @@ constexpr int kDefaultSeg = 256;
 // Scratch of one batched frame.
 struct pr_workspace {
     DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, pairs, items, keys, counters, heads;
+    DevBuf hit_entry, hit_tile;  // (triangle, tile) hits of the binning count pass, before the scatter
     DevBuf cand, cand_off;         // candidate tiles per triangle and their prefix sum
     DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
     DevBuf stage;                  // device copies of host-side outputs
@@ -438,6 +439,8 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
         PR_TRY(ensure(ws->pairs, sizeof(unsigned long long) * want_pairs));
     }
     ws->cap_pairs = (long long)(ws->pairs.cap / sizeof(unsigned long long));
+    PR_TRY(ensure(ws->hit_entry, sizeof(unsigned long long) * ws->cap_pairs));
+    PR_TRY(ensure(ws->hit_tile, sizeof(unsigned) * ws->cap_pairs));
     const long long want_items = std::max(ws->cap_items, ws->cap_pairs / seg + P.ntiles + 1024);
     if ((size_t)want_items * sizeof(int4) > ws->items.cap || !ws->items.p) {
         PR_TRY(ensure(ws->items, sizeof(int4) * want_items));
@@ -510,9 +513,10 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, cnt, st));
     PR_TRY(mark(1));
     PR_TRY(launch_scan(cand, cand_off, ws->sums.as<unsigned long long>(), P.ttot, 0, cnt, st));
-    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
+    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt,
+                            ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, cnt, st));
-    PR_TRY(launch_bin_scatter(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, scan,
+    PR_TRY(launch_bin_scatter(ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), scan,
                               ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,
                         ws->cap_pairs, seg, cnt, st));

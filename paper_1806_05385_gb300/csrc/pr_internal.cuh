@@ -57,6 +57,7 @@ struct ViewDev {
 struct Counters {
     unsigned long long tests, hits, culled, flagged, changed;
     unsigned long long pairs_total, items_total;  // copied from the scan for the host
+    unsigned long long hits_listed;               // (triangle, tile) hits appended by the binning count pass
     unsigned int status;
     unsigned int depth_err_bits;  // bits of the largest FP32-vs-FP64 relative depth error (re-test)
 };

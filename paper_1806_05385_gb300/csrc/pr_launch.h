@@ -20,18 +20,19 @@ cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long 
 cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
                          float4 *hp, int4 *tbox, unsigned long long *cand, Counters *cnt, cudaStream_t st);
 
-// stage (b): tile binning
+// stage (b): tile binning -- count pass (tile counts, and every hit appended to the hit list),
+// then after the scan the scatter of the list into the bins
 cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                              const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
-                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt, cudaStream_t st);
+                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt,
+                             unsigned long long *hit_entry, unsigned *hit_tile, long long cap_pairs, Counters *cnt,
+                             cudaStream_t st);
+cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
+                               const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
+                               long long cap_pairs, Counters *cnt, cudaStream_t st);
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
                         int seg, Counters *cnt, cudaStream_t st);
 size_t scan_block_sums_needed(long long n);
-cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
-                               const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
-                               const int4 *tbox, const float4 *tile_box, const unsigned long long *scan,
-                               unsigned int *fill, unsigned long long *pairs, long long cap_pairs, Counters *cnt,
-                               cudaStream_t st);
 cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
                          const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
                          long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);

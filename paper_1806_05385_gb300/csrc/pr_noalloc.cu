@@ -211,11 +211,13 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     // the rest: work items and bin entries
     const long long rest = (long long)kNoAllocBytes - (long long)((c.off + 255) & ~(size_t)255) - 512;
     const long long item_fixed = nt + 1024;
-    if (rest < (long long)(16 * item_fixed + 8 * (2 * Tn + nt)))
+    if (rest < (long long)(16 * item_fixed + 21 * (2 * Tn + nt)))
         return PR_ERR_INVALID_ARG;  // too little room left for the bins of this frame
-    const long long cap_pairs = (rest - 16 * item_fixed) / (8 + 16 / seg + 1);
+    // per bin entry: the entry (8 B) and its listed hit (8 B entry + 4 B tile)
+    const long long cap_pairs = (rest - 16 * item_fixed) / (20 + 16 / seg + 1);
     const long long cap_items = item_fixed + cap_pairs / seg + 1;
     const size_t o_items = c.take(sizeof(int4) * cap_items), o_tris = c.take(8 * cap_pairs);
+    const size_t o_hit_e = c.take(8 * cap_pairs), o_hit_t = c.take(4 * cap_pairs);
     if (!c.ok)
         return PR_ERR_INVALID_ARG;
 
@@ -239,6 +241,8 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     int4 *tbox = (int4 *)(arena + o_tbox), *items = (int4 *)(arena + o_items);
     unsigned *fill = (unsigned *)(arena + o_fill);
     unsigned long long *pairs = (unsigned long long *)(arena + o_tris);
+    unsigned long long *hit_entry = (unsigned long long *)(arena + o_hit_e);
+    unsigned *hit_tile = (unsigned *)(arena + o_hit_t);
     unsigned long long *sums = (unsigned long long *)(arena + o_sums), *keys = (unsigned long long *)(arena + o_keys);
 
     // host-side constants go up by plain (pageable) copies; they complete
@@ -259,10 +263,10 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_tile_boxes(dv, 1, tile_offs, nt, tile_box, st));
     NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, cnt, st));
     NA_TRY(launch_scan(cand, cand_off, sums, T, 0, cnt, st));
-    NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, st));
+    NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry, hit_tile,
+                            cap_pairs, cnt, st));
     NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, cnt, st));
-    NA_TRY(launch_bin_scatter(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, scan, fill, pairs,
-                              cap_pairs, cnt, st));
+    NA_TRY(launch_bin_scatter(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
     NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, st));
     NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, pairs, rec, keys, nullptr,

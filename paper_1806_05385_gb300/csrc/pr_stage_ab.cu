@@ -430,13 +430,17 @@ __device__ __forceinline__ bool tile_meets(const float4 tb, const float4 bb, con
 {
     if (bb.x > tb.y || bb.y < tb.x || bb.z > tb.w || bb.w < tb.z)
         return false;
-    for (int k = 0; k < nh; ++k) {
-        const float4 p = h[k];
-        const float m = fmaf(p.x, p.x > 0.f ? tb.x : tb.y, fmaf(p.y, p.y > 0.f ? tb.z : tb.w, p.z));
-        if (m > 0.f)
-            return false;
+    // all half-planes are loaded before any is tested (no chain of loads)
+    bool out = false;
+#pragma unroll
+    for (int k = 0; k < kMaxHp; ++k) {
+        if (k < nh) {
+            const float4 p = h[k];
+            const float m = fmaf(p.x, p.x > 0.f ? tb.x : tb.y, fmaf(p.y, p.y > 0.f ? tb.z : tb.w, p.z));
+            out |= m > 0.f;
+        }
     }
-    return true;
+    return !out;
 }
 
 // Bins.  Every triangle's framebuffer box spans a rectangle of candidate
@@ -464,15 +468,14 @@ __device__ __forceinline__ long long owner_of(const unsigned long long *cand_off
 
 constexpr int kBinChunks = 4;
 
-template <bool kScatter>
 __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, int nviews,
                                              const long long *__restrict__ tri_offs, long long ttot,
                                              const unsigned long long *__restrict__ cand_off,
                                              const float4 *__restrict__ rec, const float4 *__restrict__ hp,
                                              const int4 *__restrict__ tbox, const float4 *__restrict__ tile_box,
                                              unsigned long long *__restrict__ tile_cnt,
-                                             const unsigned long long *__restrict__ scan, unsigned int *__restrict__ fill,
-                                             unsigned long long *__restrict__ pairs, long long cap_pairs, Counters *cnt)
+                                             unsigned long long *__restrict__ hit_entry, unsigned *__restrict__ hit_tile,
+                                             long long cap_pairs, Counters *cnt)
 {
     const long long total = (long long)cand_off[ttot];
     const int lane = threadIdx.x & 31;
@@ -525,26 +528,60 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                 hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
             }
             const unsigned want = __ballot_sync(0xffffffffu, hit);
+            if (!want)
+                continue;
+            // the warp's hits go to the hit list with one atomic ...
+            unsigned long long wbase = 0;
+            if (lane == 0)
+                wbase = atomicAdd(&cnt->hits_listed, (unsigned long long)__popc(want));
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
             if (!hit)
                 continue;
-            const unsigned peers = __match_any_sync(want, (unsigned long long)tile);
-            const int leader = __ffs(peers) - 1;
-            if (!kScatter) {
-                if (lane == leader)
-                    atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
+            const long long slot = (long long)wbase + __popc(want & ((1u << lane) - 1u));
+            if (slot < cap_pairs) {
+                hit_entry[slot] = ((unsigned long long)key << 32) | (unsigned long long)g;
+                hit_tile[slot] = (unsigned)tile;
             } else {
-                unsigned base = 0;
-                if (lane == leader)
-                    base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
-                base = __shfl_sync(peers, base, leader);
-                const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-                const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + rank;
-                if (pos < cap_pairs)
-                    pairs[pos] = ((unsigned long long)key << 32) | (unsigned long long)g;
-                else
-                    atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+                atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
             }
+            // ... and every tile's count with one atomic per tile met
+            const unsigned peers = __match_any_sync(want, (unsigned long long)tile);
+            if (lane == __ffs(peers) - 1)
+                atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
         }
+    }
+}
+
+// Moves the listed hits into their tile bins (after the scan of the tile
+// counts): entry k goes to scan[tile] + its rank among the tile's entries.
+__global__ void __launch_bounds__(256) k_bin_scatter(const unsigned long long *__restrict__ hit_entry,
+                                                     const unsigned *__restrict__ hit_tile,
+                                                     const unsigned long long *__restrict__ scan,
+                                                     unsigned int *__restrict__ fill,
+                                                     unsigned long long *__restrict__ pairs, long long cap_pairs,
+                                                     Counters *cnt)
+{
+    const long long n = min((long long)cnt->hits_listed, cap_pairs);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < n; k0 += stride) {
+        const long long k = k0 + lane;
+        const bool ok = k < n;
+        const unsigned tile = ok ? hit_tile[k] : 0u;
+        const unsigned want = __ballot_sync(0xffffffffu, ok);
+        if (!ok)
+            continue;
+        const unsigned peers = __match_any_sync(want, tile);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (lane == leader)
+            base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + __popc(peers & ((1u << lane) - 1u));
+        if (pos < cap_pairs)
+            pairs[pos] = hit_entry[k];
+        else
+            atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
     }
 }
 
@@ -562,23 +599,21 @@ static int bin_grid()
 
 cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                              const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
-                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt, cudaStream_t st)
+                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt,
+                             unsigned long long *hit_entry, unsigned *hit_tile, long long cap_pairs, Counters *cnt,
+                             cudaStream_t st)
 {
     if (ttot > 0)
-        k_bin<false><<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box,
-                                                 tile_cnt, nullptr, nullptr, nullptr, 0, nullptr);
+        k_bin<<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt,
+                                          hit_entry, hit_tile, cap_pairs, cnt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_scatter(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
-                               const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
-                               const int4 *tbox, const float4 *tile_box, const unsigned long long *scan,
-                               unsigned int *fill, unsigned long long *pairs, long long cap_pairs, Counters *cnt,
-                               cudaStream_t st)
+cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
+                               const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
+                               long long cap_pairs, Counters *cnt, cudaStream_t st)
 {
-    if (ttot > 0)
-        k_bin<true><<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box,
-                                                nullptr, scan, fill, pairs, cap_pairs, cnt);
+    k_bin_scatter<<<bin_grid(), 256, 0, st>>>(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, cnt);
     return cudaGetLastError();
 }
 
