@@ -110,34 +110,6 @@ __host__ __device__ inline bool catch_interval(const float3 S[3], const float3 D
     return true;
 }
 
-// Convex hull (Andrew's monotone chain) of n <= 16 points; writes the hull
-// counter-clockwise (cross > 0 turns) without repeating the first point and
-// returns its size.  pts is sorted in place.
-__host__ __device__ inline int convex_hull(float2 *pts, int n, float2 *out)
-{
-    for (int i = 1; i < n; ++i) {
-        float2 key = pts[i];
-        int j = i - 1;
-        while (j >= 0 && (pts[j].x > key.x || (pts[j].x == key.x && pts[j].y > key.y))) {
-            pts[j + 1] = pts[j];
-            --j;
-        }
-        pts[j + 1] = key;
-    }
-    int k = 0;
-    for (int i = 0; i < n; ++i) {
-        while (k >= 2 && cross2(f2sub(out[k - 1], out[k - 2]), f2sub(pts[i], out[k - 2])) <= 0.f)
-            --k;
-        out[k++] = pts[i];
-    }
-    for (int i = n - 2, t = k + 1; i >= 0; --i) {
-        while (k >= t && cross2(f2sub(out[k - 1], out[k - 2]), f2sub(pts[i], out[k - 2])) <= 0.f)
-            --k;
-        out[k++] = pts[i];
-    }
-    return k > 1 ? k - 1 : k;
-}
-
 // Bounding box (x0, x1, y0, y1) of the annular sector around f between the
 // unit directions a (clockwise end) and b (counter-clockwise end, less than
 // half a turn from a) and the radii [rho0, rho1]; full = the whole disc.
@@ -166,17 +138,6 @@ __host__ __device__ inline float4 sector_box(float2 f, float2 a, float2 b, float
     return make_float4(x0, x1, y0, y1);
 }
 
-// Distance from f to the segment [p, q].
-__host__ __device__ inline float seg_dist(float2 f, float2 p, float2 q)
-{
-    const float2 e = f2sub(q, p), w = f2sub(f, p);
-    const float ee = e.x * e.x + e.y * e.y;
-    float s = ee > 0.f ? (w.x * e.x + w.y * e.y) / ee : 0.f;
-    s = fminf(fmaxf(s, 0.f), 1.f);
-    const float dx = w.x - s * e.x, dy = w.y - s * e.y;
-    return sqrtf(dx * dx + dy * dy);
-}
-
 // Rotate the unit vector a by the small angle whose sine is sn (positive =
 // counter-clockwise).
 __host__ __device__ inline float2 rot_small(float2 a, float sn)
@@ -184,61 +145,6 @@ __host__ __device__ inline float2 rot_small(float2 a, float sn)
     sn = fminf(fmaxf(sn, -1.f), 1.f);
     const float cs = sqrtf(fmaxf(0.f, 1.f - sn * sn));
     return make_float2(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
-}
-
-// Framebuffer box (u0, u1, v0, v1) that contains q^-1 of the convex display
-// polygon poly[0..n) grown by eps.  q^-1 is radial about the fovea f with
-// radius map p^-1 (Sec. 3.1.1), so the preimage lies in the annular sector
-// spanned by the polygon's directions and the radii p^-1 of its nearest and
-// farthest distances from f.  inv_alpha = 1/alpha.
-__host__ __device__ inline float4 fov_preimage_box(const float2 *poly, int n, float2 f, float inv_alpha, float eps)
-{
-    float rmax = 0.f, rmin = INFINITY;
-    for (int k = 0; k < n; ++k) {
-        const float2 w = f2sub(poly[k], f);
-        rmax = fmaxf(rmax, sqrtf(w.x * w.x + w.y * w.y));
-    }
-    // is f inside the polygon (within eps)?
-    float area = 0.f;
-    for (int k = 0; k < n; ++k)
-        area += cross2(poly[k], poly[(k + 1) % n]);
-    bool inside = n >= 3 && area != 0.f;
-    for (int k = 0; k < n && inside; ++k) {
-        const float2 p = poly[k], q = poly[(k + 1) % n];
-        const float2 e = f2sub(q, p);
-        const float len = sqrtf(e.x * e.x + e.y * e.y);
-        const float side = (area > 0.f ? 1.f : -1.f) * cross2(e, f2sub(f, p));
-        if (side < -eps * len)
-            inside = false;
-    }
-    if (!inside) {
-        for (int k = 0; k < n; ++k)
-            rmin = fminf(rmin, seg_dist(f, poly[k], poly[(k + 1) % n]));
-        rmin = fmaxf(0.f, rmin - eps);
-    }
-    rmax += eps;
-    const float kD1 = powf(kSqrt2, 1.f - inv_alpha);
-    const float rho1 = kD1 * powf(rmax, inv_alpha) * (1.f + 1e-5f) + 1e-6f;
-    if (inside || rmin <= 0.f)
-        return sector_box(f, make_float2(1.f, 0.f), make_float2(1.f, 0.f), 0.f, rho1, true);
-    const float rho0 = kD1 * powf(rmin, inv_alpha) * (1.f - 1e-5f);
-    float2 a = f2sub(poly[0], f), b = a;
-    for (int k = 1; k < n; ++k) {
-        const float2 w = f2sub(poly[k], f);
-        if (cross2(a, w) < 0.f)
-            a = w;
-        if (cross2(b, w) > 0.f)
-            b = w;
-    }
-    const float la = sqrtf(a.x * a.x + a.y * a.y), lb = sqrtf(b.x * b.x + b.y * b.y);
-    a = make_float2(a.x / la, a.y / la);
-    b = make_float2(b.x / lb, b.y / lb);
-    // the grown polygon spans a little more angle: asin(eps / r)
-    a = rot_small(a, -(eps / fmaxf(la, eps) + 1e-6f));
-    b = rot_small(b, eps / fmaxf(lb, eps) + 1e-6f);
-    if (cross2(a, b) <= 0.f)  // span reached half a turn: give up on angles
-        return sector_box(f, a, b, 0.f, rho1, true);
-    return sector_box(f, a, b, rho0, rho1, false);
 }
 
 // Display box (x0, x1, y0, y1) that contains q of the framebuffer box

@@ -139,12 +139,16 @@ cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long 
 
 // ---------------------------------------------------------------- bound
 
-// Result of stage (a) for one triangle.
+// Result of stage (a) for one triangle.  The half-planes sit in fixed slots
+// (kHpEdge + 0..2: edges of the triangle at t_min, kHpMotion + 0..1: across
+// its motion, kHpStrip + 0..1: the time strip) so that they stay in
+// registers; hmask marks the slots in use.
+constexpr int kHpEdge = 0, kHpMotion = 3, kHpStrip = 5;
 struct Bound {
     float xmin, xmax, ymin, ymax;  // display box
     float tmin, tmax;              // catch-up interval (0, 0 when not rolling)
     float4 hp[kMaxHp];             // outside iff a x + b y + c > 0
-    int nhp;
+    unsigned hmask;
     int i0, i1, j0, j1;            // framebuffer pixel box (inclusive)
     bool culled;
 };
@@ -154,38 +158,124 @@ __device__ __forceinline__ float3 lerp_pt(float3 S, float3 D, float t)
     return make_float3(fmaf(t, D.x, S.x), fmaf(t, D.y, S.y), fmaf(t, D.z, S.z));
 }
 
-// Half-plane through p -> q (counter-clockwise hull) with outward unit
-// normal, grown outward by eps.
-__device__ __forceinline__ float4 edge_halfplane(float2 p, float2 q, float eps)
+// Half-plane with unit normal n that holds the points q[0..nq): n . x <= the
+// largest n . q[k], grown by eps.
+template <int N>
+__device__ __forceinline__ float4 support_halfplane(float2 n, const float2 (&q)[N], int nq, float eps)
 {
-    const float ex = q.x - p.x, ey = q.y - p.y;
-    const float len = sqrtf(ex * ex + ey * ey);
-    const float a = ey / len, b = -ex / len;
-    return make_float4(a, b, -(a * p.x + b * p.y) - eps, 0.f);
+    float c = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (k < nq)
+            c = fmaxf(c, fmaf(n.x, q[k].x, n.y * q[k].y));
+    return make_float4(n.x, n.y, -c - eps, 0.f);
 }
 
-__device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 D[3], Bound &B)
+// Framebuffer box that holds q^-1 of a display region R (Sec. 3.1.1: q^-1
+// is radial about the fovea f with radius map p^-1).  pts[0..n) span at
+// least the angles of R about f and reach at least its largest distance
+// from f; rlo is a lower bound of the distance from f to R, used when f is
+// outside R.  The preimage then lies in the annular sector of those angles
+// and of the radii p^-1 of the nearest and farthest distance.
+template <int N>
+__device__ __forceinline__ float4 fov_sector_preimage(const float2 (&pts)[N], int n, float2 f, float inv_alpha,
+                                                      float eps, bool f_inside, float rlo)
+{
+    float rmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (k < n) {
+            const float2 w = f2sub(pts[k], f);
+            rmax = fmaxf(rmax, sqrtf(w.x * w.x + w.y * w.y));
+        }
+    rmax += eps;
+    const float kD1 = powf(kSqrt2, 1.f - inv_alpha);
+    const float rho1 = kD1 * powf(rmax, inv_alpha) * (1.f + 1e-5f) + 1e-6f;
+    const float rmin = f_inside ? 0.f : fmaxf(0.f, rlo - eps);
+    if (rmin <= 0.f)
+        return sector_box(f, make_float2(1.f, 0.f), make_float2(1.f, 0.f), 0.f, rho1, true);
+    const float rho0 = kD1 * powf(rmin, inv_alpha) * (1.f - 1e-5f);
+    // f lies outside the convex hull of the points: their directions from
+    // f span less than half a turn, and one sweep finds the two extremes
+    float2 a = f2sub(pts[0], f), b = a;
+#pragma unroll
+    for (int k = 1; k < N; ++k)
+        if (k < n) {
+            const float2 w = f2sub(pts[k], f);
+            if (cross2(a, w) < 0.f)
+                a = w;
+            if (cross2(b, w) > 0.f)
+                b = w;
+        }
+    const float la = sqrtf(a.x * a.x + a.y * a.y), lb = sqrtf(b.x * b.x + b.y * b.y);
+    a = make_float2(a.x / la, a.y / la);
+    b = make_float2(b.x / lb, b.y / lb);
+    // the region grown by eps spans a little more angle: asin(eps / r)
+    a = rot_small(a, -(eps / fmaxf(la, eps) + 1e-6f));
+    b = rot_small(b, eps / fmaxf(lb, eps) + 1e-6f);
+    if (cross2(a, b) <= 0.f)  // span reached half a turn: give up on angles
+        return sector_box(f, a, b, 0.f, rho1, true);
+    return sector_box(f, a, b, rho0, rho1, false);
+}
+
+// Triangles that reach the near plane (Sec. 4.2.2): the display box of the
+// points in front of it and of the crossings of all segments between the
+// space-time vertices (loops unrolled, so the points stay in registers).
+__device__ __forceinline__ void near_plane_box(const ViewDev &v, const float3 (&P)[6], int np, float &xmin,
+                                               float &xmax, float &ymin, float &ymax)
+{
+    xmin = INFINITY;
+    xmax = -INFINITY;
+    ymin = INFINITY;
+    ymax = -INFINITY;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        if (a < np && P[a].z >= v.z_near) {
+            const float2 q = project(v, P[a]);
+            xmin = fminf(xmin, q.x);
+            xmax = fmaxf(xmax, q.x);
+            ymin = fminf(ymin, q.y);
+            ymax = fmaxf(ymax, q.y);
+        }
+#pragma unroll
+        for (int b = a + 1; b < 6; ++b) {
+            const float za = P[a].z - v.z_near, zb = P[b].z - v.z_near;
+            if (b < np && (za < 0.f) != (zb < 0.f)) {
+                const float s = za / (za - zb);
+                const float2 q = project(
+                    v, make_float3(fmaf(s, P[b].x - P[a].x, P[a].x), fmaf(s, P[b].y - P[a].y, P[a].y), v.z_near));
+                xmin = fminf(xmin, q.x);
+                xmax = fmaxf(xmax, q.x);
+                ymin = fminf(ymin, q.y);
+                ymax = fmaxf(ymax, q.y);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 D[3], Bound &B)
 {
     const bool rolling = is_rolling(v.mode), fov = is_foveated(v.mode);
     const float eps = kEpsDisp;
-    B.nhp = 0;
+    B.hmask = 0u;
     B.culled = false;
     B.tmin = rolling ? v.t_lo : 0.f;
     B.tmax = rolling ? v.t_hi : 0.f;
 
     // the relevant space-time points: the triangle at the ends of the time domain
     float3 P[6];
-    int np = 3;
-    for (int k = 0; k < 3; ++k)
+    const int np = rolling && B.tmax != B.tmin ? 6 : 3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
         P[k] = lerp_pt(S[k], D[k], B.tmin);
-    if (rolling && B.tmax != B.tmin) {
-        for (int k = 0; k < 3; ++k)
-            P[3 + k] = lerp_pt(S[k], D[k], B.tmax);
-        np = 6;
+        P[3 + k] = lerp_pt(S[k], D[k], B.tmax);
     }
     // frustum culling against the near plane and the four side planes
     bool all_near = true, all_l = true, all_r = true, all_t = true, all_b = true, any_near = false;
-    for (int k = 0; k < np; ++k) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k >= np)
+            break;
         const float3 p = P[k];
         const float mx = 1e-6f * (fabsf(p.x) + v.tan_x * fabsf(p.z)) + 1e-30f;
         const float my = 1e-6f * (fabsf(p.y) + v.tan_y * fabsf(p.z)) + 1e-30f;
@@ -201,29 +291,17 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
         return;
     }
 
-    float2 Q[16];
+    float2 Q[6];  // display points of the region (projected space-time vertices)
     int nq = 0;
     bool use_hull = v.bound != PR_BOUND_QUAD && v.bound != PR_BOUND_TRIVIAL;
     bool strip = false;
+    float xmin, xmax, ymin, ymax;
     if (any_near) {
-        // split by the near plane (Sec. 4.2.2): keep the points in front of it
-        // and the crossings of all segments between the space-time vertices
-        for (int k = 0; k < np; ++k)
-            if (P[k].z >= v.z_near)
-                Q[nq++] = project(v, P[k]);
-        for (int a = 0; a < np; ++a)
-            for (int b = a + 1; b < np; ++b) {
-                const float za = P[a].z - v.z_near, zb = P[b].z - v.z_near;
-                if ((za < 0.f) != (zb < 0.f) && nq < 16) {
-                    const float s = za / (za - zb);
-                    float3 x = make_float3(fmaf(s, P[b].x - P[a].x, P[a].x), fmaf(s, P[b].y - P[a].y, P[a].y), v.z_near);
-                    Q[nq++] = project(v, x);
-                }
-            }
+        near_plane_box(v, P, np, xmin, xmax, ymin, ymax);
         use_hull = false;
     } else {
+        float tmin = B.tmin, tmax = B.tmax;
         if (rolling) {
-            float tmin = v.t_lo, tmax = v.t_hi;
             if (v.bound == PR_BOUND_ZENON) {
                 if (!catch_interval(S, D, v.tan_x, v.tan_y, v.d0, v.d1, v.t_lo, v.t_hi, tmin, tmax)) {
                     B.culled = true;
@@ -234,7 +312,10 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
                 // Sec. 4.2.3: the times at which the projected space-time
                 // vertices are shown bound the times of every covered pixel
                 float lo = INFINITY, hi = -INFINITY;
-                for (int k = 0; k < np; ++k) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    if (k >= np)
+                        break;
                     const float2 x = project(v, P[k]);
                     const float r = fmaf(x.x, v.d0, x.y * v.d1);
                     lo = fminf(lo, r);
@@ -250,23 +331,23 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
             }
             B.tmin = tmin;
             B.tmax = tmax;
-            for (int k = 0; k < 3; ++k)
-                Q[nq++] = project(v, lerp_pt(S[k], D[k], tmin));
-            if (tmax != tmin)
-                for (int k = 0; k < 3; ++k)
-                    Q[nq++] = project(v, lerp_pt(S[k], D[k], tmax));
-        } else {
-            for (int k = 0; k < 3; ++k)
-                Q[nq++] = project(v, S[k]);
         }
-    }
-
-    float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
-    for (int k = 0; k < nq; ++k) {
-        xmin = fminf(xmin, Q[k].x);
-        xmax = fmaxf(xmax, Q[k].x);
-        ymin = fminf(ymin, Q[k].y);
-        ymax = fmaxf(ymax, Q[k].y);
+        nq = rolling && tmax != tmin ? 6 : 3;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Q[k] = project(v, lerp_pt(S[k], D[k], tmin));
+            Q[3 + k] = project(v, lerp_pt(S[k], D[k], tmax));
+        }
+        xmin = ymin = INFINITY;
+        xmax = ymax = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < nq) {
+                xmin = fminf(xmin, Q[k].x);
+                xmax = fmaxf(xmax, Q[k].x);
+                ymin = fminf(ymin, Q[k].y);
+                ymax = fmaxf(ymax, Q[k].y);
+            }
     }
     const float mx = eps * fmaxf(1.f, fmaxf(fabsf(xmin), fabsf(xmax)));
     const float my = eps * fmaxf(1.f, fmaxf(fabsf(ymin), fabsf(ymax)));
@@ -288,8 +369,9 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
             ymin = fmaxf(ymin, (B.tmin - kEpsT) / v.d1);
             ymax = fminf(ymax, (B.tmax + kEpsT) / v.d1);
         }
-        B.hp[B.nhp++] = make_float4(-v.d0 / dn, -v.d1 / dn, (B.tmin - kEpsT) / dn, 0.f);
-        B.hp[B.nhp++] = make_float4(v.d0 / dn, v.d1 / dn, -(B.tmax + kEpsT) / dn, 0.f);
+        B.hp[kHpStrip] = make_float4(-v.d0 / dn, -v.d1 / dn, (B.tmin - kEpsT) / dn, 0.f);
+        B.hp[kHpStrip + 1] = make_float4(v.d0 / dn, v.d1 / dn, -(B.tmax + kEpsT) / dn, 0.f);
+        B.hmask |= 3u << kHpStrip;
     }
     // clip to the viewport (every ray's display location lies in [0,1]^2)
     xmin = fmaxf(xmin, -eps);
@@ -305,20 +387,42 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
     B.ymin = ymin;
     B.ymax = ymax;
 
-    // convex hull (Sec. 4.2.2) -> half-planes
-    float2 H[16];
-    int nh = 0;
+    // Sec. 4.2.2: the convex hull of the projected space-time vertices.  Its
+    // half-planes are taken as support lines of the points in the three edge
+    // directions of the triangle at t_min and the two directions across the
+    // triangle's mean motion: for a motion that is a translation these are
+    // exactly the hull's edges, otherwise they bound a slightly larger
+    // convex region -- still a bound.
     if (use_hull) {
-        float2 tmp[32];
-        nh = convex_hull(Q, nq, tmp);
-        for (int k = 0; k < nh; ++k)
-            H[k] = tmp[k];
-        if (nh >= 3) {
-            const float gm = eps * fmaxf(1.f, fmaxf(fmaxf(fabsf(xmin), fabsf(xmax)), fmaxf(fabsf(ymin), fabsf(ymax))));
-            for (int k = 0; k < nh && B.nhp < kMaxHp; ++k) {
-                const float2 p = H[k], q = H[(k + 1) % nh];
-                if (p.x != q.x || p.y != q.y)
-                    B.hp[B.nhp++] = edge_halfplane(p, q, gm);
+        const float gm = eps * fmaxf(1.f, fmaxf(fmaxf(fabsf(xmin), fabsf(xmax)), fmaxf(fabsf(ymin), fabsf(ymax))));
+        const float area = cross2(f2sub(Q[1], Q[0]), f2sub(Q[2], Q[0]));
+        if (area != 0.f) {
+            const float orient = area > 0.f ? 1.f : -1.f;  // outward normal = orient * (ey, -ex)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const float2 p = Q[e], q = Q[(e + 1) % 3];
+                const float ex = q.x - p.x, ey = q.y - p.y, l2 = ex * ex + ey * ey;
+                if (l2 > 0.f) {
+                    const float il = orient / sqrtf(l2);
+                    B.hp[kHpEdge + e] = support_halfplane(make_float2(ey * il, -ex * il), Q, nq, gm);
+                    B.hmask |= 1u << (kHpEdge + e);
+                }
+            }
+        }
+        if (nq == 6) {
+            float mvx = 0.f, mvy = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                mvx += Q[3 + k].x - Q[k].x;
+                mvy += Q[3 + k].y - Q[k].y;
+            }
+            const float l2 = mvx * mvx + mvy * mvy;
+            if (l2 > 0.f) {
+                const float il = 1.f / sqrtf(l2);
+                const float2 n = make_float2(-mvy * il, mvx * il);
+                B.hp[kHpMotion] = support_halfplane(n, Q, nq, gm);
+                B.hp[kHpMotion + 1] = support_halfplane(make_float2(-n.x, -n.y), Q, nq, gm);
+                B.hmask |= 3u << kHpMotion;
             }
         }
     }
@@ -326,20 +430,24 @@ __device__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 
     // framebuffer pixel box
     float u0, u1, w0, w1;
     if (fov) {
-        float2 poly[16];
-        int n;
-        if (use_hull && nh >= 3) {
-            for (int k = 0; k < nh; ++k)
-                poly[k] = H[k];
-            n = nh;
+        const float2 f = make_float2(v.fx, v.fy);
+        // distance from f to the region: at least its distance to the box and
+        // to every half-plane it violates
+        const float dbx = fmaxf(fmaxf(xmin - f.x, f.x - xmax), 0.f), dby = fmaxf(fmaxf(ymin - f.y, f.y - ymax), 0.f);
+        float rlo = sqrtf(dbx * dbx + dby * dby);
+#pragma unroll
+        for (int h = 0; h < kMaxHp; ++h)
+            if (B.hmask & (1u << h))
+                rlo = fmaxf(rlo, fmaf(B.hp[h].x, f.x, fmaf(B.hp[h].y, f.y, B.hp[h].z)));
+        const bool inside = rlo <= 2.f * eps;
+        float4 fb;
+        if (use_hull) {
+            fb = fov_sector_preimage(Q, nq, f, v.inv_alpha, 2.f * eps, inside, rlo);
         } else {
-            poly[0] = make_float2(xmin, ymin);
-            poly[1] = make_float2(xmax, ymin);
-            poly[2] = make_float2(xmax, ymax);
-            poly[3] = make_float2(xmin, ymax);
-            n = 4;
+            const float2 corners[4] = {make_float2(xmin, ymin), make_float2(xmax, ymin), make_float2(xmax, ymax),
+                                       make_float2(xmin, ymax)};
+            fb = fov_sector_preimage(corners, 4, f, v.inv_alpha, 2.f * eps, inside, rlo);
         }
-        const float4 fb = fov_preimage_box(poly, n, make_float2(v.fx, v.fy), v.inv_alpha, 2.f * eps);
         u0 = fb.x;
         u1 = fb.y;
         w0 = fb.z;
@@ -402,13 +510,16 @@ __global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views
     }
     r[4] = make_float4(B.xmin, B.xmax, B.ymin, B.ymax);
     r[5] = make_float4(B.tmin - kEpsT, B.tmax + kEpsT, D[2].y, D[2].z);
-    for (int h = 0; h < B.nhp; ++h)
-        hp[g * kMaxHp + h] = B.hp[h];
+    int nhp = 0;
+#pragma unroll
+    for (int h = 0; h < kMaxHp; ++h)
+        if (B.hmask & (1u << h))
+            hp[g * kMaxHp + nhp++] = B.hp[h];
     // nearest camera depth the moving triangle reaches (z is linear in t on
     // every vertex): min_k S_k.z + min(0, D_k.z), the sort key of its pairs
     const float near = fminf(fminf(S[0].z + fminf(0.f, D[0].z), S[1].z + fminf(0.f, D[1].z)),
                              S[2].z + fminf(0.f, D[2].z));
-    tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), B.nhp, (int)depth_order_key(near));
+    tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), nhp, (int)depth_order_key(near));
     cand[g] = (unsigned long long)(B.i1 / v.S - B.i0 / v.S + 1) * (unsigned long long)(B.j1 / v.S - B.j0 / v.S + 1);
 }
 

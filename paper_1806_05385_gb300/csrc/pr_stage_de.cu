@@ -70,8 +70,10 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     h.b2 = W * inv;
     float3 n = cross3(sub3(h.B, h.A), sub3(h.C, h.A));
     h.flip = dot3(n, h.dir) > 0.f ? -1.f : 1.f;
-    h.nlen = sqrtf(dot3(n, n));
-    const float in = h.nlen > 0.f ? h.flip / h.nlen : 0.f;
+    const float nn = dot3(n, n);
+    const float rs = nn > 0.f ? rsqrtf(nn) : 0.f;
+    h.nlen = nn * rs;
+    const float in = h.flip * rs;
     h.n = scale3(n, in);
     float3 l = make_float3(fmaf(t, v.l1[0] - v.l0[0], v.l0[0]), fmaf(t, v.l1[1] - v.l0[1], v.l0[1]),
                            fmaf(t, v.l1[2] - v.l0[2], v.l0[2]));
