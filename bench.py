@@ -201,20 +201,30 @@ def reference_arm(args, rank, world):
 METRIC = "Mpix/s & ray-tri tests/s at 1 GB300 (batched vs plain); fwd+bwd ms/frame"
 
 
-def source_hash():
-    p = os.path.join(ROOT, "paper_1806_05385_gb300", "csrc", "pr_stage_c.cu")
+def source_hash(name: str = "pr_stage_c.cu"):
+    p = os.path.join(ROOT, "paper_1806_05385_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def ncu_traffic(workload_kind: str):
-    """DRAM bytes per fragment launch from the committed ncu summary, only
-    if it was taken on this workload and on the current fragment source."""
-    p = os.path.join(ROOT, "profiles", "fragment_traffic.json")
+def measured_peak(key: str):
     try:
-        d = json.load(open(p))
-    except (OSError, ValueError):
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0 if key == "hbm_gbs" else None  # the recipe's fallback
+
+
+KERNEL_SOURCES = {"k_fragment": "pr_stage_c.cu", "k_shade<1>": "pr_stage_de.cu"}
+
+
+def ncu_traffic(workload_kind: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, only
+    if it was taken on this workload and on the kernel's current source."""
+    p = os.path.join(ROOT, "profiles", "traffic_hmd.json")
+    try:
+        d = json.load(open(p))[kernel]
+    except (OSError, ValueError, KeyError):
         return None
-    if d.get("source_sha256_16") != source_hash() or d.get("workload") != workload_kind:
+    if d.get("source_sha256_16") != source_hash(KERNEL_SOURCES[kernel]) or d.get("workload") != workload_kind:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -357,17 +367,36 @@ def our_arm(args, rank, world):
         e2e = {"value": world * pix / (statistics.mean(ems) * 1e-3) / 1e6, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant kernel (stage c, FP32 ALU bound)
+    # rooflines: stage (c) k_fragment (FP32 ALU) and the training frame's
+    # shading + adjoint kernel k_shade<1> (HBM); the bench line's "roofline"
+    # is the one of the two that takes longer per frame
     sm_mhz = clocks.get("sm_mhz") or 1470.0
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     achieved = st["tests"] * FLOP_PER_TEST / (frag_ms * 1e-3) / 1e12 if frag_ms > 0 else 0.0
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": ncu_traffic(args.workload),
-            "kernel": "k_fragment", "flop_per_test": FLOP_PER_TEST,
-            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x median SM clock {sm_mhz:.0f} MHz "
-                          f"sampled during the timed region (no FP32 figure in MEASURED_PEAKS.json)",
-            "achieved_basis": "ray-triangle tests of one forward frame x 39 FLOP / fragment-stage time of that "
-                              "frame (CUDA events on the launching stream, inside the graph replay)"}
+    roof_frag = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak if peak else None, "traffic": ncu_traffic(args.workload, "k_fragment"),
+                 "kernel": "k_fragment", "time_ms": frag_ms, "flop_per_test": FLOP_PER_TEST,
+                 "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x median SM clock {sm_mhz:.0f} MHz "
+                               f"sampled during the timed region (no FP32 figure in MEASURED_PEAKS.json)",
+                 "achieved_basis": "ray-triangle tests of one frame x 39 FLOP / fragment-stage time of that frame "
+                                   "(CUDA events on the launching stream, inside the graph replay)"}
+    # k_shade<1>: per pixel 8 B key in, 4 B id + 4 B depth + 12 B rgb out, 12 B
+    # upstream gradient in; per visible triangle 108 B vertex data in (3 x
+    # position, velocity, colour) and 108 B gradients out (3 x dcol, dpos, dvel)
+    shade_ms = st["stage_ms"][5]
+    visible = sum(int(torch.unique(x[x >= 0]).numel()) for x in ids)
+    shade_bytes = 40 * pix + 216 * visible
+    hbm_peak = measured_peak("hbm_gbs")
+    shade_gbs = shade_bytes / (shade_ms * 1e-3) / 1e9 if shade_ms > 0 else 0.0
+    roof_shade = {"bound": "hbm", "achieved": shade_gbs, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": shade_gbs / hbm_peak if hbm_peak else None,
+                  "traffic": ncu_traffic(args.workload, "k_shade<1>"), "kernel": "k_shade<1>", "time_ms": shade_ms,
+                  "algorithmic_bytes": shade_bytes, "visible_triangles": visible,
+                  "peak_basis": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                  "achieved_basis": "40 B per pixel + 216 B per visible triangle / shading + adjoint stage time "
+                                    "(CUDA events inside the graph replay)"}
+    roof, roof2 = (roof_shade, roof_frag) if shade_ms > frag_ms else (roof_frag, roof_shade)
+    roof = dict(roof, secondary=roof2)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
