@@ -56,7 +56,8 @@ typedef enum {
     PR_ERR_INVALID_ARG = 1, /* a size, mode, pointer or parameter is out of range */
     PR_ERR_CUDA = 2,        /* a CUDA runtime call failed (no device, launch error, ...) */
     PR_ERR_OOM = 3,         /* device allocation failed */
-    PR_ERR_OVERFLOW = 4,    /* a device buffer was too small even after regrowing */
+    PR_ERR_OVERFLOW = 4,    /* a device buffer was too small even after regrowing, or a frame
+                               needs more than 2^31 - 1 bin entries (split it into smaller calls) */
     PR_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
     PR_ERR_NONFINITE = 6,   /* an input position/velocity/colour is NaN or Inf */
     PR_ERR_NO_CUDA = 7      /* no CUDA device is visible */
@@ -81,6 +82,16 @@ typedef enum {
     PR_BOUND_TRIVIAL = 4   /* the whole viewport */
 } pr_bound;
 
+/* Foveation part of the bound (foveated and joint modes).  The triangle's
+ * region is always tested in display space against each tile's display
+ * image; this selects how its framebuffer extent is found and, for the
+ * paper's two edge bounds, the polygon that bins tiles. */
+typedef enum {
+    PR_FOV_SECTOR = 0,     /* annular sector of q^-1 of the region (rigorous, default) */
+    PR_FOV_SIMPLE = 1,     /* Sec. 4.1.1: each region edge displaced parallel to itself */
+    PR_FOV_RECURSIVE = 2   /* Sec. 4.1.2: displaced parallel to the chord of its foveated end points */
+} pr_fov_bound;
+
 /* One view: the camera, the two poses that bracket the frame, the fovea,
  * the display's rolling direction and the shading constants. */
 typedef struct {
@@ -103,6 +114,10 @@ typedef struct {
     int32_t tile;         /* bin tile side in pixels: 8, 16 or 32; 0 = library default (16) */
     int32_t fp64_retest;  /* 1: re-test fragments flagged by the FP32 error bound in FP64 */
     int32_t seg;          /* triangles per fragment work item; 0 = default (256), at most 1024 */
+    int32_t fov_bound;    /* pr_fov_bound.  SIMPLE and RECURSIVE rest on the paper's assumption that
+                             an edge's displacement is unimodal (ternary search); the library seeds
+                             the search with a coarse scan and adds half a pixel, but they are not
+                             rigorous for every edge (the sector bound is) */
 } pr_params;
 
 /* Counters of the last rasterize call on a scene or workspace. */

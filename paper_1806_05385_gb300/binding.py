@@ -21,6 +21,8 @@ PR_OK, PR_ERR_INVALID_ARG, PR_ERR_CUDA, PR_ERR_OOM, PR_ERR_OVERFLOW, PR_ERR_TIME
     PR_ERR_NO_CUDA = range(8)
 PR_CLASSIC, PR_ROLLING, PR_FOVEATED, PR_BOTH = range(4)
 PR_BOUND_ZENON, PR_BOUND_ADAPTIVE, PR_BOUND_HULL, PR_BOUND_QUAD, PR_BOUND_TRIVIAL = range(5)
+PR_FOV_SECTOR, PR_FOV_SIMPLE, PR_FOV_RECURSIVE = range(3)
+FOV_BOUND_NAMES = {"sector": PR_FOV_SECTOR, "simple": PR_FOV_SIMPLE, "recursive": PR_FOV_RECURSIVE}
 BOUND_NAMES = {"zenon": 0, "adaptive": 1, "hull": 2, "quad": 3, "trivial": 4}
 BG = 0xFFFFFFFF
 
@@ -45,7 +47,8 @@ class PrView(C.Structure):
 
 
 class PrParams(C.Structure):
-    _fields_ = [("bound", C.c_int32), ("tile", C.c_int32), ("fp64_retest", C.c_int32), ("seg", C.c_int32)]
+    _fields_ = [("bound", C.c_int32), ("tile", C.c_int32), ("fp64_retest", C.c_int32), ("seg", C.c_int32),
+                ("fov_bound", C.c_int32)]
 
 
 class PrStats(C.Structure):
@@ -175,10 +178,12 @@ def make_view(v) -> PrView:
     return out
 
 
-def make_params(bound=PR_BOUND_ZENON, tile=0, fp64_retest=0, seg=0) -> PrParams:
+def make_params(bound=PR_BOUND_ZENON, tile=0, fp64_retest=0, seg=0, fov_bound=PR_FOV_SECTOR) -> PrParams:
     if isinstance(bound, str):
         bound = BOUND_NAMES[bound]
-    return PrParams(int(bound), int(tile), int(fp64_retest), int(seg))
+    if isinstance(fov_bound, str):
+        fov_bound = FOV_BOUND_NAMES[fov_bound]
+    return PrParams(int(bound), int(tile), int(fp64_retest), int(seg), int(fov_bound))
 
 
 # ------------------------------------------------------------------ entry points

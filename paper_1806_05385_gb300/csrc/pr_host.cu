@@ -123,6 +123,7 @@ pr_status from_cuda(cudaError_t e)
 
 constexpr int kDefaultTile = 16;
 constexpr int kDefaultSeg = 256;
+constexpr long long kMaxPairs = 0x7FFFFFFFll;  // bin entries per frame: work items hold 32-bit offsets
 
 }  // namespace
 
@@ -285,7 +286,7 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
 
 pr_params default_params(const pr_params *p)
 {
-    pr_params d{PR_BOUND_ZENON, kDefaultTile, 0, kDefaultSeg};
+    pr_params d{PR_BOUND_ZENON, kDefaultTile, 0, kDefaultSeg, PR_FOV_SECTOR};
     if (p) {
         d = *p;
         if (d.tile == 0)
@@ -308,6 +309,7 @@ struct BatchPlan {
         long long tile_lo, tile_hi;
     };
     bool any_fp64 = false;
+    bool any_paper_fov = false;  // some foveated view asks for the paper's edge bound
     std::vector<Cls> classes;
     // output staging: per view (in order) device pointers used by kernels
     std::vector<pr_frame_grad> grads;  // per view (in order); empty: no adjoint
@@ -354,6 +356,10 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
         pr_status s = make_viewdev(bv.view, bv.scene, tiles[P.order[q]], prm.bound, prm.fp64_retest, P.vd[q]);
         if (s != PR_OK)
             return s;
+        if (prm.fov_bound < PR_FOV_SECTOR || prm.fov_bound > PR_FOV_RECURSIVE)
+            return PR_ERR_INVALID_ARG;
+        P.vd[q].fov_bound = prm.fov_bound;
+        P.any_paper_fov |= prm.fov_bound != PR_FOV_SECTOR && (bv.view.mode == PR_FOVEATED || bv.view.mode == PR_BOTH);
         ViewDev &v = P.vd[q];
         v.tri_off = P.tri_off[q];
         v.tile_off = P.tile_off[q];
@@ -434,18 +440,18 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->counters, sizeof(Counters)));
     PR_TRY(ensure(ws->heads, sizeof(int) * 8));
     PR_TRY(ensure(ws->stage, std::max<size_t>(P.stage_bytes, 256)));
-    const long long want_pairs = std::max(ws->cap_pairs, 2 * P.ttot + P.ntiles + 1024);
+    const long long want_pairs = std::min(std::max(ws->cap_pairs, 2 * P.ttot + P.ntiles + 1024), kMaxPairs);
     if ((size_t)want_pairs * sizeof(unsigned long long) > ws->pairs.cap || !ws->pairs.p) {
         PR_TRY(ensure(ws->pairs, sizeof(unsigned long long) * want_pairs));
     }
-    ws->cap_pairs = (long long)(ws->pairs.cap / sizeof(unsigned long long));
+    ws->cap_pairs = std::min((long long)(ws->pairs.cap / sizeof(unsigned long long)), kMaxPairs);
     PR_TRY(ensure(ws->hit_entry, sizeof(unsigned long long) * ws->cap_pairs));
     PR_TRY(ensure(ws->hit_tile, sizeof(unsigned) * ws->cap_pairs));
     const long long want_items = std::max(ws->cap_items, ws->cap_pairs / seg + P.ntiles + 1024);
     if ((size_t)want_items * sizeof(int4) > ws->items.cap || !ws->items.p) {
         PR_TRY(ensure(ws->items, sizeof(int4) * want_items));
     }
-    ws->cap_items = (long long)(ws->items.cap / sizeof(int4));
+    ws->cap_items = std::min((long long)(ws->items.cap / sizeof(int4)), kMaxPairs);
     PR_TRY(ws->h_views.ensure(n));
     PR_TRY(ws->h_offs.ensure(4 * (n + 1)));
     PR_TRY(ws->h_cnt.ensure(1));
@@ -511,6 +517,8 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(mark(0));
     PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
     PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, cnt, st));
+    if (P.any_paper_fov)
+        PR_TRY(launch_paper_fov(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, st));
     PR_TRY(mark(1));
     PR_TRY(launch_scan(cand, cand_off, ws->sums.as<unsigned long long>(), P.ttot, 0, cnt, st));
     PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt,
@@ -604,10 +612,14 @@ pr_status run_batch(pr_workspace *ws, const pr_batch_view *views, int n, const p
         if (s != PR_ERR_OVERFLOW)
             return s;
         const Counters &c = *ws->h_cnt.p;
+        // work items address bin entries with 32-bit offsets: a frame with
+        // more entries than that is refused, not regrown
+        if ((long long)c.pairs_total > kMaxPairs || (long long)c.items_total > kMaxPairs)
+            return PR_ERR_OVERFLOW;
         ws->cap_pairs = std::max<long long>(ws->cap_pairs, (long long)c.pairs_total + 1024);
         ws->cap_items = std::max<long long>(ws->cap_items, (long long)c.items_total + 1024);
-        ws->cap_pairs += ws->cap_pairs / 4;
-        ws->cap_items += ws->cap_items / 4;  // size_workspace grows both buffers to these
+        ws->cap_pairs = std::min(ws->cap_pairs + ws->cap_pairs / 4, kMaxPairs);
+        ws->cap_items = std::min(ws->cap_items + ws->cap_items / 4, kMaxPairs);  // size_workspace grows both to these
     }
     return PR_ERR_OVERFLOW;
 }

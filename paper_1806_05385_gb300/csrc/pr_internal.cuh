@@ -39,6 +39,7 @@ struct ViewDev {
     float k_a, k_d;
     int W, H, mode, S;                 // framebuffer, pr_mode, bin tile side
     int tiles_x, tiles_y, bound, fp64;
+    int fov_bound;                     // pr_fov_bound
     long long tri_off, tile_off, pix_off;  // offsets of this view in the batch-wide arrays
     long long blk_off;                 // offset of its 8x4 pixel blocks (stages d, e)
     int T, V;

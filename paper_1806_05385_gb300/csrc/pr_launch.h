@@ -19,6 +19,9 @@ cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long 
                               float4 *tile_box, cudaStream_t st);
 cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
                          float4 *hp, int4 *tbox, unsigned long long *cand, Counters *cnt, cudaStream_t st);
+// the paper's foveation edge bounds for the views that select them (after launch_bound)
+cudaError_t launch_paper_fov(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
+                             const float4 *rec, float4 *hp, int4 *tbox, unsigned long long *cand, cudaStream_t st);
 
 // stage (b): tile binning -- count pass (tile counts, and every hit appended to the hit list),
 // then after the scan the scatter of the list into the bins

@@ -227,6 +227,10 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     pr_status s = view_constants(*view, tile, bound, soa, idx, V, T, v);
     if (s != PR_OK)
         return s;
+    const int fov_bound = params ? params->fov_bound : PR_FOV_SECTOR;
+    if (fov_bound < PR_FOV_SECTOR || fov_bound > PR_FOV_RECURSIVE)
+        return PR_ERR_INVALID_ARG;
+    v.fov_bound = fov_bound;
     v.id_out = id_out;
     v.depth_out = depth_out;
     long long offs[8] = {0, T, 0, nt, 0, np, 0, 0};  // tri, tile, pixel offsets of the one view
@@ -262,6 +266,8 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_scene_check(soa, V, cnt, st));
     NA_TRY(launch_tile_boxes(dv, 1, tile_offs, nt, tile_box, st));
     NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, cnt, st));
+    if (fov_bound != PR_FOV_SECTOR && (view->mode == PR_FOVEATED || view->mode == PR_BOTH))
+        NA_TRY(launch_paper_fov(dv, 1, tri_offs, T, rec, hp, tbox, cand, st));
     NA_TRY(launch_scan(cand, cand_off, sums, T, 0, cnt, st));
     NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry, hit_tile,
                             cap_pairs, cnt, st));

@@ -253,6 +253,153 @@ __device__ __forceinline__ void near_plane_box(const ViewDev &v, const float3 (&
     }
 }
 
+// q^-1 (display -> framebuffer): radial about the fovea with p^-1(d) = D (d/D)^(1/alpha).
+__device__ __forceinline__ float2 fov_inverse(float2 x, float2 f, float inv_alpha)
+{
+    const float ex = x.x - f.x, ey = x.y - f.y, r = sqrtf(ex * ex + ey * ey);
+    const float s = r > 0.f ? powf(r * (1.f / kSqrt2), inv_alpha - 1.f) : 0.f;
+    return make_float2(fmaf(ex, s, f.x), fmaf(ey, s, f.y));
+}
+
+// Clips the convex polygon in[0..n) by a x + b y + c <= 0; returns the new size (<= cap).
+__device__ __forceinline__ int clip_polygon(const float2 *in, int n, float4 h, float2 *out, int cap)
+{
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const float2 p = in[i], q = in[i + 1 < n ? i + 1 : 0];
+        const float dp = fmaf(h.x, p.x, fmaf(h.y, p.y, h.z)), dq = fmaf(h.x, q.x, fmaf(h.y, q.y, h.z));
+        if (dp <= 0.f && m < cap)
+            out[m++] = p;
+        if (((dp < 0.f && dq > 0.f) || (dp > 0.f && dq < 0.f)) && m < cap) {
+            const float t = dp / (dp - dq);
+            out[m++] = make_float2(fmaf(t, q.x - p.x, p.x), fmaf(t, q.y - p.y, p.y));
+        }
+    }
+    return m;
+}
+
+// The paper's foveated edge bounds (Sec. 4.1).  The region's display
+// polygon (its box clipped by its half-planes) is bounded edge by edge in
+// the framebuffer: the image under q^-1 of the straight edge x0 -> x1 is a
+// curve, and the bounding line has the edge's own direction (Simple) or the
+// direction of the chord between q^-1(x0) and q^-1(x1) (Recursive), pushed
+// out to the farthest point of the curved region along its normal.  The
+// paper pushes each line out to its own curve only, which does not hold the
+// region when a neighbouring curve bulges past the line under a strong warp;
+// here every curve is searched.  Each farthest point is found, as in the
+// paper, by a ternary search over the edge parameter (a number of steps
+// logarithmic in the edge's length in pixels), here seeded by a coarse scan
+// of 9 points, and the line gets half a pixel of margin.  Writes the
+// framebuffer half-planes to out (at most kMaxHp); returns their number
+// (0 when the polygon has more edges than that) and their box.
+struct PaperFov {
+    int n;
+    float4 fb;
+};
+__device__ __forceinline__ PaperFov paper_fov_bound(const ViewDev &v, const float4 *hps, unsigned hmask, float xmin,
+                                                 float xmax, float ymin, float ymax, float4 *out)
+{
+    PaperFov r;
+    r.n = 0;
+    r.fb = make_float4(1.f, 0.f, 1.f, 0.f);  // empty
+    float2 A[16], Bv[16];
+    A[0] = make_float2(xmin, ymin);
+    A[1] = make_float2(xmax, ymin);
+    A[2] = make_float2(xmax, ymax);
+    A[3] = make_float2(xmin, ymax);
+    int n = 4;
+    for (int h = 0; h < kMaxHp; ++h)
+        if (hmask & (1u << h)) {
+            n = clip_polygon(A, n, hps[h], Bv, 16);
+            for (int k = 0; k < n; ++k)
+                A[k] = Bv[k];
+        }
+    // drop repeated vertices (zero-length edges)
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        const float2 p = A[k], q = m > 0 ? A[m - 1] : A[n - 1];
+        if (m == 0 ? true : (fabsf(p.x - q.x) + fabsf(p.y - q.y) > 1e-9f))
+            A[m++] = p;
+    }
+    if (m > 1 && fabsf(A[0].x - A[m - 1].x) + fabsf(A[0].y - A[m - 1].y) <= 1e-9f)
+        --m;
+    if (m < 3 || m > kMaxHp)
+        return r;
+    const float2 f = make_float2(v.fx, v.fy);
+    const float margin = 0.5f / (float)max(v.W, v.H) + 1e-6f;
+    const float px = (float)max(v.W, v.H);
+    for (int k = 0; k < m; ++k) {
+        const float2 x0 = A[k], x1 = A[k + 1 < m ? k + 1 : 0];
+        float2 d = make_float2(x1.x - x0.x, x1.y - x0.y);
+        if (v.fov_bound == PR_FOV_RECURSIVE) {
+            const float2 a = fov_inverse(x0, f, v.inv_alpha), b = fov_inverse(x1, f, v.inv_alpha);
+            const float2 c = make_float2(b.x - a.x, b.y - a.y);
+            if (c.x * c.x + c.y * c.y > 1e-20f)
+                d = c;
+        }
+        const float len = sqrtf(d.x * d.x + d.y * d.y);
+        const float2 nrm = make_float2(d.y / len, -d.x / len);  // outward for the counter-clockwise polygon
+        // the line must hold the whole curved region, not only its own edge's
+        // image (under a strong warp a neighbouring curve can bulge past it):
+        // the farthest point along the normal over every curved edge
+        float best = -INFINITY;
+        for (int e = 0; e < m; ++e) {
+            const float2 y0 = A[e], y1 = A[e + 1 < m ? e + 1 : 0];
+            auto support = [&](float s) {
+                const float2 u = fov_inverse(make_float2(fmaf(s, y1.x - y0.x, y0.x), fmaf(s, y1.y - y0.y, y0.y)), f,
+                                             v.inv_alpha);
+                return fmaf(nrm.x, u.x, nrm.y * u.y);
+            };
+            int kb = 0;
+            float eb = -INFINITY;
+            for (int j = 0; j <= 8; ++j) {
+                const float val = support(j * 0.125f);
+                if (val > eb) {
+                    eb = val;
+                    kb = j;
+                }
+            }
+            float lo = fmaxf(0.f, (kb - 1) * 0.125f), hi = fminf(1.f, (kb + 1) * 0.125f);
+            const float edge_px = sqrtf((y1.x - y0.x) * (y1.x - y0.x) + (y1.y - y0.y) * (y1.y - y0.y)) * px;
+            const int steps = 2 + (int)ceilf(log2f(fmaxf(edge_px, 1.f)));
+            for (int it = 0; it < steps; ++it) {
+                const float m1 = lo + (hi - lo) * (1.f / 3.f), m2 = hi - (hi - lo) * (1.f / 3.f);
+                const float f1 = support(m1), f2 = support(m2);
+                eb = fmaxf(eb, fmaxf(f1, f2));
+                if (f1 < f2)
+                    lo = m1;
+                else
+                    hi = m2;
+            }
+            best = fmaxf(best, eb);
+        }
+        out[k] = make_float4(nrm.x, nrm.y, -(best + margin), 0.f);
+    }
+    // framebuffer box: the viewport clipped by the bounding lines
+    A[0] = make_float2(-margin, -margin);
+    A[1] = make_float2(1.f + margin, -margin);
+    A[2] = make_float2(1.f + margin, 1.f + margin);
+    A[3] = make_float2(-margin, 1.f + margin);
+    n = 4;
+    for (int k = 0; k < m; ++k) {
+        n = clip_polygon(A, n, out[k], Bv, 16);
+        for (int j = 0; j < n; ++j)
+            A[j] = Bv[j];
+    }
+    r.n = m;
+    if (n == 0)
+        return r;
+    float4 fb = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    for (int j = 0; j < n; ++j) {
+        fb.x = fminf(fb.x, A[j].x);
+        fb.y = fmaxf(fb.y, A[j].x);
+        fb.z = fminf(fb.z, A[j].y);
+        fb.w = fmaxf(fb.w, A[j].y);
+    }
+    r.fb = fb;
+    return r;
+}
+
 __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3], const float3 D[3], Bound &B)
 {
     const bool rolling = is_rolling(v.mode), fov = is_foveated(v.mode);
@@ -532,6 +679,60 @@ cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_
     return cudaGetLastError();
 }
 
+// The paper's foveation edge bounds (pr_fov_bound SIMPLE / RECURSIVE), as
+// a pass over the stage (a) output of the foveated views that ask for them:
+// the display region (box and half-planes) becomes a framebuffer polygon,
+// whose half-planes (flag 0x100 in tbox.z) and box replace the sector
+// bound's for binning.  Kept out of k_bound so that the default path keeps
+// its registers.
+__global__ void __launch_bounds__(128) k_paper_fov(const ViewDev *__restrict__ views, int nviews,
+                                                   const long long *__restrict__ tri_offs, long long ttot,
+                                                   const float4 *__restrict__ rec, float4 *__restrict__ hp,
+                                                   int4 *__restrict__ tbox, unsigned long long *__restrict__ cand)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ttot || cand[g] == 0ull)
+        return;
+    const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+    if (!is_foveated(v.mode) || v.fov_bound == PR_FOV_SECTOR)
+        return;
+    const int4 tb = tbox[g];
+    const float4 box = rec[g * kRecF4 + 4];
+    float4 hps[kMaxHp];
+    unsigned hmask = 0u;
+    for (int h = 0; h < kMaxHp; ++h) {
+        hps[h] = hp[g * kMaxHp + h];
+        if (h < (tb.z & 0xff))
+            hmask |= 1u << h;
+    }
+    float4 out[kMaxHp];
+    const PaperFov pf = paper_fov_bound(v, hps, hmask, box.x, box.y, box.z, box.w, out);
+    if (pf.n == 0)
+        return;  // more edges than half-plane slots: keep the sector bound
+    for (int h = 0; h < pf.n; ++h)
+        hp[g * kMaxHp + h] = out[h];
+    const float fi0 = ceilf(pf.fb.x * v.W - 0.5f) - 1.f, fi1 = floorf(pf.fb.y * v.W - 0.5f) + 1.f;
+    const float fj0 = ceilf(pf.fb.z * v.H - 0.5f) - 1.f, fj1 = floorf(pf.fb.w * v.H - 0.5f) + 1.f;
+    const int i0 = (int)fmaxf(fi0, 0.f), i1 = (int)fminf(fi1, (float)(v.W - 1));
+    const int j0 = (int)fmaxf(fj0, 0.f), j1 = (int)fminf(fj1, (float)(v.H - 1));
+    if (i0 > i1 || j0 > j1) {
+        tbox[g] = make_int4(1, 1, 0, tb.w);
+        cand[g] = 0ull;
+        return;
+    }
+    tbox[g] = make_int4(i0 | (i1 << 16), j0 | (j1 << 16), pf.n | 0x100, tb.w);
+    cand[g] = (unsigned long long)(i1 / v.S - i0 / v.S + 1) * (unsigned long long)(j1 / v.S - j0 / v.S + 1);
+}
+
+cudaError_t launch_paper_fov(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
+                             const float4 *rec, float4 *hp, int4 *tbox, unsigned long long *cand, cudaStream_t st)
+{
+    if (ttot > 0)
+        k_paper_fov<<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox,
+                                                                    cand);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- binning
 
 // Does the display region of a triangle meet the display box of a tile?
@@ -635,8 +836,21 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                 const int tx = tx0 + (q - qy * w), ty = ty0 + qy;
                 tile = v.tile_off + (long long)ty * v.tiles_x + tx;
                 const float4 bb = rec[g * kRecF4 + 4];
-                const int nh = cand_off[g + 1] - cand_off[g] > 1 ? tb.z : 0;
-                hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
+                const bool fbspace = (tb.z & 0x100) != 0;
+                const int nh = cand_off[g + 1] - cand_off[g] > 1 ? (tb.z & 0xff) : 0;
+                if (!fbspace) {
+                    hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
+                } else {
+                    // the tile's pixel-centre box in framebuffer coordinates
+                    const int i0 = tx << sh, i1 = min(v.W, (tx + 1) << sh) - 1;
+                    const int j0 = ty << sh, j1 = min(v.H, (ty + 1) << sh) - 1;
+                    const float4 fbt = make_float4(__fdiv_rn((float)i0 + 0.5f, (float)v.W),
+                                                   __fdiv_rn((float)i1 + 0.5f, (float)v.W),
+                                                   __fdiv_rn((float)j0 + 0.5f, (float)v.H),
+                                                   __fdiv_rn((float)j1 + 0.5f, (float)v.H));
+                    const float4 big = make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
+                    hit = tile_meets(tile_box[tile], bb, hp, 0) && tile_meets(fbt, big, hp + g * kMaxHp, nh);
+                }
             }
             const unsigned want = __ballot_sync(0xffffffffu, hit);
             if (!want)

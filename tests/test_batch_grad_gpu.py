@@ -351,3 +351,21 @@ def test_frame_gradient_rejects_host_buffers(pr):
         pr.pr_workspace_free(ws)
         for h in handles:
             pr.pr_scene_free(h)
+
+
+def test_sweep_tool_runs(pr):
+    """The bound-variant sweep measures every bound kind on a small view and
+    reports STE = hits / tests in (0, 1]."""
+    from paper_1806_05385_gb300 import sweep
+    sc, view = sweep.one_eye(W=160, H=176, objects=20)
+    b = sweep.Bench(sc, reps=2)
+    try:
+        rows = [b.run(view, k) for k in ("trivial", "quad", "hull", "adaptive", "zenon")]
+        rows += [b.run(view, "zenon", fov_bound=f) for f in ("simple", "recursive")]
+    finally:
+        b.close()
+    for r in rows:
+        assert 0.0 < r["ste"] <= 1.0 and r["ms"] > 0.0
+    # tighter rolling bounds test no more pixels (Sec. 6: Trivial > Quad > Hull, Zenon tightest)
+    t = [r["tests"] for r in rows[:5]]
+    assert t[0] >= t[1] >= t[2] and t[4] <= t[2]

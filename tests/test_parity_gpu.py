@@ -88,6 +88,26 @@ def test_work_item_runs_give_identical_images(pr, seg):
     assert np.array_equal(g["id"], ref["id"]) and np.array_equal(g["depth"], ref["depth"])
 
 
+@pytest.mark.parametrize("fov_bound", ["simple", "recursive"])
+@pytest.mark.parametrize("mode", [S.MODE_FOVEATED, S.MODE_BOTH])
+def test_paper_foveation_bounds_give_identical_images(pr, mode, fov_bound):
+    """Sec. 4.1: the Simple and Recursive edge bounds change which tiles are
+    tested, never the image; on this scene their ternary searches hold."""
+    sc, view = small_case(mode, seed=4, W=224, H=176, T=900)
+    ref = gpu_frame(pr, sc, view, shade=False)
+    h = pr.pr_scene_upload(*(_dev(a) for a in (sc.pos, sc.vel, sc.col, sc.tri)))
+    import torch
+    n = view.W * view.H
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    dep = torch.empty(n, device="cuda")
+    pr.pr_rasterize(h, view, pr.make_params("zenon", 16, 0, 0, fov_bound=fov_bound), ids, dep)
+    st = pr.pr_scene_stats(h)
+    pr.pr_scene_free(h)
+    assert np.array_equal(ids.cpu().numpy().view(np.uint32), ref["id"])
+    assert np.array_equal(dep.cpu().numpy(), ref["depth"])
+    assert st["tests"] > 0 and st["pairs"] > 0
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_bound_kinds_give_identical_images(pr, mode):
     """Sec. 3.2: the intersection test is the same whatever bound is used,
