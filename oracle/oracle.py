@@ -63,6 +63,11 @@ def lib():
         L.or_pinv.argtypes = [C.c_double, C.c_double]
         L.or_pinv.restype = C.c_double
         L.or_num_threads.restype = C.c_int
+        L.or_unfoveate.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, C.c_double, P, C.c_int64, P, P]
+        L.or_mip_levels.argtypes = [C.c_int64, C.c_int64, P]
+        L.or_mip_levels.restype = C.c_int64
+        L.or_unfoveate_lod.argtypes = [P, P, C.c_int64, C.c_int64]
+        L.or_unfoveate_lod.restype = C.c_double
         _lib = L
     return _lib
 
@@ -207,6 +212,44 @@ def p(dist: float, alpha: float) -> float:
 
 def pinv(r: float, alpha: float) -> float:
     return lib().or_pinv(float(r), float(alpha))
+
+
+def unfoveate(view, rgb, Wd: int, Hd: int, method: str = "mip", sigma: float = 0.5, pix=None):
+    """Display image I_u(x) = I_f(q^-1(x)) of a planar framebuffer image rgb
+    [3][H][W] (Sec. 3.1.1, "Display"): method "mip" (MIP pyramid, tri-linear,
+    3-tap cubic) or "projected" (5 x 5 Gaussian reconstruction filter of
+    width sigma display pixels).  Returns (out [3][npix] or [3][Hd][Wd],
+    margin [npix]): margin = distance in texels of the discrete texel choices
+    from their decision boundaries."""
+    L = lib()
+    v = make_view(view)
+    img = np.ascontiguousarray(np.asarray(rgb, dtype=np.float32).reshape(-1))
+    assert img.size == 3 * view.W * view.H
+    if pix is None:
+        npix, pp = Wd * Hd, None
+    else:
+        pix = np.ascontiguousarray(pix, dtype=np.int64)
+        npix, pp = pix.size, pix.ctypes.data_as(C.c_void_p)
+    out = np.empty(3 * npix)
+    margin = np.empty(npix)
+    L.or_unfoveate(C.byref(v), img.ctypes.data_as(C.c_void_p), int(Wd), int(Hd), 0 if method == "mip" else 1,
+                   float(sigma), pp, int(npix), out.ctypes.data_as(C.c_void_p), margin.ctypes.data_as(C.c_void_p))
+    out = out.reshape(3, npix) if pix is not None else out.reshape(3, Hd, Wd)
+    return out, margin
+
+
+def unfoveate_lod(view, x, Wd: int, Hd: int) -> float:
+    v = make_view(view)
+    xx = _d(x).reshape(2)
+    return lib().or_unfoveate_lod(C.byref(v), _ptr(xx), int(Wd), int(Hd))
+
+
+def mip_levels(W: int, H: int):
+    L = lib()
+    n = L.or_mip_levels(int(W), int(H), None)
+    dims = np.empty(2 * n, dtype=np.int64)
+    L.or_mip_levels(int(W), int(H), dims.ctypes.data_as(C.c_void_p))
+    return [(int(dims[2 * k]), int(dims[2 * k + 1])) for k in range(n)]
 
 
 def num_threads() -> int:

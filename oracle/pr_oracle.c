@@ -525,3 +525,225 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------- display unfoveation */
+
+/* Sec. 3.1.1, "Display": the foveated framebuffer image I_f (planar rgb
+ * [3][H][W]) is converted into the display image I_u (planar rgb
+ * [3][Hd][Wd]) by I_u(x) = I_f(q^-1(x)).  Display pixel (a, b) has its
+ * centre at x = ((a + 1/2)/Wd, (b + 1/2)/Hd); non-foveated views use the
+ * identity map.  Two methods, as in the paper:
+ *
+ * method 0, MIP + cubic.  A MIP pyramid of I_f (level k + 1 = the average
+ *   of each 2x2 block of level k, sizes ceil(W_k / 2) x ceil(H_k / 2),
+ *   blocks cut by the border averaged over their texels, down to 1 x 1) is
+ *   sampled tri-linearly: the level of detail is lambda = log2 of the
+ *   largest stretch of q^-1 at x (radial p^-1' or tangential p^-1(r)/r)
+ *   times max(W/Wd, H/Hd), clamped to the pyramid, and the two levels
+ *   around it are blended by its fraction.  Within a level the texel
+ *   coordinate s = u W_k - 1/2 is sampled with a 3-tap cubic filter: the
+ *   nearest texel and its two neighbours per axis (clamped to the edge),
+ *   weighted by the cubic B-spline at their distance from s and
+ *   normalised by the weights' sum.
+ *
+ * method 1, projected 5 x 5.  The framebuffer pixel that holds u = q^-1(x)
+ *   and its 5 x 5 neighbourhood are weighted by a Gaussian reconstruction
+ *   filter r(d) = exp(-d^2 / (2 sigma^2)) of the display-space distance d
+ *   (in display pixels) between x and q of each framebuffer pixel centre,
+ *   normalised by the weights' sum (pixels outside the framebuffer are
+ *   skipped; all-zero weights fall back to the pixel that holds u).
+ *
+ * margin[k]: distance, in texels, of the discrete choices the result
+ * depends on (the nearest texel of each level used, or the pixel that
+ * holds u) from their decision boundaries; near zero, floating point
+ * rounding may tip the choice.  pix: requested display pixels (b * Wd + a)
+ * or NULL for all; out: [3][npix]. */
+
+static double or_bspline3(double x)
+{
+    x = fabs(x);
+    if (x < 1.0)
+        return 2.0 / 3.0 - x * x + 0.5 * x * x * x;
+    if (x < 2.0) {
+        double y = 2.0 - x;
+        return y * y * y / 6.0;
+    }
+    return 0.0;
+}
+
+int64_t or_mip_levels(int64_t W, int64_t H, int64_t *dims)
+{
+    int64_t L = 0;
+    for (;;) {
+        if (dims) {
+            dims[2 * L] = W;
+            dims[2 * L + 1] = H;
+        }
+        ++L;
+        if (W == 1 && H == 1)
+            return L;
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+    }
+}
+
+static double *or_mip_build(const float *rgb, int64_t W, int64_t H, int64_t *L_out, int64_t **dims_out,
+                            int64_t **offs_out)
+{
+    int64_t L = or_mip_levels(W, H, NULL);
+    int64_t *dims = malloc(sizeof(int64_t) * 2 * L), *offs = malloc(sizeof(int64_t) * (L + 1));
+    or_mip_levels(W, H, dims);
+    offs[0] = 0;
+    for (int64_t k = 0; k < L; ++k)
+        offs[k + 1] = offs[k] + 3 * dims[2 * k] * dims[2 * k + 1];
+    double *pyr = malloc(sizeof(double) * offs[L]);
+    for (int64_t i = 0; i < 3 * W * H; ++i)
+        pyr[i] = (double)rgb[i];
+    for (int64_t k = 1; k < L; ++k) {
+        const int64_t w0 = dims[2 * k - 2], h0 = dims[2 * k - 1], w1 = dims[2 * k], h1 = dims[2 * k + 1];
+        const double *src = pyr + offs[k - 1];
+        double *dst = pyr + offs[k];
+        for (int64_t c = 0; c < 3; ++c)
+            for (int64_t y = 0; y < h1; ++y)
+                for (int64_t x = 0; x < w1; ++x) {
+                    double s = 0.0;
+                    int n = 0;
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int64_t sx = 2 * x + dx, sy = 2 * y + dy;
+                            if (sx < w0 && sy < h0) {
+                                s += src[c * w0 * h0 + sy * w0 + sx];
+                                ++n;
+                            }
+                        }
+                    dst[c * w1 * h1 + y * w1 + x] = s / n;
+                }
+    }
+    *L_out = L;
+    *dims_out = dims;
+    *offs_out = offs;
+    return pyr;
+}
+
+/* 3-tap cubic sample of one level at texel coordinates (s, t); returns the
+ * margin of the nearest-texel choice. */
+static double or_sample3(const double *lev, int64_t w, int64_t h, double s, double t, double out[3])
+{
+    const double fs = floor(s + 0.5), ft = floor(t + 0.5);
+    /* the nearest texel flips where s (or t) crosses n + 1/2 */
+    const double margin = fmin(0.5 - fabs(s - fs), 0.5 - fabs(t - ft));
+    double wx[3], wy[3], sx = 0.0, sy = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        wx[k] = or_bspline3(s - (fs + k - 1));
+        wy[k] = or_bspline3(t - (ft + k - 1));
+        sx += wx[k];
+        sy += wy[k];
+    }
+    out[0] = out[1] = out[2] = 0.0;
+    for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+            int64_t x = (int64_t)fs + kx - 1, y = (int64_t)ft + ky - 1;
+            x = x < 0 ? 0 : (x >= w ? w - 1 : x);
+            y = y < 0 ? 0 : (y >= h ? h - 1 : y);
+            const double wgt = wx[kx] * wy[ky] / (sx * sy);
+            for (int c = 0; c < 3; ++c)
+                out[c] += wgt * lev[c * w * h + y * w + x];
+        }
+    return margin;
+}
+
+/* Unclamped level of detail of method 0 at display location x. */
+double or_unfoveate_lod(const or_view *v, const double x[2], int64_t Wd, int64_t Hd)
+{
+    const int fov = v->mode == OR_FOVEATED || v->mode == OR_BOTH;
+    double stretch = 1.0;
+    if (fov) {
+        const double e0 = x[0] - v->fovea[0], e1 = x[1] - v->fovea[1], r = sqrt(e0 * e0 + e1 * e1);
+        const double tang = r > 0.0 ? pow(r / OR_D, 1.0 / v->alpha - 1.0) : INFINITY;
+        stretch = fmax(tang, tang / v->alpha);
+    }
+    return log2(stretch * fmax((double)v->W / (double)Wd, (double)v->H / (double)Hd));
+}
+
+void or_unfoveate(const or_view *v, const float *rgb, int64_t Wd, int64_t Hd, int32_t method, double sigma,
+                  const int64_t *pix, int64_t npix, double *out, double *margin)
+{
+    const int64_t W = v->W, H = v->H;
+    const int fov = v->mode == OR_FOVEATED || v->mode == OR_BOTH;
+    int64_t L = 0, *dims = NULL, *offs = NULL;
+    double *pyr = method == 0 ? or_mip_build(rgb, W, H, &L, &dims, &offs) : NULL;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < npix; ++k) {
+        const int64_t lin = pix ? pix[k] : k;
+        const int64_t a = lin % Wd, b = lin / Wd;
+        const double x[2] = {((double)a + 0.5) / (double)Wd, ((double)b + 0.5) / (double)Hd};
+        double u[2];
+        if (fov)
+            or_qinv(v, x, u);
+        else {
+            u[0] = x[0];
+            u[1] = x[1];
+        }
+        double res[3] = {0.0, 0.0, 0.0}, mg = INFINITY;
+        if (method == 0) {
+            /* largest stretch of q^-1 at x: radial d p^-1/dr = (1/alpha)(r/D)^(1/alpha - 1),
+             * tangential p^-1(r)/r = (r/D)^(1/alpha - 1) */
+            double lambda = or_unfoveate_lod(v, x, Wd, Hd);
+            if (!(lambda > 0.0))
+                lambda = 0.0;
+            if (lambda > (double)(L - 1))
+                lambda = (double)(L - 1);
+            const int64_t k0 = (int64_t)floor(lambda), k1 = k0 + 1 < L ? k0 + 1 : k0;
+            const double f = lambda - (double)k0;
+            double s0[3], s1[3];
+            const int64_t w0 = dims[2 * k0], h0 = dims[2 * k0 + 1], w1 = dims[2 * k1], h1 = dims[2 * k1 + 1];
+            mg = or_sample3(pyr + offs[k0], w0, h0, u[0] * w0 - 0.5, u[1] * h0 - 0.5, s0);
+            const double m1 = or_sample3(pyr + offs[k1], w1, h1, u[0] * w1 - 0.5, u[1] * h1 - 0.5, s1);
+            if (f > 0.0)
+                mg = fmin(mg, m1);
+            for (int c = 0; c < 3; ++c)
+                res[c] = (1.0 - f) * s0[c] + f * s1[c];
+        } else {
+            const double su = u[0] * (double)W, sv = u[1] * (double)H;
+            const double fi = floor(su), fj = floor(sv);
+            mg = fmin(fmin(su - fi, 1.0 - (su - fi)), fmin(sv - fj, 1.0 - (sv - fj)));
+            int64_t i = (int64_t)fi, j = (int64_t)fj;
+            i = i < 0 ? 0 : (i >= W ? W - 1 : i);
+            j = j < 0 ? 0 : (j >= H ? H - 1 : j);
+            double wsum = 0.0;
+            for (int dy = -2; dy <= 2; ++dy)
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int64_t pi = i + dx, pj = j + dy;
+                    if (pi < 0 || pj < 0 || pi >= W || pj >= H)
+                        continue;
+                    const double c_u[2] = {((double)pi + 0.5) / (double)W, ((double)pj + 0.5) / (double)H};
+                    double c_x[2];
+                    if (fov)
+                        or_q(v, c_u, c_x);
+                    else {
+                        c_x[0] = c_u[0];
+                        c_x[1] = c_u[1];
+                    }
+                    const double d0 = (x[0] - c_x[0]) * (double)Wd, d1 = (x[1] - c_x[1]) * (double)Hd;
+                    const double wgt = exp(-(d0 * d0 + d1 * d1) / (2.0 * sigma * sigma));
+                    wsum += wgt;
+                    for (int c = 0; c < 3; ++c)
+                        res[c] += wgt * (double)rgb[c * W * H + pj * W + pi];
+                }
+            if (wsum > 1e-300) {
+                for (int c = 0; c < 3; ++c)
+                    res[c] /= wsum;
+            } else {
+                for (int c = 0; c < 3; ++c)
+                    res[c] = (double)rgb[c * W * H + j * W + i];
+            }
+        }
+        for (int c = 0; c < 3; ++c)
+            out[c * npix + k] = res[c];
+        if (margin)
+            margin[k] = mg;
+    }
+    free(pyr);
+    free(dims);
+    free(offs);
+}
