@@ -551,7 +551,9 @@ int or_num_threads(void)
  *   filter r(d) = exp(-d^2 / (2 sigma^2)) of the display-space distance d
  *   (in display pixels) between x and q of each framebuffer pixel centre,
  *   normalised by the weights' sum (pixels outside the framebuffer are
- *   skipped; all-zero weights fall back to the pixel that holds u).
+ *   skipped).  The weights are taken relative to the nearest sample, whose
+ *   factor cancels in the normalisation, so far from the framebuffer (where
+ *   every sample is many display pixels away) they do not underflow.
  *
  * margin[k]: distance, in texels, of the discrete choices the result
  * depends on (the nearest texel of each level used, or the pixel that
@@ -710,10 +712,13 @@ void or_unfoveate(const or_view *v, const float *rgb, int64_t Wd, int64_t Hd, in
             int64_t i = (int64_t)fi, j = (int64_t)fj;
             i = i < 0 ? 0 : (i >= W ? W - 1 : i);
             j = j < 0 ? 0 : (j >= H ? H - 1 : j);
-            double wsum = 0.0;
+            /* squared display distances of the window's pixels (NAN: outside) */
+            double d2[25], d2min = INFINITY;
             for (int dy = -2; dy <= 2; ++dy)
                 for (int dx = -2; dx <= 2; ++dx) {
                     const int64_t pi = i + dx, pj = j + dy;
+                    double *slot = &d2[(dy + 2) * 5 + dx + 2];
+                    *slot = NAN;
                     if (pi < 0 || pj < 0 || pi >= W || pj >= H)
                         continue;
                     const double c_u[2] = {((double)pi + 0.5) / (double)W, ((double)pj + 0.5) / (double)H};
@@ -725,18 +730,24 @@ void or_unfoveate(const or_view *v, const float *rgb, int64_t Wd, int64_t Hd, in
                         c_x[1] = c_u[1];
                     }
                     const double d0 = (x[0] - c_x[0]) * (double)Wd, d1 = (x[1] - c_x[1]) * (double)Hd;
-                    const double wgt = exp(-(d0 * d0 + d1 * d1) / (2.0 * sigma * sigma));
+                    *slot = d0 * d0 + d1 * d1;
+                    d2min = fmin(d2min, *slot);
+                }
+            /* weights relative to the nearest sample: the common factor
+             * exp(-d2min / (2 sigma^2)) cancels in the normalisation */
+            double wsum = 0.0;
+            for (int dy = -2; dy <= 2; ++dy)
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const double q2 = d2[(dy + 2) * 5 + dx + 2];
+                    if (isnan(q2))
+                        continue;
+                    const double wgt = exp(-(q2 - d2min) / (2.0 * sigma * sigma));
                     wsum += wgt;
                     for (int c = 0; c < 3; ++c)
-                        res[c] += wgt * (double)rgb[c * W * H + pj * W + pi];
+                        res[c] += wgt * (double)rgb[c * W * H + (j + dy) * W + (i + dx)];
                 }
-            if (wsum > 1e-300) {
-                for (int c = 0; c < 3; ++c)
-                    res[c] /= wsum;
-            } else {
-                for (int c = 0; c < 3; ++c)
-                    res[c] = (double)rgb[c * W * H + j * W + i];
-            }
+            for (int c = 0; c < 3; ++c)
+                res[c] /= wsum;
         }
         for (int c = 0; c < 3; ++c)
             out[c * npix + k] = res[c];
