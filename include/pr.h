@@ -244,6 +244,38 @@ typedef struct {
 pr_status pr_frame_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
                          const pr_frame_grad *grads, void *stream);
 
+/* ---- display step (Sec. 3.1.1, "Display") ----
+ * The foveated framebuffer image I_f of a view becomes the display image
+ * I_u(x) = I_f(q^-1(x)).  Display pixel (a, b) has its centre at
+ * x = ((a + 1/2)/Wd, (b + 1/2)/Hd); views that are not foveated use the
+ * identity map.  Under the power map the framebuffer covers a disc around
+ * the fovea of the display; display pixels beyond it take the framebuffer's
+ * edge values. */
+typedef enum {
+    PR_UNFOVEATE_MIP_CUBIC = 0, /* MIP pyramid (2x2 box, sizes halved with ceil) sampled tri-linearly at
+                                   the level log2(largest stretch of q^-1 at x * max(W/Wd, H/Hd)), each
+                                   level with a 3-tap cubic B-spline filter per axis (normalised) */
+    PR_UNFOVEATE_PROJECTED = 1  /* the framebuffer pixel holding q^-1(x) and its 5x5 neighbourhood, weighted
+                                   by exp(-d^2 / (2 sigma^2)), d = display-pixel distance between x and q of
+                                   each pixel centre, normalised by the weights' sum (computed relative
+                                   to the nearest sample, so far from the framebuffer they do not all
+                                   underflow) */
+} pr_unfoveate_method;
+
+typedef struct {
+    int32_t method;       /* pr_unfoveate_method */
+    int32_t Wd, Hd;       /* display size, 1..16384 */
+    float sigma;          /* PROJECTED: filter width in display pixels (> 0) */
+} pr_unfoveate_params;
+
+/* rgb: DEVICE planar [3][view.H][view.W] f32 (e.g. a shaded frame); out:
+ * DEVICE planar [3][Hd][Wd] f32, written.  view: W, H, mode, fovea and alpha
+ * are used.  The MIP pyramid lives in the workspace (grown on demand).
+ * Asynchronous on `stream`.  PR_ERR_INVALID_ARG for host pointers or
+ * invalid sizes / parameters. */
+pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, float *out,
+                       const pr_unfoveate_params *params, void *stream);
+
 /* Captures the same sequence into a CUDA graph (after one eager run that
  * sizes every buffer) and replays it with pr_graph_launch.  The views and
  * their buffers must stay valid and unchanged in shape while the graph

@@ -30,7 +30,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_workspace_create", "pr_workspace_free", "pr_rasterize_batch", "pr_graph_capture_batch",
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
-           "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame")
+           "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate")
 
 
 class PrError(RuntimeError):
@@ -66,6 +66,13 @@ class PrStats(C.Structure):
 class PrBackwardView(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("view", PrView), ("id", C.c_void_p), ("grad_rgb", C.c_void_p),
                 ("dcol", C.c_void_p), ("dpos", C.c_void_p), ("dvel", C.c_void_p)]
+
+
+class PrUnfoveateParams(C.Structure):
+    _fields_ = [("method", C.c_int32), ("Wd", C.c_int32), ("Hd", C.c_int32), ("sigma", C.c_float)]
+
+
+UNFOVEATE_METHODS = {"mip": 0, "projected": 1}
 
 
 class PrFrameGrad(C.Structure):
@@ -115,6 +122,7 @@ def load(build_if_missing: bool = True):
             "pr_version": ([], I32),
             "pr_rasterize_noalloc": ([P, P, P, P, I64, I64, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
             "pr_backward_batch": ([P, C.POINTER(PrBackwardView), I32, P], I32),
+            "pr_unfoveate": ([P, C.POINTER(PrView), P, P, C.POINTER(PrUnfoveateParams), P], I32),
             "pr_frame_batch": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P], I32),
             "pr_graph_capture_frame": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P,
                                         C.POINTER(P)], I32),
@@ -318,6 +326,16 @@ def pr_graph_capture_frame(ws, entries, grads, params=None, stream=None) -> int:
                                          stream if stream is not None else current_stream(), C.byref(h)),
            "pr_graph_capture_frame")
     return h.value
+
+
+def pr_unfoveate(ws, view, rgb, out, Wd: int, Hd: int, method: str = "mip", sigma: float = 0.5, stream=None):
+    """Display image out [3][Hd][Wd] from the framebuffer image rgb
+    [3][H][W] of `view` (CUDA tensors): method "mip" or "projected"."""
+    pp = PrUnfoveateParams(UNFOVEATE_METHODS[method] if isinstance(method, str) else int(method), int(Wd), int(Hd),
+                           float(sigma))
+    v = view if isinstance(view, PrView) else make_view(view)
+    _check(load().pr_unfoveate(C.c_void_p(ws), C.byref(v), _ptr(rgb), _ptr(out), C.byref(pp),
+                               stream if stream is not None else current_stream()), "pr_unfoveate")
 
 
 def pr_graph_launch(graph, stream=None):

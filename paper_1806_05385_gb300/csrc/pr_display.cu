@@ -1,0 +1,275 @@
+// pr_display.cu -- the display step after shading (Sec. 3.1.1, "Display"):
+// the foveated framebuffer image I_f becomes the display image
+// I_u(x) = I_f(q^-1(x)).  Two methods, as in the paper:
+//
+//  - MIP + cubic: a MIP pyramid of I_f (2x2 box averages, sizes halved
+//    with ceil, blocks cut by the border averaged over their texels) is
+//    sampled tri-linearly at the level of detail of the largest stretch of
+//    q^-1 at x times the size ratio, each level with a 3-tap cubic filter
+//    (the nearest texel and its two neighbours per axis, cubic B-spline
+//    weights normalised by their sum, clamped to the edge);
+//  - projected 5x5: the framebuffer pixel that holds q^-1(x) and its 5x5
+//    neighbourhood, weighted by a Gaussian reconstruction filter of the
+//    display-space distance between x and q of each pixel centre,
+//    normalised (the paper's projection of the display's reconstruction
+//    filter into the foveated domain); weights are taken relative to the
+//    nearest sample, whose factor cancels, so they cannot all underflow.
+//
+// One thread per display pixel; planar rgb in and out, coalesced along x.
+#include <cstring>
+
+#include "pr_launch.h"
+
+namespace pr {
+
+constexpr int kMaxMipLevels = 16;  // 16384 x 16384 needs 15
+
+struct MipPyramid {
+    const float *lev[kMaxMipLevels];
+    int w[kMaxMipLevels], h[kMaxMipLevels];
+    int L;
+};
+
+// Display-step constants of a view (by value into the kernel).
+struct DisplayView {
+    int W, H, Wd, Hd;
+    int fov;             // foveated or joint mode: q is the power map, else the identity
+    float fx, fy;        // fovea
+    float alpha, inv_alpha;
+    float scale;         // max(W / Wd, H / Hd)
+    float sigma;         // projected filter width, display pixels
+};
+
+__global__ void k_mip_down(const float *__restrict__ src, int w0, int h0, float *__restrict__ dst, int w1, int h1)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w1 || y >= h1)
+        return;
+    const int x0 = 2 * x, y0 = 2 * y;
+    const bool xr = x0 + 1 < w0, yr = y0 + 1 < h0;
+    const float n = (float)((1 + xr) * (1 + yr));
+    for (int c = 0; c < 3; ++c) {
+        const float *s = src + (size_t)c * w0 * h0;
+        float a = s[(size_t)y0 * w0 + x0];
+        if (xr)
+            a += s[(size_t)y0 * w0 + x0 + 1];
+        if (yr) {
+            a += s[(size_t)(y0 + 1) * w0 + x0];
+            if (xr)
+                a += s[(size_t)(y0 + 1) * w0 + x0 + 1];
+        }
+        dst[(size_t)c * w1 * h1 + (size_t)y * w1 + x] = a / n;
+    }
+}
+
+__device__ __forceinline__ float bspline3(float x)
+{
+    x = fabsf(x);
+    if (x < 1.f)
+        return fmaf(0.5f * x, x * x, 2.f / 3.f - x * x);
+    if (x < 2.f) {
+        const float y = 2.f - x;
+        return y * y * y * (1.f / 6.f);
+    }
+    return 0.f;
+}
+
+// 3-tap cubic sample of one level at texel coordinates (s, t).
+__device__ __forceinline__ void sample3(const float *__restrict__ lev, int w, int h, float s, float t, float out[3])
+{
+    const float fs = floorf(s + 0.5f), ft = floorf(t + 0.5f);
+    float wx[3], wy[3], sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        wx[k] = bspline3(s - (fs + (float)(k - 1)));
+        wy[k] = bspline3(t - (ft + (float)(k - 1)));
+        sx += wx[k];
+        sy += wy[k];
+    }
+    const float inv = 1.f / (sx * sy);
+    out[0] = out[1] = out[2] = 0.f;
+    const int is = (int)fs, it = (int)ft;
+    const size_t plane = (size_t)w * h;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+        const int y = min(max(it + ky - 1, 0), h - 1);
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            const int x = min(max(is + kx - 1, 0), w - 1);
+            const float wgt = wx[kx] * wy[ky] * inv;
+            const size_t o = (size_t)y * w + x;
+            out[0] = fmaf(wgt, __ldg(lev + o), out[0]);
+            out[1] = fmaf(wgt, __ldg(lev + plane + o), out[1]);
+            out[2] = fmaf(wgt, __ldg(lev + 2 * plane + o), out[2]);
+        }
+    }
+}
+
+template <int kMethod>
+__global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid pyr, const float *__restrict__ rgb,
+                                                  float *__restrict__ out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= dv.Wd)
+        return;
+    const float x0 = __fdiv_rn((float)a + 0.5f, (float)dv.Wd), x1 = __fdiv_rn((float)b + 0.5f, (float)dv.Hd);
+    // u = q^-1(x): the offset from the fovea scaled by (|e|/D)^(1/alpha - 1)
+    float u0 = x0, u1 = x1, tang = 1.f;
+    if (dv.fov) {
+        const float e0 = x0 - dv.fx, e1 = x1 - dv.fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
+        tang = r > 0.f ? powf(r * (1.f / kSqrt2), dv.inv_alpha - 1.f) : INFINITY;
+        const float s = r > 0.f ? tang : 0.f;
+        u0 = fmaf(e0, s, dv.fx);
+        u1 = fmaf(e1, s, dv.fy);
+    }
+    float res[3];
+    if (kMethod == PR_UNFOVEATE_MIP_CUBIC) {
+        // level of detail: the largest stretch of q^-1 (tangential for alpha >= 1)
+        float lambda = log2f(fmaxf(tang, tang * dv.inv_alpha) * dv.scale);
+        lambda = fminf(fmaxf(lambda, 0.f), (float)(pyr.L - 1));  // NaN-free: tang >= 0
+        const int k0 = (int)floorf(lambda), k1 = min(k0 + 1, pyr.L - 1);
+        const float f = lambda - (float)k0;
+        float s0[3], s1[3];
+        sample3(pyr.lev[k0], pyr.w[k0], pyr.h[k0], fmaf(u0, (float)pyr.w[k0], -0.5f),
+                fmaf(u1, (float)pyr.h[k0], -0.5f), s0);
+        if (f > 0.f) {
+            sample3(pyr.lev[k1], pyr.w[k1], pyr.h[k1], fmaf(u0, (float)pyr.w[k1], -0.5f),
+                    fmaf(u1, (float)pyr.h[k1], -0.5f), s1);
+            for (int c = 0; c < 3; ++c)
+                res[c] = fmaf(f, s1[c] - s0[c], s0[c]);
+        } else {
+            for (int c = 0; c < 3; ++c)
+                res[c] = s0[c];
+        }
+    } else {
+        const int i = min(max((int)floorf(u0 * (float)dv.W), 0), dv.W - 1);
+        const int j = min(max((int)floorf(u1 * (float)dv.H), 0), dv.H - 1);
+        const float k2 = -0.5f / (dv.sigma * dv.sigma);
+        const size_t plane = (size_t)dv.W * dv.H;
+        // display location q(c) of a window pixel's centre (the offset from
+        // the fovea scaled by (|e|/D)^(alpha - 1))
+        auto qc = [&](int pi, int pj, float &q0, float &q1) {
+            q0 = __fdiv_rn((float)pi + 0.5f, (float)dv.W);
+            q1 = __fdiv_rn((float)pj + 0.5f, (float)dv.H);
+            if (dv.fov) {
+                const float e0 = q0 - dv.fx, e1 = q1 - dv.fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
+                const float s = r > 0.f ? powf(r * (1.f / kSqrt2), dv.alpha - 1.f) : 0.f;
+                q0 = fmaf(e0, s, dv.fx);
+                q1 = fmaf(e1, s, dv.fy);
+            }
+        };
+        // pass 1: the nearest sample in display space
+        float d2min = INFINITY, qm0 = 0.f, qm1 = 0.f;
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int pi = i + dx, pj = j + dy;
+                if (pj < 0 || pj >= dv.H || pi < 0 || pi >= dv.W)
+                    continue;
+                float q0, q1;
+                qc(pi, pj, q0, q1);
+                const float d0 = (x0 - q0) * (float)dv.Wd, d1 = (x1 - q1) * (float)dv.Hd;
+                const float q2 = fmaf(d0, d0, d1 * d1);
+                if (q2 < d2min) {
+                    d2min = q2;
+                    qm0 = q0;
+                    qm1 = q1;
+                }
+            }
+        // pass 2: weights relative to the nearest sample (its factor cancels
+        // in the normalisation, so they never all underflow), with
+        // d^2 - d_min^2 = (d - d_min)(d + d_min) per axis, where d - d_min
+        // comes from the difference of the two samples' display locations
+        float acc[3] = {0.f, 0.f, 0.f}, wsum = 0.f;
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int pi = i + dx, pj = j + dy;
+                if (pj < 0 || pj >= dv.H || pi < 0 || pi >= dv.W)
+                    continue;
+                float q0, q1;
+                qc(pi, pj, q0, q1);
+                const float a0 = (qm0 - q0) * (float)dv.Wd, a1 = (qm1 - q1) * (float)dv.Hd;  // d - d_min
+                const float b0 = (2.f * x0 - q0 - qm0) * (float)dv.Wd, b1 = (2.f * x1 - q1 - qm1) * (float)dv.Hd;
+                const float w = expf(k2 * fmaf(a0, b0, a1 * b1));
+                const size_t o = (size_t)pj * dv.W + pi;
+                wsum += w;
+                acc[0] = fmaf(w, __ldg(rgb + o), acc[0]);
+                acc[1] = fmaf(w, __ldg(rgb + plane + o), acc[1]);
+                acc[2] = fmaf(w, __ldg(rgb + 2 * plane + o), acc[2]);
+            }
+        const float inv = 1.f / wsum;
+        for (int c = 0; c < 3; ++c)
+            res[c] = acc[c] * inv;
+    }
+    const size_t dplane = (size_t)dv.Wd * dv.Hd, o = (size_t)b * dv.Wd + a;
+    out[o] = res[0];
+    out[dplane + o] = res[1];
+    out[2 * dplane + o] = res[2];
+}
+
+int mip_level_count(int W, int H)
+{
+    int L = 1;
+    while (W > 1 || H > 1) {
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+        ++L;
+    }
+    return L;
+}
+
+size_t mip_pyramid_floats(int W, int H)
+{
+    size_t n = 0;
+    for (;;) {
+        n += (size_t)3 * W * H;
+        if (W == 1 && H == 1)
+            return n;
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+    }
+}
+
+cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, int Wd, int Hd,
+                             float sigma, const float *rgb, float *pyramid, float *out, cudaStream_t st)
+{
+    DisplayView dv;
+    dv.W = W;
+    dv.H = H;
+    dv.Wd = Wd;
+    dv.Hd = Hd;
+    dv.fov = mode == PR_FOVEATED || mode == PR_BOTH;
+    dv.fx = fx;
+    dv.fy = fy;
+    dv.alpha = alpha;
+    dv.inv_alpha = 1.f / alpha;
+    dv.scale = fmaxf((float)W / (float)Wd, (float)H / (float)Hd);
+    dv.sigma = sigma;
+    MipPyramid pyr;
+    std::memset(&pyr, 0, sizeof pyr);
+    const dim3 blk(256), grd((unsigned)((Wd + 255) / 256), (unsigned)Hd);
+    if (method == PR_UNFOVEATE_MIP_CUBIC) {
+        const int L = mip_level_count(W, H);
+        if (L > kMaxMipLevels)
+            return cudaErrorInvalidValue;
+        pyr.L = L;
+        pyr.lev[0] = rgb;
+        pyr.w[0] = W;
+        pyr.h[0] = H;
+        float *p = pyramid;
+        for (int k = 1; k < L; ++k) {
+            const int w1 = (pyr.w[k - 1] + 1) / 2, h1 = (pyr.h[k - 1] + 1) / 2;
+            const dim3 b2(32, 8), g2((unsigned)((w1 + 31) / 32), (unsigned)((h1 + 7) / 8));
+            k_mip_down<<<g2, b2, 0, st>>>(pyr.lev[k - 1], pyr.w[k - 1], pyr.h[k - 1], p, w1, h1);
+            pyr.lev[k] = p;
+            pyr.w[k] = w1;
+            pyr.h[k] = h1;
+            p += (size_t)3 * w1 * h1;
+        }
+        k_unfoveate<PR_UNFOVEATE_MIP_CUBIC><<<grd, blk, 0, st>>>(dv, pyr, rgb, out);
+    } else {
+        k_unfoveate<PR_UNFOVEATE_PROJECTED><<<grd, blk, 0, st>>>(dv, pyr, rgb, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pr

@@ -131,6 +131,7 @@ constexpr long long kMaxPairs = 0x7FFFFFFFll;  // bin entries per frame: work it
 struct pr_workspace {
     DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, pairs, items, keys, counters, heads;
     DevBuf hit_entry, hit_tile;  // (triangle, tile) hits of the binning count pass, before the scatter
+    DevBuf mip;                  // display step: MIP pyramid of the framebuffer image
     DevBuf cand, cand_off;         // candidate tiles per triangle and their prefix sum
     DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
     DevBuf stage;                  // device copies of host-side outputs
@@ -920,6 +921,35 @@ pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int
     PR_TRY(cudaMemcpyAsync(ws->offs.p, blk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
     PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], nullptr, st));
     PR_TRY(cudaStreamSynchronize(st));
+    return PR_OK;
+}
+
+pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, float *out,
+                       const pr_unfoveate_params *params, void *stream)
+{
+    if (!ws || !view || !rgb || !out || !params)
+        return PR_ERR_INVALID_ARG;
+    const pr_view &v = *view;
+    const pr_unfoveate_params &p = *params;
+    if (v.W < 1 || v.H < 1 || v.W > 16384 || v.H > 16384 || p.Wd < 1 || p.Hd < 1 || p.Wd > 16384 || p.Hd > 16384)
+        return PR_ERR_INVALID_ARG;
+    if (v.mode < PR_CLASSIC || v.mode > PR_BOTH || !(v.alpha >= 1.f && v.alpha <= 5.f) ||
+        !(v.fovea[0] >= 0.f && v.fovea[0] <= 1.f && v.fovea[1] >= 0.f && v.fovea[1] <= 1.f))
+        return PR_ERR_INVALID_ARG;
+    if (p.method != PR_UNFOVEATE_MIP_CUBIC && p.method != PR_UNFOVEATE_PROJECTED)
+        return PR_ERR_INVALID_ARG;
+    if (p.method == PR_UNFOVEATE_PROJECTED && !(p.sigma > 0.f && std::isfinite(p.sigma)))
+        return PR_ERR_INVALID_ARG;
+    if (!is_device_ptr(rgb) || !is_device_ptr(out))
+        return PR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *pyr = nullptr;
+    if (p.method == PR_UNFOVEATE_MIP_CUBIC) {
+        PR_TRY(ensure(ws->mip, sizeof(float) * mip_pyramid_floats(v.W, v.H)));
+        pyr = ws->mip.as<float>();
+    }
+    PR_TRY(launch_unfoveate(p.method, v.W, v.H, v.mode, v.fovea[0], v.fovea[1], v.alpha, p.Wd, p.Hd, p.sigma, rgb,
+                            pyr, out, st));
     return PR_OK;
 }
 

@@ -66,4 +66,10 @@ cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                             const Counters *frame_cnt, cudaStream_t st);
 
+// display step: unfoveation of a framebuffer image (pyramid: scratch of
+// mip_pyramid_floats(W, H) floats for the MIP method)
+size_t mip_pyramid_floats(int W, int H);
+cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, int Wd, int Hd,
+                             float sigma, const float *rgb, float *pyramid, float *out, cudaStream_t st);
+
 }  // namespace pr
