@@ -337,6 +337,29 @@ def our_arm(args, rank, world):
     fwd_plain = timed(plain, max(3, args.steps // 2))
     bwd_ms = timed(backward, max(3, args.steps // 2))
 
+    # the display step after shading (Sec. 3.1.1, "Display"): every view's
+    # framebuffer image unfoveated to a display of the same size, both methods
+    disp_out = [torch.empty(3 * n, device="cuda") for n in npx]
+    ws_d = B.pr_workspace_create()
+
+    def display(method):
+        for k, v in enumerate(views):
+            B.pr_unfoveate(ws_d, v, rgb[k], disp_out[k], v.W, v.H, method, 0.5)
+    display_ms = {}
+    for m in ("mip", "projected"):
+        for _ in range(2):
+            display(m)
+        display_ms[m] = statistics.mean(timed(lambda: display(m), max(3, args.steps // 2)))
+    B.pr_workspace_free(ws_d)
+    hbm = measured_peak("hbm_gbs")
+    # algorithmic bytes: 12 B rgb in + 12 B rgb out per pixel; the pyramid adds
+    # one read of the image and writes / reads a third of it
+    disp_bytes = {"mip": sum(12 * n + 12 * n + 12 * n + 8 * n for n in npx), "projected": sum(24 * n for n in npx)}
+    display_step = {m: {"ms": display_ms[m], "mpix_s": world * sum(npx) / (display_ms[m] * 1e-3) / 1e6,
+                        "gbs": disp_bytes[m] / (display_ms[m] * 1e-3) / 1e9,
+                        "hbm_frac": disp_bytes[m] / (display_ms[m] * 1e-3) / 1e9 / hbm if hbm else None}
+                    for m in display_ms}
+
     pix = sum(npx)
     value, mean_ms = aggregate(sum(step_ms) / len(step_ms), pix, dist, "cuda")
 
@@ -433,6 +456,7 @@ def our_arm(args, rank, world):
         "fwd_mpix_s": {"batched_graph": world * pix / (statistics.mean(fwd_batched) * 1e-3) / 1e6,
                        "plain_per_view": world * pix / (statistics.mean(fwd_plain) * 1e-3) / 1e6},
         "fwd_bwd_ms_per_frame": mean_ms, "bwd_ms_separate_call": statistics.mean(bwd_ms),
+        "display_step": display_step,
         "tiles": sorted(set(tiles)),
     }
     B.pr_graph_free(graph)
