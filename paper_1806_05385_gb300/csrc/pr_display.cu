@@ -62,6 +62,23 @@ __global__ void k_mip_down(const float *__restrict__ src, int w0, int h0, float 
     }
 }
 
+// Display location q(c) of every framebuffer pixel centre c (the offset from
+// the fovea scaled by (|e|/D)^(alpha - 1)), for the projected filter.
+__global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha, float2 *__restrict__ table)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= W)
+        return;
+    float q0 = __fdiv_rn((float)i + 0.5f, (float)W), q1 = __fdiv_rn((float)j + 0.5f, (float)H);
+    if (fov) {
+        const float e0 = q0 - fx, e1 = q1 - fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
+        const float s = r > 0.f ? powf(r * (1.f / kSqrt2), alpha - 1.f) : 0.f;
+        q0 = fmaf(e0, s, fx);
+        q1 = fmaf(e1, s, fy);
+    }
+    table[(size_t)j * W + i] = make_float2(q0, q1);
+}
+
 __device__ __forceinline__ float bspline3(float x)
 {
     x = fabsf(x);
@@ -107,7 +124,7 @@ __device__ __forceinline__ void sample3(const float *__restrict__ lev, int w, in
 
 template <int kMethod>
 __global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid pyr, const float *__restrict__ rgb,
-                                                  float *__restrict__ out)
+                                                  const float2 *__restrict__ qtab, float *__restrict__ out)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (a >= dv.Wd)
@@ -146,17 +163,11 @@ __global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid py
         const int j = min(max((int)floorf(u1 * (float)dv.H), 0), dv.H - 1);
         const float k2 = -0.5f / (dv.sigma * dv.sigma);
         const size_t plane = (size_t)dv.W * dv.H;
-        // display location q(c) of a window pixel's centre (the offset from
-        // the fovea scaled by (|e|/D)^(alpha - 1))
+        // display location q(c) of a window pixel's centre, from the table
         auto qc = [&](int pi, int pj, float &q0, float &q1) {
-            q0 = __fdiv_rn((float)pi + 0.5f, (float)dv.W);
-            q1 = __fdiv_rn((float)pj + 0.5f, (float)dv.H);
-            if (dv.fov) {
-                const float e0 = q0 - dv.fx, e1 = q1 - dv.fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
-                const float s = r > 0.f ? powf(r * (1.f / kSqrt2), dv.alpha - 1.f) : 0.f;
-                q0 = fmaf(e0, s, dv.fx);
-                q1 = fmaf(e1, s, dv.fy);
-            }
+            const float2 q = __ldg(qtab + (size_t)pj * dv.W + pi);
+            q0 = q.x;
+            q1 = q.y;
         };
         // pass 1: the nearest sample in display space
         float d2min = INFINITY, qm0 = 0.f, qm1 = 0.f;
@@ -217,6 +228,8 @@ int mip_level_count(int W, int H)
     return L;
 }
 
+// Scratch floats of the display step: the MIP pyramid, or the q table of
+// the projected filter (2 per framebuffer pixel).
 size_t mip_pyramid_floats(int W, int H)
 {
     size_t n = 0;
@@ -265,9 +278,12 @@ cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float
             pyr.h[k] = h1;
             p += (size_t)3 * w1 * h1;
         }
-        k_unfoveate<PR_UNFOVEATE_MIP_CUBIC><<<grd, blk, 0, st>>>(dv, pyr, rgb, out);
+        k_unfoveate<PR_UNFOVEATE_MIP_CUBIC><<<grd, blk, 0, st>>>(dv, pyr, rgb, nullptr, out);
     } else {
-        k_unfoveate<PR_UNFOVEATE_PROJECTED><<<grd, blk, 0, st>>>(dv, pyr, rgb, out);
+        float2 *qtab = reinterpret_cast<float2 *>(pyramid);
+        const dim3 gq((unsigned)((W + 255) / 256), (unsigned)H);
+        k_q_table<<<gq, 256, 0, st>>>(W, H, dv.fov, fx, fy, alpha, qtab);
+        k_unfoveate<PR_UNFOVEATE_PROJECTED><<<grd, blk, 0, st>>>(dv, pyr, rgb, qtab, out);
     }
     return cudaGetLastError();
 }

@@ -943,11 +943,9 @@ pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, 
     if (!is_device_ptr(rgb) || !is_device_ptr(out))
         return PR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    float *pyr = nullptr;
-    if (p.method == PR_UNFOVEATE_MIP_CUBIC) {
-        PR_TRY(ensure(ws->mip, sizeof(float) * mip_pyramid_floats(v.W, v.H)));
-        pyr = ws->mip.as<float>();
-    }
+    // scratch: the MIP pyramid, or the projected filter's table of q (2 floats per pixel)
+    PR_TRY(ensure(ws->mip, sizeof(float) * mip_pyramid_floats(v.W, v.H)));
+    float *pyr = ws->mip.as<float>();
     PR_TRY(launch_unfoveate(p.method, v.W, v.H, v.mode, v.fovea[0], v.fovea[1], v.alpha, p.Wd, p.Hd, p.sigma, rgb,
                             pyr, out, st));
     return PR_OK;
