@@ -28,6 +28,7 @@ class OrView(C.Structure):
                 ("pose0", C.c_double * 16), ("pose1", C.c_double * 16),
                 ("fovea", C.c_double * 2), ("alpha", C.c_double), ("d", C.c_double * 2),
                 ("light_w", C.c_double * 3), ("k_a", C.c_double), ("k_d", C.c_double),
+                ("k_s", C.c_double), ("shininess", C.c_double),
                 ("W", C.c_int32), ("H", C.c_int32), ("mode", C.c_int32), ("pad", C.c_int32)]
 
 
@@ -95,6 +96,7 @@ def make_view(view) -> OrView:
     for k in range(3):
         v.light_w[k] = _f32(view.light_w[k])
     v.k_a, v.k_d = _f32(view.k_a), _f32(view.k_d)
+    v.k_s, v.shininess = _f32(getattr(view, "k_s", 0.0)), _f32(getattr(view, "shininess", 1.0))
     return v
 
 

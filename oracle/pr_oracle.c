@@ -40,7 +40,10 @@
  *  - shading (Sec. 3.2, "Shading": light is interpolated at the pixel time;
  *    not affected by foveation): Lambert with albedo a = sum_k b_k col_k,
  *    face normal of the moved triangle turned to face the viewer, light
- *    l(t) = normalize((1-t) R0 l_w + t R1 l_w), rgb = a (k_a + k_d max(0, n.l)).
+ *    l(t) = normalize((1-t) R0 l_w + t R1 l_w), rgb = a (k_a + k_d max(0, n.l))
+ *    + k_s max(0, n.h)^shininess with the rolling specular half vector
+ *    h = normalize(l(t) + v), v = the reversed ray (the eye at the pixel
+ *    time is the camera origin; "Rolling Shading", Sec. 6).
  *
  * Build: plain C99 + OpenMP, -ffp-contract=off so that x86 and Arm give the
  * same bits.
@@ -58,6 +61,7 @@ typedef struct {
     double d[2];                 /* rolling skew direction, r(x) = x . d */
     double light_w[3];           /* world-space unit direction towards the light */
     double k_a, k_d;             /* ambient and diffuse weights */
+    double k_s, shininess;       /* rolling specular (Blinn-Phong): weight (0: none) and exponent */
     int32_t W, H;
     int32_t mode;                /* 0 classic, 1 rolling, 2 foveated, 3 both */
     int32_t pad;
@@ -240,17 +244,36 @@ static void face_normal(const double P[3][3], const double dir[3], double nh[3],
         nh[r] = *flip * n[r] / *len;
 }
 
+/* Rolling specular (Blinn-Phong, "Rolling Shading" of Sec. 6): the eye at
+ * the pixel time is the camera origin, so the unit vector from the hit to
+ * the eye is the reversed ray; h = normalize(l + v).  Returns n . h. */
+static double half_vector(const double l[3], const double dir[3], const double nh[3], double hv[3])
+{
+    const double dn = sqrt(dot(dir, dir));
+    for (int r = 0; r < 3; ++r)
+        hv[r] = l[r] - dir[r] / dn;
+    const double hn = sqrt(dot(hv, hv));
+    for (int r = 0; r < 3; ++r)
+        hv[r] /= hn;
+    return dot(nh, hv);
+}
+
 static void shade(const or_view *v, const double P[3][3], const double b[3], const double *col,
                   const int32_t *vid, double t, const double dir[3], double rgb[3])
 {
-    double nh[3], len, flip, l[3];
+    double nh[3], len, flip, l[3], hv[3];
     face_normal(P, dir, nh, &len, &flip);
     or_light(v, t, l);
     double ndl = dot(nh, l);
     double sigma = v->k_a + v->k_d * (ndl > 0.0 ? ndl : 0.0);
+    double spec = 0.0;
+    if (v->k_s > 0.0) {
+        const double ndh = half_vector(l, dir, nh, hv);
+        spec = ndh > 0.0 ? v->k_s * pow(ndh, v->shininess) : 0.0;
+    }
     for (int c = 0; c < 3; ++c) {
         double a = b[0] * col[3 * vid[0] + c] + b[1] * col[3 * vid[1] + c] + b[2] * col[3 * vid[2] + c];
-        rgb[c] = a * sigma;
+        rgb[c] = a * sigma + spec;
     }
 }
 
@@ -472,9 +495,16 @@ void or_grad(const or_view *v, int64_t V, int64_t T, const double *pos, const do
             gC[r] = gw0 * DxB[r] + gw1 * AxD[r];
         }
 
-        /* normal -> vertices */
-        if (ndl > 0.0) {
-            double gnh[3] = {gsig * v->k_d * l[0], gsig * v->k_d * l[1], gsig * v->k_d * l[2]};
+        /* normal -> vertices: diffuse through n . l, specular through n . h */
+        double hv[3] = {0.0, 0.0, 0.0}, ndh = 0.0;
+        if (v->k_s > 0.0)
+            ndh = half_vector(l, dir, nh, hv);
+        const int spc = v->k_s > 0.0 && ndh > 0.0;
+        if (ndl > 0.0 || spc) {
+            const double gd = ndl > 0.0 ? gsig * v->k_d : 0.0;
+            const double gs = spc ? (gn[0] + gn[1] + gn[2]) * v->k_s * v->shininess * pow(ndh, v->shininess - 1.0)
+                                  : 0.0;
+            double gnh[3] = {gd * l[0] + gs * hv[0], gd * l[1] + gs * hv[1], gd * l[2] + gs * hv[2]};
             double pr = dot(nh, gnh);
             double gnn[3];
             for (int r = 0; r < 3; ++r)

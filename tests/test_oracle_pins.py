@@ -23,7 +23,7 @@ def _f32(x):
 
 
 def mkview(W=16, H=12, mode=S.MODE_CLASSIC, tan=(0.5, 0.5), pose0=None, pose1=None, fovea=(0.5, 0.5),
-           alpha=2.0, d=(1.0, 0.0), light=(0.0, 0.0, -1.0), k_a=0.1, k_d=0.9):
+           alpha=2.0, d=(1.0, 0.0), light=(0.0, 0.0, -1.0), k_a=0.1, k_d=0.9, k_s=0.0, shininess=1.0):
     """A view whose parameters are FP32 values (the method's inputs are the
     FP32 values of the library's ABI; the oracle widens them exactly), so the
     independent computations below see exactly what the oracle sees."""
@@ -31,7 +31,8 @@ def mkview(W=16, H=12, mode=S.MODE_CLASSIC, tan=(0.5, 0.5), pose0=None, pose1=No
     return S.View(W=W, H=H, tan_x=_f32(tan[0]), tan_y=_f32(tan[1]), pose0=I if pose0 is None else pose0,
                   pose1=(I if pose0 is None else pose0) if pose1 is None else pose1, mode=mode,
                   fovea=(_f32(fovea[0]), _f32(fovea[1])), alpha=_f32(alpha), d=(_f32(d[0]), _f32(d[1])),
-                  light_w=tuple(_f32(x) for x in light), k_a=_f32(k_a), k_d=_f32(k_d))
+                  light_w=tuple(_f32(x) for x in light), k_a=_f32(k_a), k_d=_f32(k_d), k_s=_f32(k_s),
+                  shininess=_f32(shininess))
 
 
 # --------------------------------------------------------------------------
@@ -382,6 +383,29 @@ def test_shading_barycentric_albedo(oracle):
     assert np.allclose(o["rgb"][hit], lam[hit], atol=1e-12)
 
 
+@pytest.mark.parametrize("light", [(0.0, 0.0, -1.0), (0.6, -0.48, -0.64)])
+def test_specular_flat_closed_form(oracle, light):
+    """Blinn-Phong on a fronto-parallel triangle (normal (0, 0, -1) towards the
+    camera): at every covered pixel rgb = c (k_a + k_d max(0, n.l)) +
+    k_s max(0, n.h)^m with h = normalize(l - dir/|dir|), dir the pixel's ray."""
+    pos, col, tri = _flat()
+    k_s, m = 0.35, 24.0
+    W = H = 11
+    v = mkview(W=W, H=H, light=light, k_s=k_s, shininess=m)
+    o = oracle.render(v, pos, np.zeros_like(pos), col, tri)
+    l = np.array(light, dtype=np.float64) / np.linalg.norm(light)
+    n = np.array([0.0, 0.0, -1.0])
+    hit = np.nonzero(o["id"] == 0)[0]
+    assert hit.size > 20
+    for k in hit:
+        i, j = k % W, k // W
+        dvec = np.array([(2 * (i + 0.5) / W - 1) * 0.5, (2 * (j + 0.5) / H - 1) * 0.5, 1.0])
+        hv = l - dvec / np.linalg.norm(dvec)
+        hv /= np.linalg.norm(hv)
+        want = np.array([0.2, 0.5, 0.8]) * (_f32(0.1) + _f32(0.9) * max(0.0, n @ l)) + _f32(k_s) * max(0.0, n @ hv) ** m
+        assert np.allclose(o["rgb"][k], want, atol=1e-12)
+
+
 def test_rolling_light(oracle):
     """The light follows the camera pose at the pixel time: with a 90 degree
     yaw over the frame, l(t) = normalize((1-t) R0 l + t R1 l)."""
@@ -396,13 +420,13 @@ def test_rolling_light(oracle):
 # gradient: FP64 analytic vs central finite differences
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mode", [S.MODE_ROLLING, S.MODE_BOTH])
-def test_gradient_matches_finite_differences(oracle, mode):
+@pytest.mark.parametrize("mode,k_s", [(S.MODE_ROLLING, 0.0), (S.MODE_BOTH, 0.0), (S.MODE_BOTH, 0.4)])
+def test_gradient_matches_finite_differences(oracle, mode, k_s):
     rng = np.random.default_rng(11 + mode)
     sc = S.random_triangles(40, 3, vel_sigma=0.05, offset=0.6)
     pose1 = S.make_pose(S.rot_pitch(1.0) @ S.rot_yaw(4.0), (0.02, 0.0, 0.0))
     v = mkview(W=40, H=32, mode=mode, pose1=pose1, fovea=(0.45, 0.55),
-               light=tuple(np.array([-1.0, -1.0, -1.0]) / math.sqrt(3.0)))
+               light=tuple(np.array([-1.0, -1.0, -1.0]) / math.sqrt(3.0)), k_s=k_s, shininess=6.0)
     pos, vel, col = (a.astype(np.float64) for a in (sc.pos, sc.vel, sc.col))
     o = oracle.render(v, pos, vel, col, sc.tri, near=True)
     interior = (o["id"] != BG) & (o["bmin"] > 1e-3) & (o["gap"] > 1e-3) & (o["near"] > 1e-3)
