@@ -106,7 +106,10 @@ typedef struct {
     float fovea[2];       /* x_f in unit framebuffer coordinates, in [0,1]^2 */
     float d[2];           /* rolling direction: d0, d1 >= 0 and d0 + d1 <= 1 */
     float light_w[3];     /* world-space direction towards the light (normalised by the library) */
-    float k_a, k_d;       /* rgb = albedo * (k_a + k_d * max(0, n.l)) */
+    float k_a, k_d;       /* rgb = albedo * (k_a + k_d * max(0, n.l)) + the specular term below */
+    float k_s, shininess; /* rolling specular (Blinn-Phong): + k_s * max(0, n.h)^shininess on every
+                             channel, h = normalize(l(t) + v), v = unit vector from the hit to the eye at
+                             the pixel time (the reversed ray); k_s = 0: none; shininess >= 1 */
 } pr_view;
 
 typedef struct {

@@ -43,7 +43,8 @@ class PrView(C.Structure):
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("mode", C.c_int32), ("pad0", C.c_int32),
                 ("tan_x", C.c_float), ("tan_y", C.c_float), ("z_near", C.c_float), ("alpha", C.c_float),
                 ("pose0", C.c_float * 16), ("pose1", C.c_float * 16), ("fovea", C.c_float * 2),
-                ("d", C.c_float * 2), ("light_w", C.c_float * 3), ("k_a", C.c_float), ("k_d", C.c_float)]
+                ("d", C.c_float * 2), ("light_w", C.c_float * 3), ("k_a", C.c_float), ("k_d", C.c_float),
+                ("k_s", C.c_float), ("shininess", C.c_float)]
 
 
 class PrParams(C.Structure):
@@ -183,6 +184,7 @@ def make_view(v) -> PrView:
     for k in range(3):
         out.light_w[k] = float(v.light_w[k])
     out.k_a, out.k_d = float(v.k_a), float(v.k_d)
+    out.k_s, out.shininess = float(getattr(v, "k_s", 0.0)), float(getattr(v, "shininess", 1.0))
     return out
 
 

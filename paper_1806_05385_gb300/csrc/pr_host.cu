@@ -217,6 +217,8 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
         return PR_ERR_INVALID_ARG;
     if (tile != 8 && tile != 16 && tile != 32)
         return PR_ERR_INVALID_ARG;
+    if (!(in.k_s >= 0.f && std::isfinite(in.k_s)) || (in.k_s > 0.f && !(in.shininess >= 1.f && in.shininess <= 4096.f)))
+        return PR_ERR_INVALID_ARG;
     if (bound < PR_BOUND_ZENON || bound > PR_BOUND_TRIVIAL)
         return PR_ERR_INVALID_ARG;
     for (int k = 0; k < 16; ++k)
@@ -257,6 +259,8 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
     }
     v.k_a = in.k_a;
     v.k_d = in.k_d;
+    v.k_s = in.k_s;
+    v.shininess = in.shininess;
     v.W = in.W;
     v.H = in.H;
     v.mode = in.mode;

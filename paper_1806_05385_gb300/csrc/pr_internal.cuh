@@ -36,7 +36,7 @@ struct ViewDev {
     float d0, d1;                      // rolling direction, r(x) = x . d
     float t_lo, t_hi;                  // range of pixel times over the viewport
     float l0[3], l1[3];                // camera-space light direction at t = 0 and t = 1
-    float k_a, k_d;
+    float k_a, k_d, k_s, shininess;
     int W, H, mode, S;                 // framebuffer, pr_mode, bin tile side
     int tiles_x, tiles_y, bound, fp64;
     int fov_bound;                     // pr_fov_bound

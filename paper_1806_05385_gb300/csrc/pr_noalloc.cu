@@ -147,6 +147,8 @@ pr_status view_constants(const pr_view &in, int tile, int bound, float *soa, int
     v.t_hi = std::min(1.f, in.d[0] + in.d[1]);
     v.k_a = in.k_a;
     v.k_d = in.k_d;
+    v.k_s = in.k_s;
+    v.shininess = in.shininess;
     v.W = in.W;
     v.H = in.H;
     v.mode = in.mode;

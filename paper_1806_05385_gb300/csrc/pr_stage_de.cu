@@ -28,6 +28,8 @@ struct PixelHit {
     float nlen, flip;   // |(B-A) x (C-A)| and the sign applied
     float3 l;           // unit light direction at t
     float ndl, sigma;   // n.l and k_a + k_d max(0, n.l)
+    float3 hv;          // Blinn-Phong half vector normalize(l + v), v = the reversed ray
+    float ndh, spec;    // n.h and k_s max(0, n.h)^shininess (0 without specular)
 };
 
 __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsigned id, PixelHit &h)
@@ -80,6 +82,16 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     h.l = scale3(l, rsqrtf(dot3(l, l)));
     h.ndl = dot3(h.n, h.l);
     h.sigma = v.k_a + v.k_d * fmaxf(h.ndl, 0.f);
+    h.spec = 0.f;
+    h.ndh = 0.f;
+    if (v.k_s > 0.f) {
+        // the eye at the pixel time is the camera origin: v = -dir / |dir|
+        const float3 e = scale3(h.dir, -rsqrtf(dot3(h.dir, h.dir)));
+        const float3 hh = add3(h.l, e);
+        h.hv = scale3(hh, rsqrtf(fmaxf(dot3(hh, hh), 1e-30f)));
+        h.ndh = dot3(h.n, h.hv);
+        h.spec = h.ndh > 0.f ? v.k_s * powf(h.ndh, v.shininess) : 0.f;
+    }
 }
 
 // Stages (d) and (e) run one warp per 8x4 pixel block (lane -> column
@@ -103,8 +115,10 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
     return i < v.W && j < v.H;
 }
 
-// Adjoint of rgb = a sigma, a = sum_k b_k col_k, sigma = k_a + k_d max(0, n.l):
+// Adjoint of rgb = a sigma + s, a = sum_k b_k col_k, sigma = k_a + k_d max(0, n.l),
+// s = k_s max(0, n.h)^m (h depends only on the pixel's time and ray):
 //  - d/dcol_k = g b_k sigma
+//  - d/dn = (g . a) k_d l [n.l > 0] + (sum_c g_c) k_s m (n.h)^(m-1) h [n.h > 0]
 //  - barycentrics b_k = w_k / sum w with w_0 = dir.(B x C), w_1 = dir.(C x A),
 //    w_2 = dir.(A x B) (the watertight U, V, W are -w), so
 //    d sum/dw_j = (gb_j - sum_k gb_k b_k) / sum w and dw_j/dA etc. are
@@ -158,9 +172,13 @@ __device__ __forceinline__ void adjoint_pixel(const ViewDev &v, const PixelHit &
         float3 gA = add3(scale3(cross3(D, h.C), gw1), scale3(cross3(h.B, D), gw2));
         float3 gB = add3(scale3(cross3(h.C, D), gw0), scale3(cross3(D, h.A), gw2));
         float3 gC = add3(scale3(cross3(D, h.B), gw0), scale3(cross3(h.A, D), gw1));
-        // normal -> moved vertices
-        if (h.ndl > 0.f && h.nlen > 0.f) {
-            const float3 gnh = scale3(h.l, gsig * v.k_d);
+        // normal -> moved vertices: the diffuse term through n.l, the
+        // specular term k_s (n.h)^m (white) through n.h
+        const bool dif = h.ndl > 0.f, spc = h.spec > 0.f;
+        if ((dif || spc) && h.nlen > 0.f) {
+            float3 gnh = scale3(h.l, dif ? gsig * v.k_d : 0.f);
+            if (spc)
+                gnh = add3(gnh, scale3(h.hv, (g0 + g1 + g2) * v.shininess * h.spec / h.ndh));
             const float pr = dot3(h.n, gnh);
             const float3 gnn = scale3(sub3(gnh, scale3(h.n, pr)), h.flip / h.nlen);
             gA = add3(gA, cross3(sub3(h.B, h.C), gnn));
@@ -276,9 +294,9 @@ __global__ void __launch_bounds__(256) k_shade(const ViewDev *__restrict__ views
         const float r = fmaf(h.b0, v.cr[h.ia], fmaf(h.b1, v.cr[h.ib], h.b2 * v.cr[h.ic]));
         const float gg = fmaf(h.b0, v.cg[h.ia], fmaf(h.b1, v.cg[h.ib], h.b2 * v.cg[h.ic]));
         const float b = fmaf(h.b0, v.cb[h.ia], fmaf(h.b1, v.cb[h.ib], h.b2 * v.cb[h.ic]));
-        rgb[0] = r * h.sigma;
-        rgb[1] = gg * h.sigma;
-        rgb[2] = b * h.sigma;
+        rgb[0] = fmaf(r, h.sigma, h.spec);
+        rgb[1] = fmaf(gg, h.sigma, h.spec);
+        rgb[2] = fmaf(b, h.sigma, h.spec);
     }
     if (inside && v.rgb_out) {
         v.rgb_out[lin] = rgb[0];

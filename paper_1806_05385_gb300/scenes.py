@@ -61,6 +61,8 @@ class View:
     light_w: tuple = field(default_factory=lambda: tuple((np.array([-1.0, -1.0, -1.0]) / math.sqrt(3.0)).tolist()))
     k_a: float = 0.1
     k_d: float = 0.9
+    k_s: float = 0.0        # rolling specular (Blinn-Phong) weight; 0: none
+    shininess: float = 1.0
 
 
 # ----------------------------------------------------------------------------

