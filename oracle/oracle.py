@@ -29,7 +29,8 @@ class OrView(C.Structure):
                 ("fovea", C.c_double * 2), ("alpha", C.c_double), ("d", C.c_double * 2),
                 ("light_w", C.c_double * 3), ("k_a", C.c_double), ("k_d", C.c_double),
                 ("k_s", C.c_double), ("shininess", C.c_double),
-                ("W", C.c_int32), ("H", C.c_int32), ("mode", C.c_int32), ("pad", C.c_int32)]
+                ("W", C.c_int32), ("H", C.c_int32), ("mode", C.c_int32), ("p_n", C.c_int32),
+                ("p_lut", C.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -97,6 +98,13 @@ def make_view(view) -> OrView:
         v.light_w[k] = _f32(view.light_w[k])
     v.k_a, v.k_d = _f32(view.k_a), _f32(view.k_d)
     v.k_s, v.shininess = _f32(getattr(view, "k_s", 0.0)), _f32(getattr(view, "shininess", 1.0))
+    lut = getattr(view, "p_lut", None)
+    if lut is not None:
+        # the FP32 samples the library takes, widened exactly; kept alive on the record
+        arr = np.ascontiguousarray(np.asarray(lut, dtype=np.float32).astype(np.float64))
+        v._keep = arr
+        v.p_n = arr.size - 1
+        v.p_lut = arr.ctypes.data
     return v
 
 

@@ -64,7 +64,8 @@ typedef struct {
     double k_s, shininess;       /* rolling specular (Blinn-Phong): weight (0: none) and exponent */
     int32_t W, H;
     int32_t mode;                /* 0 classic, 1 rolling, 2 foveated, 3 both */
-    int32_t pad;
+    int32_t p_n;                 /* > 0: p is given by p_lut[0..p_n] instead of the power map */
+    const double *p_lut;         /* p at d_k = k D / p_n (increasing, p_lut[0] = 0) */
 } or_view;
 
 enum { OR_CLASSIC = 0, OR_ROLLING = 1, OR_FOVEATED = 2, OR_BOTH = 3 };
@@ -80,6 +81,53 @@ double or_p(double dist, double alpha) { return OR_D * pow(dist / OR_D, alpha); 
 /* p^-1(r) = D (r/D)^(1/alpha). */
 double or_pinv(double r, double alpha) { return OR_D * pow(r / OR_D, 1.0 / alpha); }
 
+/* An arbitrary monotone p (Sec. 3.1.1: "any monotonic p"), given by its
+ * values at d_k = k D / n: linear between the samples (the last segment
+ * continued beyond D), and p^-1 its exact inverse (the segment that holds r,
+ * inverted; the paper's numerical inversion). */
+static double lut_p(const or_view *v, double d)
+{
+    const int64_t n = v->p_n;
+    const double x = d * (double)n / OR_D;
+    int64_t k = (int64_t)floor(x);
+    if (k < 0)
+        k = 0;
+    if (k > n - 1)
+        k = n - 1;
+    const double t = x - (double)k;
+    return (1.0 - t) * v->p_lut[k] + t * v->p_lut[k + 1];
+}
+
+static int64_t lut_segment(const or_view *v, double r)
+{
+    int64_t lo = 0, hi = v->p_n - 1; /* last k with p_lut[k] <= r */
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (v->p_lut[mid] <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+static double lut_pinv(const or_view *v, double r)
+{
+    const int64_t k = lut_segment(v, r);
+    const double a = v->p_lut[k], b = v->p_lut[k + 1];
+    return ((double)k + (r - a) / (b - a)) * OR_D / (double)v->p_n;
+}
+
+/* d p^-1 / dr at r (the slope of the segment that holds it). */
+static double lut_dpinv(const or_view *v, double r)
+{
+    const int64_t k = lut_segment(v, r);
+    return OR_D / (double)v->p_n / (v->p_lut[k + 1] - v->p_lut[k]);
+}
+
+static double view_p(const or_view *v, double d) { return v->p_n > 0 ? lut_p(v, d) : or_p(d, v->alpha); }
+static double view_pinv(const or_view *v, double r) { return v->p_n > 0 ? lut_pinv(v, r) : or_pinv(r, v->alpha); }
+
 /* q: framebuffer -> display, radial about the fovea (Sec. 3.1.1). */
 void or_q(const or_view *v, const double u[2], double x[2])
 {
@@ -90,7 +138,7 @@ void or_q(const or_view *v, const double u[2], double x[2])
         x[1] = v->fovea[1];
         return;
     }
-    double s = or_p(dist, v->alpha) / dist;
+    double s = view_p(v, dist) / dist;
     x[0] = v->fovea[0] + e0 * s;
     x[1] = v->fovea[1] + e1 * s;
 }
@@ -105,7 +153,7 @@ void or_qinv(const or_view *v, const double x[2], double u[2])
         u[1] = v->fovea[1];
         return;
     }
-    double s = or_pinv(dist, v->alpha) / dist;
+    double s = view_pinv(v, dist) / dist;
     u[0] = v->fovea[0] + e0 * s;
     u[1] = v->fovea[1] + e1 * s;
 }
@@ -691,8 +739,12 @@ double or_unfoveate_lod(const or_view *v, const double x[2], int64_t Wd, int64_t
     double stretch = 1.0;
     if (fov) {
         const double e0 = x[0] - v->fovea[0], e1 = x[1] - v->fovea[1], r = sqrt(e0 * e0 + e1 * e1);
-        const double tang = r > 0.0 ? pow(r / OR_D, 1.0 / v->alpha - 1.0) : INFINITY;
-        stretch = fmax(tang, tang / v->alpha);
+        if (v->p_n > 0) {
+            stretch = r > 0.0 ? fmax(lut_pinv(v, r) / r, lut_dpinv(v, r)) : lut_dpinv(v, 0.0);
+        } else {
+            const double tang = r > 0.0 ? pow(r / OR_D, 1.0 / v->alpha - 1.0) : INFINITY;
+            stretch = fmax(tang, tang / v->alpha);
+        }
     }
     return log2(stretch * fmax((double)v->W / (double)Wd, (double)v->H / (double)Hd));
 }

@@ -63,6 +63,7 @@ class View:
     k_d: float = 0.9
     k_s: float = 0.0        # rolling specular (Blinn-Phong) weight; 0: none
     shininess: float = 1.0
+    p_lut: object = None    # optional samples of an arbitrary monotone p (float32 [n + 1]) instead of the power map
 
 
 # ----------------------------------------------------------------------------
