@@ -53,7 +53,7 @@ def lib():
         path = build()
         L = C.CDLL(path)
         P = C.c_void_p
-        L.or_render.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P]
+        L.or_render.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P, P]
         L.or_eval.argtypes = [P, P, P, P, C.c_int64, C.c_int64, P]
         L.or_grad.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P, P, C.c_int64, P, P, P, P, P]
         L.or_pixels.argtypes = [P, P, C.c_int64, P, P, P]
@@ -121,8 +121,10 @@ def render(view, pos, vel, col, tri, pix=None, near=False):
 
     Returns a dict of numpy arrays: id (uint32), depth (float32), s (float64),
     rgb (float64 [n,3]), bmin (winner's smallest barycentric), gap (relative
-    depth gap to the next hit) and, with ``near=True``, near (edge margin of
-    every potential occluder; costs a second sweep)."""
+    depth gap to the next hit), cos (|cosine| between the ray and the
+    winner's plane normal: the conditioning of its depth) and, with
+    ``near=True``, near (edge margin of every potential occluder; costs a
+    second sweep)."""
     L = lib()
     v = make_view(view)
     pos, vel, col = _d(pos), _d(vel), _d(col)
@@ -135,12 +137,13 @@ def render(view, pos, vel, col, tri, pix=None, near=False):
         n = int(pix.shape[0])
         pixp = pix
     out = {"id": np.empty(n, np.uint32), "depth": np.empty(n, np.float32), "s": np.empty(n, np.float64),
-           "rgb": np.empty((n, 3), np.float64), "bmin": np.empty(n, np.float64), "gap": np.empty(n, np.float64)}
+           "rgb": np.empty((n, 3), np.float64), "bmin": np.empty(n, np.float64), "gap": np.empty(n, np.float64),
+           "cos": np.empty(n, np.float64)}
     if near:
         out["near"] = np.empty(n, np.float64)
     L.or_render(C.byref(v), pos.shape[0], tri.shape[0], _ptr(pos), _ptr(vel), _ptr(col), _ptr(tri),
                 _ptr(pixp), n, _ptr(out["id"]), _ptr(out["depth"]), _ptr(out["s"]), _ptr(out["rgb"]),
-                _ptr(out["bmin"]), _ptr(out["gap"]), _ptr(out.get("near")))
+                _ptr(out["bmin"]), _ptr(out["gap"]), _ptr(out.get("near")), _ptr(out["cos"]))
     return out
 
 

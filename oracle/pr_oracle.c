@@ -341,7 +341,7 @@ static void shade(const or_view *v, const double P[3][3], const double b[3], con
 void or_render(const or_view *v, int64_t V, int64_t T, const double *pos, const double *vel,
                const double *col, const int32_t *tri, const int64_t *pix, int64_t npix,
                uint32_t *id_out, float *depth_out, double *s_out, double *rgb_out, double *bmin_out,
-               double *gap_out, double *near_out)
+               double *gap_out, double *near_out, double *cos_out)
 {
     (void)V;
     /* camera-space start/end of every vertex, computed once */
@@ -403,6 +403,19 @@ void or_render(const or_view *v, int64_t V, int64_t T, const double *pos, const 
                     m = mb;
             }
             near_out[n] = m;
+        }
+        if (cos_out) {
+            /* |cos| of the angle between the ray and the winner's plane
+             * normal: the conditioning of its depth (1 for background) */
+            double cg = 1.0;
+            if (best >= 0) {
+                double P[3][3], nh[3], len, flip;
+                for (int k = 0; k < 3; ++k)
+                    lerp3(S + 3 * tri[3 * best + k], E + 3 * tri[3 * best + k], t, P[k]);
+                face_normal(P, dir, nh, &len, &flip);
+                cg = fabs(dot(nh, dir)) / sqrt(dot(dir, dir));
+            }
+            cos_out[n] = cg;
         }
         if (rgb_out) {
             double rgb[3] = {0, 0, 0};
