@@ -92,6 +92,11 @@ typedef enum {
     PR_FOV_RECURSIVE = 2   /* Sec. 4.1.2: displaced parallel to the chord of its foveated end points */
 } pr_fov_bound;
 
+/* A foveation function given by samples (Sec. 3.1.1: p may be any
+ * monotonic function, inverted numerically in a pre-processing pass; Sec. 6,
+ * "Lens Distortion": p = p_c o p_l).  See pr_foveation_create. */
+typedef struct pr_foveation pr_foveation;
+
 /* One view: the camera, the two poses that bracket the frame, the fovea,
  * the display's rolling direction and the shading constants. */
 typedef struct {
@@ -110,6 +115,8 @@ typedef struct {
     float k_s, shininess; /* rolling specular (Blinn-Phong): + k_s * max(0, n.h)^shininess on every
                              channel, h = normalize(l(t) + v), v = unit vector from the hit to the eye at
                              the pixel time (the reversed ray); k_s = 0: none; shininess >= 1 */
+    const pr_foveation *foveation; /* NULL: p(d) = D (d/D)^alpha; else the sampled p of the handle
+                                       (alpha is then unused) */
 } pr_view;
 
 typedef struct {
@@ -144,6 +151,17 @@ typedef struct {
                              re-test removed); 0 without the re-test */
     float pad_stats;
 } pr_stats;
+
+/* p_samples: HOST float [n + 1], p at d_k = k D / n (D = sqrt(2), the
+ * largest framebuffer distance from the fovea), p_samples[0] = 0, strictly
+ * increasing, finite; 2 <= n <= 65536.  The library copies them to the
+ * device.  Every stage evaluates p linearly between the samples (the last
+ * segment continued beyond D) and p^-1 as the exact inverse of that
+ * interpolation (a binary search for the segment).  The handle must outlive
+ * every call and captured graph whose views use it.  PR_ERR_INVALID_ARG for
+ * samples that break the rules. */
+pr_status pr_foveation_create(const float *p_samples, int32_t n, pr_foveation **out);
+void pr_foveation_free(pr_foveation *f);
 
 typedef struct pr_scene pr_scene;         /* library-owned device copy of a mesh + its scratch */
 typedef struct pr_workspace pr_workspace; /* scratch of the batched entry points */

@@ -30,7 +30,8 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_workspace_create", "pr_workspace_free", "pr_rasterize_batch", "pr_graph_capture_batch",
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
-           "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate")
+           "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
+           "pr_foveation_free")
 
 
 class PrError(RuntimeError):
@@ -44,7 +45,7 @@ class PrView(C.Structure):
                 ("tan_x", C.c_float), ("tan_y", C.c_float), ("z_near", C.c_float), ("alpha", C.c_float),
                 ("pose0", C.c_float * 16), ("pose1", C.c_float * 16), ("fovea", C.c_float * 2),
                 ("d", C.c_float * 2), ("light_w", C.c_float * 3), ("k_a", C.c_float), ("k_d", C.c_float),
-                ("k_s", C.c_float), ("shininess", C.c_float)]
+                ("k_s", C.c_float), ("shininess", C.c_float), ("foveation", C.c_void_p)]
 
 
 class PrParams(C.Structure):
@@ -124,6 +125,8 @@ def load(build_if_missing: bool = True):
             "pr_rasterize_noalloc": ([P, P, P, P, I64, I64, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
             "pr_backward_batch": ([P, C.POINTER(PrBackwardView), I32, P], I32),
             "pr_unfoveate": ([P, C.POINTER(PrView), P, P, C.POINTER(PrUnfoveateParams), P], I32),
+            "pr_foveation_create": ([P, I32, C.POINTER(P)], I32),
+            "pr_foveation_free": ([P], None),
             "pr_frame_batch": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P], I32),
             "pr_graph_capture_frame": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P,
                                         C.POINTER(P)], I32),
@@ -185,6 +188,8 @@ def make_view(v) -> PrView:
         out.light_w[k] = float(v.light_w[k])
     out.k_a, out.k_d = float(v.k_a), float(v.k_d)
     out.k_s, out.shininess = float(getattr(v, "k_s", 0.0)), float(getattr(v, "shininess", 1.0))
+    lut = getattr(v, "p_lut", None)
+    out.foveation = foveation_handle(lut) if lut is not None else None
     return out
 
 
@@ -328,6 +333,38 @@ def pr_graph_capture_frame(ws, entries, grads, params=None, stream=None) -> int:
                                          stream if stream is not None else current_stream(), C.byref(h)),
            "pr_graph_capture_frame")
     return h.value
+
+
+def pr_foveation_create(samples) -> int:
+    """Handle of a sampled foveation function p (float32 [n + 1], p at
+    d_k = k sqrt(2) / n, p[0] = 0, strictly increasing)."""
+    arr = np.ascontiguousarray(np.asarray(samples, dtype=np.float32))
+    h = C.c_void_p()
+    _check(load().pr_foveation_create(arr.ctypes.data_as(C.c_void_p), int(arr.size - 1), C.byref(h)),
+           "pr_foveation_create")
+    return h.value
+
+
+def pr_foveation_free(handle):
+    if handle:
+        load().pr_foveation_free(C.c_void_p(handle))
+
+
+_foveations = {}
+
+
+def foveation_handle(samples) -> int:
+    """The (cached, process-lifetime) handle of a sample table, so that views
+    may carry their p as samples."""
+    arr = np.ascontiguousarray(np.asarray(samples, dtype=np.float32))
+    key = arr.tobytes()
+    with _lock:
+        h = _foveations.get(key)
+    if h is None:
+        h = pr_foveation_create(arr)
+        with _lock:
+            _foveations[key] = h
+    return h
 
 
 def pr_unfoveate(ws, view, rgb, out, Wd: int, Hd: int, method: str = "mip", sigma: float = 0.5, stream=None):

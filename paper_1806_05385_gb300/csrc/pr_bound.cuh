@@ -148,8 +148,10 @@ __host__ __device__ inline float2 rot_small(float2 a, float sn)
 }
 
 // Display box (x0, x1, y0, y1) that contains q of the framebuffer box
-// [u0,u1] x [v0,v1]: the same sector argument with the radius map p.
-__host__ __device__ inline float4 fov_image_box(float u0, float u1, float v0, float v1, float2 f, float alpha)
+// [u0,u1] x [v0,v1]: the same sector argument with the radius map p (the
+// power map of alpha, or the sampled p when lut is set).
+__host__ __device__ inline float4 fov_image_box(float u0, float u1, float v0, float v1, float2 f, float alpha,
+                                                const float *lut = nullptr, int n = 0)
 {
     const float2 c[4] = {make_float2(u0, v0), make_float2(u1, v0), make_float2(u1, v1), make_float2(u0, v1)};
     float rmax = 0.f;
@@ -157,14 +159,15 @@ __host__ __device__ inline float4 fov_image_box(float u0, float u1, float v0, fl
         const float2 w = f2sub(c[k], f);
         rmax = fmaxf(rmax, sqrtf(w.x * w.x + w.y * w.y));
     }
+    const SampledP sp{lut, n};
     const float kD1 = powf(kSqrt2, 1.f - alpha);
-    const float rho1 = kD1 * powf(rmax, alpha) * (1.f + 1e-5f) + 1e-7f;
+    const float rho1 = (lut ? sp.p(rmax) : kD1 * powf(rmax, alpha)) * (1.f + 1e-5f) + 1e-7f;
     const bool inside = f.x >= u0 && f.x <= u1 && f.y >= v0 && f.y <= v1;
     if (inside)
         return sector_box(f, make_float2(1.f, 0.f), make_float2(1.f, 0.f), 0.f, rho1, true);
     const float cx = fminf(fmaxf(f.x, u0), u1), cy = fminf(fmaxf(f.y, v0), v1);
     const float rmin = sqrtf((cx - f.x) * (cx - f.x) + (cy - f.y) * (cy - f.y));
-    const float rho0 = kD1 * powf(rmin, alpha) * (1.f - 1e-5f);
+    const float rho0 = (lut ? sp.p(rmin) : kD1 * powf(rmin, alpha)) * (1.f - 1e-5f);
     float2 a = f2sub(c[0], f), b = a;
     for (int k = 1; k < 4; ++k) {
         const float2 w = f2sub(c[k], f);

@@ -36,6 +36,8 @@ struct DisplayView {
     int fov;             // foveated or joint mode: q is the power map, else the identity
     float fx, fy;        // fovea
     float alpha, inv_alpha;
+    const float *p_lut;  // or: the sampled p (then alpha is unused)
+    int p_n;
     float scale;         // max(W / Wd, H / Hd)
     float sigma;         // projected filter width, display pixels
 };
@@ -64,7 +66,8 @@ __global__ void k_mip_down(const float *__restrict__ src, int w0, int h0, float 
 
 // Display location q(c) of every framebuffer pixel centre c (the offset from
 // the fovea scaled by (|e|/D)^(alpha - 1)), for the projected filter.
-__global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha, float2 *__restrict__ table)
+__global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha, const float *__restrict__ p_lut,
+                          int p_n, float2 *__restrict__ table)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= W)
@@ -72,7 +75,8 @@ __global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha
     float q0 = __fdiv_rn((float)i + 0.5f, (float)W), q1 = __fdiv_rn((float)j + 0.5f, (float)H);
     if (fov) {
         const float e0 = q0 - fx, e1 = q1 - fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
-        const float s = r > 0.f ? powf(r * (1.f / kSqrt2), alpha - 1.f) : 0.f;
+        const SampledP sp{p_lut, p_n};
+        const float s = r > 0.f ? (p_lut ? sp.p(r) / r : powf(r * (1.f / kSqrt2), alpha - 1.f)) : 0.f;
         q0 = fmaf(e0, s, fx);
         q1 = fmaf(e1, s, fy);
     }
@@ -131,10 +135,18 @@ __global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid py
         return;
     const float x0 = __fdiv_rn((float)a + 0.5f, (float)dv.Wd), x1 = __fdiv_rn((float)b + 0.5f, (float)dv.Hd);
     // u = q^-1(x): the offset from the fovea scaled by (|e|/D)^(1/alpha - 1)
-    float u0 = x0, u1 = x1, tang = 1.f;
+    float u0 = x0, u1 = x1, tang = 1.f, stretch = 1.f;
     if (dv.fov) {
         const float e0 = x0 - dv.fx, e1 = x1 - dv.fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
-        tang = r > 0.f ? powf(r * (1.f / kSqrt2), dv.inv_alpha - 1.f) : INFINITY;
+        if (dv.p_lut) {  // the sampled p: tangential stretch p^-1(r)/r, radial the slope of p^-1
+            const SampledP sp{dv.p_lut, dv.p_n};
+            const float radial = sp.dpinv(r);
+            tang = r > 0.f ? sp.pinv(r) / r : radial;
+            stretch = fmaxf(tang, radial);
+        } else {
+            tang = r > 0.f ? powf(r * (1.f / kSqrt2), dv.inv_alpha - 1.f) : INFINITY;
+            stretch = fmaxf(tang, tang * dv.inv_alpha);
+        }
         const float s = r > 0.f ? tang : 0.f;
         u0 = fmaf(e0, s, dv.fx);
         u1 = fmaf(e1, s, dv.fy);
@@ -142,7 +154,7 @@ __global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid py
     float res[3];
     if (kMethod == PR_UNFOVEATE_MIP_CUBIC) {
         // level of detail: the largest stretch of q^-1 (tangential for alpha >= 1)
-        float lambda = log2f(fmaxf(tang, tang * dv.inv_alpha) * dv.scale);
+        float lambda = log2f(stretch * dv.scale);
         lambda = fminf(fmaxf(lambda, 0.f), (float)(pyr.L - 1));  // NaN-free: tang >= 0
         const int k0 = (int)floorf(lambda), k1 = min(k0 + 1, pyr.L - 1);
         const float f = lambda - (float)k0;
@@ -242,8 +254,9 @@ size_t mip_pyramid_floats(int W, int H)
     }
 }
 
-cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, int Wd, int Hd,
-                             float sigma, const float *rgb, float *pyramid, float *out, cudaStream_t st)
+cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, const float *p_lut,
+                             int p_n, int Wd, int Hd, float sigma, const float *rgb, float *pyramid, float *out,
+                             cudaStream_t st)
 {
     DisplayView dv;
     dv.W = W;
@@ -255,6 +268,8 @@ cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float
     dv.fy = fy;
     dv.alpha = alpha;
     dv.inv_alpha = 1.f / alpha;
+    dv.p_lut = p_lut;
+    dv.p_n = p_n;
     dv.scale = fmaxf((float)W / (float)Wd, (float)H / (float)Hd);
     dv.sigma = sigma;
     MipPyramid pyr;
@@ -282,7 +297,7 @@ cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float
     } else {
         float2 *qtab = reinterpret_cast<float2 *>(pyramid);
         const dim3 gq((unsigned)((W + 255) / 256), (unsigned)H);
-        k_q_table<<<gq, 256, 0, st>>>(W, H, dv.fov, fx, fy, alpha, qtab);
+        k_q_table<<<gq, 256, 0, st>>>(W, H, dv.fov, fx, fy, alpha, p_lut, p_n, qtab);
         k_unfoveate<PR_UNFOVEATE_PROJECTED><<<grd, blk, 0, st>>>(dv, pyr, rgb, qtab, out);
     }
     return cudaGetLastError();

@@ -180,6 +180,55 @@ struct pr_workspace {
     }
 };
 
+struct pr_foveation {
+    float *lut = nullptr;  // device, n + 1 samples of p
+    int n = 0;
+};
+
+pr_status pr_foveation_create(const float *p_samples, int32_t n, pr_foveation **out)
+{
+    if (!p_samples || !out || n < 2 || n > 65536)
+        return PR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (p_samples[0] != 0.f)
+        return PR_ERR_INVALID_ARG;
+    for (int k = 1; k <= n; ++k)
+        if (!std::isfinite(p_samples[k]) || !(p_samples[k] > p_samples[k - 1]))
+            return PR_ERR_INVALID_ARG;
+    pr_foveation *f = new (std::nothrow) pr_foveation;
+    if (!f)
+        return PR_ERR_OOM;
+    cudaError_t e = cudaMalloc(&f->lut, sizeof(float) * (n + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(f->lut, p_samples, sizeof(float) * (n + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (f->lut)
+            cudaFree(f->lut);
+        delete f;
+        return from_cuda(e);
+    }
+    f->n = n;
+    *out = f;
+    return PR_OK;
+}
+
+namespace pr {
+const float *pr_foveation_samples(const pr_foveation *f, int *n)
+{
+    *n = f->n;
+    return f->lut;
+}
+}  // namespace pr
+
+void pr_foveation_free(pr_foveation *f)
+{
+    if (f) {
+        cudaFree(f->lut);
+        delete f;
+    }
+}
+
 struct pr_scene {
     long long V = 0, T = 0;
     DevBuf soa;   // 9 V floats: px py pz vx vy vz cr cg cb
@@ -240,6 +289,10 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
     v.fy = in.fovea[1];
     v.alpha = in.alpha;
     v.inv_alpha = 1.f / in.alpha;
+    if (in.foveation) {
+        v.p_lut = in.foveation->lut;
+        v.p_n = in.foveation->n;
+    }
     v.d0 = in.d[0];
     v.d1 = in.d[1];
     v.t_lo = 0.f;
@@ -530,11 +583,12 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
                             ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, cnt, st));
     PR_TRY(launch_bin_scatter(ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), scan,
-                              ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, cnt, st));
+                              ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, P.ntiles, cnt,
+                              st));
     PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,
                         ws->cap_pairs, seg, cnt, st));
     PR_TRY(launch_sort_items(ws->items.as<int4>(), scan, P.ntiles, ws->cap_items, seg,
-                             ws->pairs.as<unsigned long long>(), st));
+                             ws->pairs.as<unsigned long long>(), cnt, st));
     PR_TRY(mark(2));
     int *heads = ws->heads.as<int>();
     for (size_t c = 0; c < P.classes.size(); ++c) {
@@ -591,6 +645,8 @@ pr_status finish_stats(pr_workspace *ws, const BatchPlan &P)
     ws->read_stage_times();
     if (c.status & ST_TIMEOUT)
         return PR_ERR_TIMEOUT;
+    if (c.status & ST_BAD_INDEX)
+        return PR_ERR_CUDA;  // a kernel's own bounds check caught an inconsistent index (and skipped it)
     if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
         return PR_ERR_OVERFLOW;
     return PR_OK;
@@ -950,8 +1006,9 @@ pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, 
     // scratch: the MIP pyramid, or the projected filter's table of q (2 floats per pixel)
     PR_TRY(ensure(ws->mip, sizeof(float) * mip_pyramid_floats(v.W, v.H)));
     float *pyr = ws->mip.as<float>();
-    PR_TRY(launch_unfoveate(p.method, v.W, v.H, v.mode, v.fovea[0], v.fovea[1], v.alpha, p.Wd, p.Hd, p.sigma, rgb,
-                            pyr, out, st));
+    PR_TRY(launch_unfoveate(p.method, v.W, v.H, v.mode, v.fovea[0], v.fovea[1], v.alpha,
+                            v.foveation ? v.foveation->lut : nullptr, v.foveation ? v.foveation->n : 0, p.Wd, p.Hd,
+                            p.sigma, rgb, pyr, out, st));
     return PR_OK;
 }
 

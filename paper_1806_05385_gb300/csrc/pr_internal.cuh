@@ -32,7 +32,9 @@ struct ViewDev {
     float R0[9], T0[3], R1[9], T1[3];  // pose0 / pose1 as rotation + translation
     float tan_x, tan_y, z_near;
     float fx, fy;                      // fovea x_f (unit framebuffer coordinates)
-    float alpha, inv_alpha;            // p(d) = D (d/D)^alpha
+    float alpha, inv_alpha;            // p(d) = D (d/D)^alpha (when p_lut is null)
+    const float *p_lut;                // or: p sampled at d_k = k D / p_n (device)
+    int p_n;
     float d0, d1;                      // rolling direction, r(x) = x . d
     float t_lo, t_hi;                  // range of pixel times over the viewport
     float l0[3], l1[3];                // camera-space light direction at t = 0 and t = 1
@@ -96,6 +98,44 @@ __device__ __forceinline__ void vertex_start_end(const ViewDev &v, int k, float3
     E.z = fmaf(v.R1[6], ex, fmaf(v.R1[7], ey, fmaf(v.R1[8], ez, v.T1[2])));
 }
 
+// A foveation function given by samples (Sec. 3.1.1, any monotonic p): p
+// linear between p_k = p(k D / n) (the last segment continued), p^-1 its
+// exact inverse.  Used by every stage when a view has samples.
+struct SampledP {
+    const float *lut;
+    int n;
+    __host__ __device__ float p(float d) const
+    {
+        const float x = d * ((float)n / kSqrt2);
+        int k = (int)floorf(x);
+        k = k < 0 ? 0 : (k > n - 1 ? n - 1 : k);
+        const float t = x - (float)k;
+        return fmaf(t, lut[k + 1] - lut[k], lut[k]);
+    }
+    __host__ __device__ int segment(float r) const  // last k with lut[k] <= r
+    {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (lut[mid] <= r)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        return lo;
+    }
+    __host__ __device__ float pinv(float r) const
+    {
+        const int k = segment(r);
+        return ((float)k + (r - lut[k]) / (lut[k + 1] - lut[k])) * (kSqrt2 / (float)n);
+    }
+    __host__ __device__ float dpinv(float r) const  // slope of p^-1 at r
+    {
+        const int k = segment(r);
+        return (kSqrt2 / (float)n) / (lut[k + 1] - lut[k]);
+    }
+};
+
 // Foveation q (framebuffer -> display) of a point at offset e from the
 // fovea: the offset is scaled by p(|e|)/|e| = (|e|/D)^(alpha-1).
 __device__ __forceinline__ float fov_scale(float r, float alpha)
@@ -113,7 +153,13 @@ __device__ __forceinline__ void pixel_ray(const ViewDev &v, int i, int j, float 
     if (is_foveated(v.mode)) {
         float e0 = u0 - v.fx, e1 = u1 - v.fy;
         float r = sqrtf(fmaf(e0, e0, e1 * e1));
-        float s = fov_scale(r, v.alpha);
+        float s;
+        if (v.p_lut) {  // sampled p: the offset scaled by p(r) / r (the first slope at r = 0)
+            const SampledP sp{v.p_lut, v.p_n};
+            s = r > 0.f ? sp.p(r) / r : sp.lut[1] * ((float)sp.n / kSqrt2);
+        } else {
+            s = fov_scale(r, v.alpha);
+        }
         x0 = fmaf(e0, s, v.fx);
         x1 = fmaf(e1, s, v.fy);
     } else {

@@ -32,7 +32,7 @@ cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *
                              cudaStream_t st);
 cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
                                const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
-                               long long cap_pairs, Counters *cnt, cudaStream_t st);
+                               long long cap_pairs, long long ntiles, Counters *cnt, cudaStream_t st);
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
                         int seg, Counters *cnt, cudaStream_t st);
 size_t scan_block_sums_needed(long long n);
@@ -41,7 +41,7 @@ cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile
                          long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);
 // sorts every item's run of bin entries (nearest first); runs <= kMaxSeg
 cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
-                              int seg, unsigned long long *pairs, cudaStream_t st);
+                              int seg, unsigned long long *pairs, const Counters *cnt, cudaStream_t st);
 
 // stage (c): per-fragment ray casting, FP64 re-test, resolve
 cudaError_t launch_fragment(int S, bool flag, const ViewDev *views, const int4 *items, const unsigned long long *scan,
@@ -69,7 +69,10 @@ cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *b
 // display step: unfoveation of a framebuffer image (pyramid: scratch of
 // mip_pyramid_floats(W, H) floats for the MIP method)
 size_t mip_pyramid_floats(int W, int H);
-cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, int Wd, int Hd,
-                             float sigma, const float *rgb, float *pyramid, float *out, cudaStream_t st);
+cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, const float *p_lut,
+                             int p_n, int Wd, int Hd, float sigma, const float *rgb, float *pyramid, float *out,
+                             cudaStream_t st);
+// device samples of a foveation handle (defined with the handle)
+const float *pr_foveation_samples(const pr_foveation *f, int *n);
 
 }  // namespace pr

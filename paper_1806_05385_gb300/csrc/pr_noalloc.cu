@@ -141,6 +141,9 @@ pr_status view_constants(const pr_view &in, int tile, int bound, float *soa, int
     v.fy = in.fovea[1];
     v.alpha = in.alpha;
     v.inv_alpha = 1.f / in.alpha;
+    if (in.foveation) {
+        v.p_lut = pr_foveation_samples(in.foveation, &v.p_n);
+    }
     v.d0 = in.d[0];
     v.d1 = in.d[1];
     v.t_lo = 0.f;
@@ -274,9 +277,9 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry, hit_tile,
                             cap_pairs, cnt, st));
     NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, cnt, st));
-    NA_TRY(launch_bin_scatter(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, cnt, st));
+    NA_TRY(launch_bin_scatter(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, nt, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
-    NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, st));
+    NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, cnt, st));
     NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, pairs, rec, keys, nullptr,
                            nullptr, cnt, fragment_grid(tile, false), st));
     NA_TRY(launch_resolve(dv, 1, pix_offs, np, keys, st));

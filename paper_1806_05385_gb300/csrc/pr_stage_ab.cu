@@ -122,7 +122,7 @@ __global__ void k_tile_boxes(const ViewDev *__restrict__ views, int nviews, cons
     tile_pixel_box(v, g - v.tile_off, u0, u1, w0, w1);
     float4 b;
     if (is_foveated(v.mode))
-        b = fov_image_box(u0, u1, w0, w1, make_float2(v.fx, v.fy), v.alpha);
+        b = fov_image_box(u0, u1, w0, w1, make_float2(v.fx, v.fy), v.alpha, v.p_lut, v.p_n);
     else
         b = make_float4(u0, u1, w0, w1);
     const float e = kEpsDisp;
@@ -179,8 +179,10 @@ __device__ __forceinline__ float4 support_halfplane(float2 n, const float2 (&q)[
 // and of the radii p^-1 of the nearest and farthest distance.
 template <int N>
 __device__ __forceinline__ float4 fov_sector_preimage(const float2 (&pts)[N], int n, float2 f, float inv_alpha,
-                                                      float eps, bool f_inside, float rlo)
+                                                      float eps, bool f_inside, float rlo, const float *lut = nullptr,
+                                                      int lut_n = 0)
 {
+    const SampledP sp{lut, lut_n};
     float rmax = 0.f;
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -190,11 +192,11 @@ __device__ __forceinline__ float4 fov_sector_preimage(const float2 (&pts)[N], in
         }
     rmax += eps;
     const float kD1 = powf(kSqrt2, 1.f - inv_alpha);
-    const float rho1 = kD1 * powf(rmax, inv_alpha) * (1.f + 1e-5f) + 1e-6f;
+    const float rho1 = (lut ? sp.pinv(rmax) : kD1 * powf(rmax, inv_alpha)) * (1.f + 1e-5f) + 1e-6f;
     const float rmin = f_inside ? 0.f : fmaxf(0.f, rlo - eps);
     if (rmin <= 0.f)
         return sector_box(f, make_float2(1.f, 0.f), make_float2(1.f, 0.f), 0.f, rho1, true);
-    const float rho0 = kD1 * powf(rmin, inv_alpha) * (1.f - 1e-5f);
+    const float rho0 = (lut ? sp.pinv(rmin) : kD1 * powf(rmin, inv_alpha)) * (1.f - 1e-5f);
     // f lies outside the convex hull of the points: their directions from
     // f span less than half a turn, and one sweep finds the two extremes
     float2 a = f2sub(pts[0], f), b = a;
@@ -253,11 +255,19 @@ __device__ __forceinline__ void near_plane_box(const ViewDev &v, const float3 (&
     }
 }
 
-// q^-1 (display -> framebuffer): radial about the fovea with p^-1(d) = D (d/D)^(1/alpha).
-__device__ __forceinline__ float2 fov_inverse(float2 x, float2 f, float inv_alpha)
+// q^-1 (display -> framebuffer): radial about the fovea with p^-1(d) =
+// D (d/D)^(1/alpha), or the inverse of the view's sampled p.
+__device__ __forceinline__ float2 fov_inverse(float2 x, float2 f, float inv_alpha, const float *lut = nullptr,
+                                              int lut_n = 0)
 {
     const float ex = x.x - f.x, ey = x.y - f.y, r = sqrtf(ex * ex + ey * ey);
-    const float s = r > 0.f ? powf(r * (1.f / kSqrt2), inv_alpha - 1.f) : 0.f;
+    float s;
+    if (lut) {
+        const SampledP sp{lut, lut_n};
+        s = r > 0.f ? sp.pinv(r) / r : 0.f;
+    } else {
+        s = r > 0.f ? powf(r * (1.f / kSqrt2), inv_alpha - 1.f) : 0.f;
+    }
     return make_float2(fmaf(ex, s, f.x), fmaf(ey, s, f.y));
 }
 
@@ -332,7 +342,8 @@ __device__ __forceinline__ PaperFov paper_fov_bound(const ViewDev &v, const floa
         const float2 x0 = A[k], x1 = A[k + 1 < m ? k + 1 : 0];
         float2 d = make_float2(x1.x - x0.x, x1.y - x0.y);
         if (v.fov_bound == PR_FOV_RECURSIVE) {
-            const float2 a = fov_inverse(x0, f, v.inv_alpha), b = fov_inverse(x1, f, v.inv_alpha);
+            const float2 a = fov_inverse(x0, f, v.inv_alpha, v.p_lut, v.p_n),
+                         b = fov_inverse(x1, f, v.inv_alpha, v.p_lut, v.p_n);
             const float2 c = make_float2(b.x - a.x, b.y - a.y);
             if (c.x * c.x + c.y * c.y > 1e-20f)
                 d = c;
@@ -347,7 +358,7 @@ __device__ __forceinline__ PaperFov paper_fov_bound(const ViewDev &v, const floa
             const float2 y0 = A[e], y1 = A[e + 1 < m ? e + 1 : 0];
             auto support = [&](float s) {
                 const float2 u = fov_inverse(make_float2(fmaf(s, y1.x - y0.x, y0.x), fmaf(s, y1.y - y0.y, y0.y)), f,
-                                             v.inv_alpha);
+                                             v.inv_alpha, v.p_lut, v.p_n);
                 return fmaf(nrm.x, u.x, nrm.y * u.y);
             };
             int kb = 0;
@@ -589,11 +600,11 @@ __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3
         const bool inside = rlo <= 2.f * eps;
         float4 fb;
         if (use_hull) {
-            fb = fov_sector_preimage(Q, nq, f, v.inv_alpha, 2.f * eps, inside, rlo);
+            fb = fov_sector_preimage(Q, nq, f, v.inv_alpha, 2.f * eps, inside, rlo, v.p_lut, v.p_n);
         } else {
             const float2 corners[4] = {make_float2(xmin, ymin), make_float2(xmax, ymin), make_float2(xmax, ymax),
                                        make_float2(xmin, ymax)};
-            fb = fov_sector_preimage(corners, 4, f, v.inv_alpha, 2.f * eps, inside, rlo);
+            fb = fov_sector_preimage(corners, 4, f, v.inv_alpha, 2.f * eps, inside, rlo, v.p_lut, v.p_n);
         }
         u0 = fb.x;
         u1 = fb.y;
@@ -820,7 +831,7 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
             // past the window (a run of empty triangles): search all offsets
             const long long g = beyond ? owner_of(cand_off, ttot, p) : g0 + k;
             g0 = __shfl_sync(0xffffffffu, g, 31);  // owners ascend with p
-            bool hit = false;
+            bool hit = false, ok_tile = true;
             long long tile = -1;
             unsigned key = 0u;
             if (p < total) {
@@ -835,10 +846,17 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                 const int qy = q / w;
                 const int tx = tx0 + (q - qy * w), ty = ty0 + qy;
                 tile = v.tile_off + (long long)ty * v.tiles_x + tx;
+                if (tx < 0 || ty < 0 || tx >= v.tiles_x || ty >= v.tiles_y) {  // never for a consistent bound
+                    atomicOr(&cnt->status, ST_BAD_INDEX);
+                    tile = v.tile_off;
+                    ok_tile = false;
+                }
                 const float4 bb = rec[g * kRecF4 + 4];
                 const bool fbspace = (tb.z & 0x100) != 0;
                 const int nh = cand_off[g + 1] - cand_off[g] > 1 ? (tb.z & 0xff) : 0;
-                if (!fbspace) {
+                if (!ok_tile) {
+                    hit = false;
+                } else if (!fbspace) {
                     hit = tile_meets(tile_box[tile], bb, hp + g * kMaxHp, nh);
                 } else {
                     // the tile's pixel-centre box in framebuffer coordinates
@@ -884,15 +902,19 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const unsigned long long *_
                                                      const unsigned long long *__restrict__ scan,
                                                      unsigned int *__restrict__ fill,
                                                      unsigned long long *__restrict__ pairs, long long cap_pairs,
-                                                     Counters *cnt)
+                                                     long long ntiles, Counters *cnt)
 {
     const long long n = min((long long)cnt->hits_listed, cap_pairs);
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < n; k0 += stride) {
         const long long k = k0 + lane;
-        const bool ok = k < n;
+        bool ok = k < n;
         const unsigned tile = ok ? hit_tile[k] : 0u;
+        if (ok && (long long)tile >= ntiles) {  // never for a consistent hit list
+            atomicOr(&cnt->status, ST_BAD_INDEX);
+            ok = false;
+        }
         const unsigned want = __ballot_sync(0xffffffffu, ok);
         if (!ok)
             continue;
@@ -936,9 +958,9 @@ cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *
 
 cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
                                const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
-                               long long cap_pairs, Counters *cnt, cudaStream_t st)
+                               long long cap_pairs, long long ntiles, Counters *cnt, cudaStream_t st)
 {
-    k_bin_scatter<<<bin_grid(), 256, 0, st>>>(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, cnt);
+    k_bin_scatter<<<bin_grid(), 256, 0, st>>>(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, ntiles, cnt);
     return cudaGetLastError();
 }
 
@@ -1223,8 +1245,11 @@ template <bool kLong>
 __global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__restrict__ items,
                                                                 const unsigned long long *__restrict__ scan,
                                                                 long long ntiles, long long cap_items,
-                                                                unsigned long long *__restrict__ pairs)
+                                                                unsigned long long *__restrict__ pairs,
+                                                                const Counters *__restrict__ cnt)
 {
+    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS))
+        return;  // an overflowed attempt is rerun; its bins are incomplete
     __shared__ unsigned s_gid[kSortWarps][kSortRegMax];
     __shared__ unsigned long long s_run[kSortWarps][kLong ? kMaxSeg : 1];
     const long long nitems = min((long long)(scan[ntiles] >> 40), cap_items);
@@ -1280,7 +1305,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__re
 }
 
 cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
-                              int seg, unsigned long long *pairs, cudaStream_t st)
+                              int seg, unsigned long long *pairs, const Counters *cnt, cudaStream_t st)
 {
     static int grid = 0;
     if (grid == 0) {
@@ -1290,9 +1315,9 @@ cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan,
         grid = sms * 8;
     }
     if (seg > kSortRegMax)
-        k_sort_items<true><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs);
+        k_sort_items<true><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs, cnt);
     else
-        k_sort_items<false><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs);
+        k_sort_items<false><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs, cnt);
     return cudaGetLastError();
 }
 

@@ -157,6 +157,10 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
     __shared__ float4 s_rec[NW][32 * kStageF4];  // per warp: the records of its current 32 candidates
     __shared__ long long s_item[2];
 
+    // an attempt whose bins overflowed is rerun by the host: entries of the
+    // dropped hits were never written, so nothing here may read the bins
+    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS))
+        return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ci = (warp % WPR) * 8 + (lane & 7);
     const int cj0 = (warp / WPR) * 8 + (lane >> 3), cj1 = cj0 + 4;
@@ -358,7 +362,16 @@ __device__ Ray64 pixel_ray64(const ViewDev &v, int i, int j)
         const double e0 = x0 - f0, e1 = x1 - f1;
         const double r = sqrt(e0 * e0 + e1 * e1);
         if (r > 0.0) {
-            const double s = pow(r / 1.4142135623730950488, (double)v.alpha - 1.0);
+            double s;
+            if (v.p_lut) {  // the sampled p, linear between the samples, in FP64
+                const double D = 1.4142135623730950488, xk = r * (double)v.p_n / D;
+                int k = (int)floor(xk);
+                k = k < 0 ? 0 : (k > v.p_n - 1 ? v.p_n - 1 : k);
+                const double t = xk - (double)k;
+                s = ((1.0 - t) * (double)v.p_lut[k] + t * (double)v.p_lut[k + 1]) / r;
+            } else {
+                s = pow(r / 1.4142135623730950488, (double)v.alpha - 1.0);
+            }
             x0 = f0 + e0 * s;
             x1 = f1 + e1 * s;
         } else {
