@@ -633,7 +633,7 @@ __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3
 // S = camera-space vertex at t = 0, D = its motion over the frame, the box
 // and interval of stage (a).  tbox = (i0 | i1 << 16, j0 | j1 << 16, nhp, depth order
 // key of the nearest depth the triangle reaches).
-__global__ void __launch_bounds__(128) k_bound(const ViewDev *__restrict__ views, int nviews,
+__global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ views, int nviews,
                                                const long long *__restrict__ tri_offs, long long ttot,
                                                float4 *__restrict__ rec, float4 *__restrict__ hp,
                                                int4 *__restrict__ tbox, unsigned long long *__restrict__ cand,

@@ -101,7 +101,7 @@ __device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const
 // Build-time knob of the fragment kernel: the occupancy it is compiled for
 // (resident warps per SM, which caps registers).
 #ifndef PR_FRAG_WARPS
-#define PR_FRAG_WARPS 32
+#define PR_FRAG_WARPS 24
 #endif
 #define PR_FRAG_MINB(nt) (PR_FRAG_WARPS > 0 ? (PR_FRAG_WARPS * 32) / (nt) : 1)
 

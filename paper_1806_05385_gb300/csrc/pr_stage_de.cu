@@ -257,7 +257,7 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 // L2 target, from the colour just computed -- so the frame needs no
 // separate adjoint pass.  Whole warps run (the adjoint's reductions).
 template <bool kAdjoint>
-__global__ void __launch_bounds__(256) k_shade(const ViewDev *__restrict__ views, int nviews,
+__global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ views, int nviews,
                                               const long long *__restrict__ blk_offs, long long nthreads,
                                               const unsigned long long *__restrict__ keys,
                                               const Counters *__restrict__ frame_cnt)
@@ -339,7 +339,7 @@ cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_
 
 // Stage (e) on its own: the adjoint of a shaded frame from its id buffer
 // and an upstream gradient.
-__global__ void __launch_bounds__(256) k_backward(const ViewDev *__restrict__ views, int nviews,
+__global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__ views, int nviews,
                                                  const long long *__restrict__ blk_offs, long long nthreads,
                                                  const Counters *__restrict__ frame_cnt)
 {
