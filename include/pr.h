@@ -300,8 +300,14 @@ pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, 
 /* Captures the same sequence into a CUDA graph (after one eager run that
  * sizes every buffer) and replays it with pr_graph_launch.  The views and
  * their buffers must stay valid and unchanged in shape while the graph
- * lives; their contents may change between launches.  pr_graph_launch
- * returns after the replay's status has been read. */
+ * lives; their contents may change between launches.  The graph keeps its
+ * own copy of the view table (poses, intrinsics, modes, output pointers as
+ * given at capture) and replays that; it shares the workspace's scratch, so
+ * replays and other calls on the same workspace must not overlap on the
+ * GPU.  A later call that regrows the workspace makes the graph stale:
+ * pr_graph_launch then returns PR_ERR_INVALID_ARG without launching, and the
+ * graph must be captured again.  pr_graph_launch returns after the replay's
+ * status has been read. */
 typedef struct pr_graph pr_graph;
 pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n,
                                  const pr_params *params, void *stream, pr_graph **out);
@@ -309,7 +315,7 @@ pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, i
  * adjoint replayed as one graph.  Gradient outputs accumulate on every
  * replay (zero them between replays if a fresh gradient is wanted); a replay
  * whose forward overflows skips the adjoint and pr_graph_launch returns
- * PR_ERR_OVERFLOW (recapture after an eager call has regrown the workspace). */
+ * PR_ERR_OVERFLOW (an eager call then regrows the workspace; capture again). */
 pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, int32_t n,
                                  const pr_params *params, const pr_frame_grad *grads, void *stream,
                                  pr_graph **out);

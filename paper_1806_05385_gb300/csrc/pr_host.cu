@@ -163,6 +163,14 @@ struct pr_workspace {
         ev_ok = true;
         return cudaSuccess;
     }
+    // the device and pinned buffers a captured graph holds pointers into
+    // (a graph has its own view and offset tables, and device outputs only)
+    std::vector<const void *> buffer_set() const
+    {
+        return {rec.p, hp.p, tbox.p, tile_box.p, tile_cnt.p, scan.p, fill.p, sums.p, pairs.p, items.p,
+                keys.p, counters.p, heads.p, hit_entry.p, hit_tile.p, cand.p, cand_off.p, flag_bits.p,
+                flag_list.p, h_cnt.p};
+    }
     // stage times of the last completed frame (events already complete)
     void read_stage_times()
     {
@@ -243,6 +251,8 @@ struct pr_graph {
     cudaGraph_t graph = nullptr;
     pr_workspace *ws = nullptr;
     long long npix = 0;
+    DevBuf views, offs;                 // the graph's own view and offset tables
+    std::vector<const void *> buffers;  // the workspace's buffers at capture
 };
 
 namespace {
@@ -486,8 +496,8 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->tile_cnt, sizeof(unsigned long long) * std::max(P.ntiles, 1ll)));
     PR_TRY(ensure(ws->scan, sizeof(unsigned long long) * (P.ntiles + 1)));
     PR_TRY(ensure(ws->fill, sizeof(unsigned) * std::max(P.ntiles, 1ll)));
-    PR_TRY(ensure(ws->sums,
-                  sizeof(unsigned long long) * std::max(scan_block_sums_needed(P.ntiles), scan_block_sums_needed(P.ttot))));
+    // two scans' look-back states: the candidate-tile scan, then the tile scan
+    PR_TRY(ensure(ws->sums, sizeof(unsigned long long) * (scan_block_sums_needed(P.ttot) + scan_block_sums_needed(P.ntiles))));
     PR_TRY(ensure(ws->cand, sizeof(unsigned long long) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
     PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
@@ -516,9 +526,10 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     return PR_OK;
 }
 
-// Enqueues one frame (no host synchronisation).  shade: also run stage (d)
-// for views with an rgb output.
-pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cudaStream_t st)
+// Writes the frame's view and offset tables into the workspace's pinned
+// host copies (h_views: n views; h_offs: triangle, tile, pixel and 8x4
+// block offsets, n + 1 each).  shade: views with an rgb output get one.
+void fill_tables(pr_workspace *ws, BatchPlan &P, bool shade)
 {
     const int n = (int)P.vd.size();
     char *stage = ws->stage.as<char>();
@@ -547,19 +558,36 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
         ho[2 * (n + 1) + q] = P.pix_off[q];
         ho[3 * (n + 1) + q] = P.blk_off[q];
     }
-    const ViewDev *dv = ws->views.as<ViewDev>();
-    const long long *tri_offs = ws->offs.as<long long>(), *tile_offs = tri_offs + n + 1, *pix_offs = tile_offs + n + 1;
+}
+
+// Enqueues one frame (no host synchronisation).  shade: also run stage (d)
+// for views with an rgb output.  tables: device view and offset tables that
+// already hold what fill_tables wrote (a captured graph's own copies), or
+// null to upload the workspace's tables in the same sequence.
+pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cudaStream_t st,
+                        const ViewDev *tab_views = nullptr, const long long *tab_offs = nullptr)
+{
+    const int n = (int)P.vd.size();
+    char *stage = ws->stage.as<char>();
+    if (!tab_views) {
+        fill_tables(ws, P, shade);
+        PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
+        PR_TRY(cudaMemcpyAsync(ws->offs.p, ws->h_offs.p, sizeof(long long) * 4 * (n + 1), cudaMemcpyHostToDevice, st));
+        tab_views = ws->views.as<ViewDev>();
+        tab_offs = ws->offs.as<long long>();
+    }
+    const ViewDev *dv = tab_views;
+    const long long *tri_offs = tab_offs, *tile_offs = tri_offs + n + 1, *pix_offs = tile_offs + n + 1;
     const long long *blk_offs = pix_offs + n + 1;
     Counters *cnt = ws->counters.as<Counters>();
-    PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
-    PR_TRY(cudaMemcpyAsync(ws->offs.p, ho, sizeof(long long) * 4 * (n + 1), cudaMemcpyHostToDevice, st));
-    PR_TRY(cudaMemsetAsync(ws->counters.p, 0, sizeof(Counters), st));
-    PR_TRY(cudaMemsetAsync(ws->heads.p, 0, sizeof(int) * 8, st));
-    PR_TRY(cudaMemsetAsync(ws->tile_cnt.p, 0, sizeof(unsigned long long) * std::max(P.ntiles, 1ll), st));
-    PR_TRY(cudaMemsetAsync(ws->fill.p, 0, sizeof(unsigned) * std::max(P.ntiles, 1ll), st));
-    PR_TRY(cudaMemsetAsync(ws->keys.p, 0xFF, sizeof(unsigned long long) * std::max(P.npix, 1ll), st));
-    if (P.any_fp64)
-        PR_TRY(cudaMemsetAsync(ws->flag_bits.p, 0, sizeof(unsigned) * ((P.npix + 31) / 32 + 1), st));
+    unsigned long long *state_a = ws->sums.as<unsigned long long>();
+    unsigned long long *state_b = state_a + scan_block_sums_needed(P.ttot);
+    // one launch clears the counters, queue heads, tile counts and cursors,
+    // both scans' tickets and flags, the FP64 flags, and sets the keys to ~0
+    PR_TRY(launch_frame_init(cnt, ws->heads.as<int>(), ws->tile_cnt.as<unsigned long long>(), ws->fill.as<unsigned>(),
+                             P.ntiles, state_a, scan_state_words(P.ttot), state_b, scan_state_words(P.ntiles),
+                             ws->flag_bits.as<unsigned>(), P.any_fp64 ? (P.npix + 31) / 32 + 1 : 0,
+                             ws->keys.as<unsigned long long>(), P.npix, st));
 
     float4 *rec = ws->rec.as<float4>(), *hp = ws->hp.as<float4>(), *tile_box = ws->tile_box.as<float4>();
     int4 *tbox = ws->tbox.as<int4>();
@@ -578,10 +606,10 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     if (P.any_paper_fov)
         PR_TRY(launch_paper_fov(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, st));
     PR_TRY(mark(1));
-    PR_TRY(launch_scan(cand, cand_off, ws->sums.as<unsigned long long>(), P.ttot, 0, cnt, st));
+    PR_TRY(launch_scan(cand, cand_off, state_a, P.ttot, 0, cnt, st, true));
     PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt,
                             ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt, st));
-    PR_TRY(launch_scan(tile_cnt, scan, ws->sums.as<unsigned long long>(), P.ntiles, seg, cnt, st));
+    PR_TRY(launch_scan(tile_cnt, scan, state_b, P.ntiles, seg, cnt, st, true));
     PR_TRY(launch_bin_scatter(ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), scan,
                               ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, P.ntiles, cnt,
                               st));
@@ -1070,10 +1098,32 @@ pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, i
         return PR_ERR_OOM;
     g->ws = ws;
     g->npix = P.npix;
-    PR_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    s = enqueue_batch(ws, P, prm.seg, true, st);
+    g->buffers = ws->buffer_set();
+    // the graph's own copy of the view and offset tables, written once here:
+    // replays upload nothing, and later calls on the workspace cannot change it
+    const int nv = (int)P.vd.size();
+    fill_tables(ws, P, true);
+    cudaError_t e = ensure(g->views, sizeof(ViewDev) * nv);
+    if (e == cudaSuccess)
+        e = ensure(g->offs, sizeof(long long) * 4 * (nv + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->views.p, ws->h_views.p, sizeof(ViewDev) * nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->offs.p, ws->h_offs.p, sizeof(long long) * 4 * (nv + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    s = enqueue_batch(ws, P, prm.seg, true, st, g->views.as<ViewDev>(), g->offs.as<long long>());
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    e = cudaStreamEndCapture(st, &graph);
     if (s != PR_OK || e != cudaSuccess) {
         if (graph)
             cudaGraphDestroy(graph);
@@ -1104,9 +1154,11 @@ pr_status pr_graph_launch(pr_graph *g, void *stream)
     if (!g)
         return PR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    pr_workspace *ws = g->ws;
+    if (ws->buffer_set() != g->buffers)
+        return PR_ERR_INVALID_ARG;  // a later call regrew the workspace: the graph's pointers are stale
     PR_TRY(cudaGraphLaunch(g->exec, st));
     PR_TRY(cudaStreamSynchronize(st));
-    pr_workspace *ws = g->ws;
     const Counters &c = *ws->h_cnt.p;
     ws->stats.tests = c.tests;
     ws->stats.hits = c.hits;

@@ -33,9 +33,16 @@ cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *
 cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
                                const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
                                long long cap_pairs, long long ntiles, Counters *cnt, cudaStream_t st);
+// state_zeroed: the caller cleared the ticket and flags (state[0, 1 + nb))
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
-                        int seg, Counters *cnt, cudaStream_t st);
+                        int seg, Counters *cnt, cudaStream_t st, bool state_zeroed = false);
+cudaError_t launch_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
+                              unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
+                              long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
+                              long long npix, cudaStream_t st);
 size_t scan_block_sums_needed(long long n);
+// words of a scan's state that must start at zero (ticket and flags)
+long long scan_state_words(long long n);
 cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
                          const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
                          long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);

@@ -209,7 +209,7 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     const size_t o_tbox = c.take(sizeof(int4) * Tn), o_cand = c.take(8 * Tn), o_cand_off = c.take(8 * (Tn + 1));
     const size_t o_tile_box = c.take(sizeof(float4) * nt), o_tile_cnt = c.take(8 * nt);
     const size_t o_scan = c.take(8 * (nt + 1)), o_fill = c.take(4 * nt);
-    const size_t o_sums = c.take(8 * std::max(scan_block_sums_needed(nt), scan_block_sums_needed(Tn)));
+    const size_t o_sums = c.take(8 * (scan_block_sums_needed(Tn) + scan_block_sums_needed(nt)));
     const size_t o_keys = c.take(8 * np);
     if (!c.ok)
         return PR_ERR_INVALID_ARG;  // the frame's fixed scratch exceeds the 64 MiB arena
@@ -252,18 +252,18 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     unsigned long long *pairs = (unsigned long long *)(arena + o_tris);
     unsigned long long *hit_entry = (unsigned long long *)(arena + o_hit_e);
     unsigned *hit_tile = (unsigned *)(arena + o_hit_t);
-    unsigned long long *sums = (unsigned long long *)(arena + o_sums), *keys = (unsigned long long *)(arena + o_keys);
+    unsigned long long *keys = (unsigned long long *)(arena + o_keys);
+    // look-back states of the two scans: candidate tiles, then tile counts
+    unsigned long long *state_a = (unsigned long long *)(arena + o_sums), *state_b = state_a + scan_block_sums_needed(Tn);
 
     // host-side constants go up by plain (pageable) copies; they complete
     // before the call returns, so the stack buffers may go out of scope
     NA_TRY(cudaMemcpyAsync(dv, &v, sizeof v, cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(doffs, offs, sizeof offs, cudaMemcpyHostToDevice, st));
-    // what must start at zero (the arena keeps the previous call's contents)
-    NA_TRY(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
-    NA_TRY(cudaMemsetAsync(heads, 0, sizeof(int) * 8, st));
-    NA_TRY(cudaMemsetAsync(tile_cnt, 0, 8 * nt, st));
-    NA_TRY(cudaMemsetAsync(fill, 0, 4 * nt, st));
-    NA_TRY(cudaMemsetAsync(keys, 0xFF, 8 * np, st));
+    // what must start at zero, and the keys at ~0 (the arena keeps the
+    // previous call's contents)
+    NA_TRY(launch_frame_init(cnt, heads, tile_cnt, fill, nt, state_a, scan_state_words(T), state_b,
+                             scan_state_words(nt), nullptr, 0, keys, np, st));
 
     const long long *tri_offs = doffs, *tile_offs = doffs + 2, *pix_offs = doffs + 4;
     NA_TRY(launch_scene_soa(pos, vel, col, V, soa, st));
@@ -273,10 +273,10 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, cnt, st));
     if (fov_bound != PR_FOV_SECTOR && (view->mode == PR_FOVEATED || view->mode == PR_BOTH))
         NA_TRY(launch_paper_fov(dv, 1, tri_offs, T, rec, hp, tbox, cand, st));
-    NA_TRY(launch_scan(cand, cand_off, sums, T, 0, cnt, st));
+    NA_TRY(launch_scan(cand, cand_off, state_a, T, 0, cnt, st, true));
     NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry, hit_tile,
                             cap_pairs, cnt, st));
-    NA_TRY(launch_scan(tile_cnt, scan, sums, nt, seg, cnt, st));
+    NA_TRY(launch_scan(tile_cnt, scan, state_b, nt, seg, cnt, st, true));
     NA_TRY(launch_bin_scatter(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, nt, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
     NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, cnt, st));

@@ -964,6 +964,59 @@ cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsign
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- frame init
+
+// Clears what a frame accumulates into, in one launch: the counters, the
+// work-queue heads, the per-tile counts and fill cursors, the tickets and
+// flags of two scans' look-back state (scan_state_words of each), the FP64
+// flag bitmap (nflag words, may be 0), and sets
+// every pixel's depth|id key to "no hit" (~0).
+__global__ void k_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
+                             unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
+                             long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
+                             long long npix)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (g == 0)
+        *cnt = Counters{};
+    if (g < 8)
+        heads[g] = 0;
+    for (long long k = g; k < ntiles; k += stride) {
+        tile_cnt[k] = 0ull;
+        fill[k] = 0u;
+    }
+    for (long long k = g; k < nstate_a; k += stride)
+        state_a[k] = 0ull;
+    for (long long k = g; k < nstate_b; k += stride)
+        state_b[k] = 0ull;
+    for (long long k = g; k < nflag; k += stride)
+        flag_bits[k] = 0u;
+    // keys: 16-byte stores over the even-length prefix, then the last one
+    ulonglong2 *k2 = reinterpret_cast<ulonglong2 *>(keys);
+    for (long long k = g; k < npix / 2; k += stride)
+        k2[k] = make_ulonglong2(~0ull, ~0ull);
+    if (g == 0 && (npix & 1))
+        keys[npix - 1] = ~0ull;
+}
+
+cudaError_t launch_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
+                              unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
+                              long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
+                              long long npix, cudaStream_t st)
+{
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = sms * 8;
+    }
+    k_frame_init<<<grid, 256, 0, st>>>(cnt, heads, tile_cnt, fill, ntiles, state_a, nstate_a, state_b, nstate_b,
+                                       flag_bits, nflag, keys, npix);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- scan
 
 // Exclusive prefix sum of u64 words in one pass (decoupled look-back,
@@ -1112,6 +1165,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
         out[n] = excl + total;
 }
 
+long long scan_state_words(long long n)
+{
+    return (n + kScanBlock - 1) / kScanBlock + 1;
+}
+
 size_t scan_block_sums_needed(long long n)
 {
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
@@ -1119,16 +1177,18 @@ size_t scan_block_sums_needed(long long n)
 }
 
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
-                        int seg, Counters *cnt, cudaStream_t st)
+                        int seg, Counters *cnt, cudaStream_t st, bool state_zeroed)
 {
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) {
         cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (nb + 1), st);
-    if (e != cudaSuccess)
-        return e;
+    if (!state_zeroed) {
+        cudaError_t e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (nb + 1), st);
+        if (e != cudaSuccess)
+            return e;
+    }
     k_scan<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, seg, state, nb, cnt);
     return cudaGetLastError();
 }

@@ -111,6 +111,66 @@ def test_graph_replay_matches_eager(pr):
             pr.pr_scene_free(h)
 
 
+def test_graph_keeps_its_view_table_and_refuses_when_stale(pr):
+    """A graph replays the views it was captured with, after other calls on
+    the same workspace; a call that regrows the workspace makes it stale."""
+    import torch
+    cases = _views_mixed()[:3]
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+    ws = pr.pr_workspace_create()
+    stream = torch.cuda.Stream()
+    try:
+        with torch.cuda.stream(stream):
+            outs, entries = [], []
+            for h, (sc, v, tile) in zip(handles, cases):
+                n = v.W * v.H
+                o = tuple(torch.empty(n * k, dtype=dt, device="cuda")
+                          for k, dt in ((1, torch.int32), (1, torch.float32), (3, torch.float32)))
+                outs.append(o)
+                entries.append((h, v, o[0], o[1], o[2], tile))
+            graph = pr.pr_graph_capture_batch(ws, entries)
+            ref = [tuple(x.clone() for x in o) for o in outs]
+            # a smaller eager frame of other views on the same workspace
+            sc1, v1, t1 = cases[1]
+            p0, p1 = S.head_poses(-4.0, 2.0)
+            other = S.View(W=v1.W // 2, H=v1.H // 2, tan_x=0.4, tan_y=0.4, pose0=p0, pose1=p1, mode=S.MODE_CLASSIC,
+                           fovea=(0.5, 0.5))
+            n = other.W * other.H
+            oo = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, device="cuda"),
+                  torch.empty(3 * n, device="cuda"))
+            pr.pr_rasterize_batch(ws, [(handles[1], other, oo[0], oo[1], oo[2], t1)])
+            for o in outs:
+                for x in o:
+                    x.fill_(7)
+            pr.pr_graph_launch(graph)
+            for o, r in zip(outs, ref):
+                assert all(torch.equal(a, b) for a, b in zip(o, r))
+            # a much larger frame regrows the scratch: the graph is refused
+            big_sc = S.random_triangles(20000, 77)
+            hb = _upload(pr, big_sc)
+            handles.append(hb)
+            p0, p1 = S.head_poses(2.0, 1.0)
+            bv = S.View(W=1024, H=1024, tan_x=0.6, tan_y=0.6, pose0=p0, pose1=p1, mode=S.MODE_BOTH, fovea=(0.5, 0.5))
+            nb = bv.W * bv.H
+            ob = (torch.empty(nb, dtype=torch.int32, device="cuda"), torch.empty(nb, device="cuda"),
+                  torch.empty(3 * nb, device="cuda"))
+            pr.pr_rasterize_batch(ws, [(hb, bv, ob[0], ob[1], ob[2], 16)])
+            with pytest.raises(pr.PrError) as ei:
+                pr.pr_graph_launch(graph)
+            assert ei.value.status == pr.PR_ERR_INVALID_ARG
+            pr.pr_graph_free(graph)
+            # a fresh capture on the regrown workspace works again
+            graph = pr.pr_graph_capture_batch(ws, entries)
+            pr.pr_graph_launch(graph)
+            for o, r in zip(outs, ref):
+                assert all(torch.equal(a, b) for a, b in zip(o, r))
+            pr.pr_graph_free(graph)
+    finally:
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
 @pytest.mark.parametrize("mode", [S.MODE_ROLLING, S.MODE_BOTH, S.MODE_CLASSIC])
 def test_backward_matches_oracle_gradient(pr, oracle, mode):
     import torch
