@@ -165,8 +165,15 @@ def cpu_oracle_sample(wl: Workload, seconds: float, seed: int = 11):
             tests += pix.size * sc.T
         return time.perf_counter() - t0, tests, per * len(wl.views)
 
-    dt, _, n0 = run(max(64, 4 * len(wl.views)))
-    n = int(max(n0, min(1 << 16, n0 * seconds / max(dt, 1e-3))))
+    # calibrate on growing samples until one takes a tenth of the budget (a
+    # tiny first sample is dominated by per-call setup and overstates the cost)
+    n = max(64, 4 * len(wl.views))
+    while True:
+        dt, _, n = run(n)
+        if dt >= seconds / 10 or n >= 1 << 18:
+            break
+        n = int(min(1 << 18, n * min(8.0, max(2.0, seconds / 10 / max(dt, 1e-3)))))
+    n = int(max(n, min(1 << 18, n * seconds / max(dt, 1e-3))))
     dt, tests, n = run(n)
     return {"pixels": n, "seconds": dt, "tests": tests, "cores": O.num_threads()}
 

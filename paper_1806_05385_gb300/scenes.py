@@ -204,10 +204,11 @@ def random_triangles(T: int, seed: int, vel_sigma: float = 0.05, offset: float |
 def instance_scene(rng, T_target: int, tan_x: float, tan_y: float, kinds=("ico3",),
                    radius=(0.2, 1.5), log_size=False, z_range=(1.0, 30.0), move_frac=1.0,
                    vmax=0.3, ground: int = 0) -> Scene:
-    """Objects (icospheres/boxes) placed uniformly in the view frustum at
-    depth U[z_range], each with one linear velocity (uniform direction,
-    |v| ~ U[0, vmax]); instances are added until ``T_target`` triangles are
-    reached (the last one truncated).  ``ground`` > 0 adds a ground plane of
+    """Objects (icospheres/boxes) placed uniformly in the view frustum with
+    centre depth U[z_range[0] + bounding radius, z_range[1]] (so every
+    object lies entirely beyond z_range[0]), each with one linear velocity
+    (uniform direction, |v| ~ U[0, vmax]); instances are added until
+    ``T_target`` triangles are reached (the last one truncated).  ``ground`` > 0 adds a ground plane of
     that many triangles at y = +1.6 (y points down)."""
     meshes = {"ico3": icosphere(3), "ico2": icosphere(2), "box": unit_box()}
     parts = []
@@ -219,7 +220,10 @@ def instance_scene(rng, T_target: int, tan_x: float, tan_y: float, kinds=("ico3"
             r = math.exp(rng.uniform(math.log(radius[0]), math.log(radius[1])))
         else:
             r = rng.uniform(*radius)
-        z = rng.uniform(*z_range)
+        # the nearest point of the object stays at depth >= z_range[0]: no
+        # object encloses the eye or reaches through the near plane
+        rb = r * float(np.linalg.norm(v0, axis=1).max())
+        z = rng.uniform(z_range[0] + rb, max(z_range[1], z_range[0] + rb))
         cx = rng.uniform(-z * tan_x, z * tan_x)
         cy = rng.uniform(-z * tan_y, z * tan_y)
         p = v0 * r + np.array([cx, cy, z])
@@ -259,7 +263,8 @@ def hmd_fov(W: int, H: int, hfov_deg: float = 100.0):
 
 def config_hmd(seed: int = 2, W: int = 1440, H: int = 1600, n_objects: int = 200):
     """Stereo foveated+rolling frame: 1440x1600 per eye, 100 degree horizontal
-    FOV, 200 icospheres (subdivision 3, radius U[0.2,1.5], depth U[1,30]) plus
+    FOV, 200 icospheres (subdivision 3, radius r ~ U[0.2,1.5], centre depth
+    U[1 + r, 30]) plus
     a 10,000-triangle ground plane, per-object velocity |v| <= 0.3 per frame,
     head yaw 0->3 and pitch 0->1 degrees, IPD 0.064, fovea U[0.2,0.8]^2 per
     eye, power foveation alpha = 2."""
