@@ -300,9 +300,11 @@ def our_arm(args, rank, world):
         B.pr_backward_batch(ws_b, bwd_entries)
 
     def step():
-        B.pr_graph_launch(graph)
+        B.pr_graph_enqueue(graph)
 
-    def timed(fn, k, flush_l2=True):
+    def timed(fn, k, flush_l2=True, check=None):
+        """Per call, device time between events recorded before and after
+        fn's work on the stream; check() then reads the call's status."""
         ms = []
         for _ in range(k):
             if flush_l2:
@@ -312,18 +314,20 @@ def our_arm(args, rank, world):
             fn()
             e1.record(stream)
             e1.synchronize()
+            if check:
+                check()
             ms.append(e0.elapsed_time(e1))
         return ms
 
     for _ in range(max(3, args.warmup)):
-        step()
+        B.pr_graph_launch(graph)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    step_ms = timed(step, args.steps)
+    step_ms = timed(step, args.steps, check=lambda: B.pr_graph_status(graph))
     clocks = clk.stop()
     torch.cuda.synchronize()
     if dist:
@@ -332,7 +336,7 @@ def our_arm(args, rank, world):
     frag_ms = st["stage_ms"][2]
 
     # forward only: batched graph vs plain per-view calls
-    fwd_batched = timed(lambda: B.pr_graph_launch(graph_fwd), args.steps)
+    fwd_batched = timed(lambda: B.pr_graph_enqueue(graph_fwd), args.steps, check=lambda: B.pr_graph_status(graph_fwd))
 
     def plain():
         for k, v in enumerate(views):

@@ -248,7 +248,8 @@ pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32
  * L = sum (rgb - target)^2 (then dL/drgb = 2 (rgb - target) is formed from
  * the frame's own shaded image inside the adjoint kernel); dcol, dpos, dvel
  * [V][3] of the view's scene are ACCUMULATED (+=), any may be NULL.  All
- * DEVICE pointers.  Both NULL: no adjoint for this view. */
+ * DEVICE pointers; grad_rgb and target_rgb must not overlap the view's
+ * outputs.  Both NULL: no adjoint for this view. */
 typedef struct {
     const float *grad_rgb;
     const float *target_rgb;
@@ -320,6 +321,15 @@ pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, i
                                  const pr_params *params, const pr_frame_grad *grads, void *stream,
                                  pr_graph **out);
 pr_status pr_graph_launch(pr_graph *g, void *stream);
+/* The two halves of pr_graph_launch, for a frame loop that does not wait on
+ * the host after every frame: pr_graph_enqueue launches one replay on
+ * stream and returns at once (PR_ERR_INVALID_ARG, nothing launched, for a
+ * stale graph); pr_graph_status returns the status of the last replay and
+ * fills the workspace statistics, and may be called only once the stream
+ * has passed that replay (after a synchronisation the caller makes).
+ * Replays of graphs that share a workspace must not overlap on the GPU. */
+pr_status pr_graph_enqueue(pr_graph *g, void *stream);
+pr_status pr_graph_status(pr_graph *g);
 void pr_graph_free(pr_graph *g);
 
 /* pr_rasterize without allocating: stages (a)-(c) of one view, with every

@@ -31,7 +31,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
            "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
-           "pr_foveation_free")
+           "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status")
 
 
 class PrError(RuntimeError):
@@ -115,6 +115,8 @@ def load(build_if_missing: bool = True):
             "pr_rasterize_batch": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), P], I32),
             "pr_graph_capture_batch": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), P, C.POINTER(P)], I32),
             "pr_graph_launch": ([P, P], I32),
+            "pr_graph_enqueue": ([P, P], I32),
+            "pr_graph_status": ([P], I32),
             "pr_graph_free": ([P], None),
             "pr_scene_stats": ([P, C.POINTER(PrStats)], I32),
             "pr_workspace_stats": ([P, C.POINTER(PrStats)], I32),
@@ -380,6 +382,17 @@ def pr_unfoveate(ws, view, rgb, out, Wd: int, Hd: int, method: str = "mip", sigm
 def pr_graph_launch(graph, stream=None):
     _check(load().pr_graph_launch(C.c_void_p(graph), stream if stream is not None else current_stream()),
            "pr_graph_launch")
+
+
+def pr_graph_enqueue(graph, stream=None):
+    """Launch one replay without waiting; read its status with pr_graph_status
+    once the stream has passed it."""
+    _check(load().pr_graph_enqueue(C.c_void_p(graph), stream if stream is not None else current_stream()),
+           "pr_graph_enqueue")
+
+
+def pr_graph_status(graph):
+    _check(load().pr_graph_status(C.c_void_p(graph)), "pr_graph_status")
 
 
 def pr_graph_free(graph):

@@ -1149,16 +1149,30 @@ pr_status pr_graph_capture_batch(pr_workspace *ws, const pr_batch_view *views, i
     return pr_graph_capture_frame(ws, views, n, params, nullptr, stream, out);
 }
 
-pr_status pr_graph_launch(pr_graph *g, void *stream)
+pr_status pr_graph_enqueue(pr_graph *g, void *stream)
 {
     if (!g)
         return PR_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    pr_workspace *ws = g->ws;
-    if (ws->buffer_set() != g->buffers)
+    if (g->ws->buffer_set() != g->buffers)
         return PR_ERR_INVALID_ARG;  // a later call regrew the workspace: the graph's pointers are stale
-    PR_TRY(cudaGraphLaunch(g->exec, st));
-    PR_TRY(cudaStreamSynchronize(st));
+    PR_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return PR_OK;
+}
+
+pr_status pr_graph_launch(pr_graph *g, void *stream)
+{
+    pr_status s = pr_graph_enqueue(g, stream);
+    if (s != PR_OK)
+        return s;
+    PR_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return pr_graph_status(g);
+}
+
+pr_status pr_graph_status(pr_graph *g)
+{
+    if (!g)
+        return PR_ERR_INVALID_ARG;
+    pr_workspace *ws = g->ws;
     const Counters &c = *ws->h_cnt.p;
     ws->stats.tests = c.tests;
     ws->stats.hits = c.hits;

@@ -13,6 +13,13 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b)
 {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
+// The same cross product with every rounding fixed (no contraction left to
+// the compiler), so that every kernel that shades a pixel gets the same bits.
+__device__ __forceinline__ float3 cross3_rn(float3 a, float3 b)
+{
+    return make_float3(fmaf(a.y, b.z, -__fmul_rn(a.z, b.y)), fmaf(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                       fmaf(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
 __device__ __forceinline__ float3 scale3(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 
@@ -25,7 +32,7 @@ struct PixelHit {
     float b0, b1, b2;   // barycentrics of the ray point
     float det;          // U + V + W of the watertight test
     float3 n;           // unit normal facing the viewer
-    float nlen, flip;   // |(B-A) x (C-A)| and the sign applied
+    float inl;          // flip / |(B-A) x (C-A)| with flip = +-1 the sign applied (0 if degenerate)
     float3 l;           // unit light direction at t
     float ndl, sigma;   // n.l and k_a + k_d max(0, n.l)
     float3 hv;          // Blinn-Phong half vector normalize(l + v), v = the reversed ray
@@ -70,18 +77,17 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     h.b0 = U * inv;
     h.b1 = V * inv;
     h.b2 = W * inv;
-    float3 n = cross3(sub3(h.B, h.A), sub3(h.C, h.A));
-    h.flip = dot3(n, h.dir) > 0.f ? -1.f : 1.f;
+    float3 n = cross3_rn(sub3(h.B, h.A), sub3(h.C, h.A));
+    const float flip = dot3(n, h.dir) > 0.f ? -1.f : 1.f;
     const float nn = dot3(n, n);
     const float rs = nn > 0.f ? rsqrtf(nn) : 0.f;
-    h.nlen = nn * rs;
-    const float in = h.flip * rs;
-    h.n = scale3(n, in);
+    h.inl = flip * rs;
+    h.n = scale3(n, h.inl);
     float3 l = make_float3(fmaf(t, v.l1[0] - v.l0[0], v.l0[0]), fmaf(t, v.l1[1] - v.l0[1], v.l0[1]),
                            fmaf(t, v.l1[2] - v.l0[2], v.l0[2]));
     h.l = scale3(l, rsqrtf(dot3(l, l)));
     h.ndl = dot3(h.n, h.l);
-    h.sigma = v.k_a + v.k_d * fmaxf(h.ndl, 0.f);
+    h.sigma = fmaf(v.k_d, fmaxf(h.ndl, 0.f), v.k_a);
     h.spec = 0.f;
     h.ndh = 0.f;
     if (v.k_s > 0.f) {
@@ -94,18 +100,22 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     }
 }
 
-// Stages (d) and (e) run one warp per 8x4 pixel block (lane -> column
-// lane % 8, row lane / 8), so the lanes of a warp mostly see the same
-// triangles: gathers of vertex data coalesce and the adjoint can sum a
-// triangle's contributions over the warp before touching memory.
-// blk_offs[q] = first 8x4 block of view q in the batch.
-__device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, const long long *blk_offs, long long g,
-                                            const ViewDev *&vp, long long &lin, int &i, int &j)
+// Stages (d) and (e) run each warp over kShadeBlocks consecutive 8x4 pixel
+// blocks (lane -> column lane % 8, row lane / 8 of each), so the lanes of a
+// warp mostly see the same triangles: gathers of vertex data coalesce, and
+// the adjoint sums a triangle's contributions over a lane's pixels and then
+// over the warp before touching memory.  blk_offs[q] = first 8x4 block of
+// view q in the batch.  One block per warp measured fastest on the stereo
+// HMD frame (0.170 ms against 0.229 ms for two and 0.242 ms for four): the
+// running sums held across pixels push the kernel into register spills
+// that cost more than the warp reductions they save.
+constexpr int kShadeBlocks = 1;
+
+__device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, const long long *blk_offs, long long b,
+                                            int lane, int &q, long long &lin, int &i, int &j)
 {
-    const long long b = g >> 5;
-    const int lane = (int)(g & 31);
-    const ViewDev &v = views[find_view(blk_offs, nviews, b)];
-    vp = &v;
+    q = find_view(blk_offs, nviews, b);
+    const ViewDev &v = views[q];
     const int lb = (int)(b - v.blk_off);  // < 2^23 blocks per view: 32-bit division
     const int bw = (v.W + 7) >> 3;
     const int by = lb / bw;
@@ -113,6 +123,73 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
     j = by * 4 + (lane >> 3);
     lin = (long long)j * v.W + i;
     return i < v.W && j < v.H;
+}
+
+// Vertex colours of the visible triangle and the interpolated albedo
+// a = sum_k b_k col_k of the pixel (shared by the shading and the adjoint).
+struct PixelAlbedo {
+    float col[3][3];  // [vertex][channel]
+    float a[3];
+};
+
+__device__ __forceinline__ void pixel_albedo(const ViewDev &v, const PixelHit &h, PixelAlbedo &pa)
+{
+    const int vid[3] = {h.ia, h.ib, h.ic};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pa.col[k][0] = v.cr[vid[k]];
+        pa.col[k][1] = v.cg[vid[k]];
+        pa.col[k][2] = v.cb[vid[k]];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        pa.a[c] = fmaf(h.b0, pa.col[0][c], fmaf(h.b1, pa.col[1][c], h.b2 * pa.col[2][c]));
+}
+
+// Sums value l of every lane of `mask` over the warp and adds it to
+// gradient l of the warp's triangle with vertices (v0, v1, v2): value 9k + c
+// is d/dcol_k[c], 9k + 3 + c the sum of (1 - t) dL/dc_k[c] and 9k + 6 + c
+// the sum of t dL/dc_k[c], with c_k the moved camera-space vertex k.  The
+// position and velocity gradients follow once per triangle from the last
+// two: dc/dp = (1-t) R0 + t R1 and dc/dv = t R1, so dL/dp = R0^T sum (1-t)
+// dL/dc + R1^T sum t dL/dc and dL/dv = R1^T sum t dL/dc.  Lanes outside the
+// group pass zeros.  Reduce-scatter: at each of five steps a lane keeps the
+// half of its values selected by its lane bit and adds its partner's copy
+// of that half, so lane l ends with the warp sum of value l (31 shuffles
+// instead of 27 full butterflies).
+__device__ __forceinline__ void reduce_add_triangle(const ViewDev &v, float (&s)[32], int v0, int v1, int v2)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int half = 16 >> step;
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const float send = upper ? s[k] : s[k + half];
+            const float keep = upper ? s[k + half] : s[k];
+            s[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    const int k = min(lane / 9, 2), r = lane - 9 * k;
+    const int base = 9 * k;
+    const float o0 = __shfl_sync(0xffffffffu, s[0], base + 3), o1 = __shfl_sync(0xffffffffu, s[0], base + 4),
+                o2 = __shfl_sync(0xffffffffu, s[0], base + 5);
+    const float t0 = __shfl_sync(0xffffffffu, s[0], base + 6), t1 = __shfl_sync(0xffffffffu, s[0], base + 7),
+                t2 = __shfl_sync(0xffffffffu, s[0], base + 8);
+    if (lane < 27) {
+        const int c = r < 3 ? r : (r < 6 ? r - 3 : r - 6);
+        const int vk = k == 0 ? v0 : (k == 1 ? v1 : v2);
+        float val = s[0];
+        if (r >= 3) {
+            val = fmaf(v.R1[c], t0, fmaf(v.R1[3 + c], t1, v.R1[6 + c] * t2));
+            if (r < 6)
+                val = fmaf(v.R0[c], o0, fmaf(v.R0[3 + c], o1, fmaf(v.R0[6 + c], o2, val)));
+        }
+        float *dst = r < 3 ? v.dcol : (r < 6 ? v.dpos : v.dvel);
+        if (dst)
+            atomicAdd(&dst[3 * vk + c], val);
+    }
 }
 
 // Adjoint of rgb = a sigma + s, a = sum_k b_k col_k, sigma = k_a + k_d max(0, n.l),
@@ -124,124 +201,141 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
 //    d sum/dw_j = (gb_j - sum_k gb_k b_k) / sum w and dw_j/dA etc. are
 //    cross products with dir;
 //  - the unit normal n = flip (B-A)x(C-A) / |.|: dn gets (I - n n^T)/|.|;
-//  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1:
-//    dc/dp = (1-t) R0 + t R1, dc/dv = t R1.
-// Per warp, the 27 contributions of each distinct triangle are summed over
-// the lanes that see it with a reduce-scatter (lane l ends with the sum of
-// value l) and added with one 27-lane atomic instruction.  Called by every
-// lane of a warp; valid = this lane has a pixel with a visible triangle.
-__device__ __forceinline__ void adjoint_pixel(const ViewDev &v, const PixelHit &h, bool valid, unsigned id, float g0,
-                                              float g1, float g2)
+//  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1
+//    (applied per triangle after the warp sum, reduce_add_triangle).
+// The pixel's 27 values (layout of reduce_add_triangle) are ADDED to acc.
+__device__ __forceinline__ void adjoint_add(const ViewDev &v, const PixelHit &h, const PixelAlbedo &pa, float g0,
+                                            float g1, float g2, float (&acc)[27])
 {
-    float gc[3][3], gp[3][3], gvel[3][3];
-    int vid[3] = {0, 0, 0};
-    for (int k = 0; k < 3; ++k)
-        for (int c = 0; c < 3; ++c)
-            gc[k][c] = gp[k][c] = gvel[k][c] = 0.f;
-    if (valid) {
-        vid[0] = h.ia;
-        vid[1] = h.ib;
-        vid[2] = h.ic;
+    {
         const float b[3] = {h.b0, h.b1, h.b2};
-        float col[3][3];
-        for (int k = 0; k < 3; ++k) {
-            col[k][0] = v.cr[vid[k]];
-            col[k][1] = v.cg[vid[k]];
-            col[k][2] = v.cb[vid[k]];
-        }
-        float a[3];
-        for (int c = 0; c < 3; ++c)
-            a[c] = b[0] * col[0][c] + b[1] * col[1][c] + b[2] * col[2][c];
+        const float gs[3] = {g0 * h.sigma, g1 * h.sigma, g2 * h.sigma};
         float gb[3];
-        const float gv[3] = {g0, g1, g2};
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            gb[k] = 0.f;
-            for (int c = 0; c < 3; ++c) {
-                gc[k][c] = gv[c] * b[k] * h.sigma;
-                gb[k] += gv[c] * col[k][c];
-            }
-            gb[k] *= h.sigma;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                acc[9 * k + c] = fmaf(gs[c], b[k], acc[9 * k + c]);
+            gb[k] = fmaf(gs[0], pa.col[k][0], fmaf(gs[1], pa.col[k][1], gs[2] * pa.col[k][2]));
         }
-        const float gsig = g0 * a[0] + g1 * a[1] + g2 * a[2];
-        // barycentrics -> moved vertices
+        const float gsig = fmaf(g0, pa.a[0], fmaf(g1, pa.a[1], g2 * pa.a[2]));
+        // barycentrics -> moved vertices: with w_0 = D.(B x C) etc.,
+        // dL/dA = gw1 (D x C) + gw2 (B x D) = D x (gw1 C - gw2 B), cyclically
         const float sw = -h.det;
-        const float gdotb = gb[0] * b[0] + gb[1] * b[1] + gb[2] * b[2];
+        const float gdotb = fmaf(gb[0], b[0], fmaf(gb[1], b[1], gb[2] * b[2]));
         const float isw = sw != 0.f ? 1.f / sw : 0.f;
         const float gw0 = (gb[0] - gdotb) * isw, gw1 = (gb[1] - gdotb) * isw, gw2 = (gb[2] - gdotb) * isw;
         const float3 D = h.dir;
-        float3 gA = add3(scale3(cross3(D, h.C), gw1), scale3(cross3(h.B, D), gw2));
-        float3 gB = add3(scale3(cross3(h.C, D), gw0), scale3(cross3(D, h.A), gw2));
-        float3 gC = add3(scale3(cross3(D, h.B), gw0), scale3(cross3(h.A, D), gw1));
+        float3 gA = cross3(D, sub3(scale3(h.C, gw1), scale3(h.B, gw2)));
+        float3 gB = cross3(D, sub3(scale3(h.A, gw2), scale3(h.C, gw0)));
+        float3 gC = cross3(D, sub3(scale3(h.B, gw0), scale3(h.A, gw1)));
         // normal -> moved vertices: the diffuse term through n.l, the
-        // specular term k_s (n.h)^m (white) through n.h
+        // specular term k_s (n.h)^m (white) through n.h; the three
+        // contributions (B-C) x gn, (C-A) x gn, (A-B) x gn sum to zero
         const bool dif = h.ndl > 0.f, spc = h.spec > 0.f;
-        if ((dif || spc) && h.nlen > 0.f) {
+        if ((dif || spc) && h.inl != 0.f) {
             float3 gnh = scale3(h.l, dif ? gsig * v.k_d : 0.f);
             if (spc)
                 gnh = add3(gnh, scale3(h.hv, (g0 + g1 + g2) * v.shininess * h.spec / h.ndh));
             const float pr = dot3(h.n, gnh);
-            const float3 gnn = scale3(sub3(gnh, scale3(h.n, pr)), h.flip / h.nlen);
-            gA = add3(gA, cross3(sub3(h.B, h.C), gnn));
-            gB = add3(gB, cross3(sub3(h.C, h.A), gnn));
-            gC = add3(gC, cross3(sub3(h.A, h.B), gnn));
+            const float3 gnn = scale3(sub3(gnh, scale3(h.n, pr)), h.inl);
+            const float3 na = cross3(sub3(h.B, h.C), gnn), nb = cross3(sub3(h.C, h.A), gnn);
+            gA = add3(gA, na);
+            gB = add3(gB, nb);
+            gC = sub3(gC, add3(na, nb));
         }
-        // moved vertices -> positions and velocities
+        // the moved vertices' gradients, split by the weights (1 - t) of S
+        // and t of E
         const float3 gk[3] = {gA, gB, gC};
         const float t = h.t, omt = 1.f - t;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            for (int c = 0; c < 3; ++c) {
-                const float e1 = v.R1[c] * gk[k].x + v.R1[3 + c] * gk[k].y + v.R1[6 + c] * gk[k].z;
-                gp[k][c] = omt * (v.R0[c] * gk[k].x + v.R0[3 + c] * gk[k].y + v.R0[6 + c] * gk[k].z) + t * e1;
-                gvel[k][c] = t * e1;
+            acc[9 * k + 3] = fmaf(omt, gk[k].x, acc[9 * k + 3]);
+            acc[9 * k + 4] = fmaf(omt, gk[k].y, acc[9 * k + 4]);
+            acc[9 * k + 5] = fmaf(omt, gk[k].z, acc[9 * k + 5]);
+            acc[9 * k + 6] = fmaf(t, gk[k].x, acc[9 * k + 6]);
+            acc[9 * k + 7] = fmaf(t, gk[k].y, acc[9 * k + 7]);
+            acc[9 * k + 8] = fmaf(t, gk[k].z, acc[9 * k + 8]);
+        }
+    }
+}
+
+// A lane's running sums of the adjoint values of the pixels it has seen
+// since the last flush, all of one triangle of one view.
+struct AdjointSum {
+    float s[27];
+    int q;  // view of the triangle (-1: nothing summed)
+    unsigned id;
+    int ia, ib, ic;
+};
+
+__device__ __forceinline__ void adjoint_reset(AdjointSum &a)
+{
+#pragma unroll
+    for (int e = 0; e < 27; ++e)
+        a.s[e] = 0.f;
+    a.q = -1;
+}
+
+// Sums the lanes' running sums over the warp per distinct (view, triangle),
+// adds them to the gradients and resets them.  Called by every lane.
+__device__ __forceinline__ void adjoint_flush(const ViewDev *views, AdjointSum &a)
+{
+    unsigned rem = __ballot_sync(0xffffffffu, a.q >= 0);
+    if (rem) {
+        int leader = __ffs(rem) - 1;
+        int tq = __shfl_sync(0xffffffffu, a.q, leader);
+        unsigned tid = __shfl_sync(0xffffffffu, a.id, leader);
+        float s[32];
+        if (__all_sync(0xffffffffu, a.q < 0 || (a.q == tq && a.id == tid))) {
+            // one triangle over the warp (the common case): lanes without
+            // a sum hold zeros already
+#pragma unroll
+            for (int e = 0; e < 27; ++e)
+                s[e] = a.s[e];
+#pragma unroll
+            for (int e = 27; e < 32; ++e)
+                s[e] = 0.f;
+            reduce_add_triangle(views[tq], s, __shfl_sync(0xffffffffu, a.ia, leader),
+                                __shfl_sync(0xffffffffu, a.ib, leader), __shfl_sync(0xffffffffu, a.ic, leader));
+        } else {
+            while (true) {
+                const bool mine = a.q == tq && a.id == tid;
+                rem &= ~__ballot_sync(0xffffffffu, mine);
+#pragma unroll
+                for (int e = 0; e < 27; ++e)
+                    s[e] = mine ? a.s[e] : 0.f;
+#pragma unroll
+                for (int e = 27; e < 32; ++e)
+                    s[e] = 0.f;
+                reduce_add_triangle(views[tq], s, __shfl_sync(0xffffffffu, a.ia, leader),
+                                    __shfl_sync(0xffffffffu, a.ib, leader), __shfl_sync(0xffffffffu, a.ic, leader));
+                if (!rem)
+                    break;
+                leader = __ffs(rem) - 1;
+                tq = __shfl_sync(0xffffffffu, a.q, leader);
+                tid = __shfl_sync(0xffffffffu, a.id, leader);
             }
         }
     }
-    const int lane = threadIdx.x & 31;
-    unsigned rem = __ballot_sync(0xffffffffu, valid);
-    while (rem) {
-        const int leader = __ffs(rem) - 1;
-        const unsigned tid = __shfl_sync(0xffffffffu, id, leader);
-        const bool mine = valid && id == tid;
-        rem &= ~__ballot_sync(0xffffffffu, mine);
-        // the 27 contributions of this triangle (value 9k + c: colour,
-        // 9k + 3 + c: position, 9k + 6 + c: velocity of vertex k), zero for
-        // lanes that see another triangle, padded to 32
-        float s[32];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                s[9 * k + c] = mine ? gc[k][c] : 0.f;
-                s[9 * k + 3 + c] = mine ? gp[k][c] : 0.f;
-                s[9 * k + 6 + c] = mine ? gvel[k][c] : 0.f;
-            }
-#pragma unroll
-        for (int e = 27; e < 32; ++e)
-            s[e] = 0.f;
-        // reduce-scatter over the warp: at each step a lane keeps the half
-        // of its values selected by its lane bit and adds its partner's
-        // copy of that half; after five steps lane l holds the warp sum of
-        // value l (31 shuffles instead of 27 full butterflies)
-#pragma unroll
-        for (int step = 0; step < 5; ++step) {
-            const int half = 16 >> step;
-            const bool upper = (lane & half) != 0;
-#pragma unroll
-            for (int k = 0; k < half; ++k) {
-                const float send = upper ? s[k] : s[k + half];
-                const float keep = upper ? s[k + half] : s[k];
-                s[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-            }
-        }
-        const int k = lane / 9, r = lane - 9 * (lane / 9);
-        const int v0 = __shfl_sync(0xffffffffu, vid[0], leader), v1 = __shfl_sync(0xffffffffu, vid[1], leader),
-                  v2 = __shfl_sync(0xffffffffu, vid[2], leader);
-        if (lane < 27) {
-            const int vk = k == 0 ? v0 : (k == 1 ? v1 : v2);
-            float *dst = r < 3 ? v.dcol : (r < 6 ? v.dpos : v.dvel);
-            if (dst)
-                atomicAdd(&dst[3 * vk + (r % 3)], s[0]);
-        }
+    adjoint_reset(a);
+}
+
+// Adds a valid lane's pixel (triangle id of view q) to its running sum;
+// first, if any lane's sum is of another triangle or view, the warp
+// flushes.  Called by every lane.
+__device__ __forceinline__ void adjoint_step(const ViewDev *views, AdjointSum &a, bool valid, int q, unsigned id,
+                                             const PixelHit &h, const PixelAlbedo &pa, float g0, float g1, float g2)
+{
+    if (__any_sync(0xffffffffu, valid && a.q >= 0 && (a.q != q || a.id != id)))
+        adjoint_flush(views, a);
+    if (valid) {
+        adjoint_add(views[q], h, pa, g0, g1, g2, a.s);
+        a.q = q;
+        a.id = id;
+        a.ia = h.ia;
+        a.ib = h.ib;
+        a.ic = h.ic;
     }
 }
 
@@ -258,81 +352,97 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 // separate adjoint pass.  Whole warps run (the adjoint's reductions).
 template <bool kAdjoint>
 __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ views, int nviews,
-                                              const long long *__restrict__ blk_offs, long long nthreads,
+                                              const long long *__restrict__ blk_offs, long long nblocks,
                                               const unsigned long long *__restrict__ keys,
                                               const Counters *__restrict__ frame_cnt)
 {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((g & ~31ll) >= nthreads)
-        return;
-    const ViewDev *vp = views;
-    long long lin = 0;
-    int pi = 0, pj = 0;
-    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj);
-    const ViewDev &v = *vp;
-    unsigned id = 0xFFFFFFFFu;
-    if (inside) {
-        if (keys) {
-            const unsigned long long key = keys[v.pix_off + lin];
-            const bool bg = key == ~0ull;
-            id = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
-            if (v.id_out)
-                v.id_out[lin] = id;
-            if (v.depth_out)
-                v.depth_out[lin] = bg ? INFINITY : __uint_as_float((unsigned)(key >> 32));
-        } else {
-            id = v.id_in[lin];
+    const long long b0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kShadeBlocks;
+    if (b0 >= nblocks)
+        return;  // whole warps
+    const int lane = threadIdx.x & 31;
+    // a training frame whose forward overflowed is rerun by the host: its
+    // adjoint must not accumulate
+    const bool adjoint = kAdjoint && !frame_overflowed(frame_cnt);
+    AdjointSum acc;
+    adjoint_reset(acc);
+    for (int p = 0; p < kShadeBlocks && b0 + p < nblocks; ++p) {
+        int q, pi, pj;
+        long long lin;
+        const bool inside = block_pixel(views, nviews, blk_offs, b0 + p, lane, q, lin, pi, pj);
+        const ViewDev &v = views[q];
+        const long long plane = (long long)v.W * v.H;
+        const bool grad = adjoint && (v.grad_in || v.target);
+        // the upstream gradient (or L2 target) does not depend on the hit:
+        // its loads go out first, before the key and the stores below
+        float gin[3] = {0.f, 0.f, 0.f};
+        if (grad && inside) {
+            const float *gsrc = v.grad_in ? v.grad_in : v.target;
+            gin[0] = gsrc[lin];
+            gin[1] = gsrc[plane + lin];
+            gin[2] = gsrc[2 * plane + lin];
         }
-    }
-    // a view with neither an image nor a gradient only needs the resolve
-    const bool hit = inside && id < (unsigned)v.T && (v.rgb_out || (kAdjoint && (v.grad_in || v.target)));
-    const long long plane = (long long)v.W * v.H;
-    PixelHit h;
-    float rgb[3] = {0.f, 0.f, 0.f};
-    if (hit) {
-        pixel_hit(v, pi, pj, id, h);
-        const float r = fmaf(h.b0, v.cr[h.ia], fmaf(h.b1, v.cr[h.ib], h.b2 * v.cr[h.ic]));
-        const float gg = fmaf(h.b0, v.cg[h.ia], fmaf(h.b1, v.cg[h.ib], h.b2 * v.cg[h.ic]));
-        const float b = fmaf(h.b0, v.cb[h.ia], fmaf(h.b1, v.cb[h.ib], h.b2 * v.cb[h.ic]));
-        rgb[0] = fmaf(r, h.sigma, h.spec);
-        rgb[1] = fmaf(gg, h.sigma, h.spec);
-        rgb[2] = fmaf(b, h.sigma, h.spec);
-    }
-    if (inside && v.rgb_out) {
-        v.rgb_out[lin] = rgb[0];
-        v.rgb_out[plane + lin] = rgb[1];
-        v.rgb_out[2 * plane + lin] = rgb[2];
-    }
-    if (kAdjoint) {
-        // views of a batch without a gradient skip it (a warp covers one view)
-        if (!(v.grad_in || v.target) || frame_overflowed(frame_cnt))
-            return;
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        if (hit) {
-            if (v.target) {
-                // L2 loss sum (rgb - target)^2: its gradient from this frame's image
-                g0 = 2.f * (rgb[0] - v.target[lin]);
-                g1 = 2.f * (rgb[1] - v.target[plane + lin]);
-                g2 = 2.f * (rgb[2] - v.target[2 * plane + lin]);
+        unsigned id = 0xFFFFFFFFu;
+        if (inside) {
+            if (keys) {
+                const unsigned long long key = keys[v.pix_off + lin];
+                const bool bg = key == ~0ull;
+                id = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
+                if (v.id_out)
+                    v.id_out[lin] = id;
+                if (v.depth_out)
+                    v.depth_out[lin] = bg ? INFINITY : __uint_as_float((unsigned)(key >> 32));
             } else {
-                g0 = v.grad_in[lin];
-                g1 = v.grad_in[plane + lin];
-                g2 = v.grad_in[2 * plane + lin];
+                id = v.id_in[lin];
             }
         }
-        adjoint_pixel(v, h, hit, id, g0, g1, g2);
+        // a view with neither an image nor a gradient only needs the resolve
+        const bool hit = inside && id < (unsigned)v.T && (v.rgb_out || grad);
+        PixelHit h;
+        PixelAlbedo pa;
+        float rgb[3] = {0.f, 0.f, 0.f};
+        if (hit) {
+            pixel_hit(v, pi, pj, id, h);
+            pixel_albedo(v, h, pa);
+            rgb[0] = fmaf(pa.a[0], h.sigma, h.spec);
+            rgb[1] = fmaf(pa.a[1], h.sigma, h.spec);
+            rgb[2] = fmaf(pa.a[2], h.sigma, h.spec);
+        }
+        if (inside && v.rgb_out) {
+            v.rgb_out[lin] = rgb[0];
+            v.rgb_out[plane + lin] = rgb[1];
+            v.rgb_out[2 * plane + lin] = rgb[2];
+        }
+        if (kAdjoint) {
+            const bool valid = hit && grad;
+            float g0 = gin[0], g1 = gin[1], g2 = gin[2];
+            if (valid && !v.grad_in) {
+                // L2 loss sum (rgb - target)^2: its gradient from this frame's image
+                g0 = 2.f * (rgb[0] - gin[0]);
+                g1 = 2.f * (rgb[1] - gin[1]);
+                g2 = 2.f * (rgb[2] - gin[2]);
+            }
+            adjoint_step(views, acc, valid, q, id, h, pa, g0, g1, g2);
+        }
     }
+    if (kAdjoint)
+        adjoint_flush(views, acc);
+}
+
+// Warps of kShadeBlocks blocks, 256 threads per CTA.
+static unsigned shade_grid(long long nblocks)
+{
+    const long long warps = (nblocks + kShadeBlocks - 1) / kShadeBlocks;
+    return (unsigned)((warps * 32 + 255) / 256);
 }
 
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                          const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, cudaStream_t st)
 {
-    const long long n = nblocks * 32;
-    if (n > 0) {
+    if (nblocks > 0) {
         if (adjoint)
-            k_shade<true><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, keys, frame_cnt);
+            k_shade<true><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
         else
-            k_shade<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, keys, frame_cnt);
+            k_shade<false><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
     }
     return cudaGetLastError();
 }
@@ -340,52 +450,56 @@ cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_
 // Stage (e) on its own: the adjoint of a shaded frame from its id buffer
 // and an upstream gradient.
 __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__ views, int nviews,
-                                                 const long long *__restrict__ blk_offs, long long nthreads,
+                                                 const long long *__restrict__ blk_offs, long long nblocks,
                                                  const Counters *__restrict__ frame_cnt)
 {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((g & ~31ll) >= nthreads)
-        return;  // whole warps only
+    const long long b0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kShadeBlocks;
+    if (b0 >= nblocks)
+        return;  // whole warps
     // in a training frame: a forward that overflowed is rerun by the host,
     // so its adjoint must not accumulate
     if (frame_overflowed(frame_cnt))
         return;
-    const ViewDev *vp = views;
-    long long lin = 0;
-    int pi = 0, pj = 0;
-    const bool inside = g < nthreads && block_pixel(views, nviews, blk_offs, g, vp, lin, pi, pj);
-    const ViewDev &v = *vp;
-    if (!(v.grad_in || v.target))
-        return;  // views of a batch without a gradient (a warp covers one view)
-    unsigned id = 0xFFFFFFFFu;
-    if (inside)
-        id = v.id_in[lin];
-    const bool valid = inside && id < (unsigned)v.T;
-    PixelHit h;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (valid) {
-        const long long plane = (long long)v.W * v.H;
-        pixel_hit(v, pi, pj, id, h);
-        if (v.target) {
-            // L2 loss sum (rgb - target)^2: its gradient from this frame's image
-            g0 = 2.f * (v.rgb_out[lin] - v.target[lin]);
-            g1 = 2.f * (v.rgb_out[plane + lin] - v.target[plane + lin]);
-            g2 = 2.f * (v.rgb_out[2 * plane + lin] - v.target[2 * plane + lin]);
-        } else {
-            g0 = v.grad_in[lin];
-            g1 = v.grad_in[plane + lin];
-            g2 = v.grad_in[2 * plane + lin];
+    const int lane = threadIdx.x & 31;
+    AdjointSum acc;
+    adjoint_reset(acc);
+    for (int p = 0; p < kShadeBlocks && b0 + p < nblocks; ++p) {
+        int q, pi, pj;
+        long long lin;
+        const bool inside = block_pixel(views, nviews, blk_offs, b0 + p, lane, q, lin, pi, pj);
+        const ViewDev &v = views[q];
+        unsigned id = 0xFFFFFFFFu;
+        if (inside && (v.grad_in || v.target))  // views of a batch without a gradient are skipped
+            id = v.id_in[lin];
+        const bool valid = id < (unsigned)v.T;
+        PixelHit h;
+        PixelAlbedo pa;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (valid) {
+            const long long plane = (long long)v.W * v.H;
+            pixel_hit(v, pi, pj, id, h);
+            pixel_albedo(v, h, pa);
+            if (v.target) {
+                // L2 loss sum (rgb - target)^2: its gradient from this frame's image
+                g0 = 2.f * (v.rgb_out[lin] - v.target[lin]);
+                g1 = 2.f * (v.rgb_out[plane + lin] - v.target[plane + lin]);
+                g2 = 2.f * (v.rgb_out[2 * plane + lin] - v.target[2 * plane + lin]);
+            } else {
+                g0 = v.grad_in[lin];
+                g1 = v.grad_in[plane + lin];
+                g2 = v.grad_in[2 * plane + lin];
+            }
         }
+        adjoint_step(views, acc, valid, q, id, h, pa, g0, g1, g2);
     }
-    adjoint_pixel(v, h, valid, id, g0, g1, g2);
+    adjoint_flush(views, acc);
 }
 
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                             const Counters *frame_cnt, cudaStream_t st)
 {
-    const long long n = nblocks * 32;
-    if (n > 0)
-        k_backward<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, blk_offs, n, frame_cnt);
+    if (nblocks > 0)
+        k_backward<<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,9 @@ def test_invalid_arguments_are_statuses_not_crashes(lib):
     assert lib.pr_rasterize_batch(None, None, 0, None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_frame_batch(None, None, 0, None, None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_graph_capture_frame(None, None, 0, None, None, None, C.byref(h)) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_graph_launch(None, None) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_graph_enqueue(None, None) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_graph_status(None) == B.PR_ERR_INVALID_ARG
 
 
 def test_no_device_is_reported(lib):

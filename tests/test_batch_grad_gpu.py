@@ -155,13 +155,22 @@ def test_graph_keeps_its_view_table_and_refuses_when_stale(pr):
             ob = (torch.empty(nb, dtype=torch.int32, device="cuda"), torch.empty(nb, device="cuda"),
                   torch.empty(3 * nb, device="cuda"))
             pr.pr_rasterize_batch(ws, [(hb, bv, ob[0], ob[1], ob[2], 16)])
-            with pytest.raises(pr.PrError) as ei:
-                pr.pr_graph_launch(graph)
-            assert ei.value.status == pr.PR_ERR_INVALID_ARG
+            for launch in (pr.pr_graph_launch, pr.pr_graph_enqueue):
+                with pytest.raises(pr.PrError) as ei:
+                    launch(graph)
+                assert ei.value.status == pr.PR_ERR_INVALID_ARG
             pr.pr_graph_free(graph)
-            # a fresh capture on the regrown workspace works again
+            # a fresh capture on the regrown workspace works again, also
+            # enqueued without a host wait and its status read afterwards
             graph = pr.pr_graph_capture_batch(ws, entries)
-            pr.pr_graph_launch(graph)
+            for o in outs:
+                for x in o:
+                    x.fill_(7)
+            pr.pr_graph_enqueue(graph)
+            pr.pr_graph_enqueue(graph)
+            stream.synchronize()
+            pr.pr_graph_status(graph)
+            assert pr.pr_workspace_stats(ws)["pixels"] == sum(v.W * v.H for _, v, _ in cases)
             for o, r in zip(outs, ref):
                 assert all(torch.equal(a, b) for a, b in zip(o, r))
             pr.pr_graph_free(graph)
