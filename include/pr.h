@@ -128,6 +128,10 @@ typedef struct {
                              an edge's displacement is unimodal (ternary search); the library seeds
                              the search with a coarse scan and adds half a pixel, but they are not
                              rigorous for every edge (the sector bound is) */
+    int32_t graph_stage_times; /* captured graphs only: 1 = keep the CUDA events between the stages as
+                                  graph nodes, so every replay reports pr_stats.stage_ms; they cost
+                                  tens of microseconds per replay, so by default (0) graphs carry none
+                                  and a replay's stage_ms reads 0.  Eager calls always time stages. */
 } pr_params;
 
 /* Counters of the last rasterize call on a scene or workspace. */

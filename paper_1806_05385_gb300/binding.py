@@ -50,7 +50,7 @@ class PrView(C.Structure):
 
 class PrParams(C.Structure):
     _fields_ = [("bound", C.c_int32), ("tile", C.c_int32), ("fp64_retest", C.c_int32), ("seg", C.c_int32),
-                ("fov_bound", C.c_int32)]
+                ("fov_bound", C.c_int32), ("graph_stage_times", C.c_int32)]
 
 
 class PrStats(C.Structure):
@@ -195,12 +195,13 @@ def make_view(v) -> PrView:
     return out
 
 
-def make_params(bound=PR_BOUND_ZENON, tile=0, fp64_retest=0, seg=0, fov_bound=PR_FOV_SECTOR) -> PrParams:
+def make_params(bound=PR_BOUND_ZENON, tile=0, fp64_retest=0, seg=0, fov_bound=PR_FOV_SECTOR,
+                graph_stage_times=0) -> PrParams:
     if isinstance(bound, str):
         bound = BOUND_NAMES[bound]
     if isinstance(fov_bound, str):
         fov_bound = FOV_BOUND_NAMES[fov_bound]
-    return PrParams(int(bound), int(tile), int(fp64_retest), int(seg), int(fov_bound))
+    return PrParams(int(bound), int(tile), int(fp64_retest), int(seg), int(fov_bound), int(graph_stage_times))
 
 
 # ------------------------------------------------------------------ entry points

@@ -251,6 +251,7 @@ struct pr_graph {
     cudaGraph_t graph = nullptr;
     pr_workspace *ws = nullptr;
     long long npix = 0;
+    bool stage_times = false;           // stage events captured as graph nodes
     DevBuf views, offs;                 // the graph's own view and offset tables
     std::vector<const void *> buffers;  // the workspace's buffers at capture
 };
@@ -354,7 +355,7 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
 
 pr_params default_params(const pr_params *p)
 {
-    pr_params d{PR_BOUND_ZENON, kDefaultTile, 0, kDefaultSeg, PR_FOV_SECTOR};
+    pr_params d{PR_BOUND_ZENON, kDefaultTile, 0, kDefaultSeg, PR_FOV_SECTOR, 0};
     if (p) {
         d = *p;
         if (d.tile == 0)
@@ -563,9 +564,10 @@ void fill_tables(pr_workspace *ws, BatchPlan &P, bool shade)
 // Enqueues one frame (no host synchronisation).  shade: also run stage (d)
 // for views with an rgb output.  tables: device view and offset tables that
 // already hold what fill_tables wrote (a captured graph's own copies), or
-// null to upload the workspace's tables in the same sequence.
+// null to upload the workspace's tables in the same sequence.  marks: record
+// the stage events (always when not capturing).
 pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cudaStream_t st,
-                        const ViewDev *tab_views = nullptr, const long long *tab_offs = nullptr)
+                        const ViewDev *tab_views = nullptr, const long long *tab_offs = nullptr, bool marks = true)
 {
     const int n = (int)P.vd.size();
     char *stage = ws->stage.as<char>();
@@ -597,8 +599,11 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     // while capturing, external records keep the events as graph nodes
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     PR_TRY(cudaStreamIsCapturing(st, &cs));
-    const unsigned ev_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-    auto mark = [&](int k) { return cudaEventRecordWithFlags(ev[k], st, ev_flags); };
+    const bool capturing = cs == cudaStreamCaptureStatusActive;
+    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    auto mark = [&](int k) {
+        return marks || !capturing ? cudaEventRecordWithFlags(ev[k], st, ev_flags) : cudaSuccess;
+    };
     unsigned long long *cand = ws->cand.as<unsigned long long>(), *cand_off = ws->cand_off.as<unsigned long long>();
     PR_TRY(mark(0));
     PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
@@ -1121,7 +1126,8 @@ pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, i
         cudaGetLastError();
         return from_cuda(e);
     }
-    s = enqueue_batch(ws, P, prm.seg, true, st, g->views.as<ViewDev>(), g->offs.as<long long>());
+    g->stage_times = prm.graph_stage_times != 0;
+    s = enqueue_batch(ws, P, prm.seg, true, st, g->views.as<ViewDev>(), g->offs.as<long long>(), g->stage_times);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(st, &graph);
     if (s != PR_OK || e != cudaSuccess) {
@@ -1188,7 +1194,12 @@ pr_status pr_graph_status(pr_graph *g)
         ws->stats.fp64_depth_err = e;
     }
     ws->stats.pixels = (uint64_t)g->npix;
-    ws->read_stage_times();
+    if (g->stage_times) {
+        ws->read_stage_times();
+    } else {
+        for (int k = 0; k < 8; ++k)
+            ws->stats.stage_ms[k] = 0.f;
+    }
     if (c.status & ST_TIMEOUT)
         return PR_ERR_TIMEOUT;
     if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))

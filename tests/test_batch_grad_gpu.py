@@ -111,6 +111,45 @@ def test_graph_replay_matches_eager(pr):
             pr.pr_scene_free(h)
 
 
+def test_graph_stage_times_are_optional(pr):
+    """A graph captured with stage events reports stage times per replay; one
+    captured without (the default) reports zeros; both give the same image."""
+    import torch
+    cases = _views_mixed()[:2]
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+    ws = pr.pr_workspace_create()
+    stream = torch.cuda.Stream()
+    try:
+        with torch.cuda.stream(stream):
+            outs, entries = [], []
+            for h, (sc, v, tile) in zip(handles, cases):
+                n = v.W * v.H
+                o = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, device="cuda"),
+                     torch.empty(3 * n, device="cuda"))
+                outs.append(o)
+                entries.append((h, v, o[0], o[1], o[2], tile))
+            got = {}
+            for timed in (0, 1):
+                graph = pr.pr_graph_capture_batch(ws, entries, pr.make_params(graph_stage_times=timed))
+                for o in outs:
+                    for x in o:
+                        x.fill_(7)
+                pr.pr_graph_launch(graph)
+                ms = pr.pr_workspace_stats(ws)["stage_ms"]
+                got[timed] = [tuple(x.clone() for x in o) for o in outs]
+                pr.pr_graph_free(graph)
+                if timed:
+                    assert ms[0] > 0 and ms[1] > 0 and ms[2] > 0 and ms[5] > 0
+                else:
+                    assert all(x == 0.0 for x in ms)
+            for a, b in zip(got[0], got[1]):
+                assert all(torch.equal(x, y) for x, y in zip(a, b))
+    finally:
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
 def test_graph_keeps_its_view_table_and_refuses_when_stale(pr):
     """A graph replays the views it was captured with, after other calls on
     the same workspace; a call that regrows the workspace makes it stale."""
