@@ -348,7 +348,7 @@ void pr_graph_free(pr_graph *g);
  * uint32 [H][W] and depth_out float32 [H][W]: DEVICE buffers (either may be
  * NULL).  Host pointers are rejected (PR_ERR_INVALID_ARG): staging them
  * would need allocations.  params as for pr_rasterize.
- * Limits: a frame whose fixed scratch (about 36 V + 12 T + 280 T bytes, 60
+ * Limits: a frame whose fixed scratch (about 36 V + 12 T + 284 T bytes, 60
  * bytes per tile and 8 bytes per pixel) does not fit the 64 MiB returns
  * PR_ERR_INVALID_ARG; one whose bins then do not fit what is left returns
  * PR_ERR_OVERFLOW.  No buffer grows and nothing is retried.

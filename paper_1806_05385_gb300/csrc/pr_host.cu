@@ -132,7 +132,8 @@ struct pr_workspace {
     DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, pairs, items, keys, counters, heads;
     DevBuf hit_entry, hit_tile;  // (triangle, tile) hits of the binning count pass, before the scatter
     DevBuf mip;                  // display step: MIP pyramid of the framebuffer image
-    DevBuf cand, cand_off;         // candidate tiles per triangle and their prefix sum
+    DevBuf cand, cand_off;         // candidate tiles per triangle; prefix sum over the binned triangles
+    DevBuf binned;                 // triangles with candidate tiles (listed by the bound pass)
     DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
     DevBuf stage;                  // device copies of host-side outputs
     long long cap_pairs = 0, cap_items = 0;
@@ -168,7 +169,7 @@ struct pr_workspace {
     std::vector<const void *> buffer_set() const
     {
         return {rec.p, hp.p, tbox.p, tile_box.p, tile_cnt.p, scan.p, fill.p, sums.p, pairs.p, items.p,
-                keys.p, counters.p, heads.p, hit_entry.p, hit_tile.p, cand.p, cand_off.p, flag_bits.p,
+                keys.p, counters.p, heads.p, hit_entry.p, hit_tile.p, cand.p, cand_off.p, binned.p, flag_bits.p,
                 flag_list.p, h_cnt.p};
     }
     // stage times of the last completed frame (events already complete)
@@ -501,6 +502,7 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->sums, sizeof(unsigned long long) * (scan_block_sums_needed(P.ttot) + scan_block_sums_needed(P.ntiles))));
     PR_TRY(ensure(ws->cand, sizeof(unsigned long long) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
+    PR_TRY(ensure(ws->binned, sizeof(int) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
     if (P.any_fp64) {
         PR_TRY(ensure(ws->flag_bits, sizeof(unsigned) * ((P.npix + 31) / 32 + 1)));
@@ -607,12 +609,14 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     unsigned long long *cand = ws->cand.as<unsigned long long>(), *cand_off = ws->cand_off.as<unsigned long long>();
     PR_TRY(mark(0));
     PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
-    PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, cnt, st));
+    int *binned = ws->binned.as<int>();
+    PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, binned, cnt, st));
     if (P.any_paper_fov)
         PR_TRY(launch_paper_fov(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, st));
     PR_TRY(mark(1));
-    PR_TRY(launch_scan(cand, cand_off, state_a, P.ttot, 0, cnt, st, true));
-    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt,
+    // candidate tiles of the binned triangles (count known on the device)
+    PR_TRY(launch_scan(cand, cand_off, state_a, P.ttot, 0, cnt, st, true, binned, &cnt->binned));
+    PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, binned, cand_off, rec, hp, tbox, tile_box, tile_cnt,
                             ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt, st));
     PR_TRY(launch_scan(tile_cnt, scan, state_b, P.ntiles, seg, cnt, st, true));
     PR_TRY(launch_bin_scatter(ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), scan,

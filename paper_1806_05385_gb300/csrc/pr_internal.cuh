@@ -61,6 +61,7 @@ struct Counters {
     unsigned long long tests, hits, culled, flagged, changed;
     unsigned long long pairs_total, items_total;  // copied from the scan for the host
     unsigned long long hits_listed;               // (triangle, tile) hits appended by the binning count pass
+    unsigned long long binned;                    // triangles with candidate tiles, listed by the bound pass
     unsigned int status;
     unsigned int depth_err_bits;  // bits of the largest FP32-vs-FP64 relative depth error (re-test)
 };

@@ -17,25 +17,30 @@ cudaError_t launch_scene_check(const float *soa, long long V, Counters *cnt, cud
 // stage (a): display boxes of the framebuffer tiles, per-triangle bounds
 cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
                               float4 *tile_box, cudaStream_t st);
+// binned: the triangles with candidate tiles are appended here (cnt->binned)
 cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
-                         float4 *hp, int4 *tbox, unsigned long long *cand, Counters *cnt, cudaStream_t st);
+                         float4 *hp, int4 *tbox, unsigned long long *cand, int *binned, Counters *cnt,
+                         cudaStream_t st);
 // the paper's foveation edge bounds for the views that select them (after launch_bound)
 cudaError_t launch_paper_fov(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
                              const float4 *rec, float4 *hp, int4 *tbox, unsigned long long *cand, cudaStream_t st);
 
-// stage (b): tile binning -- count pass (tile counts, and every hit appended to the hit list),
-// then after the scan the scatter of the list into the bins
+// stage (b): tile binning -- count pass (tile counts, and every hit appended to the hit list)
+// over the binned triangles (cand_off: prefix of their candidate counts), then after the scan
+// the scatter of the list into the bins
 cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
-                             const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
-                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt,
+                             const int *binned, const unsigned long long *cand_off, const float4 *rec,
+                             const float4 *hp, const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt,
                              unsigned long long *hit_entry, unsigned *hit_tile, long long cap_pairs, Counters *cnt,
                              cudaStream_t st);
 cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
                                const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
                                long long cap_pairs, long long ntiles, Counters *cnt, cudaStream_t st);
-// state_zeroed: the caller cleared the ticket and flags (state[0, 1 + nb))
+// state_zeroed: the caller cleared the ticket and flags (state[0, 1 + nb)).
+// gather: scan in[gather[i]]; n_dev: the count is min(*n_dev, n) (device).
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
-                        int seg, Counters *cnt, cudaStream_t st, bool state_zeroed = false);
+                        int seg, Counters *cnt, cudaStream_t st, bool state_zeroed = false,
+                        const int *gather = nullptr, const unsigned long long *n_dev = nullptr);
 cudaError_t launch_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
                               unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
                               long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,

@@ -207,6 +207,7 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     const size_t o_soa = c.take(sizeof(float) * 9 * V), o_idx = c.take(sizeof(int) * 3 * Tn);
     const size_t o_rec = c.take(sizeof(float4) * kRecF4 * Tn), o_hp = c.take(sizeof(float4) * kMaxHp * Tn);
     const size_t o_tbox = c.take(sizeof(int4) * Tn), o_cand = c.take(8 * Tn), o_cand_off = c.take(8 * (Tn + 1));
+    const size_t o_binned = c.take(sizeof(int) * Tn);
     const size_t o_tile_box = c.take(sizeof(float4) * nt), o_tile_cnt = c.take(8 * nt);
     const size_t o_scan = c.take(8 * (nt + 1)), o_fill = c.take(4 * nt);
     const size_t o_sums = c.take(8 * (scan_block_sums_needed(Tn) + scan_block_sums_needed(nt)));
@@ -270,12 +271,13 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_scene_idx(tri, T, V, idx, cnt, st));
     NA_TRY(launch_scene_check(soa, V, cnt, st));
     NA_TRY(launch_tile_boxes(dv, 1, tile_offs, nt, tile_box, st));
-    NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, cnt, st));
+    int *binned = (int *)(arena + o_binned);
+    NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, binned, cnt, st));
     if (fov_bound != PR_FOV_SECTOR && (view->mode == PR_FOVEATED || view->mode == PR_BOTH))
         NA_TRY(launch_paper_fov(dv, 1, tri_offs, T, rec, hp, tbox, cand, st));
-    NA_TRY(launch_scan(cand, cand_off, state_a, T, 0, cnt, st, true));
-    NA_TRY(launch_bin_count(dv, 1, tri_offs, T, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry, hit_tile,
-                            cap_pairs, cnt, st));
+    NA_TRY(launch_scan(cand, cand_off, state_a, T, 0, cnt, st, true, binned, &cnt->binned));
+    NA_TRY(launch_bin_count(dv, 1, tri_offs, T, binned, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry,
+                            hit_tile, cap_pairs, cnt, st));
     NA_TRY(launch_scan(tile_cnt, scan, state_b, nt, seg, cnt, st, true));
     NA_TRY(launch_bin_scatter(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, nt, cnt, st));
     NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));

@@ -632,12 +632,14 @@ __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3
 //   [3] D1.x D1.y D1.z D2.x   [4] xmin xmax ymin ymax   [5] tmin tmax D2.y D2.z
 // S = camera-space vertex at t = 0, D = its motion over the frame, the box
 // and interval of stage (a).  tbox = (i0 | i1 << 16, j0 | j1 << 16, nhp, depth order
-// key of the nearest depth the triangle reaches).
+// key of the nearest depth the triangle reaches).  cand = candidate tiles of
+// the framebuffer box; the triangles that have some are also appended to
+// `binned` (cnt->binned of them), the index space of the binning pass.
 __global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ views, int nviews,
                                                const long long *__restrict__ tri_offs, long long ttot,
                                                float4 *__restrict__ rec, float4 *__restrict__ hp,
                                                int4 *__restrict__ tbox, unsigned long long *__restrict__ cand,
-                                               Counters *cnt)
+                                               int *__restrict__ binned, Counters *cnt)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ttot)
@@ -679,14 +681,23 @@ __global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ vi
                              S[2].z + fminf(0.f, D[2].z));
     tbox[g] = make_int4(B.i0 | (B.i1 << 16), B.j0 | (B.j1 << 16), nhp, (int)depth_order_key(near));
     cand[g] = (unsigned long long)(B.i1 / v.S - B.i0 / v.S + 1) * (unsigned long long)(B.j1 / v.S - B.j0 / v.S + 1);
+    // list the triangle for binning (one atomic per warp; the list order
+    // does not matter: every bin is sorted by depth later)
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader)
+        base = atomicAdd(&cnt->binned, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    binned[base + __popc(m & ((1u << lane) - 1u))] = (int)g;
 }
 
 cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
-                         float4 *hp, int4 *tbox, unsigned long long *cand, Counters *cnt, cudaStream_t st)
+                         float4 *hp, int4 *tbox, unsigned long long *cand, int *binned, Counters *cnt, cudaStream_t st)
 {
     if (ttot > 0)
         k_bound<<<(unsigned)((ttot + 127) / 128), 128, 0, st>>>(views, nviews, tri_offs, ttot, rec, hp, tbox, cand,
-                                                                cnt);
+                                                                binned, cnt);
     return cudaGetLastError();
 }
 
@@ -767,18 +778,49 @@ __device__ __forceinline__ bool tile_meets(const float4 tb, const float4 bb, con
 }
 
 // Bins.  Every triangle's framebuffer box spans a rectangle of candidate
-// tiles; cand_off is the prefix sum of those counts over the batch, so
-// candidate pair p belongs to the triangle g with cand_off[g] <= p <
-// cand_off[g+1].  One thread per candidate pair (grid-stride) keeps the
-// work balanced when a few triangles -- near the fovea, where q^-1
-// magnifies, or close to the camera -- span thousands of tiles.
-// tile_cnt[tile] = number of triangles whose region meets the tile;
-// appends are warp-aggregated (lanes that hit the same tile share one
-// atomic).  A bin entry is (depth order key of the triangle << 32) | its
-// batch-wide index, so that sorting entries sorts by nearest depth.
-__device__ __forceinline__ long long owner_of(const unsigned long long *cand_off, long long ttot, long long p)
+// tiles.  The triangles that have candidates are listed in `binned` (by the
+// bound pass, m of them) and cand_off is the prefix sum of their counts, so
+// candidate pair p belongs to list entry e with cand_off[e] <= p <
+// cand_off[e+1].  Warps take the pairs in tasks of consecutive pairs, which
+// keeps the work balanced when a few triangles -- near the fovea, where
+// q^-1 magnifies, or close to the camera -- span thousands of tiles.
+// tile_cnt[tile] = number of triangles whose region meets the tile; every
+// hit is appended to the hit list (one atomic per warp) and counted per
+// tile (one atomic per distinct tile of a warp).  A bin entry is (depth
+// order key of the triangle << 32) | its batch-wide index, so that sorting
+// entries sorts by nearest depth.
+
+// Largest e in [0, m) with cand_off[e] <= p for a warp-uniform p, found by
+// the whole warp: each step probes 32 evenly spaced offsets of the range
+// with one load and keeps the part between the last probe at or below p
+// and the next (a 32-ary search: ceil(log32 m) dependent loads).
+__device__ __forceinline__ long long warp_owner(const unsigned long long *cand_off, long long m, long long p)
 {
-    long long lo = 0, hi = ttot - 1;
+    const int lane = threadIdx.x & 31;
+    long long lo = 0, hi = m - 1;  // cand_off[lo] <= p; the answer lies in [lo, hi]
+    while (hi > lo) {
+        const long long span = hi - lo;  // probes lo + 1 .. hi
+        const long long idx = span <= 32 ? min(lo + 1 + lane, hi) : lo + 1 + (span - 1) * lane / 31;
+        const unsigned le = __ballot_sync(0xffffffffu, (long long)cand_off[idx] <= p);
+        if (!le) {
+            hi = __shfl_sync(0xffffffffu, idx, 0) - 1;
+        } else {
+            const int last = 31 - __clz(le);  // probes ascend, so `le` is a prefix of the lanes
+            const long long nlo = __shfl_sync(0xffffffffu, idx, last);
+            const long long nhi = last < 31 ? __shfl_sync(0xffffffffu, idx, last + 1) - 1 : hi;
+            lo = nlo;
+            hi = max(nhi, nlo);
+        }
+    }
+    return lo;
+}
+
+// The same for one lane's p (a plain binary search): only for pairs that a
+// warp's window of 32 list entries does not reach, which needs entries
+// without candidates (the paper's foveation bounds can empty a box).
+__device__ __forceinline__ long long owner_of(const unsigned long long *cand_off, long long m, long long p)
+{
+    long long lo = 0, hi = m - 1;
     while (lo < hi) {
         const long long mid = (lo + hi + 1) >> 1;
         if ((long long)cand_off[mid] <= p)
@@ -792,7 +834,7 @@ __device__ __forceinline__ long long owner_of(const unsigned long long *cand_off
 constexpr int kBinChunks = 4;
 
 __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, int nviews,
-                                             const long long *__restrict__ tri_offs, long long ttot,
+                                             const long long *__restrict__ tri_offs, const int *__restrict__ binned,
                                              const unsigned long long *__restrict__ cand_off,
                                              const float4 *__restrict__ rec, const float4 *__restrict__ hp,
                                              const int4 *__restrict__ tbox, const float4 *__restrict__ tile_box,
@@ -800,25 +842,28 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                                              unsigned long long *__restrict__ hit_entry, unsigned *__restrict__ hit_tile,
                                              long long cap_pairs, Counters *cnt)
 {
-    const long long total = (long long)cand_off[ttot];
+    const long long m = (long long)cnt->binned;
+    if (m == 0)
+        return;
+    const long long total = (long long)cand_off[m];
     const int lane = threadIdx.x & 31;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     // Each warp takes tasks of kBinChunks x 32 consecutive candidate pairs.
-    // The owner of the task's first pair is found by a binary search over
-    // the triangle offsets (warp-uniform, so one broadcast load per step);
-    // the owners of each chunk's pairs then follow from the offsets of the
-    // next 32 triangles, loaded with one coalesced read and searched with
-    // shuffles.  All lanes run the same iterations (for the shuffles).
+    // The list entry of the task's first pair comes from a warp-wide 32-ary
+    // search; the entries of each chunk's pairs then follow from the offsets
+    // of the next 32 entries, loaded with one coalesced read and searched
+    // with shuffles (every entry owns at least one pair, so 32 pairs never
+    // reach past them).  All lanes run the same iterations (for the shuffles).
     for (long long pt = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kBinChunks);
          pt < total; pt += nwarps * (32 * kBinChunks)) {
-        long long g0 = owner_of(cand_off, ttot, pt);
+        long long e0 = warp_owner(cand_off, m, pt);
         for (int c = 0; c < kBinChunks; ++c) {
             const long long pw = pt + 32 * c;
             if (pw >= total)
                 break;
             const long long p = pw + lane;
-            const long long gl = g0 + 1 + lane;
-            const unsigned long long o = gl <= ttot ? cand_off[gl] : ~0ull;
+            const long long el = e0 + 1 + lane;
+            const unsigned long long o = el <= m ? cand_off[el] : ~0ull;
             // every lane takes part in every shuffle; the fallback search
             // (no warp operations) runs after them
             int k = 0;  // offsets of the window at or below p
@@ -828,13 +873,14 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                     k += sstep;
             }
             const bool beyond = __shfl_sync(0xffffffffu, o, 31) <= (unsigned long long)p;
-            // past the window (a run of empty triangles): search all offsets
-            const long long g = beyond ? owner_of(cand_off, ttot, p) : g0 + k;
-            g0 = __shfl_sync(0xffffffffu, g, 31);  // owners ascend with p
+            const long long e = beyond ? owner_of(cand_off, m, p) : e0 + k;
+            e0 = __shfl_sync(0xffffffffu, e, 31);  // owners ascend with p
             bool hit = false, ok_tile = true;
             long long tile = -1;
             unsigned key = 0u;
+            long long g = 0;
             if (p < total) {
+                g = binned[e];
                 const int4 tb = tbox[g];
                 key = (unsigned)tb.w;
                 const ViewDev &v = views[find_view(tri_offs, nviews, g)];
@@ -842,7 +888,8 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                 const int tx0 = (tb.x & 0xffff) >> sh, tx1 = (tb.x >> 16) >> sh;
                 const int ty0 = (tb.y & 0xffff) >> sh;
                 const int w = tx1 - tx0 + 1;
-                const int q = (int)(p - (long long)cand_off[g]);  // < tiles of one view
+                const unsigned long long off = cand_off[e];
+                const int q = (int)(p - (long long)off);  // < tiles of one view
                 const int qy = q / w;
                 const int tx = tx0 + (q - qy * w), ty = ty0 + qy;
                 tile = v.tile_off + (long long)ty * v.tiles_x + tx;
@@ -853,7 +900,7 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                 }
                 const float4 bb = rec[g * kRecF4 + 4];
                 const bool fbspace = (tb.z & 0x100) != 0;
-                const int nh = cand_off[g + 1] - cand_off[g] > 1 ? (tb.z & 0xff) : 0;
+                const int nh = cand_off[e + 1] - off > 1 ? (tb.z & 0xff) : 0;
                 if (!ok_tile) {
                     hit = false;
                 } else if (!fbspace) {
@@ -945,14 +992,14 @@ static int bin_grid()
 }
 
 cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot,
-                             const unsigned long long *cand_off, const float4 *rec, const float4 *hp,
-                             const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt,
+                             const int *binned, const unsigned long long *cand_off, const float4 *rec,
+                             const float4 *hp, const int4 *tbox, const float4 *tile_box, unsigned long long *tile_cnt,
                              unsigned long long *hit_entry, unsigned *hit_tile, long long cap_pairs, Counters *cnt,
                              cudaStream_t st)
 {
     if (ttot > 0)
-        k_bin<<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, ttot, cand_off, rec, hp, tbox, tile_box, tile_cnt,
-                                          hit_entry, hit_tile, cap_pairs, cnt);
+        k_bin<<<bin_grid(), 256, 0, st>>>(views, nviews, tri_offs, binned, cand_off, rec, hp, tbox, tile_box,
+                                          tile_cnt, hit_entry, hit_tile, cap_pairs, cnt);
     return cudaGetLastError();
 }
 
@@ -1077,8 +1124,12 @@ __device__ __forceinline__ void store_volatile(unsigned long long *p, unsigned l
 }
 
 // state: [0] ticket, [1, 1 + nb) flags, then nb tile sums, then nb
-// inclusive prefixes; the ticket and flags start at zero.
+// inclusive prefixes; the ticket and flags start at zero.  gather: element
+// i is in[gather[i]] (else in[i]).  n_dev: the element count is
+// min(*n_dev, n), known on the device only; tiles past it leave at once.
 __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long *__restrict__ in,
+                                                      const int *__restrict__ gather,
+                                                      const unsigned long long *__restrict__ n_dev,
                                                       unsigned long long *__restrict__ out, long long n, int seg,
                                                       unsigned long long *state, long long nb, Counters *cnt)
 {
@@ -1089,11 +1140,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
         s_tile = (long long)atomicAdd(&state[0], 1ull);
     __syncthreads();
     const long long tile = s_tile;
+    if (n_dev) {
+        n = min(n, (long long)*n_dev);
+        // tiles are numbered in start order, so no tile at or before the
+        // one that holds out[n] waits on these
+        if (tile * kScanBlock > n)
+            return;
+    }
     const long long base = tile * kScanBlock + (long long)threadIdx.x * kScanPer;
     unsigned long long v[kScanPer], sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        v[k] = base + k < n ? (seg > 0 ? pack_items(in[base + k], seg) : in[base + k]) : 0ull;
+        unsigned long long x = 0ull;
+        if (base + k < n)
+            x = in[gather ? (long long)gather[base + k] : base + k];
+        v[k] = seg > 0 ? pack_items(x, seg) : x;
         sum += v[k];
     }
     unsigned long long total;
@@ -1161,7 +1222,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
             out[base + k] = excl + run;
         run += v[k];
     }
-    if (tile == nb - 1 && threadIdx.x == 0)
+    if (threadIdx.x == 0 && ((n >= tile * kScanBlock && n < (tile + 1) * kScanBlock) || (tile == nb - 1 && n == nb * kScanBlock)))
         out[n] = excl + total;
 }
 
@@ -1177,7 +1238,8 @@ size_t scan_block_sums_needed(long long n)
 }
 
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
-                        int seg, Counters *cnt, cudaStream_t st, bool state_zeroed)
+                        int seg, Counters *cnt, cudaStream_t st, bool state_zeroed, const int *gather,
+                        const unsigned long long *n_dev)
 {
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) {
@@ -1189,7 +1251,7 @@ cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, u
         if (e != cudaSuccess)
             return e;
     }
-    k_scan<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, seg, state, nb, cnt);
+    k_scan<<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt);
     return cudaGetLastError();
 }
 
