@@ -831,7 +831,7 @@ __device__ __forceinline__ long long owner_of(const unsigned long long *cand_off
     return lo;
 }
 
-constexpr int kBinChunks = 4;
+constexpr int kBinChunks = 8;
 
 __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, int nviews,
                                              const long long *__restrict__ tri_offs, const int *__restrict__ binned,
@@ -857,10 +857,18 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
     for (long long pt = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kBinChunks);
          pt < total; pt += nwarps * (32 * kBinChunks)) {
         long long e0 = warp_owner(cand_off, m, pt);
+        // the task's hits: per chunk the ballot, the lane's entry and tile
+        unsigned want_c[kBinChunks];
+        unsigned long long ent_c[kBinChunks];
+        unsigned tile_c[kBinChunks];
+#pragma unroll
         for (int c = 0; c < kBinChunks; ++c) {
+            want_c[c] = 0u;
+            ent_c[c] = 0ull;
+            tile_c[c] = 0u;
             const long long pw = pt + 32 * c;
             if (pw >= total)
-                break;
+                continue;  // warp-uniform
             const long long p = pw + lane;
             const long long el = e0 + 1 + lane;
             const unsigned long long o = el <= m ? cand_off[el] : ~0ull;
@@ -917,27 +925,40 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                     hit = tile_meets(tile_box[tile], bb, hp, 0) && tile_meets(fbt, big, hp + g * kMaxHp, nh);
                 }
             }
-            const unsigned want = __ballot_sync(0xffffffffu, hit);
+            want_c[c] = __ballot_sync(0xffffffffu, hit);
+            ent_c[c] = ((unsigned long long)key << 32) | (unsigned long long)g;
+            tile_c[c] = (unsigned)tile;
+        }
+        // the task's hits go to the hit list with one atomic ...
+        unsigned ntask = 0;
+#pragma unroll
+        for (int c = 0; c < kBinChunks; ++c)
+            ntask += __popc(want_c[c]);
+        if (ntask == 0)
+            continue;
+        unsigned long long wbase = 0;
+        if (lane == 0)
+            wbase = atomicAdd(&cnt->hits_listed, (unsigned long long)ntask);
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+#pragma unroll
+        for (int c = 0; c < kBinChunks; ++c) {
+            const unsigned want = want_c[c];
             if (!want)
-                continue;
-            // the warp's hits go to the hit list with one atomic ...
-            unsigned long long wbase = 0;
-            if (lane == 0)
-                wbase = atomicAdd(&cnt->hits_listed, (unsigned long long)__popc(want));
-            wbase = __shfl_sync(0xffffffffu, wbase, 0);
-            if (!hit)
-                continue;
-            const long long slot = (long long)wbase + __popc(want & ((1u << lane) - 1u));
-            if (slot < cap_pairs) {
-                hit_entry[slot] = ((unsigned long long)key << 32) | (unsigned long long)g;
-                hit_tile[slot] = (unsigned)tile;
-            } else {
-                atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+                continue;  // warp-uniform
+            if ((want >> lane) & 1u) {
+                const long long slot = (long long)wbase + __popc(want & ((1u << lane) - 1u));
+                if (slot < cap_pairs) {
+                    hit_entry[slot] = ent_c[c];
+                    hit_tile[slot] = tile_c[c];
+                } else {
+                    atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
+                }
+                // ... and every tile's count with one atomic per tile met
+                const unsigned peers = __match_any_sync(want, tile_c[c]);
+                if (lane == __ffs(peers) - 1)
+                    atomicAdd(&tile_cnt[tile_c[c]], (unsigned long long)__popc(peers));
             }
-            // ... and every tile's count with one atomic per tile met
-            const unsigned peers = __match_any_sync(want, (unsigned long long)tile);
-            if (lane == __ffs(peers) - 1)
-                atomicAdd(&tile_cnt[tile], (unsigned long long)__popc(peers));
+            wbase += __popc(want);
         }
     }
 }
