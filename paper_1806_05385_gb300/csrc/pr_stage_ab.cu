@@ -665,7 +665,9 @@ __global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ vi
         r[5] = make_float4(INFINITY, -INFINITY, D[2].y, D[2].z);
         tbox[g] = make_int4(1, 1, 0, 0);  // the empty box [1, 0] x [1, 0]
         cand[g] = 0ull;
-        atomicAdd(&cnt->culled, 1ull);
+        const unsigned cm = __activemask();  // one atomic per warp
+        if ((threadIdx.x & 31) == __ffs(cm) - 1)
+            atomicAdd(&cnt->culled, (unsigned long long)__popc(cm));
         return;
     }
     r[4] = make_float4(B.xmin, B.xmax, B.ymin, B.ymax);

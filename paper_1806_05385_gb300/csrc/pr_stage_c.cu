@@ -280,9 +280,20 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
         n_tests += __shfl_xor_sync(0xffffffffu, n_tests, o);
         n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
     }
+    // one pair of global atomics per CTA (every thread left the loop at the
+    // same item)
+    __shared__ unsigned long long s_tests, s_hits;
+    if (threadIdx.x == 0)
+        s_tests = s_hits = 0ull;
+    __syncthreads();
     if (lane == 0) {
-        atomicAdd(&cnt->tests, n_tests);
-        atomicAdd(&cnt->hits, n_hits);
+        atomicAdd(&s_tests, n_tests);
+        atomicAdd(&s_hits, n_hits);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&cnt->tests, s_tests);
+        atomicAdd(&cnt->hits, s_hits);
     }
 }
 
