@@ -499,7 +499,8 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->scan, sizeof(unsigned long long) * (P.ntiles + 1)));
     PR_TRY(ensure(ws->fill, sizeof(unsigned) * std::max(P.ntiles, 1ll)));
     // two scans' look-back states: the candidate-tile scan, then the tile scan
-    PR_TRY(ensure(ws->sums, sizeof(unsigned long long) * (scan_block_sums_needed(P.ttot) + scan_block_sums_needed(P.ntiles))));
+    PR_TRY(ensure(ws->sums,
+                  sizeof(unsigned long long) * (scan_block_sums_needed(P.ttot) + scan_block_sums_needed(P.ntiles))));
     PR_TRY(ensure(ws->cand, sizeof(unsigned long long) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
     PR_TRY(ensure(ws->binned, sizeof(int) * std::max(P.ttot, 1ll)));
@@ -617,7 +618,8 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     // candidate tiles of the binned triangles (count known on the device)
     PR_TRY(launch_scan(cand, cand_off, state_a, P.ttot, 0, cnt, st, true, binned, &cnt->binned));
     PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, binned, cand_off, rec, hp, tbox, tile_box, tile_cnt,
-                            ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt, st));
+                            ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt,
+                            st));
     PR_TRY(launch_scan(tile_cnt, scan, state_b, P.ntiles, seg, cnt, st, true));
     PR_TRY(launch_bin_scatter(ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), scan,
                               ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, P.ntiles, cnt,

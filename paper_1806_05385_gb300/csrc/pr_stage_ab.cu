@@ -841,8 +841,8 @@ __global__ void __launch_bounds__(256) k_bin(const ViewDev *__restrict__ views, 
                                              const float4 *__restrict__ rec, const float4 *__restrict__ hp,
                                              const int4 *__restrict__ tbox, const float4 *__restrict__ tile_box,
                                              unsigned long long *__restrict__ tile_cnt,
-                                             unsigned long long *__restrict__ hit_entry, unsigned *__restrict__ hit_tile,
-                                             long long cap_pairs, Counters *cnt)
+                                             unsigned long long *__restrict__ hit_entry,
+                                             unsigned *__restrict__ hit_tile, long long cap_pairs, Counters *cnt)
 {
     const long long m = (long long)cnt->binned;
     if (m == 0)
@@ -1105,7 +1105,12 @@ constexpr int kScanSpinLimit = 1 << 22;
 __device__ __forceinline__ unsigned long long pack_items(unsigned long long c, int seg)
 {
     const unsigned long long n = c & 0xFFFFFFFFFFull;
-    return n | (((n + seg - 1) / seg) << 40);
+    // a 32-bit division where the count allows it (a 64-bit one is a long
+    // instruction sequence)
+    const unsigned long long items = n <= 0x7FFFFFFFull
+                                         ? (unsigned long long)(((unsigned)n + (unsigned)seg - 1u) / (unsigned)seg)
+                                         : (n + seg - 1) / seg;
+    return n | (items << 40);
 }
 
 __device__ unsigned long long block_exclusive_scan(unsigned long long x, unsigned long long *total)
@@ -1245,7 +1250,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
             out[base + k] = excl + run;
         run += v[k];
     }
-    if (threadIdx.x == 0 && ((n >= tile * kScanBlock && n < (tile + 1) * kScanBlock) || (tile == nb - 1 && n == nb * kScanBlock)))
+    const bool holds_end =
+        (n >= tile * kScanBlock && n < (tile + 1) * kScanBlock) || (tile == nb - 1 && n == nb * kScanBlock);
+    if (threadIdx.x == 0 && holds_end)
         out[n] = excl + total;
 }
 
