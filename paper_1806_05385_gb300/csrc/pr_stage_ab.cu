@@ -448,6 +448,41 @@ __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3
         B.culled = true;
         return;
     }
+    // foveated: the framebuffer covers only part of the display.  The
+    // projected time-domain points bound the display region (Sec. 4.2.2), so
+    // the sector preimage of their box bounds the triangle's pixels; if that
+    // pixel box is empty the triangle leaves before the rest of the bound.
+    if (fov && !any_near) {
+        float bx0 = INFINITY, bx1 = -INFINITY, by0 = INFINITY, by1 = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (k >= np)
+                break;
+            const float2 x = project(v, P[k]);
+            bx0 = fminf(bx0, x.x);
+            bx1 = fmaxf(bx1, x.x);
+            by0 = fminf(by0, x.y);
+            by1 = fmaxf(by1, x.y);
+        }
+        const float m = eps * fmaxf(1.f, fmaxf(fmaxf(fabsf(bx0), fabsf(bx1)), fmaxf(fabsf(by0), fabsf(by1))));
+        bx0 -= m;
+        bx1 += m;
+        by0 -= m;
+        by1 += m;
+        const float2 f = make_float2(v.fx, v.fy);
+        const float dbx = fmaxf(fmaxf(bx0 - f.x, f.x - bx1), 0.f), dby = fmaxf(fmaxf(by0 - f.y, f.y - by1), 0.f);
+        const float rlo = sqrtf(dbx * dbx + dby * dby);
+        const float2 corners[4] = {make_float2(bx0, by0), make_float2(bx1, by0), make_float2(bx1, by1),
+                                   make_float2(bx0, by1)};
+        const float4 fb = fov_sector_preimage(corners, 4, f, v.inv_alpha, 2.f * eps, rlo <= 2.f * eps, rlo, v.p_lut,
+                                              v.p_n);
+        const float fi0 = ceilf(fb.x * v.W - 0.5f) - 1.f, fi1 = floorf(fb.y * v.W - 0.5f) + 1.f;
+        const float fj0 = ceilf(fb.z * v.H - 0.5f) - 1.f, fj1 = floorf(fb.w * v.H - 0.5f) + 1.f;
+        if (fmaxf(fi0, 0.f) > fminf(fi1, (float)(v.W - 1)) || fmaxf(fj0, 0.f) > fminf(fj1, (float)(v.H - 1))) {
+            B.culled = true;
+            return;
+        }
+    }
 
     float2 Q[6];  // display points of the region (projected space-time vertices)
     int nq = 0;
