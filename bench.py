@@ -421,12 +421,14 @@ def our_arm(args, rank, world):
     # is the one of the two that takes longer per frame
     sm_mhz = clocks.get("sm_mhz") or 1470.0
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    ffma = B.pr_measure_fp32_peak()  # on-box cross-check of the derived peak (independent FMA chains)
     achieved = st["tests"] * FLOP_PER_TEST / (frag_ms * 1e-3) / 1e12 if frag_ms > 0 else 0.0
     roof_frag = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak if peak else None, "traffic": ncu_traffic(args.workload, "k_fragment"),
                  "kernel": "k_fragment", "time_ms": frag_ms, "flop_per_test": FLOP_PER_TEST,
                  "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x median SM clock {sm_mhz:.0f} MHz "
                                f"sampled during the timed region (no FP32 figure in MEASURED_PEAKS.json)",
+                 "peak_measured_ffma": ffma,
                  "achieved_basis": "ray-triangle tests of one frame x 39 FLOP / fragment-stage time of that frame "
                                    "(CUDA events on the launching stream, inside replays of the frame graph captured with "
                                    "stage events, one per timed step)"}

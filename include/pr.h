@@ -378,6 +378,14 @@ pr_status pr_debug_bounds(const pr_scene *scene, int32_t *pix_box, float *t_rang
  * the rolling scan never meets the triangle.  For unit tests. */
 int32_t pr_debug_catch_interval(const pr_view *view, const float *S, const float *E, float *t_out);
 
+/* Measures the FP32 fused multiply-add throughput of the current device
+ * (TFLOP/s, best of three timed launches of independent FMA chains on every
+ * SM, after one warm-up launch) on stream; it allocates and frees a 4 KB
+ * buffer.  The paper has no counterpart: it cross-checks the peak against
+ * which the fragment stage's ALU roofline is reported.  tflops_out: host
+ * pointer, written. */
+pr_status pr_measure_fp32_peak(void *stream, double *tflops_out);
+
 const char *pr_status_string(pr_status s);
 int32_t pr_version(void);
 

@@ -31,7 +31,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
            "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
-           "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status")
+           "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status", "pr_measure_fp32_peak")
 
 
 class PrError(RuntimeError):
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
             "pr_graph_launch": ([P, P], I32),
             "pr_graph_enqueue": ([P, P], I32),
             "pr_graph_status": ([P], I32),
+            "pr_measure_fp32_peak": ([P, C.POINTER(C.c_double)], I32),
             "pr_graph_free": ([P], None),
             "pr_scene_stats": ([P, C.POINTER(PrStats)], I32),
             "pr_workspace_stats": ([P, C.POINTER(PrStats)], I32),
@@ -394,6 +395,14 @@ def pr_graph_enqueue(graph, stream=None):
 
 def pr_graph_status(graph):
     _check(load().pr_graph_status(C.c_void_p(graph)), "pr_graph_status")
+
+
+def pr_measure_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    out = C.c_double(0.0)
+    _check(load().pr_measure_fp32_peak(stream if stream is not None else current_stream(), C.byref(out)),
+           "pr_measure_fp32_peak")
+    return out.value
 
 
 def pr_graph_free(graph):

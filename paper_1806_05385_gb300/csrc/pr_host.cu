@@ -765,6 +765,15 @@ extern "C" {
 
 int32_t pr_version(void) { return 1; }
 
+pr_status pr_measure_fp32_peak(void *stream, double *tflops_out)
+{
+    if (!tflops_out)
+        return PR_ERR_INVALID_ARG;
+    *tflops_out = 0.0;
+    PR_TRY(measure_fma_peak((cudaStream_t)stream, tflops_out));
+    return PR_OK;
+}
+
 const char *pr_status_string(pr_status s)
 {
     switch (s) {

@@ -84,6 +84,9 @@ size_t mip_pyramid_floats(int W, int H);
 cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, const float *p_lut,
                              int p_n, int Wd, int Hd, float sigma, const float *rgb, float *pyramid, float *out,
                              cudaStream_t st);
+// measured FP32 FMA throughput of the current device, TFLOP/s
+cudaError_t measure_fma_peak(cudaStream_t st, double *tflops);
+
 // device samples of a foveation handle (defined with the handle)
 const float *pr_foveation_samples(const pr_foveation *f, int *n);
 

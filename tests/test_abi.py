@@ -85,6 +85,7 @@ def test_invalid_arguments_are_statuses_not_crashes(lib):
     assert lib.pr_graph_launch(None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_graph_enqueue(None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_graph_status(None) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_measure_fp32_peak(None, None) == B.PR_ERR_INVALID_ARG
 
 
 def test_no_device_is_reported(lib):

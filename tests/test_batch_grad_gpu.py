@@ -509,3 +509,10 @@ def test_specular_shading_and_gradient_match_oracle(pr, oracle, mode):
         assert err <= 1e-3, (name, err)
     # the highlight is really there: some pixels are brighter than any albedo x sigma allows
     assert (g["rgb"].reshape(3, -1).max(axis=0) > 1.0).any() or rep["hit_frac"] > 0.05
+
+
+def test_fp32_peak_measurement_is_plausible(pr):
+    """The FMA microbenchmark lands near the unit-count peak of a GB300
+    (152 SMs x 128 lanes x 2 FLOP x about 2 GHz = about 78 TFLOP/s)."""
+    t = pr.pr_measure_fp32_peak()
+    assert 20.0 < t < 120.0
