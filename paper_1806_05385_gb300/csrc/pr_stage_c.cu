@@ -25,6 +25,7 @@ namespace pr {
 // which two hits count as tied.
 constexpr float kRelCoord = 2e-6f;
 constexpr float kTieRel = 1e-4f;
+constexpr float kKeySlack = 1e-3f;
 
 // One watertight ray/triangle test (Woop, Benthin and Wald, "Watertight
 // Ray/Triangle Intersection", JCGT 2013) of the ray from the origin along
@@ -397,120 +398,258 @@ __device__ Ray64 pixel_ray64(const ViewDev &v, int i, int j)
     return ry;
 }
 
-// Vertex k at time t in FP64: (1-t)(R0 p + T0) + t(R1 (p + v) + T1).
-__device__ double3 vertex64(const ViewDev &v, int k, double t)
+// The map from a vertex (p, v) to its sheared camera-space position at the
+// pixel's time, in FP64: with M = (1-t) R0 + t R1, N = t R1 and
+// T = (1-t) T0 + t T1 the moved vertex is c = M p + N v + T (the same
+// point as (1-t)(R0 p + T0) + t(R1 (p + v) + T1)), and the shear of the
+// watertight test takes rows x - dx z, y - dy z, z.  Built once per pixel,
+// it leaves 18 multiply-adds per vertex.
+struct Shear64 {
+    double P[3][3], Q[3][3], c[3];
+};
+
+__device__ Shear64 shear64(const ViewDev &v, const Ray64 &ry)
 {
-    const double p[3] = {v.px[k], v.py[k], v.pz[k]};
-    const double e[3] = {p[0] + (double)v.vx[k], p[1] + (double)v.vy[k], p[2] + (double)v.vz[k]};
-    double c[3];
+    Shear64 sh;
+    double M[3][3], N[3][3], T[3];
     for (int r = 0; r < 3; ++r) {
-        const double S = (double)v.R0[3 * r] * p[0] + (double)v.R0[3 * r + 1] * p[1] + (double)v.R0[3 * r + 2] * p[2] +
-                         (double)v.T0[r];
-        const double E = (double)v.R1[3 * r] * e[0] + (double)v.R1[3 * r + 1] * e[1] + (double)v.R1[3 * r + 2] * e[2] +
-                         (double)v.T1[r];
-        c[r] = (1.0 - t) * S + t * E;
+        for (int k = 0; k < 3; ++k) {
+            M[r][k] = (1.0 - ry.t) * (double)v.R0[3 * r + k] + ry.t * (double)v.R1[3 * r + k];
+            N[r][k] = ry.t * (double)v.R1[3 * r + k];
+        }
+        T[r] = (1.0 - ry.t) * (double)v.T0[r] + ry.t * (double)v.T1[r];
     }
-    return make_double3(c[0], c[1], c[2]);
+    const double d[2] = {ry.dx, ry.dy};
+    for (int k = 0; k < 3; ++k) {
+        for (int r = 0; r < 2; ++r) {
+            sh.P[r][k] = M[r][k] - d[r] * M[2][k];
+            sh.Q[r][k] = N[r][k] - d[r] * N[2][k];
+        }
+        sh.P[2][k] = M[2][k];
+        sh.Q[2][k] = N[2][k];
+    }
+    for (int r = 0; r < 2; ++r)
+        sh.c[r] = T[r] - d[r] * T[2];
+    sh.c[2] = T[2];
+    return sh;
 }
 
-// Watertight test in FP64; returns true on a hit and its ray parameter.
-__device__ bool hit64(const ViewDev &v, const Ray64 &ry, int tri, double &s)
+__device__ __forceinline__ double3 sheared64(const ViewDev &v, const Shear64 &sh, int k)
 {
-    const double3 A = vertex64(v, v.i0[tri], ry.t), B = vertex64(v, v.i1[tri], ry.t), C = vertex64(v, v.i2[tri], ry.t);
-    const double ax = A.x - ry.dx * A.z, ay = A.y - ry.dy * A.z;
-    const double bx = B.x - ry.dx * B.z, by = B.y - ry.dy * B.z;
-    const double cx = C.x - ry.dx * C.z, cy = C.y - ry.dy * C.z;
+    const double p[3] = {v.px[k], v.py[k], v.pz[k]};
+    const double w[3] = {v.vx[k], v.vy[k], v.vz[k]};
+    double a[3];
+    for (int r = 0; r < 3; ++r)
+        a[r] = sh.c[r] + sh.P[r][0] * p[0] + sh.P[r][1] * p[1] + sh.P[r][2] * p[2] + sh.Q[r][0] * w[0] +
+               sh.Q[r][1] * w[1] + sh.Q[r][2] * w[2];
+    return make_double3(a[0], a[1], a[2]);
+}
+
+// Watertight test in FP64; on a hit beyond the near plane returns true with
+// the ray parameter as the fraction num / den, den > 0 (the division is left
+// to the caller, who needs it only for the winner).
+__device__ bool hit64(const ViewDev &v, const Shear64 &sh, int tri, double &num, double &den)
+{
+    const double3 A = sheared64(v, sh, v.i0[tri]), B = sheared64(v, sh, v.i1[tri]), C = sheared64(v, sh, v.i2[tri]);
+    const double ax = A.x, ay = A.y, bx = B.x, by = B.y, cx = C.x, cy = C.y;
     const double U = cx * by - cy * bx, V = ax * cy - ay * cx, W = bx * ay - by * ax;
     if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0))
         return false;
     const double det = U + V + W;
     if (det == 0.0)
         return false;
-    s = (U * A.z + V * B.z + W * C.z) / det;
-    return s > (double)v.z_near;
+    const double T = U * A.z + V * B.z + W * C.z;
+    num = det < 0.0 ? -T : T;
+    den = fabs(det);
+    return num > (double)v.z_near * den;
 }
 
-// One warp per flagged pixel.  Sweep 1 runs the FP32 test with the error
-// allowance over the pixel's whole tile bin and finds the nearest hit that
-// FP32 settles ("robust").  Sweep 2 re-evaluates in FP64 every pair that
-// could still beat it: unsettled pairs whose plane lies in front of it and
-// hits tied with it.  Every other pair is a settled miss or a settled hit
-// behind it, so the FP64 minimum over the candidates is the exact winner.
-__global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ views, int nviews,
-                                               const long long *__restrict__ pix_offs,
-                                               const unsigned long long *__restrict__ scan,
-                                               const unsigned long long *__restrict__ tile_cnt,
-                                               const unsigned long long *__restrict__ pairs, const float4 *__restrict__ rec,
-                                               const long long *__restrict__ flag_list,
-                                               unsigned long long *__restrict__ keys, long long cap_pairs, Counters *cnt)
+// Each warp re-decides up to 32 flagged pixels.  Sweep 1 runs the FP32
+// test with the error allowance over the pixel's whole tile bin and finds
+// the nearest hit that FP32 settles ("robust").  Sweep 2 re-evaluates in
+// FP64 every pair that could still beat it: unsettled pairs whose plane
+// lies in front of it and hits tied with it.  Every other pair is a settled
+// miss or a settled hit behind it, so the FP64 minimum over the candidates
+// is the exact winner.
+//
+// The FP32 sweeps of one pixel run across the warp's lanes (one bin entry
+// each), the pixels one after the other; their FP64 candidates go to a
+// per-warp list in shared memory, grouped by pixel.  FP64 runs at a small
+// fraction of the FP32 rate on this part, so the FP64 tests then run with
+// one lane per pixel, in step across the warp: each FP64 instruction serves
+// up to 32 pixels instead of one candidate.  Candidates that do not fit the
+// list are tested at once and kept as the pixel's running best.
+//
+// A bin entry carries a lower bound of the nearest depth its triangle
+// reaches (the depth order key, rounded down); a pair whose bound lies
+// behind the sweep's current limit by more than kKeySlack cannot be nearer
+// (an unsettled pair's plane point lies within the edge allowance, about
+// 1e-5 relative, of the triangle), so both sweeps skip its test.
+constexpr int kRetestWarps = 4;
+constexpr int kRetestList = 512;  // candidates listed per warp and round of 32 pixels
+
+// An FP64 hit kept as the fraction num / den (den > 0; den = 0: none) with
+// its triangle; `better` orders by depth, then by the smaller id.
+struct Hit64 {
+    double num, den;
+    unsigned id;
+};
+
+__device__ __forceinline__ bool better(double num, double den, unsigned id, const Hit64 &b)
+{
+    if (b.den == 0.0)
+        return true;
+    const double l = num * b.den, r = b.num * den;  // num / den vs b.num / b.den
+    return l < r || (l == r && id < b.id);
+}
+
+// The pixel of flag f: its view, column, row, and its tile bin [off, off + n).
+struct RetestPixel {
+    const ViewDev *v;
+    long long g, off, n;
+    int i, j;
+};
+
+__device__ __forceinline__ RetestPixel retest_pixel(const ViewDev *views, int nviews, const long long *pix_offs,
+                                                    const unsigned long long *scan,
+                                                    const unsigned long long *tile_cnt, const long long *flag_list,
+                                                    long long f, long long cap_pairs)
+{
+    RetestPixel px;
+    px.g = flag_list[f];
+    px.v = &views[find_view(pix_offs, nviews, px.g)];
+    const ViewDev &v = *px.v;
+    const long long lin = px.g - v.pix_off;
+    px.j = (int)lin / v.W;  // lin < 2^28
+    px.i = (int)lin - px.j * v.W;
+    const long long tile = v.tile_off + (long long)(px.j / v.S) * v.tiles_x + px.i / v.S;
+    px.off = (long long)(scan[tile] & 0xFFFFFFFFFFull);
+    px.n = min((long long)(tile_cnt[tile] & 0xFFFFFFFFFFull), max(cap_pairs - px.off, 0ll));
+    return px;
+}
+
+__global__ void __launch_bounds__(kRetestWarps * 32) k_retest(const ViewDev *__restrict__ views, int nviews,
+                                                              const long long *__restrict__ pix_offs,
+                                                              const unsigned long long *__restrict__ scan,
+                                                              const unsigned long long *__restrict__ tile_cnt,
+                                                              const unsigned long long *__restrict__ pairs,
+                                                              const float4 *__restrict__ rec,
+                                                              const long long *__restrict__ flag_list,
+                                                              unsigned long long *__restrict__ keys, long long cap_pairs,
+                                                              Counters *cnt)
 {
     // an attempt whose bins overflowed is rerun by the host; its bin counts
     // reach past the entries that were written
     if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
         return;
+    __shared__ unsigned s_list[kRetestWarps][kRetestList];  // candidate triangles, grouped by pixel
+    __shared__ int s_start[kRetestWarps][32], s_count[kRetestWarps][32];
+    __shared__ Hit64 s_best[kRetestWarps][32];  // per pixel: the best of the candidates tested at once
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long nflag = (long long)cnt->flagged;
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long f = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < nflag; f += warps) {
-        const long long g = flag_list[f];
-        const ViewDev &v = views[find_view(pix_offs, nviews, g)];
-        const long long lin = g - v.pix_off;
-        const int j = (int)lin / v.W, i = (int)lin - j * v.W;  // lin < 2^28
-        const long long tile = v.tile_off + (long long)(j / v.S) * v.tiles_x + i / v.S;
-        const long long off = (long long)(scan[tile] & 0xFFFFFFFFFFull);
-        const long long n = min((long long)(tile_cnt[tile] & 0xFFFFFFFFFFull), max(cap_pairs - off, 0ll));
-        float x0, x1, t, dx, dy;
-        pixel_ray(v, i, j, x0, x1, t, dx, dy);
-        const float zn = v.z_near;
-        const unsigned id_base = (unsigned)v.tri_off;
-        // sweep 1: nearest settled hit
-        float rb = INFINITY;
-        for (long long k = lane; k < n; k += 32) {
-            const unsigned gid = (unsigned)pairs[off + k];
-            const float4 *r = rec + (size_t)gid * kRecF4;
-            unsigned long long best = ~0ull;
-            float bd = INFINITY;
-            unsigned hits = 0;
-            bool fl = false;
-            ray_test<true>(r[0], r[1], r[2], r[3], r[5].z, r[5].w, t, dx, dy, zn, gid - id_base, best, bd, hits, fl);
-            if (best != ~0ull && !fl)
-                rb = fminf(rb, bd);
-        }
-        for (int o = 16; o > 0; o >>= 1)
-            rb = fminf(rb, __shfl_xor_sync(0xffffffffu, rb, o));
-        // sweep 2: FP64 over the candidates that could beat it
-        const float lim = rb * (1.f + 2.f * kTieRel);
-        const Ray64 ry = pixel_ray64(v, i, j);
-        double bs = INFINITY;
-        unsigned bid = 0xFFFFFFFFu;
-        for (long long k = lane; k < n; k += 32) {
-            const unsigned gid = (unsigned)pairs[off + k];
-            const float4 *r = rec + (size_t)gid * kRecF4;
-            unsigned long long best = ~0ull;
-            float bd = lim;  // "best so far" = the limit, so fl marks pairs in front of it
-            unsigned hits = 0;
-            bool fl = false;
-            ray_test<true>(r[0], r[1], r[2], r[3], r[5].z, r[5].w, t, dx, dy, zn, gid - id_base, best, bd, hits, fl);
-            if (!fl && best == ~0ull)
-                continue;  // settled miss, or settled hit behind the limit
-            double s;
-            const unsigned id = gid - id_base;
-            if (hit64(v, ry, (int)id, s) && (s < bs || (s == bs && id < bid))) {
-                bs = s;
-                bid = id;
+    const long long nw = (long long)gridDim.x * kRetestWarps;
+    // pixels per warp and round: spread over every warp of the grid (the
+    // pixels of a warp run one after the other), at most 32
+    const long long per = max(1ll, min(32ll, (nflag + nw - 1) / nw));
+    for (long long f0 = ((long long)blockIdx.x * kRetestWarps + w) * per; f0 < nflag; f0 += nw * per) {
+        const int npx = (int)min(per, nflag - f0);
+        int used = 0;  // list entries in use (the same in every lane)
+        for (int q = 0; q < npx; ++q) {
+            const RetestPixel px = retest_pixel(views, nviews, pix_offs, scan, tile_cnt, flag_list, f0 + q, cap_pairs);
+            const ViewDev &v = *px.v;
+            float x0, x1, t, dx, dy;
+            pixel_ray(v, px.i, px.j, x0, x1, t, dx, dy);
+            const float zn = v.z_near;
+            const unsigned id_base = (unsigned)v.tri_off;
+            // sweep 1: nearest settled hit (each lane a share of the bin)
+            float rb = INFINITY;
+            for (long long k = lane; k < px.n; k += 32) {
+                const unsigned long long ent = pairs[px.off + k];
+                if (depth_from_order_key((unsigned)(ent >> 32)) > rb * (1.f + kKeySlack))
+                    continue;  // behind this lane's nearest settled hit
+                const unsigned gid = (unsigned)ent;
+                const float4 *r = rec + (size_t)gid * kRecF4;
+                unsigned long long best = ~0ull;
+                float bd = INFINITY;
+                unsigned hits = 0;
+                bool fl = false;
+                ray_test<true>(r[0], r[1], r[2], r[3], r[5].z, r[5].w, t, dx, dy, zn, gid - id_base, best, bd, hits,
+                               fl);
+                if (best != ~0ull && !fl)
+                    rb = fminf(rb, bd);
+            }
+            rb = warp_minf(rb);
+            // sweep 2: list the pairs that could beat it
+            const float lim = rb * (1.f + 2.f * kTieRel);
+            const int start = used;
+            Hit64 ib{0.0, 0.0, 0xFFFFFFFFu};
+            for (long long k0 = 0; k0 < px.n; k0 += 32) {
+                const long long k = k0 + lane;
+                bool cand = false;
+                unsigned id = 0u;
+                if (k < px.n) {
+                    const unsigned long long ent = pairs[px.off + k];
+                    if (depth_from_order_key((unsigned)(ent >> 32)) <= lim * (1.f + kKeySlack)) {
+                        const unsigned gid = (unsigned)ent;
+                        const float4 *r = rec + (size_t)gid * kRecF4;
+                        unsigned long long best = ~0ull;
+                        float bd = lim;  // "best so far" = the limit, so fl marks pairs in front of it
+                        unsigned hits = 0;
+                        bool fl = false;
+                        ray_test<true>(r[0], r[1], r[2], r[3], r[5].z, r[5].w, t, dx, dy, zn, gid - id_base, best, bd,
+                                       hits, fl);
+                        cand = fl || best != ~0ull;  // not a settled miss, nor a settled hit behind the limit
+                        id = gid - id_base;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, cand);
+                if (!m)
+                    continue;
+                if (used + __popc(m) <= kRetestList) {
+                    if (cand)
+                        s_list[w][used + __popc(m & ((1u << lane) - 1u))] = id;
+                    used += __popc(m);
+                } else if (cand) {  // the list is full: test now
+                    const Shear64 sh = shear64(v, pixel_ray64(v, px.i, px.j));
+                    double num, den;
+                    if (hit64(v, sh, (int)id, num, den) && better(num, den, id, ib))
+                        ib = Hit64{num, den, id};
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double on = __shfl_xor_sync(0xffffffffu, ib.num, o);
+                const double od = __shfl_xor_sync(0xffffffffu, ib.den, o);
+                const unsigned oi = __shfl_xor_sync(0xffffffffu, ib.id, o);
+                if (od > 0.0 && better(on, od, oi, ib))
+                    ib = Hit64{on, od, oi};
+            }
+            if (lane == 0) {
+                s_start[w][q] = start;
+                s_count[w][q] = used - start;
+                s_best[w][q] = ib;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-            const unsigned oid = __shfl_xor_sync(0xffffffffu, bid, o);
-            if (os < bs || (os == bs && oid < bid)) {
-                bs = os;
-                bid = oid;
+        __syncwarp();
+        // the listed candidates in FP64, one lane per pixel
+        if (lane < npx) {
+            const RetestPixel px = retest_pixel(views, nviews, pix_offs, scan, tile_cnt, flag_list, f0 + lane,
+                                                cap_pairs);
+            const ViewDev &v = *px.v;
+            Hit64 b = s_best[w][lane];
+            const int c0 = s_start[w][lane], c1 = c0 + s_count[w][lane];
+            if (c1 > c0) {
+                const Shear64 sh = shear64(v, pixel_ray64(v, px.i, px.j));
+                for (int c = c0; c < c1; ++c) {
+                    const unsigned id = s_list[w][c];
+                    double num, den;
+                    if (hit64(v, sh, (int)id, num, den) && better(num, den, id, b))
+                        b = Hit64{num, den, id};
+                }
             }
-        }
-        if (lane == 0) {
+            const unsigned bid = b.den > 0.0 ? b.id : 0xFFFFFFFFu;
+            const double bs = b.den > 0.0 ? b.num / b.den : 0.0;
             const unsigned long long key = bid == 0xFFFFFFFFu ? ~0ull : pack_key((float)bs, bid);
-            const unsigned long long old = keys[g];
+            const unsigned long long old = keys[px.g];
             if (old != ~0ull && bid != 0xFFFFFFFFu && (unsigned)(old & 0xFFFFFFFFull) == bid) {
                 // same winner: record the FP32 depth error against FP64
                 const double d32 = (double)__uint_as_float((unsigned)(old >> 32));
@@ -518,10 +657,11 @@ __global__ void __launch_bounds__(256) k_retest(const ViewDev *__restrict__ view
                 atomicMax(&cnt->depth_err_bits, __float_as_uint(rel));
             }
             if (old != key) {
-                keys[g] = key;
+                keys[px.g] = key;
                 atomicAdd(&cnt->changed, 1ull);
             }
         }
+        __syncwarp();  // the list is reused by the next round
     }
 }
 
@@ -532,7 +672,7 @@ int retest_grid()
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g = sms * 4;
+        g = sms * 8;
     }
     return g;
 }
@@ -542,8 +682,8 @@ cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix
                           const long long *flag_list, unsigned long long *keys, long long cap_pairs, Counters *cnt,
                           cudaStream_t st)
 {
-    k_retest<<<retest_grid(), 256, 0, st>>>(views, nviews, pix_offs, scan, tile_cnt, pairs, rec, flag_list, keys,
-                                            cap_pairs, cnt);
+    k_retest<<<retest_grid(), kRetestWarps * 32, 0, st>>>(views, nviews, pix_offs, scan, tile_cnt, pairs, rec,
+                                                          flag_list, keys, cap_pairs, cnt);
     return cudaGetLastError();
 }
 
