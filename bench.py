@@ -389,32 +389,49 @@ def our_arm(args, rank, world):
     pix = sum(npx)
     value, mean_ms = aggregate(sum(step_ms) / len(step_ms), pix, dist, "cuda")
 
-    # end to end through the C ABI with host buffers: scene arrays in from
-    # pinned host memory, shaded images and gradients back to pinned host
+    # end to end through the public API with host buffers, as a training
+    # loop would run it: every step the scene arrays and the upstream image
+    # gradient go up from pinned host memory, the scene is updated, the frame
+    # graph (forward + adjoint) replays, and the shaded images and the
+    # gradients come back to pinned host memory, with the replay's status read
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         hsc = [(pin(sc.pos), pin(sc.vel), pin(sc.col)) for sc in wl.scenes]
+        dsc = [tuple(torch.empty_like(x, device="cuda") for x in a) for a in hsc]
         hrgb = [torch.empty(3 * n, dtype=torch.float32).pin_memory() for n in npx]
         hg = [g.cpu().pin_memory() for g in grad]
         hd = [tuple(torch.zeros(3 * sc.V).pin_memory() for _ in range(3)) for sc in wl.scenes]
-        ent_h = [(hv[k], v, ids[k], None, hrgb[k], tiles[k]) for k, v in enumerate(views)]
 
         def e2e_step():
-            for h, a in zip(handles, hsc):
-                B.pr_scene_update(h, *a)
-            B.pr_rasterize_batch(ws, ent_h, params)
-            for k, v in enumerate(views):
-                d = hd[wl.scene_of[k]]
-                B.pr_backward(hv[k], v, ids[k], hg[k], d[0], d[1], d[2])
+            for a, d in zip(hsc, dsc):
+                for x, y in zip(a, d):
+                    y.copy_(x, non_blocking=True)
+            for g, hgk in zip(grad, hg):
+                g.copy_(hgk, non_blocking=True)
+            for h, d in zip(handles, dsc):
+                B.pr_scene_update(h, *d)
+            for gs in grads:
+                for x in gs:
+                    x.zero_()
+            B.pr_graph_enqueue(graph)
+            for r, hr in zip(rgb, hrgb):
+                hr.copy_(r, non_blocking=True)
+            for gs, hgs in zip(grads, hd):
+                for x, y in zip(gs, hgs):
+                    y.copy_(x, non_blocking=True)
+            stream.synchronize()
+            B.pr_graph_status(graph)
         for _ in range(2):
             e2e_step()
         ems = timed(e2e_step, max(3, args.steps // 2))
         sv = sum(sc.V for sc in wl.scenes)
-        h2d = 3 * sv * 12 + sum(g.numel() * 4 for g in hg) + sum(3 * 3 * wl.scenes[si].V * 4 for si in wl.scene_of)
-        d2h = sum(x.numel() * 4 for x in hrgb) + sum(3 * 3 * wl.scenes[si].V * 4 for si in wl.scene_of)
+        h2d = 3 * sv * 12 + sum(g.numel() * 4 for g in hg)
+        d2h = sum(x.numel() * 4 for x in hrgb) + 3 * sv * 12
         e2e = {"value": world * pix / (statistics.mean(ems) * 1e-3) / 1e6, "unit": "Mpix/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "path": "pinned host -> device copies, pr_scene_update, pr_graph_enqueue of the training frame, "
+                       "device -> pinned host copies of the images and gradients, synchronise, pr_graph_status"}
 
     # rooflines: stage (c) k_fragment (FP32 ALU) and the training frame's
     # shading + adjoint kernel k_shade<1> (HBM); the bench line's "roofline"
