@@ -145,10 +145,11 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------- reference arm
 
-def cpu_oracle_sample(wl: Workload, seconds: float, seed: int = 11):
+def cpu_oracle_sample(wl: Workload, seconds: float, seed: int = 11, pixels: int = 0):
     """Time the FP64 oracle (forward render + shade + gradient, every
     triangle of the view's scene tested per pixel) on a seeded pixel sample
-    spread over the workload's views, sized to about `seconds` of work."""
+    spread over the workload's views, sized to about `seconds` of work (or
+    of `pixels` pixels when given, without the sizing runs)."""
     from oracle import oracle as O
     O.build()
     rng = np.random.default_rng(seed)
@@ -165,6 +166,9 @@ def cpu_oracle_sample(wl: Workload, seconds: float, seed: int = 11):
             tests += pix.size * sc.T
         return time.perf_counter() - t0, tests, per * len(wl.views)
 
+    if pixels > 0:
+        dt, tests, n = run(pixels)
+        return {"pixels": n, "seconds": dt, "tests": tests, "cores": O.num_threads()}
     # calibrate on growing samples until one takes a tenth of the budget (a
     # tiny first sample is dominated by per-call setup and overstates the cost)
     n = max(64, 4 * len(wl.views))
@@ -183,9 +187,11 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     cpu_s = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    # size the per-step sample once, then every step renders that many pixels
+    n = cpu_oracle_sample(wl, cpu_s)["pixels"]
     for _ in range(args.warmup):
-        cpu_oracle_sample(wl, cpu_s / 4)
-    runs = [cpu_oracle_sample(wl, cpu_s) for _ in range(args.steps)]
+        cpu_oracle_sample(wl, cpu_s, pixels=max(1, n // 4))
+    runs = [cpu_oracle_sample(wl, cpu_s, pixels=n) for _ in range(args.steps)]
     px = sum(r["pixels"] for r in runs)
     sec = sum(r["seconds"] for r in runs)
     val = px / sec / 1e6
