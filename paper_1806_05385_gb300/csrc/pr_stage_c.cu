@@ -238,17 +238,16 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
             __syncwarp();
             unsigned live = __ballot_sync(0xffffffffu, take);
             bool stop = stopm != 0u;
-            int since = 0;
             while (live) {
                 const int k = __ffs(live) - 1;
                 live &= live - 1u;
-                if (++since == 8) {  // the bests have moved on: re-check the cut
-                    since = 0;
-                    wmax = warp_maxf(fmaxf(ok0 ? bd0 : 0.f, ok1 ? bd1 : 0.f)) * cull;
-                    if (__shfl_sync(0xffffffffu, key, k) * 0.99999f > wmax) {
-                        stop = true;
-                        break;
-                    }
+                // the bests move with every test: re-check the cut before each
+                // (every 8 tests instead: 0.098 ms against 0.089 on the HMD
+                // frame, 0.385 against 0.276 ms on the 1M-triangle frame)
+                wmax = warp_maxf(fmaxf(ok0 ? bd0 : 0.f, ok1 ? bd1 : 0.f)) * cull;
+                if (__shfl_sync(0xffffffffu, key, k) * 0.99999f > wmax) {
+                    stop = true;
+                    break;
                 }
                 const float4 r0 = wrec[k * kStageF4 + 0], r1 = wrec[k * kStageF4 + 1];
                 const float4 r2 = wrec[k * kStageF4 + 2], r3 = wrec[k * kStageF4 + 3];
