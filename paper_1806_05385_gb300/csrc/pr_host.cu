@@ -587,13 +587,6 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     Counters *cnt = ws->counters.as<Counters>();
     unsigned long long *state_a = ws->sums.as<unsigned long long>();
     unsigned long long *state_b = state_a + scan_block_sums_needed(P.ttot);
-    // one launch clears the counters, queue heads, tile counts and cursors,
-    // both scans' tickets and flags, the FP64 flags, and sets the keys to ~0
-    PR_TRY(launch_frame_init(cnt, ws->heads.as<int>(), ws->tile_cnt.as<unsigned long long>(), ws->fill.as<unsigned>(),
-                             P.ntiles, state_a, scan_state_words(P.ttot), state_b, scan_state_words(P.ntiles),
-                             ws->flag_bits.as<unsigned>(), P.any_fp64 ? (P.npix + 31) / 32 + 1 : 0,
-                             ws->keys.as<unsigned long long>(), P.npix, st));
-
     float4 *rec = ws->rec.as<float4>(), *hp = ws->hp.as<float4>(), *tile_box = ws->tile_box.as<float4>();
     int4 *tbox = ws->tbox.as<int4>();
     unsigned long long *tile_cnt = ws->tile_cnt.as<unsigned long long>(), *scan = ws->scan.as<unsigned long long>();
@@ -609,7 +602,13 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     };
     unsigned long long *cand = ws->cand.as<unsigned long long>(), *cand_off = ws->cand_off.as<unsigned long long>();
     PR_TRY(mark(0));
-    PR_TRY(launch_tile_boxes(dv, n, tile_offs, P.ntiles, tile_box, st));
+    // one launch clears the counters, queue heads, tile counts and cursors,
+    // both scans' tickets and flags, the FP64 flags, sets the keys to ~0 and
+    // computes the tiles' display boxes
+    PR_TRY(launch_frame_init(dv, n, tile_offs, tile_box, cnt, ws->heads.as<int>(), tile_cnt, ws->fill.as<unsigned>(),
+                             P.ntiles, state_a, scan_state_words(P.ttot), state_b, scan_state_words(P.ntiles),
+                             ws->flag_bits.as<unsigned>(), P.any_fp64 ? (P.npix + 31) / 32 + 1 : 0,
+                             ws->keys.as<unsigned long long>(), P.npix, st));
     int *binned = ws->binned.as<int>();
     PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, binned, cnt, st));
     if (P.any_paper_fov)

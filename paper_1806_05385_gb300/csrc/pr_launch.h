@@ -14,9 +14,7 @@ cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int *idx,
 cudaError_t launch_planes3(const float *src, long long V, float *dst, cudaStream_t st);
 cudaError_t launch_scene_check(const float *soa, long long V, Counters *cnt, cudaStream_t st);
 
-// stage (a): display boxes of the framebuffer tiles, per-triangle bounds
-cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
-                              float4 *tile_box, cudaStream_t st);
+// stage (a): per-triangle bounds (the tiles' display boxes come with the frame init)
 // binned: the triangles with candidate tiles are appended here (cnt->binned)
 cudaError_t launch_bound(const ViewDev *views, int nviews, const long long *tri_offs, long long ttot, float4 *rec,
                          float4 *hp, int4 *tbox, unsigned long long *cand, int *binned, Counters *cnt,
@@ -41,7 +39,9 @@ cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsign
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
                         int seg, Counters *cnt, cudaStream_t st, bool state_zeroed = false,
                         const int *gather = nullptr, const unsigned long long *n_dev = nullptr);
-cudaError_t launch_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
+// the start of a frame: clears, keys to ~0, tile display boxes (one launch)
+cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long *tile_offs, float4 *tile_box,
+                              Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
                               unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
                               long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
                               long long npix, cudaStream_t st);

@@ -261,16 +261,14 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     // before the call returns, so the stack buffers may go out of scope
     NA_TRY(cudaMemcpyAsync(dv, &v, sizeof v, cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(doffs, offs, sizeof offs, cudaMemcpyHostToDevice, st));
-    // what must start at zero, and the keys at ~0 (the arena keeps the
-    // previous call's contents)
-    NA_TRY(launch_frame_init(cnt, heads, tile_cnt, fill, nt, state_a, scan_state_words(T), state_b,
-                             scan_state_words(nt), nullptr, 0, keys, np, st));
-
     const long long *tri_offs = doffs, *tile_offs = doffs + 2, *pix_offs = doffs + 4;
+    // what must start at zero, the keys at ~0 (the arena keeps the previous
+    // call's contents), and the tiles' display boxes
+    NA_TRY(launch_frame_init(dv, 1, tile_offs, tile_box, cnt, heads, tile_cnt, fill, nt, state_a, scan_state_words(T),
+                             state_b, scan_state_words(nt), nullptr, 0, keys, np, st));
     NA_TRY(launch_scene_soa(pos, vel, col, V, soa, st));
     NA_TRY(launch_scene_idx(tri, T, V, idx, cnt, st));
     NA_TRY(launch_scene_check(soa, V, cnt, st));
-    NA_TRY(launch_tile_boxes(dv, 1, tile_offs, nt, tile_box, st));
     int *binned = (int *)(arena + o_binned);
     NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, binned, cnt, st));
     if (fov_bound != PR_FOV_SECTOR && (view->mode == PR_FOVEATED || view->mode == PR_BOTH))

@@ -111,12 +111,9 @@ __device__ __forceinline__ void tile_pixel_box(const ViewDev &v, long long lt, f
 
 // Display box of every framebuffer tile: the box of its pixel centres, or
 // for foveated views the box of their image under q.
-__global__ void k_tile_boxes(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ tile_offs,
-                             long long ntiles, float4 *__restrict__ tile_box)
+__device__ __forceinline__ float4 tile_display_box(const ViewDev *views, int nviews, const long long *tile_offs,
+                                                   long long g)
 {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ntiles)
-        return;
     const ViewDev &v = views[find_view(tile_offs, nviews, g)];
     float u0, u1, w0, w1;
     tile_pixel_box(v, g - v.tile_off, u0, u1, w0, w1);
@@ -126,15 +123,7 @@ __global__ void k_tile_boxes(const ViewDev *__restrict__ views, int nviews, cons
     else
         b = make_float4(u0, u1, w0, w1);
     const float e = kEpsDisp;
-    tile_box[g] = make_float4(b.x - e, b.y + e, b.z - e, b.w + e);
-}
-
-cudaError_t launch_tile_boxes(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
-                              float4 *tile_box, cudaStream_t st)
-{
-    if (ntiles > 0)
-        k_tile_boxes<<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(views, nviews, tile_offs, ntiles, tile_box);
-    return cudaGetLastError();
+    return make_float4(b.x - e, b.y + e, b.z - e, b.w + e);
 }
 
 // ---------------------------------------------------------------- bound
@@ -1071,15 +1060,17 @@ cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsign
 
 // ---------------------------------------------------------------- frame init
 
-// Clears what a frame accumulates into, in one launch: the counters, the
-// work-queue heads, the per-tile counts and fill cursors, the tickets and
-// flags of two scans' look-back state (scan_state_words of each), the FP64
-// flag bitmap (nflag words, may be 0), and sets
-// every pixel's depth|id key to "no hit" (~0).
-__global__ void k_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
-                             unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
-                             long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
-                             long long npix)
+// The start of a frame, in one launch: clears what the frame accumulates
+// into -- the counters, the work-queue heads, the per-tile counts and fill
+// cursors, the tickets and flags of two scans' look-back state
+// (scan_state_words of each), the FP64 flag bitmap (nflag words, may be 0)
+// -- sets every pixel's depth|id key to "no hit" (~0), and computes every
+// tile's display box (stage a: the image of its pixel centres under q).
+__global__ void k_frame_init(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ tile_offs,
+                             float4 *__restrict__ tile_box, Counters *cnt, int *heads, unsigned long long *tile_cnt,
+                             unsigned *fill, long long ntiles, unsigned long long *state_a, long long nstate_a,
+                             unsigned long long *state_b, long long nstate_b, unsigned *flag_bits, long long nflag,
+                             unsigned long long *keys, long long npix)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1090,6 +1081,7 @@ __global__ void k_frame_init(Counters *cnt, int *heads, unsigned long long *tile
     for (long long k = g; k < ntiles; k += stride) {
         tile_cnt[k] = 0ull;
         fill[k] = 0u;
+        tile_box[k] = tile_display_box(views, nviews, tile_offs, k);
     }
     for (long long k = g; k < nstate_a; k += stride)
         state_a[k] = 0ull;
@@ -1105,7 +1097,8 @@ __global__ void k_frame_init(Counters *cnt, int *heads, unsigned long long *tile
         keys[npix - 1] = ~0ull;
 }
 
-cudaError_t launch_frame_init(Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
+cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long *tile_offs, float4 *tile_box,
+                              Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
                               unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
                               long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
                               long long npix, cudaStream_t st)
@@ -1117,8 +1110,8 @@ cudaError_t launch_frame_init(Counters *cnt, int *heads, unsigned long long *til
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms * 8;
     }
-    k_frame_init<<<grid, 256, 0, st>>>(cnt, heads, tile_cnt, fill, ntiles, state_a, nstate_a, state_b, nstate_b,
-                                       flag_bits, nflag, keys, npix);
+    k_frame_init<<<grid, 256, 0, st>>>(views, nviews, tile_offs, tile_box, cnt, heads, tile_cnt, fill, ntiles, state_a,
+                                       nstate_a, state_b, nstate_b, flag_bits, nflag, keys, npix);
     return cudaGetLastError();
 }
 
