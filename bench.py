@@ -483,9 +483,10 @@ def our_arm(args, rank, world):
                "tests_per_s": r["tests"] / r["seconds"]}
 
     n_classes = len({(t, wl.fp64) for t in tiles})
-    # frame init (with the tile boxes), bound, 2 scans, bin count, bin scatter, items, run sort, one
-    # fragment launch per (tile, precision) class, [FP64 re-test], resolve + shade + adjoint
-    kernels_step = 9 + n_classes + (1 if wl.fp64 else 0)
+    # frame init (with the tile boxes), bound, candidate scan, bin count, tile scan (with the work
+    # items), bin scatter, run sort, one fragment launch per (tile, precision) class, [FP64 re-test],
+    # resolve + shade + adjoint
+    kernels_step = 8 + n_classes + (1 if wl.fp64 else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",

@@ -619,12 +619,18 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(launch_bin_count(dv, n, tri_offs, P.ttot, binned, cand_off, rec, hp, tbox, tile_box, tile_cnt,
                             ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), ws->cap_pairs, cnt,
                             st));
-    PR_TRY(launch_scan(tile_cnt, scan, state_b, P.ntiles, seg, cnt, st, true));
+    // the scan of the tile counts also emits the work items
+    ItemsOut io;
+    io.views = dv;
+    io.nviews = n;
+    io.tile_offs = tile_offs;
+    io.items = ws->items.as<int4>();
+    io.cap_items = ws->cap_items;
+    io.cap_pairs = ws->cap_pairs;
+    PR_TRY(launch_scan(tile_cnt, scan, state_b, P.ntiles, seg, cnt, st, true, nullptr, nullptr, &io));
     PR_TRY(launch_bin_scatter(ws->hit_entry.as<unsigned long long>(), ws->hit_tile.as<unsigned>(), scan,
                               ws->fill.as<unsigned>(), ws->pairs.as<unsigned long long>(), ws->cap_pairs, P.ntiles, cnt,
                               st));
-    PR_TRY(launch_items(dv, n, tile_offs, P.ntiles, tile_cnt, scan, ws->items.as<int4>(), ws->cap_items,
-                        ws->cap_pairs, seg, cnt, st));
     PR_TRY(launch_sort_items(ws->items.as<int4>(), scan, P.ntiles, ws->cap_items, seg,
                              ws->pairs.as<unsigned long long>(), cnt, st));
     PR_TRY(mark(2));

@@ -34,11 +34,21 @@ cudaError_t launch_bin_count(const ViewDev *views, int nviews, const long long *
 cudaError_t launch_bin_scatter(const unsigned long long *hit_entry, const unsigned *hit_tile,
                                const unsigned long long *scan, unsigned int *fill, unsigned long long *pairs,
                                long long cap_pairs, long long ntiles, Counters *cnt, cudaStream_t st);
+// Where the scan of the tile counts writes the fragment stage's work items.
+struct ItemsOut {
+    const ViewDev *views = nullptr;
+    int nviews = 0;
+    const long long *tile_offs = nullptr;
+    int4 *items = nullptr;
+    long long cap_items = 0, cap_pairs = 0;
+};
 // state_zeroed: the caller cleared the ticket and flags (state[0, 1 + nb)).
 // gather: scan in[gather[i]]; n_dev: the count is min(*n_dev, n) (device).
+// items (with seg > 0): also emit each tile's work items and the totals.
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
                         int seg, Counters *cnt, cudaStream_t st, bool state_zeroed = false,
-                        const int *gather = nullptr, const unsigned long long *n_dev = nullptr);
+                        const int *gather = nullptr, const unsigned long long *n_dev = nullptr,
+                        const ItemsOut *items = nullptr);
 // the start of a frame: clears, keys to ~0, tile display boxes (one launch)
 cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long *tile_offs, float4 *tile_box,
                               Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
@@ -48,9 +58,6 @@ cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long 
 size_t scan_block_sums_needed(long long n);
 // words of a scan's state that must start at zero (ticket and flags)
 long long scan_state_words(long long n);
-cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
-                         const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
-                         long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st);
 // sorts every item's run of bin entries (nearest first); runs <= kMaxSeg
 cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan, long long ntiles, long long cap_items,
                               int seg, unsigned long long *pairs, const Counters *cnt, cudaStream_t st);

@@ -276,9 +276,15 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_scan(cand, cand_off, state_a, T, 0, cnt, st, true, binned, &cnt->binned));
     NA_TRY(launch_bin_count(dv, 1, tri_offs, T, binned, cand_off, rec, hp, tbox, tile_box, tile_cnt, hit_entry,
                             hit_tile, cap_pairs, cnt, st));
-    NA_TRY(launch_scan(tile_cnt, scan, state_b, nt, seg, cnt, st, true));
+    ItemsOut io;  // the scan of the tile counts also emits the work items
+    io.views = dv;
+    io.nviews = 1;
+    io.tile_offs = tile_offs;
+    io.items = items;
+    io.cap_items = cap_items;
+    io.cap_pairs = cap_pairs;
+    NA_TRY(launch_scan(tile_cnt, scan, state_b, nt, seg, cnt, st, true, nullptr, nullptr, &io));
     NA_TRY(launch_bin_scatter(hit_entry, hit_tile, scan, fill, pairs, cap_pairs, nt, cnt, st));
-    NA_TRY(launch_items(dv, 1, tile_offs, nt, tile_cnt, scan, items, cap_items, cap_pairs, seg, cnt, st));
     NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, cnt, st));
     NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, pairs, rec, keys, nullptr,
                            nullptr, cnt, fragment_grid(tile, false), st));

@@ -1183,11 +1183,36 @@ __device__ __forceinline__ void store_volatile(unsigned long long *p, unsigned l
 // inclusive prefixes; the ticket and flags start at zero.  gather: element
 // i is in[gather[i]] (else in[i]).  n_dev: the element count is
 // min(*n_dev, n), known on the device only; tiles past it leave at once.
+// Emits the work items of tile g from its bin count n and its exclusive
+// prefix (bin entries, low 40 bits; work items, high 24): the bin cut into
+// runs of at most seg triangles, item = (view, tile in view, first entry,
+// end entry).  Runs past the bin buffer (its scatter overflowed) are clamped
+// to it, so the frame stays in bounds; the overflow status reruns it.
+__device__ __forceinline__ void emit_items(const ItemsOut &io, long long g, long long n, unsigned long long pre,
+                                           int seg, Counters *cnt)
+{
+    if (n == 0)
+        return;
+    const int vi = find_view(io.tile_offs, io.nviews, g);
+    const long long lt = g - io.views[vi].tile_off;
+    const long long off = (long long)(pre & 0xFFFFFFFFFFull), ioff = (long long)(pre >> 40);
+    const long long nit = (n + seg - 1) / seg;
+    for (long long q = 0; q < nit; ++q) {
+        const long long b0 = min(off + q * seg, io.cap_pairs), b1 = min(off + min(n, (q + 1) * seg), io.cap_pairs);
+        if (ioff + q < io.cap_items)
+            io.items[ioff + q] = make_int4(vi, (int)lt, (int)b0, (int)b1);
+        else
+            atomicOr(&cnt->status, ST_OVERFLOW_ITEMS);
+    }
+}
+
+template <bool kItems>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long *__restrict__ in,
                                                       const int *__restrict__ gather,
                                                       const unsigned long long *__restrict__ n_dev,
                                                       unsigned long long *__restrict__ out, long long n, int seg,
-                                                      unsigned long long *state, long long nb, Counters *cnt)
+                                                      unsigned long long *state, long long nb, Counters *cnt,
+                                                      ItemsOut io)
 {
     unsigned long long *flags = state + 1, *agg = state + 1 + nb, *inc = state + 1 + 2 * nb;
     __shared__ long long s_tile;
@@ -1274,14 +1299,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
     const unsigned long long excl = s_excl;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        if (base + k < n)
+        if (base + k < n) {
             out[base + k] = excl + run;
+            if (kItems)
+                emit_items(io, base + k, (long long)(v[k] & 0xFFFFFFFFFFull), excl + run, seg, cnt);
+        }
         run += v[k];
     }
     const bool holds_end =
         (n >= tile * kScanBlock && n < (tile + 1) * kScanBlock) || (tile == nb - 1 && n == nb * kScanBlock);
-    if (threadIdx.x == 0 && holds_end)
+    if (threadIdx.x == 0 && holds_end) {
         out[n] = excl + total;
+        if (kItems) {
+            cnt->pairs_total = (excl + total) & 0xFFFFFFFFFFull;
+            cnt->items_total = (excl + total) >> 40;
+        }
+    }
 }
 
 long long scan_state_words(long long n)
@@ -1297,7 +1330,7 @@ size_t scan_block_sums_needed(long long n)
 
 cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, unsigned long long *state, long long n,
                         int seg, Counters *cnt, cudaStream_t st, bool state_zeroed, const int *gather,
-                        const unsigned long long *n_dev)
+                        const unsigned long long *n_dev, const ItemsOut *items)
 {
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) {
@@ -1309,45 +1342,15 @@ cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, u
         if (e != cudaSuccess)
             return e;
     }
-    k_scan<<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt);
+    if (items && seg > 0)
+        k_scan<true><<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt, *items);
+    else
+        k_scan<false><<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt,
+                                                             ItemsOut{});
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- items
-
-// Work items of the persistent fragment kernel: each non-empty tile's bin
-// cut into runs of at most seg triangles; item = (view, tile in view,
-// first entry, end entry).
-__global__ void k_items(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ tile_offs,
-                        long long ntiles, const unsigned long long *__restrict__ tile_cnt,
-                        const unsigned long long *__restrict__ scan, int4 *__restrict__ items, long long cap_items,
-                        long long cap_pairs, int seg, Counters *cnt)
-{
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g == 0) {
-        cnt->pairs_total = scan[ntiles] & 0xFFFFFFFFFFull;
-        cnt->items_total = scan[ntiles] >> 40;
-    }
-    if (g >= ntiles)
-        return;
-    const long long n = (long long)(tile_cnt[g] & 0xFFFFFFFFFFull);
-    if (n == 0)
-        return;
-    const int vi = find_view(tile_offs, nviews, g);
-    const long long lt = g - views[vi].tile_off;
-    const long long off = (long long)(scan[g] & 0xFFFFFFFFFFull);
-    const long long ioff = (long long)(scan[g] >> 40);
-    const long long nit = (n + seg - 1) / seg;
-    for (long long q = 0; q < nit; ++q) {
-        // runs past the bin buffer (its scatter overflowed) are clamped to
-        // it, so the frame stays in bounds; the overflow status reruns it
-        const long long b0 = min(off + q * seg, cap_pairs), b1 = min(off + min(n, (q + 1) * seg), cap_pairs);
-        if (ioff + q < cap_items)
-            items[ioff + q] = make_int4(vi, (int)lt, (int)b0, (int)b1);
-        else
-            atomicOr(&cnt->status, ST_OVERFLOW_ITEMS);
-    }
-}
+// ---------------------------------------------------------------- run sort
 
 // Sorts the bin run of every work item by depth key, nearest first, so the
 // fragment stage can stop a run at the first triangle that lies behind
@@ -1498,16 +1501,6 @@ cudaError_t launch_sort_items(const int4 *items, const unsigned long long *scan,
         k_sort_items<true><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs, cnt);
     else
         k_sort_items<false><<<grid, kSortWarps * 32, 0, st>>>(items, scan, ntiles, cap_items, pairs, cnt);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_items(const ViewDev *views, int nviews, const long long *tile_offs, long long ntiles,
-                         const unsigned long long *tile_cnt, const unsigned long long *scan, int4 *items,
-                         long long cap_items, long long cap_pairs, int seg, Counters *cnt, cudaStream_t st)
-{
-    const long long n = ntiles > 0 ? ntiles : 1;
-    k_items<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(views, nviews, tile_offs, ntiles, tile_cnt, scan, items,
-                                                         cap_items, cap_pairs, seg, cnt);
     return cudaGetLastError();
 }
 
