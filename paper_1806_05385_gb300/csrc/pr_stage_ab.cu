@@ -1431,8 +1431,8 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_items(const int4 *__re
                                                                 unsigned long long *__restrict__ pairs,
                                                                 const Counters *__restrict__ cnt)
 {
-    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS))
-        return;  // an overflowed attempt is rerun; its bins are incomplete
+    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_TIMEOUT))
+        return;  // an overflowed attempt (rerun) or a scan that gave up its wait (an error): bins incomplete
     __shared__ unsigned s_gid[kSortWarps][kSortRegMax];
     __shared__ unsigned long long s_run[kSortWarps][kLong ? kMaxSeg : 1];
     const long long nitems = min((long long)(scan[ntiles] >> 40), cap_items);

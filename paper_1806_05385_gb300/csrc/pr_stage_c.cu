@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
     __shared__ long long s_item[2];
 
     // an attempt whose bins overflowed is rerun by the host: entries of the
-    // dropped hits were never written, so nothing here may read the bins
-    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS))
+    // dropped hits were never written, so nothing here may read the bins;
+    // the same after a scan that gave up its wait (the frame is an error)
+    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_TIMEOUT))
         return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ci = (warp % WPR) * 8 + (lane & 7);
@@ -538,8 +539,8 @@ __global__ void __launch_bounds__(kRetestWarps * 32) k_retest(const ViewDev *__r
                                                               Counters *cnt)
 {
     // an attempt whose bins overflowed is rerun by the host; its bin counts
-    // reach past the entries that were written
-    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
+    // reach past the entries that were written (a scan timeout: the same)
+    if (cnt->status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS | ST_TIMEOUT))
         return;
     __shared__ unsigned s_list[kRetestWarps][kRetestList];  // candidate triangles, grouped by pixel
     __shared__ int s_start[kRetestWarps][32], s_count[kRetestWarps][32];
