@@ -378,6 +378,14 @@ pr_status pr_debug_bounds(const pr_scene *scene, int32_t *pix_box, float *t_rang
  * the rolling scan never meets the triangle.  For unit tests. */
 int32_t pr_debug_catch_interval(const pr_view *view, const float *S, const float *E, float *t_out);
 
+/* Failure detection of the single-pass scan's bounded wait, for tests: runs
+ * a two-tile scan as one block whose predecessor tile never runs, so its
+ * look-back wait runs out (after a short limit of polls).  Returns
+ * PR_ERR_TIMEOUT when the kernel reported the timeout and finished (the
+ * expected outcome; the context stays usable), PR_OK if it did not.  It
+ * allocates and frees about 130 KB of device memory. */
+pr_status pr_debug_scan_timeout(void *stream);
+
 /* Measures the FP32 fused multiply-add throughput of the current device
  * (TFLOP/s, best of three timed launches of independent FMA chains on every
  * SM, after one warm-up launch) on stream; it allocates and frees a 4 KB

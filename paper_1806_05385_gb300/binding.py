@@ -31,7 +31,8 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_graph_launch", "pr_graph_free", "pr_scene_stats", "pr_workspace_stats", "pr_debug_bounds",
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
            "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
-           "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status", "pr_measure_fp32_peak")
+           "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status", "pr_measure_fp32_peak",
+           "pr_debug_scan_timeout")
 
 
 class PrError(RuntimeError):
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = True):
             "pr_graph_enqueue": ([P, P], I32),
             "pr_graph_status": ([P], I32),
             "pr_measure_fp32_peak": ([P, C.POINTER(C.c_double)], I32),
+            "pr_debug_scan_timeout": ([P], I32),
             "pr_graph_free": ([P], None),
             "pr_scene_stats": ([P, C.POINTER(PrStats)], I32),
             "pr_workspace_stats": ([P, C.POINTER(PrStats)], I32),
@@ -395,6 +397,11 @@ def pr_graph_enqueue(graph, stream=None):
 
 def pr_graph_status(graph):
     _check(load().pr_graph_status(C.c_void_p(graph)), "pr_graph_status")
+
+
+def pr_debug_scan_timeout(stream=None) -> int:
+    """Status of the scan's bounded-wait probe (PR_ERR_TIMEOUT expected)."""
+    return int(load().pr_debug_scan_timeout(stream if stream is not None else current_stream()))
 
 
 def pr_measure_fp32_peak(stream=None) -> float:

@@ -770,6 +770,13 @@ extern "C" {
 
 int32_t pr_version(void) { return 1; }
 
+pr_status pr_debug_scan_timeout(void *stream)
+{
+    unsigned status = 0u;
+    PR_TRY(scan_timeout_probe((cudaStream_t)stream, &status));
+    return (status & ST_TIMEOUT) ? PR_ERR_TIMEOUT : PR_OK;
+}
+
 pr_status pr_measure_fp32_peak(void *stream, double *tflops_out)
 {
     if (!tflops_out)

@@ -56,6 +56,8 @@ cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long 
                               long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
                               long long npix, cudaStream_t st);
 size_t scan_block_sums_needed(long long n);
+// a scan whose look-back waits on a tile that never runs (status word out)
+cudaError_t scan_timeout_probe(cudaStream_t st, unsigned *status);
 // words of a scan's state that must start at zero (ticket and flags)
 long long scan_state_words(long long n);
 // sorts every item's run of bin entries (nearest first); runs <= kMaxSeg

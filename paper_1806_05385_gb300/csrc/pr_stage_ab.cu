@@ -1212,7 +1212,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
                                                       const unsigned long long *__restrict__ n_dev,
                                                       unsigned long long *__restrict__ out, long long n, int seg,
                                                       unsigned long long *state, long long nb, Counters *cnt,
-                                                      ItemsOut io)
+                                                      ItemsOut io, int spin_limit)
 {
     unsigned long long *flags = state + 1, *agg = state + 1 + nb, *inc = state + 1 + 2 * nb;
     __shared__ long long s_tile;
@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned long long 
                 if (t >= 0) {
                     int spins = 0;
                     while ((f = load_volatile(&flags[t])) == 0ull) {
-                        if (++spins > kScanSpinLimit) {
+                        if (++spins > spin_limit) {
                             late = true;
                             f = kFlagPre;
                             break;
@@ -1343,11 +1343,59 @@ cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, u
             return e;
     }
     if (items && seg > 0)
-        k_scan<true><<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt, *items);
+        k_scan<true><<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt, *items,
+                                                            kScanSpinLimit);
     else
         k_scan<false><<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n_dev, out, n, seg, state, nb, cnt,
-                                                             ItemsOut{});
+                                                             ItemsOut{}, kScanSpinLimit);
     return cudaGetLastError();
+}
+
+// Failure detection of the look-back wait, without a fault: a two-tile scan
+// launched as ONE block whose ticket is preset to 1, so its predecessor
+// (tile 0) never runs and never publishes.  The block polls tile 0's flag
+// until the (here short) spin limit runs out, sets ST_TIMEOUT and finishes;
+// every access stays inside the buffers.  Returns the status word.
+cudaError_t scan_timeout_probe(cudaStream_t st, unsigned *status)
+{
+    const long long n = 2 * kScanBlock, nb = 2;
+    unsigned long long *in = nullptr, *out = nullptr, *state = nullptr;
+    Counters *cnt = nullptr;
+    *status = 0u;
+    cudaError_t e = cudaMalloc(&in, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&out, sizeof(unsigned long long) * (n + 1));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&state, sizeof(unsigned long long) * scan_block_sums_needed(n));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&cnt, sizeof(Counters));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(in, 0, sizeof(unsigned long long) * n, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(state, 0, sizeof(unsigned long long) * scan_block_sums_needed(n), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(cnt, 0, sizeof(Counters), st);
+    if (e == cudaSuccess) {
+        const unsigned long long one = 1ull;  // the ticket: the only block becomes tile 1
+        e = cudaMemcpyAsync(state, &one, sizeof one, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) {
+        k_scan<false><<<1, kScanThreads, 0, st>>>(in, nullptr, nullptr, out, n, 0, state, nb, cnt, ItemsOut{},
+                                                  1 << 12);
+        e = cudaGetLastError();
+    }
+    Counters h{};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+        *status = h.status;
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(state);
+    cudaFree(cnt);
+    return e;
 }
 
 // ---------------------------------------------------------------- run sort

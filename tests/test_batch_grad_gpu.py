@@ -516,3 +516,26 @@ def test_fp32_peak_measurement_is_plausible(pr):
     (152 SMs x 128 lanes x 2 FLOP x about 2 GHz = about 78 TFLOP/s)."""
     t = pr.pr_measure_fp32_peak()
     assert 20.0 < t < 120.0
+
+
+def test_scan_wait_times_out_with_a_status(pr):
+    """Failure detection without a fault: a scan whose predecessor tile never
+    publishes gives up its bounded wait, reports PR_ERR_TIMEOUT, and the
+    context stays usable for the next frame."""
+    import time
+    import torch
+    t0 = time.time()
+    assert pr.pr_debug_scan_timeout() == pr.PR_ERR_TIMEOUT
+    assert time.time() - t0 < 30.0
+    sc = S.random_triangles(300, 9)
+    p0, p1 = S.head_poses(1.0, 0.0)
+    view = S.View(W=64, H=48, tan_x=0.5, tan_y=0.5, pose0=p0, pose1=p1, mode=S.MODE_ROLLING)
+    h = _upload(pr, sc)
+    try:
+        ids = torch.empty(64 * 48, dtype=torch.int32, device="cuda")
+        dep = torch.empty(64 * 48, device="cuda")
+        pr.pr_rasterize(h, view, pr.make_params("zenon", 16), ids, dep)
+        torch.cuda.synchronize()
+        assert int((ids >= 0).sum()) > 0
+    finally:
+        pr.pr_scene_free(h)
