@@ -39,6 +39,9 @@ struct PixelHit {
     float ndh, spec;    // n.h and k_s max(0, n.h)^shininess (0 without specular)
 };
 
+// kSpec: a view of the launch may have a specular term (k_s > 0); without
+// it the kernels are built without the specular path, which saves registers.
+template <bool kSpec>
 __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsigned id, PixelHit &h)
 {
     float x0, x1, dx, dy;
@@ -90,7 +93,7 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     h.sigma = fmaf(v.k_d, fmaxf(h.ndl, 0.f), v.k_a);
     h.spec = 0.f;
     h.ndh = 0.f;
-    if (v.k_s > 0.f) {
+    if (kSpec && v.k_s > 0.f) {
         // the eye at the pixel time is the camera origin: v = -dir / |dir|
         const float3 e = scale3(h.dir, -rsqrtf(dot3(h.dir, h.dir)));
         const float3 hh = add3(h.l, e);
@@ -204,6 +207,7 @@ __device__ __forceinline__ void reduce_add_triangle(const ViewDev &v, float (&s)
 //  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1
 //    (applied per triangle after the warp sum, reduce_add_triangle).
 // The pixel's 27 values (layout of reduce_add_triangle) are ADDED to acc.
+template <bool kSpec>
 __device__ __forceinline__ void adjoint_add(const ViewDev &v, const PixelHit &h, const PixelAlbedo &pa, float g0,
                                             float g1, float g2, float (&acc)[27])
 {
@@ -232,7 +236,7 @@ __device__ __forceinline__ void adjoint_add(const ViewDev &v, const PixelHit &h,
         // normal -> moved vertices: the diffuse term through n.l, the
         // specular term k_s (n.h)^m (white) through n.h; the three
         // contributions (B-C) x gn, (C-A) x gn, (A-B) x gn sum to zero
-        const bool dif = h.ndl > 0.f, spc = h.spec > 0.f;
+        const bool dif = h.ndl > 0.f, spc = kSpec && h.spec > 0.f;
         if ((dif || spc) && h.inl != 0.f) {
             float3 gnh = scale3(h.l, dif ? gsig * v.k_d : 0.f);
             if (spc)
@@ -324,13 +328,14 @@ __device__ __forceinline__ void adjoint_flush(const ViewDev *views, AdjointSum &
 // Adds a valid lane's pixel (triangle id of view q) to its running sum;
 // first, if any lane's sum is of another triangle or view, the warp
 // flushes.  Called by every lane.
+template <bool kSpec>
 __device__ __forceinline__ void adjoint_step(const ViewDev *views, AdjointSum &a, bool valid, int q, unsigned id,
                                              const PixelHit &h, const PixelAlbedo &pa, float g0, float g1, float g2)
 {
     if (__any_sync(0xffffffffu, valid && a.q >= 0 && (a.q != q || a.id != id)))
         adjoint_flush(views, a);
     if (valid) {
-        adjoint_add(views[q], h, pa, g0, g1, g2, a.s);
+        adjoint_add<kSpec>(views[q], h, pa, g0, g1, g2, a.s);
         a.q = q;
         a.id = id;
         a.ia = h.ia;
@@ -350,7 +355,7 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 // stage (e) adjoint of the pixel follows from the same PixelHit -- with an
 // L2 target, from the colour just computed -- so the frame needs no
 // separate adjoint pass.  Whole warps run (the adjoint's reductions).
-template <bool kAdjoint>
+template <bool kAdjoint, bool kSpec>
 __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ views, int nviews,
                                               const long long *__restrict__ blk_offs, long long nblocks,
                                               const unsigned long long *__restrict__ keys,
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
         PixelAlbedo pa;
         float rgb[3] = {0.f, 0.f, 0.f};
         if (hit) {
-            pixel_hit(v, pi, pj, id, h);
+            pixel_hit<kSpec>(v, pi, pj, id, h);
             pixel_albedo(v, h, pa);
             rgb[0] = fmaf(pa.a[0], h.sigma, h.spec);
             rgb[1] = fmaf(pa.a[1], h.sigma, h.spec);
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
                 g1 = 2.f * (rgb[1] - gin[1]);
                 g2 = 2.f * (rgb[2] - gin[2]);
             }
-            adjoint_step(views, acc, valid, q, id, h, pa, g0, g1, g2);
+            adjoint_step<kSpec>(views, acc, valid, q, id, h, pa, g0, g1, g2);
         }
     }
     if (kAdjoint)
@@ -436,19 +441,26 @@ static unsigned shade_grid(long long nblocks)
 }
 
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, cudaStream_t st)
+                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, bool spec,
+                         cudaStream_t st)
 {
     if (nblocks > 0) {
-        if (adjoint)
-            k_shade<true><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        const unsigned g = shade_grid(nblocks);
+        if (adjoint && spec)
+            k_shade<true, true><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        else if (adjoint)
+            k_shade<true, false><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        else if (spec)
+            k_shade<false, true><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
         else
-            k_shade<false><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+            k_shade<false, false><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
     }
     return cudaGetLastError();
 }
 
 // Stage (e) on its own: the adjoint of a shaded frame from its id buffer
 // and an upstream gradient.
+template <bool kSpec>
 __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__ views, int nviews,
                                                  const long long *__restrict__ blk_offs, long long nblocks,
                                                  const Counters *__restrict__ frame_cnt)
@@ -477,7 +489,7 @@ __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (valid) {
             const long long plane = (long long)v.W * v.H;
-            pixel_hit(v, pi, pj, id, h);
+            pixel_hit<kSpec>(v, pi, pj, id, h);
             pixel_albedo(v, h, pa);
             if (v.target) {
                 // L2 loss sum (rgb - target)^2: its gradient from this frame's image
@@ -490,16 +502,20 @@ __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__
                 g2 = v.grad_in[2 * plane + lin];
             }
         }
-        adjoint_step(views, acc, valid, q, id, h, pa, g0, g1, g2);
+        adjoint_step<kSpec>(views, acc, valid, q, id, h, pa, g0, g1, g2);
     }
     adjoint_flush(views, acc);
 }
 
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                            const Counters *frame_cnt, cudaStream_t st)
+                            const Counters *frame_cnt, bool spec, cudaStream_t st)
 {
-    if (nblocks > 0)
-        k_backward<<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+    if (nblocks > 0) {
+        if (spec)
+            k_backward<true><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+        else
+            k_backward<false><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+    }
     return cudaGetLastError();
 }
 
