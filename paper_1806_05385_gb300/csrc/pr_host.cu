@@ -530,16 +530,6 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     return PR_OK;
 }
 
-// Whether any view of a frame has a specular term (the shading kernels are
-// built with and without its path).
-bool any_specular(const std::vector<ViewDev> &vd)
-{
-    for (const ViewDev &v : vd)
-        if (v.k_s > 0.f)
-            return true;
-    return false;
-}
-
 // Writes the frame's view and offset tables into the workspace's pinned
 // host copies (h_views: n views; h_offs: triangle, tile, pixel and 8x4
 // block offsets, n + 1 each).  shade: views with an rgb output get one.
@@ -662,7 +652,7 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(mark(5));
     if (shade)  // resolves the keys too, and in a training frame runs the adjoint
         PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), !P.grads.empty(), cnt,
-                            any_specular(P.vd), st));
+                            shade_features(P.vd.data(), n), st));
     PR_TRY(mark(6));
     // host-side outputs
     for (int q = 0; q < n; ++q) {
@@ -958,7 +948,8 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
     if (s != PR_OK)
         return s;
     PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, false, nullptr, v.k_s > 0.f, st));
+                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, false, nullptr, shade_features(&v, 1),
+                        st));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
     PR_TRY(cudaStreamSynchronize(st));
@@ -1010,7 +1001,7 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     if (s != PR_OK)
         return s;
     PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                           (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, v.k_s > 0.f, st));
+                           (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, shade_features(&v, 1), st));
     for (int a = 0; a < 3; ++a)
         if (host[a])
             PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
@@ -1050,10 +1041,8 @@ pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int
     }
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
     PR_TRY(cudaMemcpyAsync(ws->offs.p, blk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
-    bool spec = false;
-    for (int k = 0; k < n; ++k)
-        spec |= ws->h_views.p[k].k_s > 0.f;
-    PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], nullptr, spec, st));
+    PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], nullptr,
+                           shade_features(ws->h_views.p, n), st));
     PR_TRY(cudaStreamSynchronize(st));
     return PR_OK;
 }

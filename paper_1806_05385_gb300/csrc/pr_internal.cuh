@@ -146,6 +146,9 @@ __device__ __forceinline__ float fov_scale(float r, float alpha)
 
 // Pixel (i, j) -> its display location x, its time t and its ray direction
 // (dx, dy, 1) (conventions of pr.h).  FP32; the same code in every stage.
+// kLut = false: the caller knows no view uses a sampled p, and the sampled
+// path is left out (same results for the power map, fewer registers).
+template <bool kLut = true>
 __device__ __forceinline__ void pixel_ray(const ViewDev &v, int i, int j, float &x0, float &x1, float &t, float &dx,
                                           float &dy)
 {
@@ -155,7 +158,7 @@ __device__ __forceinline__ void pixel_ray(const ViewDev &v, int i, int j, float 
         float e0 = u0 - v.fx, e1 = u1 - v.fy;
         float r = sqrtf(fmaf(e0, e0, e1 * e1));
         float s;
-        if (v.p_lut) {  // sampled p: the offset scaled by p(r) / r (the first slope at r = 0)
+        if (kLut && v.p_lut) {  // sampled p: the offset scaled by p(r) / r (the first slope at r = 0)
             const SampledP sp{v.p_lut, v.p_n};
             s = r > 0.f ? sp.p(r) / r : sp.lut[1] * ((float)sp.n / kSqrt2);
         } else {

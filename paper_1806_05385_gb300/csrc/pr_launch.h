@@ -80,14 +80,15 @@ cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pi
 // stages (d) and (e)
 // keys: resolve them too (or null: read id_in); adjoint: a training frame,
 // run stage (e) for the views with a gradient from the same pixel hit
-// spec: some view has a specular term (k_s > 0)
+// feat: shade_features of the launch's views (which optional paths to build in)
+int shade_features(const ViewDev *vd, int n);
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, bool spec,
+                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, int feat,
                          cudaStream_t st);
 // frame_cnt: the counters of the frame whose forward ran just before in the
 // same sequence (the adjoint is skipped if it overflowed), or null.
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                            const Counters *frame_cnt, bool spec, cudaStream_t st);
+                            const Counters *frame_cnt, int feat, cudaStream_t st);
 
 // display step: unfoveation of a framebuffer image (pyramid: scratch of
 // mip_pyramid_floats(W, H) floats for the MIP method)

@@ -39,13 +39,17 @@ struct PixelHit {
     float ndh, spec;    // n.h and k_s max(0, n.h)^shininess (0 without specular)
 };
 
-// kSpec: a view of the launch may have a specular term (k_s > 0); without
-// it the kernels are built without the specular path, which saves registers.
-template <bool kSpec>
+// Paths the shading kernels are built with: a view of the launch may have a
+// specular term (k_s > 0), a view may use a sampled foveation function.  The
+// kernels built without a path are faster (fewer registers); the results of
+// the views they shade are the same bits.
+constexpr int kFeatSpec = 1, kFeatLut = 2;
+
+template <int kFeat>
 __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsigned id, PixelHit &h)
 {
     float x0, x1, dx, dy;
-    pixel_ray(v, i, j, x0, x1, h.t, dx, dy);
+    pixel_ray<(kFeat & kFeatLut) != 0>(v, i, j, x0, x1, h.t, dx, dy);
     h.dir = make_float3(dx, dy, 1.f);
     h.ia = v.i0[id];
     h.ib = v.i1[id];
@@ -93,7 +97,7 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     h.sigma = fmaf(v.k_d, fmaxf(h.ndl, 0.f), v.k_a);
     h.spec = 0.f;
     h.ndh = 0.f;
-    if (kSpec && v.k_s > 0.f) {
+    if ((kFeat & kFeatSpec) && v.k_s > 0.f) {
         // the eye at the pixel time is the camera origin: v = -dir / |dir|
         const float3 e = scale3(h.dir, -rsqrtf(dot3(h.dir, h.dir)));
         const float3 hh = add3(h.l, e);
@@ -207,7 +211,7 @@ __device__ __forceinline__ void reduce_add_triangle(const ViewDev &v, float (&s)
 //  - moved vertex c(t) = (1-t) S + t E with S = R0 p + T0, E = R1 (p + v) + T1
 //    (applied per triangle after the warp sum, reduce_add_triangle).
 // The pixel's 27 values (layout of reduce_add_triangle) are ADDED to acc.
-template <bool kSpec>
+template <int kFeat>
 __device__ __forceinline__ void adjoint_add(const ViewDev &v, const PixelHit &h, const PixelAlbedo &pa, float g0,
                                             float g1, float g2, float (&acc)[27])
 {
@@ -236,7 +240,7 @@ __device__ __forceinline__ void adjoint_add(const ViewDev &v, const PixelHit &h,
         // normal -> moved vertices: the diffuse term through n.l, the
         // specular term k_s (n.h)^m (white) through n.h; the three
         // contributions (B-C) x gn, (C-A) x gn, (A-B) x gn sum to zero
-        const bool dif = h.ndl > 0.f, spc = kSpec && h.spec > 0.f;
+        const bool dif = h.ndl > 0.f, spc = (kFeat & kFeatSpec) && h.spec > 0.f;
         if ((dif || spc) && h.inl != 0.f) {
             float3 gnh = scale3(h.l, dif ? gsig * v.k_d : 0.f);
             if (spc)
@@ -328,14 +332,14 @@ __device__ __forceinline__ void adjoint_flush(const ViewDev *views, AdjointSum &
 // Adds a valid lane's pixel (triangle id of view q) to its running sum;
 // first, if any lane's sum is of another triangle or view, the warp
 // flushes.  Called by every lane.
-template <bool kSpec>
+template <int kFeat>
 __device__ __forceinline__ void adjoint_step(const ViewDev *views, AdjointSum &a, bool valid, int q, unsigned id,
                                              const PixelHit &h, const PixelAlbedo &pa, float g0, float g1, float g2)
 {
     if (__any_sync(0xffffffffu, valid && a.q >= 0 && (a.q != q || a.id != id)))
         adjoint_flush(views, a);
     if (valid) {
-        adjoint_add<kSpec>(views[q], h, pa, g0, g1, g2, a.s);
+        adjoint_add<kFeat>(views[q], h, pa, g0, g1, g2, a.s);
         a.q = q;
         a.id = id;
         a.ia = h.ia;
@@ -355,7 +359,7 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 // stage (e) adjoint of the pixel follows from the same PixelHit -- with an
 // L2 target, from the colour just computed -- so the frame needs no
 // separate adjoint pass.  Whole warps run (the adjoint's reductions).
-template <bool kAdjoint, bool kSpec>
+template <bool kAdjoint, int kFeat>
 __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ views, int nviews,
                                               const long long *__restrict__ blk_offs, long long nblocks,
                                               const unsigned long long *__restrict__ keys,
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
         PixelAlbedo pa;
         float rgb[3] = {0.f, 0.f, 0.f};
         if (hit) {
-            pixel_hit<kSpec>(v, pi, pj, id, h);
+            pixel_hit<kFeat>(v, pi, pj, id, h);
             pixel_albedo(v, h, pa);
             rgb[0] = fmaf(pa.a[0], h.sigma, h.spec);
             rgb[1] = fmaf(pa.a[1], h.sigma, h.spec);
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
                 g1 = 2.f * (rgb[1] - gin[1]);
                 g2 = 2.f * (rgb[2] - gin[2]);
             }
-            adjoint_step<kSpec>(views, acc, valid, q, id, h, pa, g0, g1, g2);
+            adjoint_step<kFeat>(views, acc, valid, q, id, h, pa, g0, g1, g2);
         }
     }
     if (kAdjoint)
@@ -440,27 +444,55 @@ static unsigned shade_grid(long long nblocks)
     return (unsigned)((warps * 32 + 255) / 256);
 }
 
+template <bool kAdjoint>
+static void launch_shade_t(int feat, unsigned g, const ViewDev *views, int nviews, const long long *blk_offs,
+                           long long nblocks, const unsigned long long *keys, const Counters *frame_cnt,
+                           cudaStream_t st)
+{
+    switch (feat) {
+    case 0:
+        k_shade<kAdjoint, 0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        break;
+    case kFeatSpec:
+        k_shade<kAdjoint, kFeatSpec><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        break;
+    case kFeatLut:
+        k_shade<kAdjoint, kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        break;
+    default:
+        k_shade<kAdjoint, kFeatSpec | kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+    }
+}
+
+int shade_features(const ViewDev *vd, int n)
+{
+    int f = 0;
+    for (int k = 0; k < n; ++k) {
+        if (vd[k].k_s > 0.f)
+            f |= kFeatSpec;
+        if (vd[k].p_lut && (vd[k].mode == PR_FOVEATED || vd[k].mode == PR_BOTH))
+            f |= kFeatLut;
+    }
+    return f;
+}
+
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, bool spec,
+                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, int feat,
                          cudaStream_t st)
 {
     if (nblocks > 0) {
         const unsigned g = shade_grid(nblocks);
-        if (adjoint && spec)
-            k_shade<true, true><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
-        else if (adjoint)
-            k_shade<true, false><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
-        else if (spec)
-            k_shade<false, true><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        if (adjoint)
+            launch_shade_t<true>(feat, g, views, nviews, blk_offs, nblocks, keys, frame_cnt, st);
         else
-            k_shade<false, false><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+            launch_shade_t<false>(feat, g, views, nviews, blk_offs, nblocks, keys, frame_cnt, st);
     }
     return cudaGetLastError();
 }
 
 // Stage (e) on its own: the adjoint of a shaded frame from its id buffer
 // and an upstream gradient.
-template <bool kSpec>
+template <int kFeat>
 __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__ views, int nviews,
                                                  const long long *__restrict__ blk_offs, long long nblocks,
                                                  const Counters *__restrict__ frame_cnt)
@@ -489,7 +521,7 @@ __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (valid) {
             const long long plane = (long long)v.W * v.H;
-            pixel_hit<kSpec>(v, pi, pj, id, h);
+            pixel_hit<kFeat>(v, pi, pj, id, h);
             pixel_albedo(v, h, pa);
             if (v.target) {
                 // L2 loss sum (rgb - target)^2: its gradient from this frame's image
@@ -502,19 +534,29 @@ __global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__
                 g2 = v.grad_in[2 * plane + lin];
             }
         }
-        adjoint_step<kSpec>(views, acc, valid, q, id, h, pa, g0, g1, g2);
+        adjoint_step<kFeat>(views, acc, valid, q, id, h, pa, g0, g1, g2);
     }
     adjoint_flush(views, acc);
 }
 
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                            const Counters *frame_cnt, bool spec, cudaStream_t st)
+                            const Counters *frame_cnt, int feat, cudaStream_t st)
 {
     if (nblocks > 0) {
-        if (spec)
-            k_backward<true><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
-        else
-            k_backward<false><<<shade_grid(nblocks), 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+        const unsigned g = shade_grid(nblocks);
+        switch (feat) {
+        case 0:
+            k_backward<0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            break;
+        case kFeatSpec:
+            k_backward<kFeatSpec><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            break;
+        case kFeatLut:
+            k_backward<kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            break;
+        default:
+            k_backward<kFeatSpec | kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+        }
     }
     return cudaGetLastError();
 }
