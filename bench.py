@@ -472,7 +472,20 @@ def our_arm(args, rank, world):
                                     "(CUDA events on the launching stream, inside replays of the frame graph captured "
                                     "with stage events, one per timed step)"}
     roof, roof2 = (roof_shade, roof_frag) if shade_ms > frag_ms else (roof_frag, roof_shade)
-    roof = dict(roof, secondary=roof2)
+    # stage (a) with the frame init, HBM: per triangle-view at least 84 B in
+    # (three vertices' positions and velocities, indices) and 120 B out
+    # (record, pixel box, candidate count); per pixel the 8 B key set to
+    # ~0; per tile 16 B display box + 20 B counts and cursors
+    ttot = sum(wl.scenes[wl.scene_of[k]].T for k in range(len(views)))
+    ntiles = sum(((v.W + tiles[k] - 1) // tiles[k]) * ((v.H + tiles[k] - 1) // tiles[k]) for k, v in enumerate(views))
+    a_bytes = 204 * ttot + 8 * pix + 36 * ntiles
+    a_gbs = a_bytes / (stage_ms[0] * 1e-3) / 1e9 if stage_ms[0] > 0 else 0.0
+    roof_a = {"bound": "hbm", "achieved": a_gbs, "peak": hbm_peak, "unit": "GB/s",
+              "frac": a_gbs / hbm_peak if hbm_peak else None, "traffic": None,
+              "kernel": "k_frame_init + k_bound (stage a)", "time_ms": stage_ms[0], "algorithmic_bytes": a_bytes,
+              "achieved_basis": "204 B per triangle-view + 8 B per pixel + 36 B per tile (lower bound: the "
+                                "half-planes of kept triangles not counted) / stage (a) event time"}
+    roof = dict(roof, secondary=roof2, stage_a=roof_a)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
