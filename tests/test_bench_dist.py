@@ -33,3 +33,24 @@ def test_two_rank_aggregate():
 def test_single_process_aggregate():
     import bench
     assert bench.aggregate(4.0, 2_000_000) == pytest.approx((500.0, 4.0))
+
+
+def test_reference_arm_prints_one_json_line():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints
+    one JSON line with the contract's keys, on a short sample."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--cpu-seconds", "1", "--workload", "diff"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "impl", "cpu_baseline", "e2e"):
+        assert k in d
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
