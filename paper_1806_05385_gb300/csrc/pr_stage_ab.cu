@@ -1012,15 +1012,18 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const unsigned long long *_
         const unsigned want = __ballot_sync(0xffffffffu, ok);
         if (!ok)
             continue;
+        // the bin start and the entry load while the cursor atomic runs
+        const unsigned long long first = scan[tile] & 0xFFFFFFFFFFull;
+        const unsigned long long ent = hit_entry[k];
         const unsigned peers = __match_any_sync(want, tile);
         const int leader = __ffs(peers) - 1;
         unsigned base = 0;
         if (lane == leader)
             base = atomicAdd(&fill[tile], (unsigned)__popc(peers));
         base = __shfl_sync(peers, base, leader);
-        const long long pos = (long long)(scan[tile] & 0xFFFFFFFFFFull) + base + __popc(peers & ((1u << lane) - 1u));
+        const long long pos = (long long)first + base + __popc(peers & ((1u << lane) - 1u));
         if (pos < cap_pairs)
-            pairs[pos] = hit_entry[k];
+            pairs[pos] = ent;
         else
             atomicOr(&cnt->status, ST_OVERFLOW_PAIRS);
     }
