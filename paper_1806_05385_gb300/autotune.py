@@ -35,9 +35,13 @@ def view_class(view, T: int) -> str:
 def _load(path):
     try:
         with open(path) as f:
-            return json.load(f)
+            data = json.load(f)
     except (OSError, ValueError):
         return {}
+    # Anything but a mapping of class -> {"tile": ...} is discarded.
+    if not isinstance(data, dict):
+        return {}
+    return {k: e for k, e in data.items() if isinstance(e, dict) and e.get("tile") in TILES}
 
 
 def _save(path, data):
