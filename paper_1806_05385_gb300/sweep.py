@@ -162,7 +162,9 @@ def to_markdown(rows):
             cells = []
             for k in keys:
                 x = r.get(k, "")
-                if isinstance(x, float):
+                if x is None:
+                    cells.append("-")
+                elif isinstance(x, float):
                     cells.append(f"{100 * x:.1f} %" if k == "ste" else f"{x:.3f}")
                 else:
                     cells.append(str(x))
@@ -177,11 +179,15 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=7)
     ap.add_argument("--out", default=None, help="also write the tables as markdown")
     args = ap.parse_args(argv)
+    names = [n for n in args.sweeps.split(",") if n]
+    unknown = [n for n in names if n not in SWEEPS]
+    if unknown or not names:
+        ap.error(f"--sweeps: unknown {unknown}; choose from {', '.join(SWEEPS)}")
     import torch
     torch.cuda.set_device(0)
     B.load()
     rows = []
-    for name in args.sweeps.split(","):
+    for name in names:
         for r in SWEEPS[name](args.reps):
             print(json.dumps(r), flush=True)
             rows.append(r)
