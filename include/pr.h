@@ -104,14 +104,14 @@ typedef struct {
     int32_t mode;         /* pr_mode */
     int32_t pad0;
     float tan_x, tan_y;   /* tangents of the half field of view, > 0 */
-    float z_near;         /* hits need depth > z_near > 0 */
+    float z_near;         /* hits need depth > z_near > 0, finite */
     float alpha;          /* foveation exponent, 1 <= alpha <= 5 (1 = identity) */
     float pose0[16];      /* world->camera at t = 0, row-major */
     float pose1[16];      /* world->camera at t = 1, row-major */
     float fovea[2];       /* x_f in unit framebuffer coordinates, in [0,1]^2 */
     float d[2];           /* rolling direction: d0, d1 >= 0 and d0 + d1 <= 1 */
     float light_w[3];     /* world-space direction towards the light (normalised by the library) */
-    float k_a, k_d;       /* rgb = albedo * (k_a + k_d * max(0, n.l)) + the specular term below */
+    float k_a, k_d;       /* rgb = albedo * (k_a + k_d * max(0, n.l)) + the specular term below; finite */
     float k_s, shininess; /* rolling specular (Blinn-Phong): + k_s * max(0, n.h)^shininess on every
                              channel, h = normalize(l(t) + v), v = unit vector from the hit to the eye at
                              the pixel time (the reversed ray); k_s = 0: none; shininess >= 1 */

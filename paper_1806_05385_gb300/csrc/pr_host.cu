@@ -267,7 +267,9 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
     if (in.mode < PR_CLASSIC || in.mode > PR_BOTH)
         return PR_ERR_INVALID_ARG;
     if (!(in.tan_x > 0.f) || !(in.tan_y > 0.f) || !(in.z_near > 0.f) || !std::isfinite(in.tan_x) ||
-        !std::isfinite(in.tan_y))
+        !std::isfinite(in.tan_y) || !std::isfinite(in.z_near))
+        return PR_ERR_INVALID_ARG;
+    if (!std::isfinite(in.k_a) || !std::isfinite(in.k_d))
         return PR_ERR_INVALID_ARG;
     if (!(in.alpha >= 1.f && in.alpha <= 5.f))
         return PR_ERR_INVALID_ARG;

@@ -243,6 +243,12 @@ def test_invalid_inputs_raise(pr):
         v3 = S.View(**{**view.__dict__, "d": (0.8, 0.8)})
         with pytest.raises(pr.PrError):
             pr.pr_rasterize(h, v3, None, np.empty(256, np.uint32), None)
+        # Non-finite camera or shading constants are refused before any launch.
+        for field, value in (("z_near", float("inf")), ("k_a", float("nan")), ("k_d", float("inf"))):
+            v4 = S.View(**{**view.__dict__, field: value})
+            with pytest.raises(pr.PrError) as e:
+                pr.pr_rasterize(h, v4, None, np.empty(256, np.uint32), None)
+            assert e.value.status == pr.PR_ERR_INVALID_ARG
     finally:
         pr.pr_scene_free(h)
 
