@@ -182,7 +182,12 @@ pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, 
 
 /* Replaces the positions, velocities and colours of an uploaded scene
  * (same V); any pointer may be NULL to keep that array.  Used to step the
- * scene in optimisation loops without re-uploading the indices. */
+ * scene in optimisation loops without re-uploading the indices.  Arrays
+ * may be host or device memory (host arrays are staged through the
+ * scene's own device buffer).  Runs on `stream` and synchronises it before
+ * returning, to report PR_ERR_NONFINITE for a non-finite value; the caller
+ * must not update a scene while a frame that reads it may still be running
+ * on another stream (keep two scenes to overlap an update with a frame). */
 pr_status pr_scene_update(pr_scene *scene, const float *pos, const float *vel, const float *col,
                           void *stream);
 
