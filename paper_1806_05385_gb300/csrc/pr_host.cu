@@ -27,6 +27,9 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;  // sole owner of its allocation
+    DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf()
     {
         if (p)
@@ -64,6 +67,9 @@ template <class T>
 struct PinnedBuf {
     T *p = nullptr;
     size_t cap = 0;
+    PinnedBuf() = default;
+    PinnedBuf(const PinnedBuf &) = delete;  // sole owner of its allocation
+    PinnedBuf &operator=(const PinnedBuf &) = delete;
     ~PinnedBuf()
     {
         if (p)
