@@ -54,3 +54,34 @@ def test_reference_arm_prints_one_json_line():
         assert k in d
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The ncu DRAM traffic of a kernel is reported only while the kernel's
+    source is the one the counters were taken on, and only for the workload
+    they were taken on; otherwise it is null."""
+    import json
+    import bench
+    src = tmp_path / "paper_1806_05385_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "pr_stage_c.cu").write_text("// kernel source\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    entry = {"workload": "hmd", "source_sha256_16": bench.source_hash("pr_stage_c.cu"),
+             "dram_bytes_per_launch": 1234.0}
+    (tmp_path / "profiles" / "traffic_hmd.json").write_text(json.dumps({"k_fragment": entry}))
+    assert bench.ncu_traffic("hmd", "k_fragment") == 1234.0
+    assert bench.ncu_traffic("large", "k_fragment") is None
+    assert bench.ncu_traffic("hmd", "k_shade<1>") is None  # never captured
+    (src / "pr_stage_c.cu").write_text("// kernel source, changed\n")
+    assert bench.ncu_traffic("hmd", "k_fragment") is None
+
+
+def test_measured_peak_and_fallback(tmp_path, monkeypatch):
+    import json
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peak("hbm_gbs") == 6800.0  # no file: the stated fallback
+    assert bench.measured_peak("bf16_tflops") is None
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6674.2}))
+    assert bench.measured_peak("hbm_gbs") == 6674.2
