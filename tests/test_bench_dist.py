@@ -1,6 +1,8 @@
-"""The multi-GPU (replica) path of bench.py on CPU: two gloo ranks with
-different step times; the whole-job value is the pixels of both ranks over
-the slower rank's time, identical on every rank."""
+"""Host logic of bench.py on CPU.  The multi-GPU (replica) path: two gloo
+ranks with different step times; the whole-job value is the pixels of both
+ranks over the slower rank's time, identical on every rank.  Also the
+reference arm's JSON line, the gate on reported ncu traffic and the peak
+fallback."""
 import os
 
 import pytest
