@@ -352,16 +352,24 @@ void pr_graph_free(pr_graph *g);
  * pos, vel, col: DEVICE float32 [V][3]; tri: DEVICE int32 [T][3]; id_out
  * uint32 [H][W] and depth_out float32 [H][W]: DEVICE buffers (either may be
  * NULL).  Host pointers are rejected (PR_ERR_INVALID_ARG): staging them
- * would need allocations.  params as for pr_rasterize.
- * Limits: a frame whose fixed scratch (about 36 V + 12 T + 284 T bytes, 60
- * bytes per tile and 8 bytes per pixel) does not fit the 64 MiB returns
- * PR_ERR_INVALID_ARG; one whose bins then do not fit what is left returns
- * PR_ERR_OVERFLOW.  No buffer grows and nothing is retried.
+ * would need allocations.  view and params are validated as for
+ * pr_rasterize, except that fp64_retest must be 0 (the re-test's flag
+ * buffers are not part of the array): fp64_retest = 1 returns
+ * PR_ERR_INVALID_ARG.
+ * Limits: a frame whose fixed scratch (36 V + 272 T bytes, about 52 bytes
+ * per tile, 8 bytes per pixel and the scans' state) does not fit the 64 MiB
+ * returns PR_ERR_INVALID_ARG; one whose bins do not fit what is left (20
+ * bytes per bin entry) returns PR_ERR_OVERFLOW, whether that is known before
+ * the launch or found by the binning kernels.  No buffer grows and nothing
+ * is retried.  A bounded device-side wait that ran out returns
+ * PR_ERR_TIMEOUT.
  * The first call on a device looks up the array's device address on that
  * device (with it current); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (each call
- * clears what must start at zero); calls that overlap on the GPU -- other
- * streams or other host threads -- race on it and must be serialised.
+ * Every call waits for its stream before it returns (it reads the frame's
+ * status word back).  All calls share the array and it keeps the last
+ * call's contents (each call clears what must start at zero); calls that
+ * overlap on the GPU -- other streams or other host threads -- race on it
+ * and must be serialised.
  * Output equals pr_rasterize with the same arguments. */
 pr_status pr_rasterize_noalloc(const float *pos, const float *vel, const float *col, const int32_t *tri,
                                int64_t V, int64_t T, const pr_view *view, const pr_params *params,

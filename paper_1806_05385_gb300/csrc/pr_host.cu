@@ -263,10 +263,11 @@ struct pr_graph {
     std::vector<const void *> buffers;  // the workspace's buffers at capture
 };
 
-namespace {
+namespace pr {
 
-// Host-side derivation of a view's device constants.
-pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int bound, int fp64, ViewDev &v)
+// Host-side validation of a view and derivation of its device constants,
+// shared by every entry point (the scene's arrays are set by the caller).
+pr_status derive_view(const pr_view &in, int tile, int bound, int fp64, ViewDev &v)
 {
     if (in.W < 1 || in.H < 1 || in.W > 16384 || in.H > 16384)
         return PR_ERR_INVALID_ARG;
@@ -342,6 +343,19 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
     v.tiles_y = (in.H + tile - 1) / tile;
     v.bound = bound;
     v.fp64 = fp64;
+    return PR_OK;
+}
+
+}  // namespace pr
+
+namespace {
+
+// Host-side derivation of a view's device constants for a scene.
+pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int bound, int fp64, ViewDev &v)
+{
+    const pr_status ds = derive_view(in, tile, bound, fp64, v);
+    if (ds != PR_OK)
+        return ds;
     v.T = (int)sc->T;
     v.V = (int)sc->V;
     const float *s = sc->soa.as<float>();

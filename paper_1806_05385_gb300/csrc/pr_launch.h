@@ -102,4 +102,9 @@ cudaError_t measure_fma_peak(cudaStream_t st, double *tflops);
 // device samples of a foveation handle (defined with the handle)
 const float *pr_foveation_samples(const pr_foveation *f, int *n);
 
+// validation of a view and its device constants (all but the scene's
+// arrays and sizes, which the caller sets); PR_ERR_INVALID_ARG for any
+// out-of-range field, tile or bound kind
+pr_status derive_view(const pr_view &in, int tile, int bound, int fp64, ViewDev &v);
+
 }  // namespace pr

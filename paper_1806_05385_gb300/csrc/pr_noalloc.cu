@@ -106,59 +106,14 @@ struct Carver {
     }
 };
 
-// View constants of pr_view (the same derivation as the allocating path).
+// View constants of pr_view from the shared validation of every entry
+// point, with the scene arrays in the arena.
 pr_status view_constants(const pr_view &in, int tile, int bound, float *soa, int *idx, long long V, long long T,
                          ViewDev &v)
 {
-    if (in.W < 1 || in.H < 1 || in.W > 16384 || in.H > 16384 || in.mode < PR_CLASSIC || in.mode > PR_BOTH)
-        return PR_ERR_INVALID_ARG;
-    if (!(in.tan_x > 0.f) || !(in.tan_y > 0.f) || !(in.z_near > 0.f) || !std::isfinite(in.tan_x) ||
-        !std::isfinite(in.tan_y) || !(in.alpha >= 1.f && in.alpha <= 5.f))
-        return PR_ERR_INVALID_ARG;
-    if (!(in.d[0] >= 0.f && in.d[1] >= 0.f && in.d[0] + in.d[1] <= 1.f + 1e-6f) ||
-        ((in.mode == PR_ROLLING || in.mode == PR_BOTH) && in.d[0] + in.d[1] <= 0.f))
-        return PR_ERR_INVALID_ARG;
-    if (!(in.fovea[0] >= 0.f && in.fovea[0] <= 1.f && in.fovea[1] >= 0.f && in.fovea[1] <= 1.f))
-        return PR_ERR_INVALID_ARG;
-    if ((tile != 8 && tile != 16 && tile != 32) || bound < PR_BOUND_ZENON || bound > PR_BOUND_TRIVIAL)
-        return PR_ERR_INVALID_ARG;
-    for (int k = 0; k < 16; ++k)
-        if (!std::isfinite(in.pose0[k]) || !std::isfinite(in.pose1[k]))
-            return PR_ERR_INVALID_ARG;
-    std::memset(&v, 0, sizeof v);
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) {
-            v.R0[3 * r + c] = in.pose0[4 * r + c];
-            v.R1[3 * r + c] = in.pose1[4 * r + c];
-        }
-        v.T0[r] = in.pose0[4 * r + 3];
-        v.T1[r] = in.pose1[4 * r + 3];
-    }
-    v.tan_x = in.tan_x;
-    v.tan_y = in.tan_y;
-    v.z_near = in.z_near;
-    v.fx = in.fovea[0];
-    v.fy = in.fovea[1];
-    v.alpha = in.alpha;
-    v.inv_alpha = 1.f / in.alpha;
-    if (in.foveation) {
-        v.p_lut = pr_foveation_samples(in.foveation, &v.p_n);
-    }
-    v.d0 = in.d[0];
-    v.d1 = in.d[1];
-    v.t_lo = 0.f;
-    v.t_hi = std::min(1.f, in.d[0] + in.d[1]);
-    v.k_a = in.k_a;
-    v.k_d = in.k_d;
-    v.k_s = in.k_s;
-    v.shininess = in.shininess;
-    v.W = in.W;
-    v.H = in.H;
-    v.mode = in.mode;
-    v.S = tile;
-    v.tiles_x = (in.W + tile - 1) / tile;
-    v.tiles_y = (in.H + tile - 1) / tile;
-    v.bound = bound;
+    const pr_status s = derive_view(in, tile, bound, 0, v);
+    if (s != PR_OK)
+        return s;
     v.T = (int)T;
     v.V = (int)V;
     v.px = soa;
@@ -187,6 +142,8 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     if (!on_device(pos) || !on_device(vel) || !on_device(col) || (T > 0 && !on_device(tri)) ||
         (id_out && !on_device(id_out)) || (depth_out && !on_device(depth_out)))
         return PR_ERR_INVALID_ARG;  // device buffers only: staging host memory would need allocations
+    if (params && params->fp64_retest != 0)
+        return PR_ERR_INVALID_ARG;  // the FP64 re-test's flag buffers are not carved from the arena
     cudaStream_t st = (cudaStream_t)stream;
     const int tile = params && params->tile ? params->tile : 16;
     const int bound = params ? params->bound : PR_BOUND_ZENON;
@@ -218,14 +175,14 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     const long long rest = (long long)kNoAllocBytes - (long long)((c.off + 255) & ~(size_t)255) - 512;
     const long long item_fixed = nt + 1024;
     if (rest < (long long)(16 * item_fixed + 21 * (2 * Tn + nt)))
-        return PR_ERR_INVALID_ARG;  // too little room left for the bins of this frame
+        return PR_ERR_OVERFLOW;  // too little room left for the bins of this frame
     // per bin entry: the entry (8 B) and its listed hit (8 B entry + 4 B tile)
     const long long cap_pairs = (rest - 16 * item_fixed) / (20 + 16 / seg + 1);
     const long long cap_items = item_fixed + cap_pairs / seg + 1;
     const size_t o_items = c.take(sizeof(int4) * cap_items), o_tris = c.take(8 * cap_pairs);
     const size_t o_hit_e = c.take(8 * cap_pairs), o_hit_t = c.take(4 * cap_pairs);
     if (!c.ok)
-        return PR_ERR_INVALID_ARG;
+        return PR_ERR_OVERFLOW;  // the bins' alignment padding did not fit either
 
     float *soa = (float *)(arena + o_soa);
     int *idx = (int *)(arena + o_idx);
@@ -292,6 +249,8 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     Counters h;
     NA_TRY(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));
+    if (h.status & ST_TIMEOUT)
+        return PR_ERR_TIMEOUT;  // a scan's bounded wait ran out: its offsets and the bins behind them are invalid
     if (h.status & ST_NONFINITE)
         return PR_ERR_NONFINITE;
     if (h.status & ST_BAD_INDEX)

@@ -58,3 +58,40 @@ def test_noalloc_rejects_host_buffers_and_oversize(pr):
     with pytest.raises(pr.PrError) as e:
         pr.pr_rasterize_noalloc(_dev(sc.pos), _dev(sc.vel), _dev(sc.col), _dev(sc.tri), big, None, ids, None)
     assert e.value.status == pr.PR_ERR_INVALID_ARG
+
+
+def test_noalloc_bins_that_do_not_fit_report_overflow_and_the_next_call_is_correct(pr):
+    """A frame whose fixed scratch fits the array but whose bins do not
+    (every one of 3,000 triangles binned to each of 16,384 tiles by the
+    whole-viewport bound: 49 M entries at 20 bytes, against about 54 MiB
+    left) runs, stops filling the bins at their capacity and returns
+    PR_ERR_OVERFLOW; the call after it on the same array is exact again."""
+    import torch
+    sc = S.random_triangles(3000, 23)
+    p0, p1 = S.head_poses(1.0, 0.0)
+    view = S.View(W=1024, H=1024, tan_x=0.5, tan_y=0.5, pose0=p0, pose1=p1, mode=S.MODE_ROLLING)
+    n = view.W * view.H
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    dep = torch.empty(n, dtype=torch.float32, device="cuda")
+    with pytest.raises(pr.PrError) as e:
+        pr.pr_rasterize_noalloc(_dev(sc.pos), _dev(sc.vel), _dev(sc.col), _dev(sc.tri), view,
+                                pr.make_params("trivial", 8), ids, dep)
+    assert e.value.status == pr.PR_ERR_OVERFLOW
+    test_noalloc_matches_rasterize_on_two_calls(pr)
+
+
+def test_noalloc_rejects_what_it_cannot_run(pr):
+    """The FP64 re-test needs flag buffers the array does not provide, so
+    fp64_retest = 1 is refused; view fields are validated exactly as for
+    pr_rasterize (an infinite z_near is refused)."""
+    import torch
+    sc, view, tile = _frames()[1]
+    args = (_dev(sc.pos), _dev(sc.vel), _dev(sc.col), _dev(sc.tri))
+    ids = torch.empty(view.W * view.H, dtype=torch.int32, device="cuda")
+    with pytest.raises(pr.PrError) as e:
+        pr.pr_rasterize_noalloc(*args, view, pr.make_params("zenon", tile, 1), ids, None)
+    assert e.value.status == pr.PR_ERR_INVALID_ARG
+    bad = S.View(**{**view.__dict__, "z_near": float("inf")})
+    with pytest.raises(pr.PrError) as e:
+        pr.pr_rasterize_noalloc(*args, bad, pr.make_params("zenon", tile), ids, None)
+    assert e.value.status == pr.PR_ERR_INVALID_ARG
