@@ -128,6 +128,119 @@ def test_centre_ray_is_optical_axis(oracle):
     assert d[0, 0] == pytest.approx((2 * 0.5 / W - 1) * 0.7)
 
 
+def _q_closed_form(u, f, alpha):
+    """q(u) = f + (u - f)/|u - f| * D (|u - f|/D)^alpha, D = sqrt 2, written
+    out here on its own (Sec. 3.1.1 with the power p of Sec. 5.1)."""
+    D = math.sqrt(2.0)
+    e = np.asarray(u, dtype=np.float64) - f
+    r = math.hypot(e[0], e[1])
+    return f.copy() if r == 0.0 else f + e * (D * (r / D) ** alpha / r)
+
+
+@pytest.mark.parametrize("mode", [S.MODE_FOVEATED, S.MODE_BOTH])
+def test_foveated_ray_goes_through_the_display_location(oracle, mode):
+    """Sec. 3.1.1: a foveated pixel u is seen along the ray of its display
+    location q(u), dir = ((2 q0 - 1) tanX, (2 q1 - 1) tanY, 1); the joint
+    mode takes the same ray (Sec. 3.1.3).  The fovea is off centre and
+    alpha = 2, so the ray of u itself differs from it by up to a few tenths
+    and this tells dir(q(u)) from dir(u)."""
+    W, H = 9, 7
+    v = mkview(W=W, H=H, mode=mode, tan=(0.7, 0.4), fovea=(0.3, 0.65), alpha=2.0)
+    _, x, d = oracle.pixels(v)
+    f = np.array(v.fovea, dtype=np.float64)
+    worst_u = 0.0
+    for k in range(W * H):
+        u = np.array([(k % W + 0.5) / W, (k // W + 0.5) / H])
+        xq = _q_closed_form(u, f, 2.0)
+        want = np.array([(2 * xq[0] - 1) * v.tan_x, (2 * xq[1] - 1) * v.tan_y, 1.0])
+        assert np.allclose(x[k], xq, rtol=0, atol=1e-14)
+        assert np.allclose(d[k], want, rtol=0, atol=1e-14)
+        du = np.array([(2 * u[0] - 1) * v.tan_x, (2 * u[1] - 1) * v.tan_y, 1.0])
+        worst_u = max(worst_u, float(np.abs(du - want).max()))
+    assert worst_u > 0.1
+
+
+def _seg_dist_sampled(p, a, b, n=20001):
+    """Distance from p to the segment ab by brute force over n points."""
+    s = np.linspace(0.0, 1.0, n)[:, None]
+    pts = a[None, :] * (1 - s) + b[None, :] * s
+    return float(np.sqrt(((pts - p[None, :]) ** 2).sum(1)).min())
+
+
+def _right_triangle_boundary_distance(p, a0, b0, a1, b1):
+    """Distance from an interior point p to the boundary of the right
+    triangle (a0, b0), (a1, b0), (a0, b1): the smallest of its distances to
+    the two legs and to the hypotenuse line."""
+    w, h = a1 - a0, b1 - b0
+    hyp = abs((p[0] - a0) * h + (p[1] - b0) * w - w * h) / math.hypot(w, h)
+    return min(p[0] - a0, p[1] - b0, hyp)
+
+
+@pytest.mark.parametrize("mode,vx", [(S.MODE_CLASSIC, 0.0), (S.MODE_ROLLING, 0.4), (S.MODE_BOTH, 0.4)])
+def test_eval_display_edge_distance_closed_form(oracle, mode, vx):
+    """or_eval's sixth output, the distance in unit display coordinates from
+    a pixel's display location to the boundary of the triangle projected at
+    the pixel time (it decides which FP32 id mismatches are excused).  A
+    fronto-parallel triangle at depth z whose display image is the right
+    triangle (a0, b0), (a1, b0), (a0, b1), translating along camera x by a
+    display distance V per frame: at the pixel time t its image is shifted by
+    V t (Sec. 3.1.2).  Inside: the smallest distance to the legs and the
+    hypotenuse line; everywhere: brute force over points of the three
+    edges.  The display location is q(u) in the joint mode (Sec. 3.1.1)."""
+    W, H, z, tx, ty = 24, 20, 4.0, 0.5, 0.375   # tangents exact in FP32
+    a0, b0, a1, b1 = 0.25, 0.3, 0.8, 0.9
+    disp = np.array([[a0, b0], [a1, b0], [a0, b1]])
+    cam = np.stack([(2 * disp[:, 0] - 1) * tx * z, (2 * disp[:, 1] - 1) * ty * z, np.full(3, z)], 1)
+    vel = np.zeros((3, 3))
+    vel[:, 0] = vx * 2 * tx * z            # camera x displacement that moves the image by vx
+    tri = np.array([[0, 1, 2]], dtype=np.int32)
+    v = mkview(W=W, H=H, mode=mode, tan=(tx, ty), fovea=(0.55, 0.45))
+    f = np.array(v.fovea, dtype=np.float64)
+    checked_inside = 0
+    for k in range(W * H):
+        u = np.array([(k % W + 0.5) / W, (k // W + 0.5) / H])
+        x = _q_closed_form(u, f, 2.0) if mode == S.MODE_BOTH else u
+        t = x[0] if mode != S.MODE_CLASSIC else 0.0
+        sh = np.array([vx * t, 0.0])
+        A, B, C = disp[0] + sh, disp[1] + sh, disp[2] + sh
+        ev = oracle.evaluate(v, cam, vel, tri, k, 0)
+        want = min(_seg_dist_sampled(x, A, B), _seg_dist_sampled(x, B, C), _seg_dist_sampled(x, C, A))
+        assert ev[5] == pytest.approx(want, abs=5e-5)   # sampling error <= edge length / 40000
+        xs = x - sh
+        inside = xs[0] >= a0 and xs[1] >= b0 and (xs[0] - a0) / (a1 - a0) + (xs[1] - b0) / (b1 - b0) <= 1
+        assert bool(ev[4]) == inside
+        if inside:
+            checked_inside += 1
+            assert ev[5] == pytest.approx(_right_triangle_boundary_distance(xs, a0, b0, a1, b1), abs=1e-12)
+    assert checked_inside > 40
+    # a vertex behind the camera: no projected triangle, distance 0
+    cam2 = cam.copy()
+    cam2[0, 2] = -1.0
+    assert oracle.evaluate(v, cam2, vel, tri, (H // 2) * W + W // 2, 0)[5] == 0.0
+
+
+@pytest.mark.parametrize("g,h", [(0.5, 0.0), (0.0, -0.8), (1.3, 0.6)])
+def test_depth_conditioning_cosine_of_a_tilted_plane(oracle, g, h):
+    """The oracle's `cos` output, |cos| of the angle between a pixel's ray
+    and its winner's plane normal (it sets the depth allowance of the parity
+    rule), against a hand-computed normal: the plane z = 5 + g x + h y has
+    the normal (-g, -h, 1), so cos = |d . (-g, -h, 1)| / (|d| sqrt(1 + g^2 +
+    h^2)) for the pixel ray d."""
+    W, H, tx, ty = 12, 10, 0.5, 0.5
+    plane = lambda X, Y: 5.0 + g * X + h * Y
+    corners = [(-4.0, -4.0), (4.0, -4.0), (0.0, 4.0)]
+    pos = np.array([[X, Y, plane(X, Y)] for X, Y in corners])
+    v = mkview(W=W, H=H, tan=(tx, ty))
+    o = oracle.render(v, pos, np.zeros_like(pos), np.ones_like(pos), np.array([[0, 1, 2]], np.int32))
+    hit = o["id"] == 0
+    assert hit.sum() > W * H // 3
+    n = np.array([-g, -h, 1.0]) / math.sqrt(1 + g * g + h * h)
+    for k in np.nonzero(hit)[0]:
+        d = np.array([(2 * ((k % W) + 0.5) / W - 1) * tx, (2 * ((k // W) + 0.5) / H - 1) * ty, 1.0])
+        assert o["cos"][k] == pytest.approx(abs(d @ n) / np.linalg.norm(d), rel=1e-12)
+    assert np.all(o["cos"][~hit] == 1.0)
+
+
 # --------------------------------------------------------------------------
 # classic special case == an independent pinhole rasterizer
 # --------------------------------------------------------------------------
