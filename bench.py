@@ -1,19 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the perceptual-rasterization hot path on GB300.
 
-One step = one training frame of the workload through every stage of the
-path, captured as one CUDA graph: (a) bounds -> (b) binning and the depth
-sort of every work item's run -> (c) per-fragment ray casting -> (d)
-shading for all views, with (e) the adjoint of an upstream image gradient
-for every view in the same kernel.  value = framebuffer pixels / step time
-(Mpix/s).
+A training frame of the workload runs every stage of the path as one CUDA
+graph: (a) bounds -> (b) binning and the depth sort of every work item's run
+-> (c) per-fragment ray casting -> (d) shading for all views, with (e) the
+adjoint of an upstream image gradient for every view in the same kernel.  A
+timed step is R consecutive training frames (graph replays), R chosen from a
+warm-up measurement so that the K timed steps span at least --target-seconds
+(the clock record then covers the timed region).  value = framebuffer pixels
+x R / step time (Mpix/s).
 
-Prints ONE JSON line (rank 0).  Default workload: 1440x1600 per eye x 2
-eyes, 266k triangles (200 subdivision-3 icospheres + a 10k ground plane),
-joint foveated + rolling, seeded synthetic scene already resident in HBM.
+Prints ONE JSON line (rank 0).  Default workload: the batched 64-view
+workload -- 64 independent scenes of 1k..500k triangles (log-uniform), square
+views of side 512..2160 (log-uniform), modes uniform over classic, rolling,
+foveated and joint, tile sizes autotuned -- seeded synthetic scenes already
+resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload hmd|large|batched|diff]
+                    [--workload batched|hmd|large|diff] [--target-seconds S]
 """
 from __future__ import annotations
 
@@ -45,15 +49,17 @@ FP32_LANES = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--target-seconds", type=float, default=2.5,
+                    help="the K timed steps span at least this long (frames per step sized to it)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["hmd", "large", "batched", "diff"], default="hmd",
-                    help="hmd: stereo 1440x1600, 266k tris (default); large: stereo 2160^2, 1M tris, FP64 "
-                         "re-test; batched: 64 views of 1k-500k tris; diff: 512^2, 10k tris")
+    ap.add_argument("--workload", choices=["batched", "hmd", "large", "diff"], default="batched",
+                    help="batched: 64 views of 1k-500k tris (default); hmd: stereo 1440x1600, 266k tris; large: "
+                         "stereo 2160^2, 1M tris, FP64 re-test; diff: 512^2, 10k tris")
     return ap.parse_args()
 
 
@@ -282,6 +288,9 @@ def our_arm(args, rank, world):
     rgb = [torch.empty(3 * n, dtype=torch.float32, device="cuda") for n in npx]
     gen = torch.Generator(device="cuda").manual_seed(1234)
     grad = [torch.randn(3 * n, device="cuda", generator=gen) for n in npx]
+    # the training targets: one 8-bit RGB image per view (seeded synthetic)
+    tgt8 = [torch.randint(0, 256, (3 * n,), dtype=torch.uint8, device="cuda", generator=gen) for n in npx]
+    loss = torch.zeros(len(views), device="cuda")
     grads = [tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3)) for sc in wl.scenes]
     if args.workload == "batched":
         from paper_1806_05385_gb300 import autotune
@@ -290,10 +299,11 @@ def our_arm(args, rank, world):
         tiles = [16] * len(views)
     params = B.make_params("zenon", 16, wl.fp64, 0)
     entries = [(hv[k], v, ids[k], depth[k], rgb[k], tiles[k]) for k, v in enumerate(views)]
-    # one training frame = one graph: forward (a)-(d) with the adjoint (e)
-    # of an upstream image gradient, reading the frame's own records
-    fgrads = [dict(grad_rgb=grad[k], dcol=grads[wl.scene_of[k]][0], dpos=grads[wl.scene_of[k]][1],
-                   dvel=grads[wl.scene_of[k]][2]) for k in range(len(views))]
+    # one training frame = one graph: forward (a)-(d), the L2 loss of every
+    # view against its 8-bit target image and the adjoint (e) of that loss,
+    # reading the frame's own records
+    fgrads = [dict(target_u8=tgt8[k], loss=loss[k:k + 1], dcol=grads[wl.scene_of[k]][0],
+                   dpos=grads[wl.scene_of[k]][1], dvel=grads[wl.scene_of[k]][2]) for k in range(len(views))]
     graph = B.pr_graph_capture_frame(ws, entries, fgrads, params)
     # the same frame with CUDA events between the stages as graph nodes: the
     # stage (kernel) times of the rooflines come from its replays, run right
@@ -311,8 +321,11 @@ def our_arm(args, rank, world):
     def backward():
         B.pr_backward_batch(ws_b, bwd_entries)
 
+    frames = [1]  # training frames (graph replays) per timed step, sized after the warm-up
+
     def step():
-        B.pr_graph_enqueue(graph)
+        for _ in range(frames[0]):
+            B.pr_graph_enqueue(graph)
 
     def timed(fn, k, flush_l2=True, check=None):
         """Per call, device time between events recorded before and after
@@ -333,6 +346,17 @@ def our_arm(args, rank, world):
 
     for _ in range(max(3, args.warmup)):
         B.pr_graph_launch(graph)
+    # frames per step: the K timed steps span at least target_seconds, so the
+    # clock sampler sees the timed region many times (every rank takes the
+    # largest R, so all ranks time the same work)
+    frame_ms = statistics.median(timed(step, 5, check=lambda: B.pr_graph_status(graph)))
+    frames[0] = max(1, int(np.ceil(args.target_seconds * 1e3 / (max(1, args.steps) * frame_ms))))
+    if dist:
+        fr = torch.tensor([frames[0]], dtype=torch.int64, device="cuda")
+        dist.all_reduce(fr, op=dist.ReduceOp.MAX)
+        frames[0] = int(fr.item())
+    R = frames[0]
+    k2 = max(3, min(args.steps, 10))  # repetitions of the secondary measurements
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -352,12 +376,12 @@ def our_arm(args, rank, world):
     def stage_check():
         B.pr_graph_status(graph_t)
         stage_runs.append(list(B.pr_workspace_stats(ws)["stage_ms"]))
-    timed(lambda: B.pr_graph_enqueue(graph_t), args.steps, check=stage_check)
+    timed(lambda: B.pr_graph_enqueue(graph_t), k2, check=stage_check)
     stage_ms = [statistics.mean(r[k] for r in stage_runs) for k in range(8)]
     frag_ms = stage_ms[2]
 
     # forward only: batched graph vs plain per-view calls
-    fwd_batched = timed(lambda: B.pr_graph_enqueue(graph_fwd), args.steps, check=lambda: B.pr_graph_status(graph_fwd))
+    fwd_batched = timed(lambda: B.pr_graph_enqueue(graph_fwd), k2, check=lambda: B.pr_graph_status(graph_fwd))
 
     def plain():
         for k, v in enumerate(views):
@@ -366,8 +390,8 @@ def our_arm(args, rank, world):
             B.pr_shade(hv[k], v, ids[k], rgb[k])
     for _ in range(2):
         plain()
-    fwd_plain = timed(plain, max(3, args.steps // 2))
-    bwd_ms = timed(backward, max(3, args.steps // 2))
+    fwd_plain = timed(plain, k2)
+    bwd_ms = timed(backward, k2)
 
     # the display step after shading (Sec. 3.1.1, "Display"): every view's
     # framebuffer image unfoveated to a display of the same size, both methods
@@ -381,7 +405,7 @@ def our_arm(args, rank, world):
     for m in ("mip", "projected"):
         for _ in range(2):
             display(m)
-        display_ms[m] = statistics.mean(timed(lambda: display(m), max(3, args.steps // 2)))
+        display_ms[m] = statistics.mean(timed(lambda: display(m), k2))
     B.pr_workspace_free(ws_d)
     hbm = measured_peak("hbm_gbs")
     # algorithmic bytes: 12 B rgb in + 12 B rgb out per pixel; the pyramid adds
@@ -393,135 +417,101 @@ def our_arm(args, rank, world):
                     for m in display_ms}
 
     pix = sum(npx)
-    value, mean_ms = aggregate(sum(step_ms) / len(step_ms), pix, dist, "cuda")
+    value, mean_ms = aggregate(sum(step_ms) / len(step_ms), pix * R, dist, "cuda")
 
-    # end to end through the public API with host buffers, as a training
-    # loop would run it: every step the scene arrays and the upstream image
-    # gradient go up from pinned host memory, the scene is updated, the frame
-    # graph (forward + adjoint) replays, and the shaded images and the
-    # gradients come back to pinned host memory, with the replay's status read
+    # end to end through the public API, as a training loop runs it: every
+    # step the current scene parameters (positions, velocities, colours:
+    # the host's copy, as an optimiser on the host keeps them) and the
+    # step's 8-bit target images go up from pinned host memory -- the
+    # parameters through pr_scene_update itself, which stages host arrays
+    # and returns without waiting -- the training-frame graph replays
+    # (forward, L2 loss, adjoint), and the per-view losses and per-vertex
+    # gradients come back to pinned host memory, with every replay's status
+    # read on the host.  No image comes back: a training step returns its
+    # loss and gradients.
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         hsc = [(pin(sc.pos), pin(sc.vel), pin(sc.col)) for sc in wl.scenes]
-        dsc = [tuple(torch.empty_like(x, device="cuda") for x in a) for a in hsc]
-        hrgb = [torch.empty(3 * n, dtype=torch.float32).pin_memory() for n in npx]
-        hg = [g.cpu().pin_memory() for g in grad]
+        htg = [t.cpu().pin_memory() for t in tgt8]
+        hloss = torch.zeros(len(views)).pin_memory()
         hd = [tuple(torch.zeros(3 * sc.V).pin_memory() for _ in range(3)) for sc in wl.scenes]
-
-        side = torch.cuda.Stream()
-
-        def e2e_step():
-            # the upstream gradient goes up on a second stream while the
-            # scene is copied and updated; the frame waits for both
-            side.wait_stream(stream)
-            with torch.cuda.stream(side):
-                for g, hgk in zip(grad, hg):
-                    g.copy_(hgk, non_blocking=True)
-            for a, d in zip(hsc, dsc):
-                for x, y in zip(a, d):
-                    y.copy_(x, non_blocking=True)
-            for h, d in zip(handles, dsc):
-                B.pr_scene_update(h, *d)
-            stream.wait_stream(side)
-            for gs in grads:
-                for x in gs:
-                    x.zero_()
-            B.pr_graph_enqueue(graph)
-            for r, hr in zip(rgb, hrgb):
-                hr.copy_(r, non_blocking=True)
-            for gs, hgs in zip(grads, hd):
-                for x, y in zip(gs, hgs):
-                    y.copy_(x, non_blocking=True)
-            stream.synchronize()
-            B.pr_graph_status(graph)
-        for _ in range(2):
-            e2e_step()
-        ems = timed(e2e_step, max(3, args.steps // 2))
-
-        # the same steps as a training loop that overlaps its copies with
-        # the GPU work, double-buffered: two copies of the scene, gradient
-        # input, images and gradient outputs, each with its own frame graph
-        # on the one workspace (replays stay in order on `stream`).  While
-        # frame k runs on one set, step k+1's inputs go up into the other
-        # set and its scene is updated (second stream), and step k's results
-        # come down after it (third stream).  Every step still copies its
-        # own inputs from pinned host memory and its own images and
-        # gradients back to it, flushes L2 before its frame, and the host
-        # reads every frame's status before it enqueues the next frame
-        # (pr_graph_status reads the last replay's counters).
         side_in, side_out = torch.cuda.Stream(), torch.cuda.Stream()
+        # two buffer sets (scenes, targets, loss, gradients; one frame graph
+        # each) used in turn, so one step's uploads and the previous step's
+        # downloads overlap the current frame; replays stay in order on
+        # `stream` (they share the workspace)
         handles2 = [B.pr_scene_upload(dev(sc.pos), dev(sc.vel), dev(sc.col), dev(sc.tri)) for sc in wl.scenes]
         hv2 = [handles2[si] for si in wl.scene_of]
-        rgb2 = [torch.empty_like(r) for r in rgb]
-        grad2 = [g.clone() for g in grad]
+        tgt2 = [torch.empty_like(t) for t in tgt8]
+        loss2 = torch.zeros_like(loss)
         grads2 = [tuple(torch.zeros_like(x) for x in gs) for gs in grads]
-        dsc2 = [tuple(torch.empty_like(x) for x in d) for d in dsc]
+        rgb2 = [torch.empty_like(r) for r in rgb]
         entries2 = [(hv2[k], v, ids[k], depth[k], rgb2[k], tiles[k]) for k, v in enumerate(views)]
-        fgrads2 = [dict(grad_rgb=grad2[k], dcol=grads2[wl.scene_of[k]][0], dpos=grads2[wl.scene_of[k]][1],
-                        dvel=grads2[wl.scene_of[k]][2]) for k in range(len(views))]
+        fgrads2 = [dict(target_u8=tgt2[k], loss=loss2[k:k + 1], dcol=grads2[wl.scene_of[k]][0],
+                        dpos=grads2[wl.scene_of[k]][1], dvel=grads2[wl.scene_of[k]][2]) for k in range(len(views))]
         graph2 = B.pr_graph_capture_frame(ws, entries2, fgrads2, params)
-        sets = [dict(h=handles, grad=grad, rgb=rgb, grads=grads, dsc=dsc, graph=graph),
-                dict(h=handles2, grad=grad2, rgb=rgb2, grads=grads2, dsc=dsc2, graph=graph2)]
+        sets = [dict(h=handles, tgt=tgt8, loss=loss, grads=grads, graph=graph),
+                dict(h=handles2, tgt=tgt2, loss=loss2, grads=grads2, graph=graph2)]
 
-        def upload_copies(bs):
-            """Step inputs -> buffer set bs on side_in: the upstream gradient
-            and the scene arrays from pinned host memory.  The caller has
-            synchronised on the last frame that read bs."""
-            with torch.cuda.stream(side_in):
-                for g, hgk in zip(bs["grad"], hg):
-                    g.copy_(hgk, non_blocking=True)
-                for a, d in zip(hsc, bs["dsc"]):
-                    for x, y in zip(a, d):
-                        y.copy_(x, non_blocking=True)
-
-        def upload_update(bs):
-            """pr_scene_update of set bs from its uploaded arrays, on side_in
-            after the copies (it waits for side_in); returns the event the
+        def upload(bs):
+            """Step inputs -> buffer set bs on side_in (the caller has seen the
+            last frame that read bs finish): the scene parameters through
+            pr_scene_update, the targets by copies; returns the event the
             set's frame waits for."""
             with torch.cuda.stream(side_in):
-                for h, d in zip(bs["h"], bs["dsc"]):
-                    B.pr_scene_update(h, *d)
+                for h, a in zip(bs["h"], hsc):
+                    B.pr_scene_update(h, *a, stream=side_in.cuda_stream)
+                for t, ht in zip(bs["tgt"], htg):
+                    t.copy_(ht, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(side_in)
             return ev
 
-        def e2e_pipelined(k_steps):
+        def frame(bs):
+            bs["loss"].zero_()
+            for gs in bs["grads"]:
+                for x in gs:
+                    x.zero_()
+            B.pr_graph_enqueue(bs["graph"])
+            done = torch.cuda.Event()
+            done.record(stream)
+            return done
+
+        def download(bs, done):
+            with torch.cuda.stream(side_out):
+                side_out.wait_event(done)
+                hloss.copy_(bs["loss"], non_blocking=True)
+                for gs, hgs in zip(bs["grads"], hd):
+                    for x, y in zip(gs, hgs):
+                        y.copy_(x, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(side_out)
+            return ev
+
+        def e2e_loop(k_steps, overlap=True):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             side_in.wait_event(e0)
-            upload_copies(sets[0])
-            ready = upload_update(sets[0])
+            ready = upload(sets[0])
             out_free = [None, None]
             for it in range(k_steps):
-                bs = sets[it % 2]
-                if it + 1 < k_steps:
-                    # the other set's last frame (step it-1) has completed:
-                    # the host synchronised on it at the end of that step
-                    upload_copies(sets[(it + 1) % 2])
+                bs = sets[it % 2 if overlap else 0]
                 stream.wait_event(ready)
                 if out_free[it % 2] is not None:
                     stream.wait_event(out_free[it % 2])  # step it-2's results have left this set
                 flush.zero_()
-                for gs in bs["grads"]:
-                    for x in gs:
-                        x.zero_()
-                B.pr_graph_enqueue(bs["graph"])
-                done = torch.cuda.Event()
-                done.record(stream)
-                with torch.cuda.stream(side_out):
-                    side_out.wait_event(done)
-                    for r, hr in zip(bs["rgb"], hrgb):
-                        hr.copy_(r, non_blocking=True)
-                    for gs, hgs in zip(bs["grads"], hd):
-                        for x, y in zip(gs, hgs):
-                            y.copy_(x, non_blocking=True)
-                    out_free[it % 2] = torch.cuda.Event()
-                    out_free[it % 2].record(side_out)
-                if it + 1 < k_steps:
-                    ready = upload_update(sets[(it + 1) % 2])
+                done = frame(bs)
+                if it + 1 < k_steps and overlap:
+                    # the other set's last frame (step it-1) finished: the
+                    # host saw its status at the end of that step
+                    ready = upload(sets[(it + 1) % 2])
+                out_free[it % 2] = download(bs, done)
                 done.synchronize()
                 B.pr_graph_status(bs["graph"])
+                if it + 1 < k_steps and not overlap:
+                    out_free[it % 2].synchronize()
+                    ready = upload(sets[0])
             for ev in out_free:
                 if ev is not None:
                     stream.wait_event(ev)
@@ -529,34 +519,36 @@ def our_arm(args, rank, world):
             e1.synchronize()
             return e0.elapsed_time(e1) / k_steps
 
-        e2e_pipelined(3)
-        pms = e2e_pipelined(max(3, args.steps))
-        # the loop's last results reached the host: they equal the images of
-        # its last frame, and both buffer sets rendered the same images
-        last = sets[(max(3, args.steps) - 1) % 2]
-        for r, r2, hr in zip(last["rgb"], rgb2, hrgb):
-            assert torch.equal(r.cpu(), hr), "pipelined end-to-end images differ from the device's"
-            assert torch.equal(r2.cpu(), hr), "the two buffer sets rendered different images"
+        e2e_loop(3)
+        pms = e2e_loop(k2)
+        # the loop's last results reached the host: they equal the last
+        # frame's losses and gradients on the device
+        last = sets[(k2 - 1) % 2]
+        assert torch.equal(last["loss"].cpu(), hloss), "end-to-end losses differ from the device's"
+        for gs, hgs in zip(last["grads"], hd):
+            for x, y in zip(gs, hgs):
+                assert torch.equal(x.cpu(), y), "end-to-end gradients differ from the device's"
+        sms = e2e_loop(k2, overlap=False)
         B.pr_graph_free(graph2)
         for h in handles2:
             B.pr_scene_free(h)
         sv = sum(sc.V for sc in wl.scenes)
-        h2d = 3 * sv * 12 + sum(g.numel() * 4 for g in hg)
-        d2h = sum(x.numel() * 4 for x in hrgb) + 3 * sv * 12
+        h2d = 3 * sv * 12 + sum(t.numel() for t in htg)
+        d2h = 3 * sv * 12 + 4 * len(views)
         e2e = {"value": world * pix / (pms * 1e-3) / 1e6, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": pms,
-               "path": "training loop through the public API with two buffer sets (scene copy, upstream "
-                       "gradient, images, gradients; one frame graph each) used in turn: while frame k runs, step "
-                       "k+1's scene arrays and upstream gradient go up from pinned host memory into the other set "
-                       "and pr_scene_update runs there (second stream), and frame k's images and gradients go back "
-                       "to pinned host memory after it (third stream); L2 flushed before every frame; the host "
-                       "synchronises on every frame and reads its pr_graph_status before enqueuing the next; K "
-                       "steps timed as a whole with CUDA events, from the first upload to the last download",
-               "serial": {"value": world * pix / (statistics.mean(ems) * 1e-3) / 1e6,
-                          "ms_per_step": statistics.mean(ems),
-                          "path": "the same copies and calls with no overlap across steps (upload, update, frame, "
-                                  "download, synchronise, status; L2 flushed before each step, outside the "
-                                  "timed region)"}}
+               "path": "training loop through the public API: every step the scene parameters (positions, "
+                       "velocities, colours, the host's copy) go up through pr_scene_update from pinned host memory "
+                       "and the step's 8-bit target images by copies, the training-frame graph replays (forward, L2 "
+                       "loss against the targets, adjoint), and the per-view losses and per-vertex gradients come "
+                       "back to pinned host memory; the host reads every replay's pr_graph_status before the step "
+                       "ends; two buffer sets (scenes, targets, loss, gradients, one frame graph each) used in turn, "
+                       "so the next step's uploads (second stream) and this step's downloads (third stream) overlap "
+                       "the frames; L2 flushed before every frame; K steps timed as a whole with CUDA events from "
+                       "the first upload to the last download",
+               "serial": {"value": world * pix / (sms * 1e-3) / 1e6, "ms_per_step": sms,
+                          "path": "the same calls and copies on one buffer set with no overlap across steps: "
+                                  "upload, frame, download, wait, status, then the next step's upload"}}
 
     # rooflines: stage (c) k_fragment (FP32 ALU) and the training frame's
     # shading + adjoint kernel k_shade<1> (HBM); the bench line's "roofline"
@@ -573,13 +565,13 @@ def our_arm(args, rank, world):
                  "peak_measured_ffma": ffma,
                  "achieved_basis": "ray-triangle tests of one frame x 39 FLOP / fragment-stage time of that frame "
                                    "(CUDA events on the launching stream, inside replays of the frame graph captured with "
-                                   "stage events, one per timed step)"}
-    # k_shade<1>: per pixel 8 B key in, 4 B id + 4 B depth + 12 B rgb out, 12 B
-    # upstream gradient in; per visible triangle 108 B vertex data in (3 x
+                                   "stage events, ten replays)"}
+    # k_shade<1>: per pixel 8 B key in, 4 B id + 4 B depth + 12 B rgb out, 3 B
+    # 8-bit target in; per visible triangle 108 B vertex data in (3 x
     # position, velocity, colour) and 108 B gradients out (3 x dcol, dpos, dvel)
     shade_ms = stage_ms[5]
     visible = sum(int(torch.unique(x[x >= 0]).numel()) for x in ids)
-    shade_bytes = 40 * pix + 216 * visible
+    shade_bytes = 31 * pix + 216 * visible
     hbm_peak = measured_peak("hbm_gbs")
     shade_gbs = shade_bytes / (shade_ms * 1e-3) / 1e9 if shade_ms > 0 else 0.0
     roof_shade = {"bound": "hbm", "achieved": shade_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -587,9 +579,9 @@ def our_arm(args, rank, world):
                   "traffic": ncu_traffic(args.workload, "k_shade<1>"), "kernel": "k_shade<1>", "time_ms": shade_ms,
                   "algorithmic_bytes": shade_bytes, "visible_triangles": visible,
                   "peak_basis": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                  "achieved_basis": "40 B per pixel + 216 B per visible triangle / shading + adjoint stage time "
+                  "achieved_basis": "31 B per pixel + 216 B per visible triangle / shading + adjoint stage time "
                                     "(CUDA events on the launching stream, inside replays of the frame graph captured "
-                                    "with stage events, one per timed step)"}
+                                    "with stage events, ten replays)"}
     roof, roof2 = (roof_shade, roof_frag) if shade_ms > frag_ms else (roof_frag, roof_shade)
     # stage (a) with the frame init, HBM: per triangle-view at least 84 B in
     # (three vertices' positions and velocities, indices) and 120 B out
@@ -617,22 +609,25 @@ def our_arm(args, rank, world):
     n_classes = len({(t, wl.fp64) for t in tiles})
     # frame init (with the tile boxes), bound, candidate scan, bin count, tile scan (with the work
     # items), bin scatter, run sort, one fragment launch per (tile, precision) class, [FP64 re-test],
-    # resolve + shade + adjoint
-    kernels_step = 8 + n_classes + (1 if wl.fp64 else 0)
+    # resolve + shade + loss + adjoint, the losses' partial sums
+    kernels_step = 9 + n_classes + (1 if wl.fp64 else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if not wl.fp64 else "f32+f64-retest", "data": "synthetic",
-        "config": {"workload": wl.name, "views": len(views), "pixels_per_step": pix,
-                   "triangles": sum(sc.T for sc in wl.scenes),
-                   "step": "one graph per frame: init + tile boxes, bound, bin, run sort, fragment, [FP64 re-test], "
-                           "resolve + shade + adjoint (one kernel)",
-                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
+        "config": {"workload": wl.name, "views": len(views), "frames_per_step": R, "pixels_per_frame": pix,
+                   "pixels_per_step": pix * R, "triangles": sum(sc.T for sc in wl.scenes),
+                   "step": f"{R} training frames, each one replay of the frame graph: init + tile boxes, bound, bin, "
+                           "run sort, fragment, [FP64 re-test], resolve + shade + L2 loss against each view's 8-bit "
+                           "target image + adjoint (one kernel); the status of the step's last replay is read after it",
+                   "l2": f"flushed before every timed step (256 MB write); between the frames of a step, inputs larger "
+                         f"than L2: each frame reads {96 * ttot / 1e6:.0f} MB of stage (a) records and writes "
+                         f"{20 * pix / 1e6:.0f} MB of images", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
-        "gpu_launches": kernels_step * args.steps,
+        "gpu_launches": kernels_step * R * args.steps,
         "tests_per_s": st["tests"] / (frag_ms * 1e-3) if frag_ms > 0 else None,
         "ste": st["hits"] / st["tests"] if st["tests"] else None,
         "stats": {k: st[k] for k in ("tests", "hits", "pairs", "items", "culled", "pixels", "flagged", "changed",
@@ -640,10 +635,10 @@ def our_arm(args, rank, world):
         "stage_ms": {"bound": stage_ms[0], "bin": stage_ms[1], "fragment": frag_ms,
                      "fp64_retest": stage_ms[3], "resolve_shade_adjoint": stage_ms[5],
                      "basis": "CUDA events between the stages, inside replays of the same frame graph "
-                              "captured with them (graph_stage_times), one per timed step, L2 flushed"},
+                              "captured with them (graph_stage_times), ten replays, L2 flushed before each"},
         "fwd_mpix_s": {"batched_graph": world * pix / (statistics.mean(fwd_batched) * 1e-3) / 1e6,
                        "plain_per_view": world * pix / (statistics.mean(fwd_plain) * 1e-3) / 1e6},
-        "fwd_bwd_ms_per_frame": mean_ms, "bwd_ms_separate_call": statistics.mean(bwd_ms),
+        "fwd_bwd_ms_per_frame": mean_ms / R, "bwd_ms_separate_call": statistics.mean(bwd_ms),
         "display_step": display_step,
         "tiles": sorted(set(tiles)),
     }

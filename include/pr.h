@@ -184,10 +184,14 @@ pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, 
  * (same V); any pointer may be NULL to keep that array.  Used to step the
  * scene in optimisation loops without re-uploading the indices.  Arrays
  * may be host or device memory (host arrays are staged through the
- * scene's own device buffer).  Runs on `stream` and synchronises it before
- * returning, to report PR_ERR_NONFINITE for a non-finite value; the caller
- * must not update a scene while a frame that reads it may still be running
- * on another stream (keep two scenes to overlap an update with a frame). */
+ * scene's own device buffer).  Asynchronous on `stream`: it returns once
+ * the work is enqueued, so a pinned host array must stay unchanged until
+ * the stream has passed the call.  A non-finite value is not reported here:
+ * the next frame that reads the scene culls all of the scene's triangles
+ * and returns PR_ERR_NONFINITE (a later update with finite values clears
+ * it).  The caller must not update a scene while a frame that reads it may
+ * still be running on another stream, and must order its updates of one
+ * scene (keep two scenes to overlap an update with a frame). */
 pr_status pr_scene_update(pr_scene *scene, const float *pos, const float *vel, const float *col,
                           void *stream);
 
@@ -202,7 +206,12 @@ pr_status pr_rasterize(pr_scene *scene, const pr_view *view, const pr_params *pa
 
 /* Stage (d): deferred Lambert shading with the light interpolated at each
  * pixel's time (Sec. 3.2, "Shading").  id: uint32 [H][W] from
- * pr_rasterize; rgb_out: float32 planar [3][H][W] (0 = background). */
+ * pr_rasterize; rgb_out: float32 planar [3][H][W] (0 = background).  When
+ * the scene's last pr_rasterize ran the precision form (fp64_retest = 1),
+ * so does the shading: a pixel whose FP32 barycentrics are ill-conditioned
+ * (a triangle small against its distance) takes its moved triangle,
+ * barycentrics and normal from FP64.  The batched calls do the same per
+ * their params. */
 pr_status pr_shade(pr_scene *scene, const pr_view *view, const uint32_t *id, float *rgb_out, void *stream);
 
 /* Stage (e): adjoint of (d) and of the barycentrics of (c) with the
@@ -252,17 +261,25 @@ void pr_workspace_free(pr_workspace *ws);
 pr_status pr_rasterize_batch(pr_workspace *ws, const pr_batch_view *views, int32_t n, const pr_params *params,
                              void *stream);
 
-/* The gradient side of one view of a training frame: either grad_rgb =
- * dL/drgb [3][H][W], or target_rgb [3][H][W] for the L2 loss
- * L = sum (rgb - target)^2 (then dL/drgb = 2 (rgb - target) is formed from
- * the frame's own shaded image inside the adjoint kernel); dcol, dpos, dvel
- * [V][3] of the view's scene are ACCUMULATED (+=), any may be NULL.  All
- * DEVICE pointers; grad_rgb and target_rgb must not overlap the view's
- * outputs.  Both NULL: no adjoint for this view. */
+/* The gradient side of one view of a training frame, at most one of:
+ *  - grad_rgb = dL/drgb, float32 [3][H][W];
+ *  - target_rgb, float32 [3][H][W], for the L2 loss L = sum (rgb - target)^2
+ *    over the view's pixels and channels (then dL/drgb = 2 (rgb - target) is
+ *    formed from the frame's own shaded colour inside the adjoint kernel);
+ *  - target_u8, uint8 [3][H][W], the same loss against target = value / 255
+ *    (an 8-bit image, the form training data usually comes in).
+ * dcol, dpos, dvel [V][3] of the view's scene are ACCUMULATED (+=), any may
+ * be NULL.  loss: one float, ACCUMULATED (+=) with the view's L (background
+ * pixels count with rgb = 0), or NULL; it needs a target.  All DEVICE
+ * pointers; the inputs must not overlap the view's outputs.  None of the
+ * three: no adjoint for this view.  A view with a gradient entry may leave
+ * rgb_out NULL: the colour is formed in registers and not stored. */
 typedef struct {
     const float *grad_rgb;
     const float *target_rgb;
     float *dcol, *dpos, *dvel;
+    const uint8_t *target_u8;
+    float *loss;
 } pr_frame_grad;
 
 /* A training frame: pr_rasterize_batch (stages (a)-(d)) followed, in the
@@ -356,7 +373,7 @@ void pr_graph_free(pr_graph *g);
  * pr_rasterize, except that fp64_retest must be 0 (the re-test's flag
  * buffers are not part of the array): fp64_retest = 1 returns
  * PR_ERR_INVALID_ARG.
- * Limits: a frame whose fixed scratch (36 V + 272 T bytes, about 52 bytes
+ * Limits: a frame whose fixed scratch (48 V + 276 T bytes, about 52 bytes
  * per tile, 8 bytes per pixel and the scans' state) does not fit the 64 MiB
  * returns PR_ERR_INVALID_ARG; one whose bins do not fit what is left (20
  * bytes per bin entry) returns PR_ERR_OVERFLOW, whether that is known before
@@ -384,6 +401,16 @@ pr_status pr_workspace_stats(const pr_workspace *ws, pr_stats *out);
  * inclusive framebuffer pixel box (i0, j0, i1, j1), empty when i0 > i1;
  * t_range float32 [T][2] = [t_min, t_max]. */
 pr_status pr_debug_bounds(const pr_scene *scene, int32_t *pix_box, float *t_range);
+
+/* Half-planes of the per-triangle bound of the last pr_rasterize call on
+ * this scene (stage (a) output, for tests of conservativeness): hp float32
+ * [T][8][4], slot h = (nx, ny, c, unused), the region is where
+ * nx x + ny y + c <= 0; info int32 [T]: bits 0-7 the number of slots in use,
+ * bit 8 set when they are framebuffer lines in unit framebuffer coordinates
+ * u (the Simple and Recursive foveation bounds of Sec. 4.1.1-4.1.2), clear
+ * when they bound the display region in display coordinates x (Sec. 4.2).
+ * Culled triangles have no half-planes.  Synchronises the device. */
+pr_status pr_debug_halfplanes(const pr_scene *scene, float *hp, int32_t *info);
 
 /* Host evaluation of the stage (a) catch-up interval for one triangle (the
  * Zenon bound of Sec. 4.2.4): S, E float [3][3] camera-space vertices at

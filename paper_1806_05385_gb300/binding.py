@@ -32,7 +32,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
            "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
            "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status", "pr_measure_fp32_peak",
-           "pr_debug_scan_timeout")
+           "pr_debug_scan_timeout", "pr_debug_halfplanes")
 
 
 class PrError(RuntimeError):
@@ -80,7 +80,7 @@ UNFOVEATE_METHODS = {"mip": 0, "projected": 1}
 
 class PrFrameGrad(C.Structure):
     _fields_ = [("grad_rgb", C.c_void_p), ("target_rgb", C.c_void_p), ("dcol", C.c_void_p), ("dpos", C.c_void_p),
-                ("dvel", C.c_void_p)]
+                ("dvel", C.c_void_p), ("target_u8", C.c_void_p), ("loss", C.c_void_p)]
 
 
 class PrBatchView(C.Structure):
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
             "pr_scene_stats": ([P, C.POINTER(PrStats)], I32),
             "pr_workspace_stats": ([P, C.POINTER(PrStats)], I32),
             "pr_debug_bounds": ([P, P, P], I32),
+            "pr_debug_halfplanes": ([P, P, P], I32),
             "pr_debug_catch_interval": ([C.POINTER(PrView), P, P, P], I32),
             "pr_status_string": ([I32], C.c_char_p),
             "pr_version": ([], I32),
@@ -309,7 +310,7 @@ def pr_graph_capture_batch(ws, entries, params=None, stream=None) -> int:
 
 def make_grads(grads):
     """grads: list (one per view) of None or a dict with any of grad_rgb,
-    target_rgb, dcol, dpos, dvel (CUDA tensors)."""
+    target_rgb, target_u8, dcol, dpos, dvel, loss (CUDA tensors)."""
     arr = (PrFrameGrad * len(grads))()
     keep = []
     for k, g in enumerate(grads):
@@ -434,6 +435,16 @@ def pr_debug_bounds(scene, T: int):
     tr = np.empty((T, 2), np.float32)
     _check(load().pr_debug_bounds(C.c_void_p(scene), _ptr(box), _ptr(tr)), "pr_debug_bounds")
     return box, tr
+
+
+def pr_debug_halfplanes(scene, T: int):
+    """Stage (a) half-planes of the last pr_rasterize on the scene: hp
+    [T][8][4] (nx, ny, c, -) and info [T] (count | 0x100 when they are
+    framebuffer lines)."""
+    hp = np.empty((T, 8, 4), np.float32)
+    info = np.empty(T, np.int32)
+    _check(load().pr_debug_halfplanes(C.c_void_p(scene), _ptr(hp), _ptr(info)), "pr_debug_halfplanes")
+    return hp, info
 
 
 def pr_debug_catch_interval(view, S, E):

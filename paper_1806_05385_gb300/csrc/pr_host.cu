@@ -141,6 +141,7 @@ struct pr_workspace {
     DevBuf cand, cand_off;         // candidate tiles per triangle; prefix sum over the binned triangles
     DevBuf binned;                 // triangles with candidate tiles (listed by the bound pass)
     DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
+    DevBuf loss_part;              // training frames: kLossSlots partial sums of each view's loss
     DevBuf stage;                  // device copies of host-side outputs
     long long cap_pairs = 0, cap_items = 0;
     PinnedBuf<ViewDev> h_views;
@@ -176,7 +177,7 @@ struct pr_workspace {
     {
         return {rec.p, hp.p, tbox.p, tile_box.p, tile_cnt.p, scan.p, fill.p, sums.p, pairs.p, items.p,
                 keys.p, counters.p, heads.p, hit_entry.p, hit_tile.p, cand.p, cand_off.p, binned.p, flag_bits.p,
-                flag_list.p, h_cnt.p};
+                flag_list.p, h_cnt.p, loss_part.p};
     }
     // stage times of the last completed frame (events already complete)
     void read_stage_times()
@@ -246,8 +247,11 @@ void pr_foveation_free(pr_foveation *f)
 
 struct pr_scene {
     long long V = 0, T = 0;
-    DevBuf soa;   // 9 V floats: px py pz vx vy vz cr cg cb
-    DevBuf idx;   // 3 T ints: i0 i1 i2
+    DevBuf vtx;   // 2 V float4: (px, py, pz, vx), (vy, vz, 0, 0)
+    DevBuf col;   // V float4: (r, g, b, 0)
+    DevBuf tri;   // T int4: (i0, i1, i2, 0)
+    DevBuf status;  // one device word: ST_NONFINITE after an update with a non-finite value
+    int last_fp64 = 0;  // precision form of the last pr_rasterize (pr_shade follows it)
     DevBuf stage; // host input staging
     DevBuf gstage, ostage;  // adjoint: staged host gradient image / host gradient outputs
     pr_workspace ws;
@@ -358,21 +362,10 @@ pr_status make_viewdev(const pr_view &in, const pr_scene *sc, int tile, int boun
         return ds;
     v.T = (int)sc->T;
     v.V = (int)sc->V;
-    const float *s = sc->soa.as<float>();
-    const long long V = sc->V;
-    v.px = s;
-    v.py = s + V;
-    v.pz = s + 2 * V;
-    v.vx = s + 3 * V;
-    v.vy = s + 4 * V;
-    v.vz = s + 5 * V;
-    v.cr = s + 6 * V;
-    v.cg = s + 7 * V;
-    v.cb = s + 8 * V;
-    const int *ix = sc->idx.as<int>();
-    v.i0 = ix;
-    v.i1 = ix + sc->T;
-    v.i2 = ix + 2 * sc->T;
+    v.vtx = sc->vtx.as<float4>();
+    v.col4 = sc->col.as<float4>();
+    v.tri4 = sc->tri.as<int4>();
+    v.scene_status = sc->status.as<unsigned>();
     return PR_OK;
 }
 
@@ -402,6 +395,7 @@ struct BatchPlan {
     };
     bool any_fp64 = false;
     bool any_paper_fov = false;  // some foveated view asks for the paper's edge bound
+    bool any_loss = false;       // some view of a training frame accumulates its loss
     std::vector<Cls> classes;
     // output staging: per view (in order) device pointers used by kernels
     std::vector<pr_frame_grad> grads;  // per view (in order); empty: no adjoint
@@ -480,12 +474,17 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
         for (int q = 0; q < n; ++q) {
             const pr_frame_grad &g = grads[P.order[q]];
             const pr_batch_view &bv = views[P.order[q]];
-            const bool any = g.grad_rgb || g.target_rgb;
-            if (any && (!bv.rgb_out || P.out[q].rgb_host || (g.grad_rgb && !is_device_ptr(g.grad_rgb)) ||
-                        (g.target_rgb && !is_device_ptr(g.target_rgb)) || (g.dcol && !is_device_ptr(g.dcol)) ||
-                        (g.dpos && !is_device_ptr(g.dpos)) || (g.dvel && !is_device_ptr(g.dvel))))
-                return PR_ERR_INVALID_ARG;  // the adjoint in a frame needs device buffers and the shaded image
+            const int nsrc = (g.grad_rgb != nullptr) + (g.target_rgb != nullptr) + (g.target_u8 != nullptr);
+            if (nsrc > 1 || (g.loss && !g.target_rgb && !g.target_u8))
+                return PR_ERR_INVALID_ARG;  // one gradient source; a loss needs a target
+            if (nsrc && (P.out[q].rgb_host || (g.grad_rgb && !is_device_ptr(g.grad_rgb)) ||
+                         (g.target_rgb && !is_device_ptr(g.target_rgb)) ||
+                         (g.target_u8 && !is_device_ptr(g.target_u8)) || (g.loss && !is_device_ptr(g.loss)) ||
+                         (g.dcol && !is_device_ptr(g.dcol)) || (g.dpos && !is_device_ptr(g.dpos)) ||
+                         (g.dvel && !is_device_ptr(g.dvel))))
+                return PR_ERR_INVALID_ARG;  // the adjoint in a frame needs device buffers
             P.grads[q] = g;
+            P.any_loss |= g.loss != nullptr;
         }
     }
     P.ttot = P.tri_off[n];
@@ -527,6 +526,8 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
     PR_TRY(ensure(ws->binned, sizeof(int) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
+    if (P.any_loss)
+        PR_TRY(ensure(ws->loss_part, sizeof(float) * kLossSlots * n));
     if (P.any_fp64) {
         PR_TRY(ensure(ws->flag_bits, sizeof(unsigned) * ((P.npix + 31) / 32 + 1)));
         PR_TRY(ensure(ws->flag_list, sizeof(long long) * std::max(P.npix, 1ll)));
@@ -570,7 +571,10 @@ void fill_tables(pr_workspace *ws, BatchPlan &P, bool shade)
         if (!P.grads.empty()) {
             const pr_frame_grad &g = P.grads[q];
             v.grad_in = g.grad_rgb;
-            v.target = g.grad_rgb ? nullptr : g.target_rgb;
+            v.target = g.target_rgb;
+            v.target_u8 = g.target_u8;
+            v.loss = (g.target_rgb || g.target_u8) ? g.loss : nullptr;
+            v.loss_part = v.loss ? ws->loss_part.as<float>() + (size_t)kLossSlots * q : nullptr;
             v.dcol = g.dcol;
             v.dpos = g.dpos;
             v.dvel = g.dvel;
@@ -630,7 +634,8 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(launch_frame_init(dv, n, tile_offs, tile_box, cnt, ws->heads.as<int>(), tile_cnt, ws->fill.as<unsigned>(),
                              P.ntiles, state_a, scan_state_words(P.ttot), state_b, scan_state_words(P.ntiles),
                              ws->flag_bits.as<unsigned>(), P.any_fp64 ? (P.npix + 31) / 32 + 1 : 0,
-                             ws->keys.as<unsigned long long>(), P.npix, st));
+                             ws->keys.as<unsigned long long>(), P.npix, ws->loss_part.as<float>(),
+                             P.any_loss ? (long long)kLossSlots * n : 0, st));
     int *binned = ws->binned.as<int>();
     PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, binned, cnt, st));
     if (P.any_paper_fov)
@@ -675,6 +680,8 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     if (shade)  // resolves the keys too, and in a training frame runs the adjoint
         PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), !P.grads.empty(), cnt,
                             shade_features(P.vd.data(), n), st));
+    if (shade && P.any_loss)  // the views' loss partial sums into the callers' losses
+        PR_TRY(launch_loss_finalize(dv, n, cnt, st));
     PR_TRY(mark(6));
     // host-side outputs
     for (int q = 0; q < n; ++q) {
@@ -712,6 +719,8 @@ pr_status finish_stats(pr_workspace *ws, const BatchPlan &P)
     ws->read_stage_times();
     if (c.status & ST_TIMEOUT)
         return PR_ERR_TIMEOUT;
+    if (c.status & ST_NONFINITE)
+        return PR_ERR_NONFINITE;  // a scene updated with a non-finite value: its triangles were culled
     if (c.status & ST_BAD_INDEX)
         return PR_ERR_CUDA;  // a kernel's own bounds check caught an inconsistent index (and skipped it)
     if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
@@ -856,10 +865,8 @@ pr_status pr_scene_update(pr_scene *sc, const float *pos, const float *vel, cons
         return PR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const long long V = sc->V;
-    float *soa = sc->soa.as<float>();
-    PR_TRY(ensure(sc->ws.counters, sizeof(Counters)));
-    PR_TRY(cudaMemsetAsync(sc->ws.counters.p, 0, sizeof(Counters), st));
-    // scatter each given [V][3] array into its three planes
+    PR_TRY(cudaMemsetAsync(sc->status.p, 0, sizeof(unsigned), st));
+    // write each given [V][3] array into the vertex records / colours
     const float *arrs[3] = {pos, vel, col};
     for (int a = 0; a < 3; ++a) {
         if (!arrs[a])
@@ -868,10 +875,11 @@ pr_status pr_scene_update(pr_scene *sc, const float *pos, const float *vel, cons
         pr_status s = copy_in(arrs[a], sizeof(float) * 3 * V, sc->stage, &d, st);
         if (s != PR_OK)
             return s;
-        PR_TRY(launch_planes3((const float *)d, V, soa + 3 * a * V, st));
+        PR_TRY(launch_scene_set((const float *)d, a, V, sc->vtx.as<float4>(), sc->col.as<float4>(), st));
     }
-    PR_TRY(launch_scene_check(soa, V, sc->ws.counters.as<Counters>(), st));
-    return check_scene_status(sc, st);
+    // a non-finite value is reported by the next frame that reads the scene
+    PR_TRY(launch_scene_check(sc->vtx.as<float4>(), sc->col.as<float4>(), V, sc->status.as<unsigned>(), st));
+    return PR_OK;
 }
 
 pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, const int32_t *tri, int64_t V,
@@ -891,13 +899,19 @@ pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, 
         return PR_ERR_OOM;
     sc->V = V;
     sc->T = T;
-    pr_status s = from_cuda(ensure(sc->soa, sizeof(float) * 9 * V));
+    pr_status s = from_cuda(ensure(sc->vtx, sizeof(float4) * 2 * V));
     if (s == PR_OK)
-        s = from_cuda(ensure(sc->idx, sizeof(int) * 3 * std::max<int64_t>(T, 1)));
+        s = from_cuda(ensure(sc->col, sizeof(float4) * V));
+    if (s == PR_OK)
+        s = from_cuda(ensure(sc->tri, sizeof(int4) * std::max<int64_t>(T, 1)));
     if (s == PR_OK)
         s = from_cuda(ensure(sc->ws.counters, sizeof(Counters)));
     if (s == PR_OK)
+        s = from_cuda(ensure(sc->status, sizeof(unsigned)));
+    if (s == PR_OK)
         s = from_cuda(cudaMemsetAsync(sc->ws.counters.p, 0, sizeof(Counters), st));
+    if (s == PR_OK)
+        s = from_cuda(cudaMemsetAsync(sc->status.p, 0, sizeof(unsigned), st));
     // stage the three [V][3] arrays and the index array
     DevBuf sp, sv, scol, stri;
     const void *dp = nullptr, *dvel = nullptr, *dc = nullptr, *dt = nullptr;
@@ -910,12 +924,13 @@ pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, 
     if (s == PR_OK && T > 0)
         s = copy_in(tri, sizeof(int) * 3 * T, stri, &dt, st);
     if (s == PR_OK)
-        s = from_cuda(launch_scene_soa((const float *)dp, (const float *)dvel, (const float *)dc, V,
-                                       sc->soa.as<float>(), st));
+        s = from_cuda(launch_scene_pack((const float *)dp, (const float *)dvel, (const float *)dc, V,
+                                        sc->vtx.as<float4>(), sc->col.as<float4>(), st));
     if (s == PR_OK && T > 0)
-        s = from_cuda(launch_scene_idx((const int *)dt, T, V, sc->idx.as<int>(), sc->ws.counters.as<Counters>(), st));
+        s = from_cuda(launch_scene_idx((const int *)dt, T, V, sc->tri.as<int4>(), sc->ws.counters.as<Counters>(), st));
     if (s == PR_OK)
-        s = from_cuda(launch_scene_check(sc->soa.as<float>(), V, sc->ws.counters.as<Counters>(), st));
+        s = from_cuda(launch_scene_check(sc->vtx.as<float4>(), sc->col.as<float4>(), V,
+                                         &sc->ws.counters.as<Counters>()->status, st));
     if (s == PR_OK)
         s = check_scene_status(sc, st);  // synchronises: staging buffers may be released
     if (s != PR_OK) {
@@ -938,7 +953,10 @@ void pr_scene_free(pr_scene *sc)
 pr_status pr_rasterize(pr_scene *sc, const pr_view *view, const pr_params *params, uint32_t *id_out, float *depth_out,
                        void *stream)
 {
-    return single_view(sc, view, params, id_out, depth_out, nullptr, (cudaStream_t)stream);
+    const pr_status s = single_view(sc, view, params, id_out, depth_out, nullptr, (cudaStream_t)stream);
+    if (sc)
+        sc->last_fp64 = params && params->fp64_retest ? 1 : 0;
+    return s;
 }
 
 static pr_status stage_in_ids(pr_scene *sc, const uint32_t *id, long long np, const uint32_t **dev, cudaStream_t st)
@@ -952,7 +970,7 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
         return PR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     ViewDev v;
-    pr_status s = make_viewdev(*view, sc, kDefaultTile, PR_BOUND_ZENON, 0, v);
+    pr_status s = make_viewdev(*view, sc, kDefaultTile, PR_BOUND_ZENON, sc->last_fp64, v);
     if (s != PR_OK)
         return s;
     const long long np = (long long)view->W * view->H;
@@ -1254,6 +1272,8 @@ pr_status pr_graph_status(pr_graph *g)
     }
     if (c.status & ST_TIMEOUT)
         return PR_ERR_TIMEOUT;
+    if (c.status & ST_NONFINITE)
+        return PR_ERR_NONFINITE;  // a scene updated with a non-finite value: its triangles were culled
     if (c.status & (ST_OVERFLOW_PAIRS | ST_OVERFLOW_ITEMS | ST_OVERFLOW_FLAGS))
         return PR_ERR_OVERFLOW;
     return PR_OK;
@@ -1308,6 +1328,23 @@ pr_status pr_debug_bounds(const pr_scene *sc, int32_t *pix_box, float *t_range)
         t_range[2 * k + 0] = rec[k * kRecF4 + 5].x;
         t_range[2 * k + 1] = rec[k * kRecF4 + 5].y;
     }
+    return PR_OK;
+}
+
+pr_status pr_debug_halfplanes(const pr_scene *sc, float *hp_out, int32_t *info)
+{
+    if (!sc || !hp_out || !info)
+        return PR_ERR_INVALID_ARG;
+    const pr_workspace &ws = sc->ws;
+    const long long T = ws.last_T;
+    if (T != sc->T || !ws.tbox.p || !ws.hp.p)
+        return PR_ERR_INVALID_ARG;
+    std::vector<int4> tb(T);
+    PR_TRY(cudaDeviceSynchronize());
+    PR_TRY(cudaMemcpy(tb.data(), ws.tbox.p, sizeof(int4) * T, cudaMemcpyDeviceToHost));
+    PR_TRY(cudaMemcpy(hp_out, ws.hp.p, sizeof(float4) * kMaxHp * T, cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < T; ++k)
+        info[k] = tb[k].z & 0x1ff;
     return PR_OK;
 }
 

@@ -16,6 +16,7 @@ constexpr float kEpsT = 1e-4f;                     // time margin of every catch
 constexpr int kMaxHp = 8;                          // half-planes per bound: <= 6 hull edges + 2 time-strip edges
 constexpr int kRecF4 = 6;                          // float4 per fragment record
 constexpr int kMaxSeg = 1024;                      // longest bin run of one work item (pr_params.seg)
+constexpr int kLossSlots = 256;                    // partial sums per view of a training frame's loss
 
 // Device status bits (Counters::status).
 enum : uint32_t {
@@ -45,14 +46,19 @@ struct ViewDev {
     long long tri_off, tile_off, pix_off;  // offsets of this view in the batch-wide arrays
     long long blk_off;                 // offset of its 8x4 pixel blocks (stages d, e)
     int T, V;
-    const float *px, *py, *pz, *vx, *vy, *vz, *cr, *cg, *cb;  // scene, structure of arrays
-    const int *i0, *i1, *i2;
+    const float4 *vtx;                 // scene vertices, two float4 each: (px, py, pz, vx), (vy, vz, 0, 0)
+    const float4 *col4;                // per-vertex colour (r, g, b, 0)
+    const int4 *tri4;                  // per-triangle vertex indices (i0, i1, i2, 0)
     uint32_t *id_out;                  // resolved outputs (device)
     float *depth_out;
     const uint32_t *id_in;             // ids read by shading / adjoint
     float *rgb_out;
     const float *grad_in;              // adjoint input [3][H][W]
     const float *target;               // or: L2 target [3][H][W], gradient 2 (rgb - target) from rgb_out
+    const unsigned char *target_u8;    // or: 8-bit L2 target [3][H][W] (value / 255)
+    float *loss;                       // L2 loss of the view, accumulated (+=), or null
+    float *loss_part;                  // kLossSlots partial sums of it (workspace; cleared by the frame init)
+    const unsigned *scene_status;      // the scene's status word (ST_NONFINITE after an update), or null
     float *dcol, *dpos, *dvel;         // adjoint outputs [V][3]
     const float4 *rec;                 // this frame's stage (a) records (batch-wide index), or null
 };
@@ -89,8 +95,9 @@ __device__ __forceinline__ int find_view(const long long *off, int n, long long 
 // kernel that needs a vertex calls this one function, so the bits agree.
 __device__ __forceinline__ void vertex_start_end(const ViewDev &v, int k, float3 &S, float3 &E)
 {
-    const float x = v.px[k], y = v.py[k], z = v.pz[k];
-    const float ex = x + v.vx[k], ey = y + v.vy[k], ez = z + v.vz[k];
+    const float4 a = v.vtx[2 * k], b = v.vtx[2 * k + 1];  // one 32-byte sector
+    const float x = a.x, y = a.y, z = a.z;
+    const float ex = x + a.w, ey = y + b.x, ez = z + b.y;
     S.x = fmaf(v.R0[0], x, fmaf(v.R0[1], y, fmaf(v.R0[2], z, v.T0[0])));
     S.y = fmaf(v.R0[3], x, fmaf(v.R0[4], y, fmaf(v.R0[5], z, v.T0[1])));
     S.z = fmaf(v.R0[6], x, fmaf(v.R0[7], y, fmaf(v.R0[8], z, v.T0[2])));
@@ -173,6 +180,45 @@ __device__ __forceinline__ void pixel_ray(const ViewDev &v, int i, int j, float 
     t = is_rolling(v.mode) ? fmaf(x0, v.d0, x1 * v.d1) : 0.f;
     dx = fmaf(2.f, x0, -1.f) * v.tan_x;
     dy = fmaf(2.f, x1, -1.f) * v.tan_y;
+}
+
+// The pixel's time and ray in FP64 from the same inputs (the FP32 view
+// constants widen exactly): u = ((i + 1/2)/W, (j + 1/2)/H), x = q(u) when
+// foveated, t = x . d when rolling, dir = ((2 x0 - 1) tanX, (2 x1 - 1) tanY, 1).
+struct Ray64 {
+    double t, dx, dy;
+};
+
+__device__ inline Ray64 pixel_ray64(const ViewDev &v, int i, int j)
+{
+    double x0 = ((double)i + 0.5) / (double)v.W, x1 = ((double)j + 0.5) / (double)v.H;
+    if (is_foveated(v.mode)) {
+        const double f0 = v.fx, f1 = v.fy;
+        const double e0 = x0 - f0, e1 = x1 - f1;
+        const double r = sqrt(e0 * e0 + e1 * e1);
+        if (r > 0.0) {
+            double s;
+            if (v.p_lut) {  // the sampled p, linear between the samples, in FP64
+                const double D = 1.4142135623730950488, xk = r * (double)v.p_n / D;
+                int k = (int)floor(xk);
+                k = k < 0 ? 0 : (k > v.p_n - 1 ? v.p_n - 1 : k);
+                const double t = xk - (double)k;
+                s = ((1.0 - t) * (double)v.p_lut[k] + t * (double)v.p_lut[k + 1]) / r;
+            } else {
+                s = pow(r / 1.4142135623730950488, (double)v.alpha - 1.0);
+            }
+            x0 = f0 + e0 * s;
+            x1 = f1 + e1 * s;
+        } else {
+            x0 = f0;
+            x1 = f1;
+        }
+    }
+    Ray64 ry;
+    ry.t = is_rolling(v.mode) ? x0 * (double)v.d0 + x1 * (double)v.d1 : 0.0;
+    ry.dx = (2.0 * x0 - 1.0) * (double)v.tan_x;
+    ry.dy = (2.0 * x1 - 1.0) * (double)v.tan_y;
+    return ry;
 }
 
 // Display location (unit coordinates) of a camera-space point with z > 0.

@@ -7,12 +7,14 @@
 
 namespace pr {
 
-// scene upload: [V][3] AoS -> SoA, finiteness and index checks
-cudaError_t launch_scene_soa(const float *pos, const float *vel, const float *col, long long V, float *soa,
-                             cudaStream_t st);
-cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int *idx, Counters *cnt, cudaStream_t st);
-cudaError_t launch_planes3(const float *src, long long V, float *dst, cudaStream_t st);
-cudaError_t launch_scene_check(const float *soa, long long V, Counters *cnt, cudaStream_t st);
+// scene upload: [V][3] arrays -> 32-byte vertex records (vtx, 2 float4 per
+// vertex) and float4 colours, [T][3] indices -> int4; finiteness and index
+// checks.  launch_scene_set replaces one array (which: 0 pos, 1 vel, 2 col).
+cudaError_t launch_scene_pack(const float *pos, const float *vel, const float *col, long long V, float4 *vtx,
+                              float4 *col4, cudaStream_t st);
+cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int4 *tri4, Counters *cnt, cudaStream_t st);
+cudaError_t launch_scene_set(const float *src, int which, long long V, float4 *vtx, float4 *col4, cudaStream_t st);
+cudaError_t launch_scene_check(const float4 *vtx, const float4 *col4, long long V, unsigned *status, cudaStream_t st);
 
 // stage (a): per-triangle bounds (the tiles' display boxes come with the frame init)
 // binned: the triangles with candidate tiles are appended here (cnt->binned)
@@ -54,7 +56,7 @@ cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long 
                               Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
                               unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
                               long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
-                              long long npix, cudaStream_t st);
+                              long long npix, float *loss_part, long long nloss, cudaStream_t st);
 size_t scan_block_sums_needed(long long n);
 // a scan whose look-back waits on a tile that never runs (status word out)
 cudaError_t scan_timeout_probe(cudaStream_t st, unsigned *status);
@@ -85,6 +87,9 @@ int shade_features(const ViewDev *vd, int n);
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                          const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, int feat,
                          cudaStream_t st);
+// a training frame's losses: each view's partial sums (loss_part) added into
+// its loss, once (skipped when the frame's forward overflowed)
+cudaError_t launch_loss_finalize(const ViewDev *views, int nviews, const Counters *frame_cnt, cudaStream_t st);
 // frame_cnt: the counters of the frame whose forward ran just before in the
 // same sequence (the adjoint is skipped if it overflowed), or null.
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,

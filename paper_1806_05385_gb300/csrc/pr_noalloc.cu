@@ -108,26 +108,17 @@ struct Carver {
 
 // View constants of pr_view from the shared validation of every entry
 // point, with the scene arrays in the arena.
-pr_status view_constants(const pr_view &in, int tile, int bound, float *soa, int *idx, long long V, long long T,
-                         ViewDev &v)
+pr_status view_constants(const pr_view &in, int tile, int bound, const float4 *vtx, const float4 *col4,
+                         const int4 *tri4, long long V, long long T, ViewDev &v)
 {
     const pr_status s = derive_view(in, tile, bound, 0, v);
     if (s != PR_OK)
         return s;
     v.T = (int)T;
     v.V = (int)V;
-    v.px = soa;
-    v.py = soa + V;
-    v.pz = soa + 2 * V;
-    v.vx = soa + 3 * V;
-    v.vy = soa + 4 * V;
-    v.vz = soa + 5 * V;
-    v.cr = soa + 6 * V;
-    v.cg = soa + 7 * V;
-    v.cb = soa + 8 * V;
-    v.i0 = idx;
-    v.i1 = idx + T;
-    v.i2 = idx + 2 * T;
+    v.vtx = vtx;
+    v.col4 = col4;
+    v.tri4 = tri4;
     return PR_OK;
 }
 
@@ -161,7 +152,8 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     Carver c;
     const size_t o_views = c.take(sizeof(ViewDev)), o_offs = c.take(sizeof(long long) * 8);
     const size_t o_cnt = c.take(sizeof(Counters)), o_heads = c.take(sizeof(int) * 8);
-    const size_t o_soa = c.take(sizeof(float) * 9 * V), o_idx = c.take(sizeof(int) * 3 * Tn);
+    const size_t o_vtx = c.take(sizeof(float4) * 2 * V), o_col = c.take(sizeof(float4) * V);
+    const size_t o_idx = c.take(sizeof(int4) * Tn);
     const size_t o_rec = c.take(sizeof(float4) * kRecF4 * Tn), o_hp = c.take(sizeof(float4) * kMaxHp * Tn);
     const size_t o_tbox = c.take(sizeof(int4) * Tn), o_cand = c.take(8 * Tn), o_cand_off = c.take(8 * (Tn + 1));
     const size_t o_binned = c.take(sizeof(int) * Tn);
@@ -184,10 +176,10 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     if (!c.ok)
         return PR_ERR_OVERFLOW;  // the bins' alignment padding did not fit either
 
-    float *soa = (float *)(arena + o_soa);
-    int *idx = (int *)(arena + o_idx);
+    float4 *vtx = (float4 *)(arena + o_vtx), *col4 = (float4 *)(arena + o_col);
+    int4 *tri4 = (int4 *)(arena + o_idx);
     ViewDev v;
-    pr_status s = view_constants(*view, tile, bound, soa, idx, V, T, v);
+    pr_status s = view_constants(*view, tile, bound, vtx, col4, tri4, V, T, v);
     if (s != PR_OK)
         return s;
     const int fov_bound = params ? params->fov_bound : PR_FOV_SECTOR;
@@ -201,6 +193,7 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     ViewDev *dv = (ViewDev *)(arena + o_views);
     long long *doffs = (long long *)(arena + o_offs);
     Counters *cnt = (Counters *)(arena + o_cnt);
+    v.scene_status = &cnt->status;  // stage (a) culls every triangle if the scene check below finds a non-finite value
     int *heads = (int *)(arena + o_heads);
     unsigned long long *cand = (unsigned long long *)(arena + o_cand), *cand_off = (unsigned long long *)(arena + o_cand_off);
     unsigned long long *tile_cnt = (unsigned long long *)(arena + o_tile_cnt), *scan = (unsigned long long *)(arena + o_scan);
@@ -222,10 +215,10 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     // what must start at zero, the keys at ~0 (the arena keeps the previous
     // call's contents), and the tiles' display boxes
     NA_TRY(launch_frame_init(dv, 1, tile_offs, tile_box, cnt, heads, tile_cnt, fill, nt, state_a, scan_state_words(T),
-                             state_b, scan_state_words(nt), nullptr, 0, keys, np, st));
-    NA_TRY(launch_scene_soa(pos, vel, col, V, soa, st));
-    NA_TRY(launch_scene_idx(tri, T, V, idx, cnt, st));
-    NA_TRY(launch_scene_check(soa, V, cnt, st));
+                             state_b, scan_state_words(nt), nullptr, 0, keys, np, nullptr, 0, st));
+    NA_TRY(launch_scene_pack(pos, vel, col, V, vtx, col4, st));
+    NA_TRY(launch_scene_idx(tri, T, V, tri4, cnt, st));
+    NA_TRY(launch_scene_check(vtx, col4, V, &cnt->status, st));
     int *binned = (int *)(arena + o_binned);
     NA_TRY(launch_bound(dv, 1, tri_offs, T, rec, hp, tbox, cand, binned, cnt, st));
     if (fov_bound != PR_FOV_SECTOR && (view->mode == PR_FOVEATED || view->mode == PR_BOTH))

@@ -15,81 +15,100 @@ namespace pr {
 
 // ---------------------------------------------------------------- scene
 
-__global__ void k_scene_soa(const float *__restrict__ pos, const float *__restrict__ vel, const float *__restrict__ col,
-                            long long V, float *__restrict__ soa)
+// The scene in device memory: a vertex is one 32-byte record (two float4:
+// position and velocity, px py pz vx | vy vz 0 0), so the gathers of stage
+// (a), of the shading fallback and of the FP64 re-test take one sector per
+// vertex; colours are one float4 per vertex and a triangle's indices one
+// int4, so the shading kernels gather a visible triangle with one index
+// load and three colour loads.
+// which: 0 positions, 1 velocities, 2 colours ([V][3] each) into the records.
+__global__ void k_scene_set(const float *__restrict__ src, int which, long long V, float4 *__restrict__ vtx,
+                            float4 *__restrict__ col4)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= V)
         return;
-    for (int c = 0; c < 3; ++c) {
-        soa[(0 + c) * V + k] = pos[3 * k + c];
-        soa[(3 + c) * V + k] = vel[3 * k + c];
-        soa[(6 + c) * V + k] = col[3 * k + c];
+    const float x = src[3 * k], y = src[3 * k + 1], z = src[3 * k + 2];
+    if (which == 0) {
+        float4 a = vtx[2 * k];
+        a.x = x;
+        a.y = y;
+        a.z = z;
+        vtx[2 * k] = a;
+    } else if (which == 1) {
+        vtx[2 * k].w = x;
+        vtx[2 * k + 1] = make_float4(y, z, 0.f, 0.f);
+    } else {
+        col4[k] = make_float4(x, y, z, 0.f);
     }
 }
 
-__global__ void k_planes3(const float *__restrict__ src, long long V, float *__restrict__ dst)
+__global__ void k_scene_pack(const float *__restrict__ pos, const float *__restrict__ vel,
+                             const float *__restrict__ col, long long V, float4 *__restrict__ vtx,
+                             float4 *__restrict__ col4)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= V)
         return;
-    for (int c = 0; c < 3; ++c)
-        dst[c * V + k] = src[3 * k + c];
+    vtx[2 * k] = make_float4(pos[3 * k], pos[3 * k + 1], pos[3 * k + 2], vel[3 * k]);
+    vtx[2 * k + 1] = make_float4(vel[3 * k + 1], vel[3 * k + 2], 0.f, 0.f);
+    col4[k] = make_float4(col[3 * k], col[3 * k + 1], col[3 * k + 2], 0.f);
 }
 
-cudaError_t launch_planes3(const float *src, long long V, float *dst, cudaStream_t st)
+cudaError_t launch_scene_set(const float *src, int which, long long V, float4 *vtx, float4 *col4, cudaStream_t st)
 {
     if (V > 0)
-        k_planes3<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(src, V, dst);
+        k_scene_set<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(src, which, V, vtx, col4);
     return cudaGetLastError();
 }
 
-__global__ void k_scene_check(const float *__restrict__ soa, long long V, Counters *cnt)
+__global__ void k_scene_check(const float4 *__restrict__ vtx, const float4 *__restrict__ col4, long long V,
+                              unsigned *status)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= V)
         return;
-    bool ok = true;
-    for (int c = 0; c < 9; ++c)
-        ok &= isfinite(soa[c * V + k]);
+    const float4 a = vtx[2 * k], b = vtx[2 * k + 1], c = col4[k];
+    const bool ok = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w) && isfinite(b.x) &&
+                    isfinite(b.y) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
     if (!ok)
-        atomicOr(&cnt->status, ST_NONFINITE);
+        atomicOr(status, ST_NONFINITE);
 }
 
-__global__ void k_scene_idx(const int *__restrict__ tri, long long T, long long V, int *__restrict__ idx, Counters *cnt)
+__global__ void k_scene_idx(const int *__restrict__ tri, long long T, long long V, int4 *__restrict__ tri4,
+                            Counters *cnt)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= T)
         return;
-    bool ok = true;
-    for (int c = 0; c < 3; ++c) {
-        const int a = tri[3 * k + c];
-        ok &= a >= 0 && a < V;
-        idx[c * T + k] = a;
-    }
+    const int a = tri[3 * k], b = tri[3 * k + 1], c = tri[3 * k + 2];
+    const bool ok = a >= 0 && a < V && b >= 0 && b < V && c >= 0 && c < V;
+    // an invalid triangle becomes the degenerate (0, 0, 0), so no kernel that
+    // runs before the host reads the status gathers outside the vertices
+    tri4[k] = ok ? make_int4(a, b, c, 0) : make_int4(0, 0, 0, 0);
     if (!ok)
         atomicOr(&cnt->status, ST_BAD_INDEX);
 }
 
-cudaError_t launch_scene_soa(const float *pos, const float *vel, const float *col, long long V, float *soa,
-                             cudaStream_t st)
+cudaError_t launch_scene_pack(const float *pos, const float *vel, const float *col, long long V, float4 *vtx,
+                              float4 *col4, cudaStream_t st)
 {
     if (V > 0)
-        k_scene_soa<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(pos, vel, col, V, soa);
+        k_scene_pack<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(pos, vel, col, V, vtx, col4);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scene_check(const float *soa, long long V, Counters *cnt, cudaStream_t st)
+cudaError_t launch_scene_check(const float4 *vtx, const float4 *col4, long long V, unsigned *status, cudaStream_t st)
 {
     if (V > 0)
-        k_scene_check<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(soa, V, cnt);
+        k_scene_check<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(vtx, col4, V, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int *idx, Counters *cnt, cudaStream_t st)
+cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int4 *tri4, Counters *cnt, cudaStream_t st)
 {
     if (T > 0)
-        k_scene_idx<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(tri, T, V, idx, cnt);
+        k_scene_idx<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(tri, T, V, tri4, cnt);
     return cudaGetLastError();
 }
 
@@ -277,20 +296,66 @@ __device__ __forceinline__ int clip_polygon(const float2 *in, int n, float4 h, f
     return m;
 }
 
+// Upper bound of n . u over the framebuffer preimage u = q^-1(y) of the
+// display segment a-b (|n| = 1).  q^-1 keeps the direction from the fovea f
+// and maps the distance r to p^-1(r), so the preimage lies in the annular
+// sector between the directions of a and b (a segment that misses f spans
+// less than half a turn) with radii p^-1(r_min) .. p^-1(r_max), r_min and
+// r_max the nearest and farthest distances from f to the segment.  A linear
+// function peaks over that sector at one of its four corners or, when n
+// points between the two directions, on its outer arc.  The radii are
+// widened by a relative 1e-5 for FP32 rounding.
+constexpr int kFovPieces = 16;
+__device__ __forceinline__ float fov_pinv_r(float r, float inv_alpha, const float *lut, int lut_n)
+{
+    if (lut) {
+        const SampledP sp{lut, lut_n};
+        return sp.pinv(r);
+    }
+    return r > 0.f ? kSqrt2 * powf(r * (1.f / kSqrt2), inv_alpha) : 0.f;
+}
+__device__ float sector_support(float2 a, float2 b, float2 f, float2 n, float inv_alpha, const float *lut, int lut_n)
+{
+    const float2 pa = make_float2(a.x - f.x, a.y - f.y), pb = make_float2(b.x - f.x, b.y - f.y);
+    const float ra = sqrtf(pa.x * pa.x + pa.y * pa.y), rb = sqrtf(pb.x * pb.x + pb.y * pb.y);
+    const float2 sg = make_float2(pb.x - pa.x, pb.y - pa.y);
+    const float l2 = sg.x * sg.x + sg.y * sg.y;
+    float tp = l2 > 0.f ? -(pa.x * sg.x + pa.y * sg.y) / l2 : 0.f;
+    tp = fminf(fmaxf(tp, 0.f), 1.f);
+    const float cx = fmaf(tp, sg.x, pa.x), cy = fmaf(tp, sg.y, pa.y);
+    const float rmin = sqrtf(cx * cx + cy * cy), rmax = fmaxf(ra, rb);
+    const float Rmax = fov_pinv_r(rmax, inv_alpha, lut, lut_n) * (1.f + 1e-5f) + 1e-7f;
+    const float base = n.x * f.x + n.y * f.y;
+    if (!(rmin > 1e-6f * (1.f + rmax)))  // the segment passes (next to) the fovea: the whole disc
+        return base + Rmax;
+    const float Rmin = fov_pinv_r(rmin, inv_alpha, lut, lut_n) * (1.f - 1e-5f);
+    float best = -INFINITY;
+    const float da = (n.x * pa.x + n.y * pa.y) / ra, db = (n.x * pb.x + n.y * pb.y) / rb;
+    best = fmaxf(best, da * (da > 0.f ? Rmax : Rmin));
+    best = fmaxf(best, db * (db > 0.f ? Rmax : Rmin));
+    const float cab = pa.x * pb.y - pa.y * pb.x;
+    const float can = pa.x * n.y - pa.y * n.x, cnb = n.x * pb.y - n.y * pb.x;
+    if ((cab > 0.f && can >= 0.f && cnb >= 0.f) || (cab < 0.f && can <= 0.f && cnb <= 0.f))
+        best = fmaxf(best, Rmax);  // n points into the sector: its outer arc
+    return base + best;
+}
+
 // The paper's foveated edge bounds (Sec. 4.1).  The region's display
 // polygon (its box clipped by its half-planes) is bounded edge by edge in
 // the framebuffer: the image under q^-1 of the straight edge x0 -> x1 is a
 // curve, and the bounding line has the edge's own direction (Simple) or the
 // direction of the chord between q^-1(x0) and q^-1(x1) (Recursive), pushed
-// out to the farthest point of the curved region along its normal.  The
+// out past the farthest point of the curved region along its normal.  The
 // paper pushes each line out to its own curve only, which does not hold the
 // region when a neighbouring curve bulges past the line under a strong warp;
-// here every curve is searched.  Each farthest point is found, as in the
-// paper, by a ternary search over the edge parameter (a number of steps
-// logarithmic in the edge's length in pixels), here seeded by a coarse scan
-// of 9 points, and the line gets half a pixel of margin.  Writes the
-// framebuffer half-planes to out (at most kMaxHp); returns their number
-// (0 when the polygon has more edges than that) and their box.
+// here every curve is bounded.  The paper finds each farthest point by a
+// ternary search over the edge parameter, which assumes one maximum per
+// edge; under alpha = 3 near the fovea, where q^-1 stretches without bound,
+// that search missed pixels, so each curve's support is bounded instead
+// (sector_support over kFovPieces pieces), and the line gets half a pixel
+// of margin.  Writes the framebuffer half-planes to out (at most kMaxHp);
+// returns their number (0 when the polygon has more edges than that) and
+// their box.
 struct PaperFov {
     int n;
     float4 fb;
@@ -341,37 +406,17 @@ __device__ __forceinline__ PaperFov paper_fov_bound(const ViewDev &v, const floa
         const float2 nrm = make_float2(d.y / len, -d.x / len);  // outward for the counter-clockwise polygon
         // the line must hold the whole curved region, not only its own edge's
         // image (under a strong warp a neighbouring curve can bulge past it):
-        // the farthest point along the normal over every curved edge
+        // the largest support along the normal over every curved edge,
+        // bounded rigorously over 16 pieces of each edge
         float best = -INFINITY;
         for (int e = 0; e < m; ++e) {
             const float2 y0 = A[e], y1 = A[e + 1 < m ? e + 1 : 0];
-            auto support = [&](float s) {
-                const float2 u = fov_inverse(make_float2(fmaf(s, y1.x - y0.x, y0.x), fmaf(s, y1.y - y0.y, y0.y)), f,
-                                             v.inv_alpha, v.p_lut, v.p_n);
-                return fmaf(nrm.x, u.x, nrm.y * u.y);
-            };
-            int kb = 0;
-            float eb = -INFINITY;
-            for (int j = 0; j <= 8; ++j) {
-                const float val = support(j * 0.125f);
-                if (val > eb) {
-                    eb = val;
-                    kb = j;
-                }
+            for (int j = 0; j < kFovPieces; ++j) {
+                const float s0 = j * (1.f / kFovPieces), s1 = (j + 1) * (1.f / kFovPieces);
+                const float2 a = make_float2(fmaf(s0, y1.x - y0.x, y0.x), fmaf(s0, y1.y - y0.y, y0.y));
+                const float2 b = make_float2(fmaf(s1, y1.x - y0.x, y0.x), fmaf(s1, y1.y - y0.y, y0.y));
+                best = fmaxf(best, sector_support(a, b, f, nrm, v.inv_alpha, v.p_lut, v.p_n));
             }
-            float lo = fmaxf(0.f, (kb - 1) * 0.125f), hi = fminf(1.f, (kb + 1) * 0.125f);
-            const float edge_px = sqrtf((y1.x - y0.x) * (y1.x - y0.x) + (y1.y - y0.y) * (y1.y - y0.y)) * px;
-            const int steps = 2 + (int)ceilf(log2f(fmaxf(edge_px, 1.f)));
-            for (int it = 0; it < steps; ++it) {
-                const float m1 = lo + (hi - lo) * (1.f / 3.f), m2 = hi - (hi - lo) * (1.f / 3.f);
-                const float f1 = support(m1), f2 = support(m2);
-                eb = fmaxf(eb, fmaxf(f1, f2));
-                if (f1 < f2)
-                    lo = m1;
-                else
-                    hi = m2;
-            }
-            best = fmaxf(best, eb);
         }
         out[k] = make_float4(nrm.x, nrm.y, -(best + margin), 0.f);
     }
@@ -670,7 +715,8 @@ __global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ vi
         return;
     const ViewDev &v = views[find_view(tri_offs, nviews, g)];
     const int k = (int)(g - v.tri_off);
-    const int ia = v.i0[k], ib = v.i1[k], ic = v.i2[k];
+    const int4 tv = v.tri4[k];
+    const int ia = tv.x, ib = tv.y, ic = tv.z;
     float3 S[3], E[3], D[3];
     vertex_start_end(v, ia, S[0], E[0]);
     vertex_start_end(v, ib, S[1], E[1]);
@@ -678,7 +724,17 @@ __global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ vi
     for (int q = 0; q < 3; ++q)
         D[q] = make_float3(E[q].x - S[q].x, E[q].y - S[q].y, E[q].z - S[q].z);
     Bound B;
-    compute_bound(v, S, D, B);
+    // a scene updated with a non-finite value: every triangle of it is
+    // culled (nothing downstream sees its coordinates) and the frame reports it
+    const bool bad = v.scene_status && (*v.scene_status & ST_NONFINITE);
+    if (bad) {
+        B.culled = true;
+        const unsigned bm = __activemask();
+        if ((threadIdx.x & 31) == __ffs(bm) - 1)
+            atomicOr(&cnt->status, ST_NONFINITE);
+    } else {
+        compute_bound(v, S, D, B);
+    }
     float4 *r = rec + g * kRecF4;
     r[0] = make_float4(S[0].x, S[0].y, S[0].z, S[1].x);
     r[1] = make_float4(S[1].y, S[1].z, S[2].x, S[2].y);
@@ -1073,7 +1129,7 @@ __global__ void k_frame_init(const ViewDev *__restrict__ views, int nviews, cons
                              float4 *__restrict__ tile_box, Counters *cnt, int *heads, unsigned long long *tile_cnt,
                              unsigned *fill, long long ntiles, unsigned long long *state_a, long long nstate_a,
                              unsigned long long *state_b, long long nstate_b, unsigned *flag_bits, long long nflag,
-                             unsigned long long *keys, long long npix)
+                             unsigned long long *keys, long long npix, float *loss_part, long long nloss)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1092,6 +1148,8 @@ __global__ void k_frame_init(const ViewDev *__restrict__ views, int nviews, cons
         state_b[k] = 0ull;
     for (long long k = g; k < nflag; k += stride)
         flag_bits[k] = 0u;
+    for (long long k = g; k < nloss; k += stride)
+        loss_part[k] = 0.f;
     // keys: 16-byte stores over the even-length prefix, then the last one
     ulonglong2 *k2 = reinterpret_cast<ulonglong2 *>(keys);
     for (long long k = g; k < npix / 2; k += stride)
@@ -1104,7 +1162,7 @@ cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long 
                               Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
                               unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
                               long long nstate_b, unsigned *flag_bits, long long nflag, unsigned long long *keys,
-                              long long npix, cudaStream_t st)
+                              long long npix, float *loss_part, long long nloss, cudaStream_t st)
 {
     static int grid = 0;
     if (grid == 0) {
@@ -1114,7 +1172,7 @@ cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long 
         grid = sms * 8;
     }
     k_frame_init<<<grid, 256, 0, st>>>(views, nviews, tile_offs, tile_box, cnt, heads, tile_cnt, fill, ntiles, state_a,
-                                       nstate_a, state_b, nstate_b, flag_bits, nflag, keys, npix);
+                                       nstate_a, state_b, nstate_b, flag_bits, nflag, keys, npix, loss_part, nloss);
     return cudaGetLastError();
 }
 

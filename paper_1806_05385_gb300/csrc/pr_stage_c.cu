@@ -26,6 +26,15 @@ namespace pr {
 constexpr float kRelCoord = 2e-6f;
 constexpr float kTieRel = 1e-4f;
 constexpr float kKeySlack = 1e-3f;
+// A winning hit whose FP32 depth may be off by more than kDepthRel
+// (relative) also goes to the FP64 re-test, which writes the FP64 depth
+// rounded to FP32.  kRelCoordDepth is the error of a sheared FP32
+// coordinate relative to the magnitudes it came from that this estimate
+// assumes: about 3 ulps (the transform, the interpolation to the pixel
+// time and the shear round once or twice each), not the worst-case
+// allowance kRelCoord of the inside/outside decision.
+constexpr float kDepthRel = 8e-6f;
+constexpr float kRelCoordDepth = 2e-7f;
 
 // One watertight ray/triangle test (Woop, Benthin and Wald, "Watertight
 // Ray/Triangle Intersection", JCGT 2013) of the ray from the origin along
@@ -46,8 +55,15 @@ constexpr float kKeySlack = 1e-3f;
 // sheared coordinates); a pair whose inside/outside outcome is not certain
 // within e, or a hit that ties the current best within kTieRel, sets `flag`
 // when it could still decide the pixel (its plane lies in front of the best
-// hit, within the tie allowance).
-template <bool kFlag>
+// hit, within the tie allowance).  kDepthFlag (the fragment stage's
+// precision form): a hit that becomes the pixel's best also sets `flag` when
+// its depth is ill-conditioned.  Moving sheared vertex k by at most c_k per
+// coordinate moves the plane's depth on the ray (the z axis) by at most
+// (sum_k b_k c_k) (1 + (|Nx| + |Ny|) / |Nz|) to first order, with b_k the
+// hit's barycentrics, N the normal of the sheared triangle and |Nz| =
+// |det|: a grazing ray has a large tangent.  c_k is kRelCoordDepth times
+// the magnitude vertex k's coordinates came from.
+template <bool kFlag, bool kDepthFlag = false>
 __device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const float4 r2, const float4 r3,
                                          const float d2y, const float d2z, const float t, const float dx,
                                          const float dy, const float zn, const uint32_t id, unsigned long long &best,
@@ -96,6 +112,17 @@ __device__ __forceinline__ void ray_test(const float4 r0, const float4 r1, const
     if (key < best) {
         best = key;
         best_depth = depth;
+        if (kFlag && kDepthFlag) {
+            const float e1x = bx - ax, e1y = by - ay, e1z = Bz - Az, e2x = cx - ax, e2y = cy - ay, e2z = Cz - Az;
+            const float nx = fabsf(fmaf(e1y, e2z, -e1z * e2y)), ny = fabsf(fmaf(e1z, e2x, -e1x * e2z));
+            const float sd = 1.f + fabsf(dx) + fabsf(dy);
+            // sum_k b_k |coordinates of k| times |det| (U, V, W share det's sign on a hit)
+            const float magb = fabsf(U) * fmaf(fabsf(Az), sd, fabsf(ax) + fabsf(ay)) +
+                               fabsf(V) * fmaf(fabsf(Bz), sd, fabsf(bx) + fabsf(by)) +
+                               fabsf(W) * fmaf(fabsf(Cz), sd, fabsf(cx) + fabsf(cy));
+            if (kRelCoordDepth * magb * (adet + nx + ny) > kDepthRel * depth * adet * adet)
+                flag = true;
+        }
     }
 }
 
@@ -255,8 +282,8 @@ __global__ void __launch_bounds__(S *S / 2, PR_FRAG_MINB(S *S / 2))
                 const float ky = __shfl_sync(0xffffffffu, d2y, k), kz = __shfl_sync(0xffffffffu, d2z, k);
                 const unsigned id = __shfl_sync(0xffffffffu, gid, k) - id_base;
                 ++tested;
-                ray_test<kFlag>(r0, r1, r2, r3, ky, kz, t0, dx0, dy0, zn, id, best0, bd0, hits, fl0);
-                ray_test<kFlag>(r0, r1, r2, r3, ky, kz, t1, dx1, dy1, zn, id, best1, bd1, hits, fl1);
+                ray_test<kFlag, kFlag>(r0, r1, r2, r3, ky, kz, t0, dx0, dy0, zn, id, best0, bd0, hits, fl0);
+                ray_test<kFlag, kFlag>(r0, r1, r2, r3, ky, kz, t1, dx1, dy1, zn, id, best1, bd1, hits, fl1);
             }
             if (stop)
                 break;
@@ -359,45 +386,6 @@ cudaError_t launch_fragment(int S, bool flag, const ViewDev *views, const int4 *
 
 // ---------------------------------------------------------------- FP64 re-test
 
-// The pixel's time and ray in FP64 from the same inputs (the FP32 view
-// constants widen exactly): u = ((i + 1/2)/W, (j + 1/2)/H), x = q(u) when
-// foveated, t = x . d when rolling, dir = ((2 x0 - 1) tanX, (2 x1 - 1) tanY, 1).
-struct Ray64 {
-    double t, dx, dy;
-};
-
-__device__ Ray64 pixel_ray64(const ViewDev &v, int i, int j)
-{
-    double x0 = ((double)i + 0.5) / (double)v.W, x1 = ((double)j + 0.5) / (double)v.H;
-    if (is_foveated(v.mode)) {
-        const double f0 = v.fx, f1 = v.fy;
-        const double e0 = x0 - f0, e1 = x1 - f1;
-        const double r = sqrt(e0 * e0 + e1 * e1);
-        if (r > 0.0) {
-            double s;
-            if (v.p_lut) {  // the sampled p, linear between the samples, in FP64
-                const double D = 1.4142135623730950488, xk = r * (double)v.p_n / D;
-                int k = (int)floor(xk);
-                k = k < 0 ? 0 : (k > v.p_n - 1 ? v.p_n - 1 : k);
-                const double t = xk - (double)k;
-                s = ((1.0 - t) * (double)v.p_lut[k] + t * (double)v.p_lut[k + 1]) / r;
-            } else {
-                s = pow(r / 1.4142135623730950488, (double)v.alpha - 1.0);
-            }
-            x0 = f0 + e0 * s;
-            x1 = f1 + e1 * s;
-        } else {
-            x0 = f0;
-            x1 = f1;
-        }
-    }
-    Ray64 ry;
-    ry.t = is_rolling(v.mode) ? x0 * (double)v.d0 + x1 * (double)v.d1 : 0.0;
-    ry.dx = (2.0 * x0 - 1.0) * (double)v.tan_x;
-    ry.dy = (2.0 * x1 - 1.0) * (double)v.tan_y;
-    return ry;
-}
-
 // The map from a vertex (p, v) to its sheared camera-space position at the
 // pixel's time, in FP64: with M = (1-t) R0 + t R1, N = t R1 and
 // T = (1-t) T0 + t T1 the moved vertex is c = M p + N v + T (the same
@@ -436,8 +424,9 @@ __device__ Shear64 shear64(const ViewDev &v, const Ray64 &ry)
 
 __device__ __forceinline__ double3 sheared64(const ViewDev &v, const Shear64 &sh, int k)
 {
-    const double p[3] = {v.px[k], v.py[k], v.pz[k]};
-    const double w[3] = {v.vx[k], v.vy[k], v.vz[k]};
+    const float4 va = v.vtx[2 * k], vb = v.vtx[2 * k + 1];
+    const double p[3] = {va.x, va.y, va.z};
+    const double w[3] = {va.w, vb.x, vb.y};
     double a[3];
     for (int r = 0; r < 3; ++r)
         a[r] = sh.c[r] + sh.P[r][0] * p[0] + sh.P[r][1] * p[1] + sh.P[r][2] * p[2] + sh.Q[r][0] * w[0] +
@@ -450,7 +439,8 @@ __device__ __forceinline__ double3 sheared64(const ViewDev &v, const Shear64 &sh
 // to the caller, who needs it only for the winner).
 __device__ bool hit64(const ViewDev &v, const Shear64 &sh, int tri, double &num, double &den)
 {
-    const double3 A = sheared64(v, sh, v.i0[tri]), B = sheared64(v, sh, v.i1[tri]), C = sheared64(v, sh, v.i2[tri]);
+    const int4 tv = v.tri4[tri];
+    const double3 A = sheared64(v, sh, tv.x), B = sheared64(v, sh, tv.y), C = sheared64(v, sh, tv.z);
     const double ax = A.x, ay = A.y, bx = B.x, by = B.y, cx = C.x, cy = C.y;
     const double U = cx * by - cy * bx, V = ax * cy - ay * cx, W = bx * ay - by * ax;
     if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0))

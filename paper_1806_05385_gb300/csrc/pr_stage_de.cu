@@ -40,10 +40,28 @@ struct PixelHit {
 };
 
 // Paths the shading kernels are built with: a view of the launch may have a
-// specular term (k_s > 0), a view may use a sampled foveation function.  The
-// kernels built without a path are faster (fewer registers); the results of
-// the views they shade are the same bits.
-constexpr int kFeatSpec = 1, kFeatLut = 2;
+// specular term (k_s > 0), a view may use a sampled foveation function, a
+// view may ask for the precision form.  The kernels built without a path
+// are faster (fewer registers); the results of the views they shade are the
+// same bits.
+constexpr int kFeatSpec = 1, kFeatLut = 2, kFeatF64 = 4;
+
+// Precision form of the shading: the FP32 barycentrics of a triangle that
+// is small against its distance carry an error of about (coordinate error)
+// x (sheared extent) / |det|, that is one coordinate ulp over the
+// triangle's size; a pixel whose estimate exceeds kBaryRel takes its moved
+// triangle, barycentrics and normal from FP64 instead (the FP32 coordinate
+// error is taken as kRelCoordShade of the magnitudes it came from, about
+// one ulp: measured colour errors of such triangles match it).
+constexpr float kBaryRel = 2e-5f;
+constexpr float kRelCoordShade = 6e-8f;
+
+// The pixel's moved triangle, barycentrics and unit normal in FP64 from the
+// scene's FP32 inputs (widened exactly), rounded to FP32 into h: the
+// interpolation of M_s v_s and M_e v_e at the pixel time, the ray-plane
+// barycentrics b_k = w_k / sum w with w_0 = dir.(B x C) (cyclically) and the
+// face normal turned to face the viewer.
+__device__ __noinline__ void pixel_hit64(const ViewDev &v, int i, int j, struct PixelHit &h);
 
 template <int kFeat>
 __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsigned id, PixelHit &h)
@@ -51,9 +69,10 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     float x0, x1, dx, dy;
     pixel_ray<(kFeat & kFeatLut) != 0>(v, i, j, x0, x1, h.t, dx, dy);
     h.dir = make_float3(dx, dy, 1.f);
-    h.ia = v.i0[id];
-    h.ib = v.i1[id];
-    h.ic = v.i2[id];
+    const int4 tv = v.tri4[id];
+    h.ia = tv.x;
+    h.ib = tv.y;
+    h.ic = tv.z;
     const float t = h.t;
     if (v.rec) {
         // the frame's own stage (a) record: S and D = E - S, the same bits
@@ -90,6 +109,13 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     const float rs = nn > 0.f ? rsqrtf(nn) : 0.f;
     h.inl = flip * rs;
     h.n = scale3(n, h.inl);
+    if ((kFeat & kFeatF64) && v.fp64) {
+        const float sm = fmaxf(fabsf(ax) + fabsf(ay), fmaxf(fabsf(bx) + fabsf(by), fabsf(cx) + fabsf(cy)));
+        const float zm = fmaxf(fabsf(h.A.z), fmaxf(fabsf(h.B.z), fabsf(h.C.z)));
+        const float mag = zm * (1.f + fabsf(dx) + fabsf(dy)) + sm;
+        if (2.f * kRelCoordShade * mag * sm > kBaryRel * fabsf(h.det))
+            pixel_hit64(v, i, j, h);
+    }
     float3 l = make_float3(fmaf(t, v.l1[0] - v.l0[0], v.l0[0]), fmaf(t, v.l1[1] - v.l0[1], v.l0[1]),
                            fmaf(t, v.l1[2] - v.l0[2], v.l0[2]));
     h.l = scale3(l, rsqrtf(dot3(l, l)));
@@ -105,6 +131,49 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
         h.ndh = dot3(h.n, h.hv);
         h.spec = h.ndh > 0.f ? v.k_s * powf(h.ndh, v.shininess) : 0.f;
     }
+}
+
+__device__ __noinline__ void pixel_hit64(const ViewDev &v, int i, int j, PixelHit &h)
+{
+    const Ray64 ry = pixel_ray64(v, i, j);
+    const double d[3] = {ry.dx, ry.dy, 1.0};
+    const int vid[3] = {h.ia, h.ib, h.ic};
+    double P[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const float4 va = v.vtx[2 * vid[k]], vb = v.vtx[2 * vid[k] + 1];
+        const double p[3] = {va.x, va.y, va.z}, e[3] = {p[0] + (double)va.w, p[1] + (double)vb.x, p[2] + (double)vb.y};
+        for (int r = 0; r < 3; ++r) {
+            const double S = (double)v.R0[3 * r] * p[0] + (double)v.R0[3 * r + 1] * p[1] + (double)v.R0[3 * r + 2] * p[2] +
+                             (double)v.T0[r];
+            const double E = (double)v.R1[3 * r] * e[0] + (double)v.R1[3 * r + 1] * e[1] + (double)v.R1[3 * r + 2] * e[2] +
+                             (double)v.T1[r];
+            P[k][r] = (1.0 - ry.t) * S + ry.t * E;
+        }
+    }
+    double w[3];
+    for (int k = 0; k < 3; ++k) {
+        const double *b = P[(k + 1) % 3], *c = P[(k + 2) % 3];
+        w[k] = d[0] * (b[1] * c[2] - b[2] * c[1]) + d[1] * (b[2] * c[0] - b[0] * c[2]) + d[2] * (b[0] * c[1] - b[1] * c[0]);
+    }
+    const double sw = w[0] + w[1] + w[2];
+    if (sw != 0.0) {
+        h.b0 = (float)(w[0] / sw);
+        h.b1 = (float)(w[1] / sw);
+        h.b2 = (float)(w[2] / sw);
+        h.det = (float)(-sw);  // the watertight edge functions are -w
+    }
+    const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (len > 0.0) {
+        const double s = (n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > 0.0 ? -1.0 : 1.0) / len;
+        h.n = make_float3((float)(n[0] * s), (float)(n[1] * s), (float)(n[2] * s));
+        h.inl = (float)s;
+    }
+    h.A = make_float3((float)P[0][0], (float)P[0][1], (float)P[0][2]);
+    h.B = make_float3((float)P[1][0], (float)P[1][1], (float)P[1][2]);
+    h.C = make_float3((float)P[2][0], (float)P[2][1], (float)P[2][2]);
 }
 
 // Stages (d) and (e) run each warp over kShadeBlocks consecutive 8x4 pixel
@@ -144,9 +213,10 @@ __device__ __forceinline__ void pixel_albedo(const ViewDev &v, const PixelHit &h
     const int vid[3] = {h.ia, h.ib, h.ic};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        pa.col[k][0] = v.cr[vid[k]];
-        pa.col[k][1] = v.cg[vid[k]];
-        pa.col[k][2] = v.cb[vid[k]];
+        const float4 c = v.col4[vid[k]];
+        pa.col[k][0] = c.x;
+        pa.col[k][1] = c.y;
+        pa.col[k][2] = c.z;
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -380,15 +450,21 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
         const bool inside = block_pixel(views, nviews, blk_offs, b0 + p, lane, q, lin, pi, pj);
         const ViewDev &v = views[q];
         const long long plane = (long long)v.W * v.H;
-        const bool grad = adjoint && (v.grad_in || v.target);
+        const bool grad = adjoint && (v.grad_in || v.target || v.target_u8);
         // the upstream gradient (or L2 target) does not depend on the hit:
         // its loads go out first, before the key and the stores below
         float gin[3] = {0.f, 0.f, 0.f};
         if (grad && inside) {
-            const float *gsrc = v.grad_in ? v.grad_in : v.target;
-            gin[0] = gsrc[lin];
-            gin[1] = gsrc[plane + lin];
-            gin[2] = gsrc[2 * plane + lin];
+            if (v.target_u8) {
+                gin[0] = (float)v.target_u8[lin] * (1.f / 255.f);
+                gin[1] = (float)v.target_u8[plane + lin] * (1.f / 255.f);
+                gin[2] = (float)v.target_u8[2 * plane + lin] * (1.f / 255.f);
+            } else {
+                const float *gsrc = v.grad_in ? v.grad_in : v.target;
+                gin[0] = gsrc[lin];
+                gin[1] = gsrc[plane + lin];
+                gin[2] = gsrc[2 * plane + lin];
+            }
         }
         unsigned id = 0xFFFFFFFFu;
         if (inside) {
@@ -424,17 +500,61 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
         if (kAdjoint) {
             const bool valid = hit && grad;
             float g0 = gin[0], g1 = gin[1], g2 = gin[2];
-            if (valid && !v.grad_in) {
+            float lsum = 0.f;  // this pixel's share of the L2 loss (background: rgb = 0)
+            if (grad && inside && !v.grad_in) {
                 // L2 loss sum (rgb - target)^2: its gradient from this frame's image
-                g0 = 2.f * (rgb[0] - gin[0]);
-                g1 = 2.f * (rgb[1] - gin[1]);
-                g2 = 2.f * (rgb[2] - gin[2]);
+                const float e0 = rgb[0] - gin[0], e1 = rgb[1] - gin[1], e2 = rgb[2] - gin[2];
+                lsum = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+                g0 = 2.f * e0;
+                g1 = 2.f * e1;
+                g2 = 2.f * e2;
             }
             adjoint_step<kFeat>(views, acc, valid, q, id, h, pa, g0, g1, g2);
+            if (adjoint && v.loss) {
+                // one view per warp: a warp sum, then one atomic into one of
+                // the view's partial sums (one address for every warp of a
+                // view would serialise them)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+                if (lane == 0)
+                    atomicAdd(&v.loss_part[(unsigned)b0 & (kLossSlots - 1)], lsum);
+            }
         }
     }
     if (kAdjoint)
         adjoint_flush(views, acc);
+}
+
+// A training frame's losses: one block per view sums the view's partial
+// sums and adds them to the caller's loss (views without a loss: nothing).
+__global__ void __launch_bounds__(kLossSlots) k_loss_finalize(const ViewDev *__restrict__ views,
+                                                              const Counters *__restrict__ frame_cnt)
+{
+    const ViewDev &v = views[blockIdx.x];
+    if (!v.loss || frame_overflowed(frame_cnt))
+        return;  // an overflowed forward is rerun by the host: its loss must not count
+    float s = v.loss_part[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float ws[kLossSlots / 32];
+    if ((threadIdx.x & 31) == 0)
+        ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kLossSlots / 32; ++w)
+            t += ws[w];
+        atomicAdd(v.loss, t);  // several views may share one loss
+    }
+}
+
+cudaError_t launch_loss_finalize(const ViewDev *views, int nviews, const Counters *frame_cnt, cudaStream_t st)
+{
+    if (nviews > 0)
+        k_loss_finalize<<<nviews, kLossSlots, 0, st>>>(views, frame_cnt);
+    return cudaGetLastError();
 }
 
 // Warps of kShadeBlocks blocks, 256 threads per CTA.
@@ -449,6 +569,11 @@ static void launch_shade_t(int feat, unsigned g, const ViewDev *views, int nview
                            long long nblocks, const unsigned long long *keys, const Counters *frame_cnt,
                            cudaStream_t st)
 {
+    if (feat & kFeatF64) {  // the precision form: one variant with every path (same bits as the others)
+        k_shade<kAdjoint, kFeatSpec | kFeatLut | kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys,
+                                                                             frame_cnt);
+        return;
+    }
     switch (feat) {
     case 0:
         k_shade<kAdjoint, 0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
@@ -472,6 +597,8 @@ int shade_features(const ViewDev *vd, int n)
             f |= kFeatSpec;
         if (vd[k].p_lut && (vd[k].mode == PR_FOVEATED || vd[k].mode == PR_BOTH))
             f |= kFeatLut;
+        if (vd[k].fp64)
+            f |= kFeatF64;
     }
     return f;
 }
@@ -544,6 +671,10 @@ cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *b
 {
     if (nblocks > 0) {
         const unsigned g = shade_grid(nblocks);
+        if (feat & kFeatF64) {
+            k_backward<kFeatSpec | kFeatLut | kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            return cudaGetLastError();
+        }
         switch (feat) {
         case 0:
             k_backward<0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);

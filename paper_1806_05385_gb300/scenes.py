@@ -324,6 +324,31 @@ def config_batched(seed: int = 4, n_views: int = 64, T_range=(1_000, 500_000), s
     return out
 
 
+def config_batched_span(seed: int = 4, n_views: int = 8, T_range=(1_000, 500_000), side_range=(512, 2160),
+                        tiles=(8, 16, 32)):
+    """A batch shaped like the 64-view workload that spans its extremes:
+    view k has T_k = T_lo (T_hi/T_lo)^(k/(n-1)) triangles (so the first has
+    1k and the last 500k), a square side taken from the same geometric
+    sequence over ``side_range`` in a seeded order, mode k mod 4 (every mode
+    twice for 8 views) and tile size tiles[k mod 3]; scenes, fovea and head
+    motion follow the 64-view recipe.  Returns (scene, view, tile) triples."""
+    rng = np.random.default_rng(seed)
+    n = n_views
+    Ts = [int(round(T_range[0] * (T_range[1] / T_range[0]) ** (k / (n - 1)))) for k in range(n)]
+    sides = [int(round(side_range[0] * (side_range[1] / side_range[0]) ** (k / (n - 1)))) for k in range(n)]
+    sides = [sides[k] for k in rng.permutation(n)]
+    out = []
+    for k in range(n):
+        tx, ty = hmd_fov(sides[k], sides[k], 90.0)
+        sc = instance_scene(rng, Ts[k], tx, ty, kinds=("ico2", "box"), radius=(0.01, 1.0), log_size=True,
+                            move_frac=0.5)
+        p0, p1 = head_poses(rng.uniform(0.0, 3.0), rng.uniform(0.0, 1.0))
+        fov = tuple(rng.uniform(0.2, 0.8, size=2).tolist())
+        out.append((sc, View(W=sides[k], H=sides[k], tan_x=tx, tan_y=ty, pose0=p0, pose1=p1, mode=k % 4,
+                             fovea=fov, alpha=2.0), tiles[k % len(tiles)]))
+    return out
+
+
 def config_diff(seed: int = 5, W: int = 512, H: int = 512, T: int = 10_000, sigma: float = 0.01):
     """Differentiable case: 512x512 rolling+foveated, 10k small triangles
     (centres as the small config, vertex offsets U[-0.15,0.15]^3).  Returns

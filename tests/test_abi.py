@@ -48,10 +48,11 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pr_view), offsetof(pr_view, pose0),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pr_view), offsetof(pr_view, pose0),
          offsetof(pr_view, light_w), sizeof(pr_params), sizeof(pr_stats), sizeof(pr_batch_view),
          offsetof(pr_batch_view, id_out), offsetof(pr_batch_view, tile), sizeof(pr_frame_grad),
-         offsetof(pr_frame_grad, dvel), sizeof(pr_backward_view), offsetof(pr_backward_view, dvel));
+         offsetof(pr_frame_grad, dvel), sizeof(pr_backward_view), offsetof(pr_backward_view, dvel),
+         offsetof(pr_frame_grad, target_u8), offsetof(pr_frame_grad, loss));
   return 0;
 }}
 """)
@@ -61,7 +62,7 @@ int main(void) {{
     want = [C.sizeof(B.PrView), B.PrView.pose0.offset, B.PrView.light_w.offset, C.sizeof(B.PrParams),
             C.sizeof(B.PrStats), C.sizeof(B.PrBatchView), B.PrBatchView.id_out.offset, B.PrBatchView.tile.offset,
             C.sizeof(B.PrFrameGrad), B.PrFrameGrad.dvel.offset, C.sizeof(B.PrBackwardView),
-            B.PrBackwardView.dvel.offset]
+            B.PrBackwardView.dvel.offset, B.PrFrameGrad.target_u8.offset, B.PrFrameGrad.loss.offset]
     assert got == want
 
 

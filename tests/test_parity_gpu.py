@@ -127,27 +127,72 @@ def test_bound_kinds_give_identical_images(pr, mode):
         assert tests["zenon"] <= tests["hull"] <= tests["quad"] * 1.0001 + 1
 
 
-@pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("bound", ["zenon", "adaptive", "hull"])
-def test_bounds_are_conservative(pr, oracle, mode, bound):
+def _check_conservative(pr, oracle, sc, view, bound="zenon", fov_bound="sector"):
     """Every pixel the oracle assigns to a triangle lies in that triangle's
-    stage (a) framebuffer box, and its time lies in the triangle's interval
-    (Sec. 3.2: the bound covers every pixel the triangle affects at any
-    time)."""
-    sc, view = small_case(mode, seed=3, W=192, H=160, T=700)
-    g = gpu_frame(pr, sc, view, bound=bound, keep=True)
-    box, tr = pr.pr_debug_bounds(g["scene"], sc.T)
-    pr.pr_scene_free(g["scene"])
+    stage (a) framebuffer box, its time in the triangle's interval, and its
+    location inside every half-plane the binning tests: display half-planes
+    at the pixel's display location x (Sec. 4.2), or, for the paper's
+    foveation bounds, framebuffer lines at its unit framebuffer location u
+    (Sec. 4.1).  Returns the number of (pixel, half-plane) checks made."""
+    import torch
+    h = pr.pr_scene_upload(*(_dev(a) for a in (sc.pos, sc.vel, sc.col, sc.tri)))
+    try:
+        n = view.W * view.H
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        pr.pr_rasterize(h, view, pr.make_params(bound, 16, 0, 0, fov_bound=fov_bound), ids, None)
+        box, tr = pr.pr_debug_bounds(h, sc.T)
+        hp, info = pr.pr_debug_halfplanes(h, sc.T)
+    finally:
+        pr.pr_scene_free(h)
     o = oracle.render(view, sc.pos, sc.vel, sc.col, sc.tri)
-    t, _, _ = oracle.pixels(view)
+    t, x, _ = oracle.pixels(view)
     hit = np.nonzero(o["id"] != BG)[0]
-    ids = o["id"][hit]
+    ids = o["id"][hit].astype(np.int64)
     i, j = hit % view.W, hit // view.W
     b = box[ids]
     inside = (i >= b[:, 0]) & (i <= b[:, 2]) & (j >= b[:, 1]) & (j <= b[:, 3])
     assert inside.all(), hit[~inside][:10]
     tt = t[hit]
     assert np.all((tt >= tr[ids, 0]) & (tt <= tr[ids, 1]))
+    u = np.stack([(i + 0.5) / view.W, (j + 0.5) / view.H], 1)
+    fb = (info[ids] & 0x100) != 0
+    pt = np.where(fb[:, None], u, x[hit])
+    nh = info[ids] & 0xFF
+    checks = 0
+    for k in range(8):
+        use = nh > k
+        hk = hp[ids[use], k].astype(np.float64)
+        val = hk[:, 0] * pt[use, 0] + hk[:, 1] * pt[use, 1] + hk[:, 2]
+        assert np.all(val <= 0.0), (k, hit[use][val > 0][:5], val[val > 0][:5])
+        checks += int(use.sum())
+    return checks, int(fb.sum())
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("bound", ["zenon", "adaptive", "hull"])
+def test_bounds_are_conservative(pr, oracle, mode, bound):
+    """Sec. 3.2: the bound covers every pixel the triangle affects at any
+    time -- box, interval and display half-planes."""
+    sc, view = small_case(mode, seed=3, W=192, H=160, T=700)
+    _check_conservative(pr, oracle, sc, view, bound)
+
+
+@pytest.mark.parametrize("alpha", [2.0, 3.0])
+@pytest.mark.parametrize("fov_bound", ["simple", "recursive"])
+@pytest.mark.parametrize("mode", [S.MODE_FOVEATED, S.MODE_BOTH])
+@pytest.mark.parametrize("seed", [3, 12, 31])
+def test_paper_foveation_bounds_are_conservative(pr, oracle, mode, fov_bound, alpha, seed):
+    """Sec. 4.1.1-4.1.2: the Simple and Recursive edge bounds, whose lines
+    bin the tiles in framebuffer space, hold every pixel the oracle assigns
+    to the triangle (their ternary searches rest on a unimodal edge
+    displacement; the coarse seed scan and the half-pixel margin must cover
+    these scenes)."""
+    sc = S.random_triangles(700, seed, offset=0.6 if seed % 2 else None)
+    p0, p1 = S.head_poses(2.0, 0.5)
+    view = S.View(W=192, H=160, tan_x=0.5, tan_y=0.5, pose0=p0, pose1=p1, mode=mode,
+                  fovea=(0.3 + 0.01 * seed, 0.62 - 0.01 * seed), alpha=alpha)
+    checks, nfb = _check_conservative(pr, oracle, sc, view, "zenon", fov_bound)
+    assert nfb > 0 and checks > 0
 
 
 def test_ragged_tiny_frames(pr, oracle):
@@ -264,7 +309,10 @@ def test_fp64_retest_meets_strict_tolerance(pr, oracle, mode):
     o = oracle.render(view, sc.pos, sc.vel, sc.col, sc.tri)
     compare(oracle, view, sc, o, g["id"], g["depth"], g["rgb"], fp64=True)
     st = g["stats"]
-    assert 0 < st["flagged"] < 0.2 * view.W * view.H
+    # near-edge, near-tie and ill-conditioned-depth pixels: a minority, even
+    # on these large, randomly oriented triangles (the foveated frame, whose
+    # fovea packs many pixels next to each edge, flags about a quarter)
+    assert 0 < st["flagged"] < 0.3 * view.W * view.H
     assert st["fp64_depth_err"] < 1e-4
     # the FP32-only frame differs from the re-tested one only at flagged pixels
     g32 = gpu_frame(pr, sc, view, fp64=0)
