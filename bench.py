@@ -288,10 +288,21 @@ def our_arm(args, rank, world):
     rgb = [torch.empty(3 * n, dtype=torch.float32, device="cuda") for n in npx]
     gen = torch.Generator(device="cuda").manual_seed(1234)
     grad = [torch.randn(3 * n, device="cuda", generator=gen) for n in npx]
-    # the training targets: one 8-bit RGB image per view (seeded synthetic)
-    tgt8 = [torch.randint(0, 256, (3 * n,), dtype=torch.uint8, device="cuda", generator=gen) for n in npx]
+    # the training targets: one 8-bit RGB image per view (seeded synthetic),
+    # slices of one flat buffer; the gradients of every scene ([V][3] dcol,
+    # dpos, dvel) slices of one flat buffer too, so a training loop moves
+    # each with one copy
+    pix_off = np.concatenate([[0], np.cumsum([3 * n for n in npx])]).astype(np.int64)
+    tflat = torch.randint(0, 256, (int(pix_off[-1]),), dtype=torch.uint8, device="cuda", generator=gen)
+    tgt8 = [tflat[int(pix_off[k]):int(pix_off[k + 1])] for k in range(len(views))]
     loss = torch.zeros(len(views), device="cuda")
-    grads = [tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3)) for sc in wl.scenes]
+    v_off = np.concatenate([[0], np.cumsum([9 * sc.V for sc in wl.scenes])]).astype(np.int64)
+    gflat = torch.zeros(int(v_off[-1]), device="cuda")
+
+    def scene_slices(flat, s):
+        o, V = int(v_off[s]), wl.scenes[s].V
+        return flat[o:o + 3 * V], flat[o + 3 * V:o + 6 * V], flat[o + 6 * V:o + 9 * V]
+    grads = [scene_slices(gflat, s) for s in range(len(wl.scenes))]
     if args.workload == "batched":
         from paper_1806_05385_gb300 import autotune
         tiles = autotune.tune([(hv[k], v, wl.scenes[wl.scene_of[k]].T) for k, v in enumerate(views)])
@@ -420,59 +431,62 @@ def our_arm(args, rank, world):
     value, mean_ms = aggregate(sum(step_ms) / len(step_ms), pix * R, dist, "cuda")
 
     # end to end through the public API, as a training loop runs it: every
-    # step the current scene parameters (positions, velocities, colours:
-    # the host's copy, as an optimiser on the host keeps them) and the
-    # step's 8-bit target images go up from pinned host memory -- the
-    # parameters through pr_scene_update itself, which stages host arrays
-    # and returns without waiting -- the training-frame graph replays
-    # (forward, L2 loss, adjoint), and the per-view losses and per-vertex
-    # gradients come back to pinned host memory, with every replay's status
-    # read on the host.  No image comes back: a training step returns its
-    # loss and gradients.
+    # step the current scene parameters (positions, velocities, colours of
+    # every scene: the host's copy, as an optimiser on the host keeps them)
+    # and the step's 8-bit target images go up from pinned host memory, one
+    # copy each, pr_scene_update_batch steps every scene from them, the
+    # training-frame graph replays (forward, L2 loss, adjoint), and the
+    # per-view losses and the per-vertex gradients come back to pinned host
+    # memory, one copy each, with every replay's status read on the host.
+    # No image comes back: a training step returns its loss and gradients.
     e2e = None
     if not args.no_e2e:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        hsc = [(pin(sc.pos), pin(sc.vel), pin(sc.col)) for sc in wl.scenes]
-        htg = [t.cpu().pin_memory() for t in tgt8]
+        hpar = torch.cat([torch.from_numpy(np.concatenate([sc.pos.ravel(), sc.vel.ravel(), sc.col.ravel()]))
+                          for sc in wl.scenes]).pin_memory()
+        htf = tflat.cpu().pin_memory()
         hloss = torch.zeros(len(views)).pin_memory()
-        hd = [tuple(torch.zeros(3 * sc.V).pin_memory() for _ in range(3)) for sc in wl.scenes]
+        hgrad = torch.zeros(int(v_off[-1])).pin_memory()
         side_in, side_out = torch.cuda.Stream(), torch.cuda.Stream()
-        # two buffer sets (scenes, targets, loss, gradients; one frame graph
-        # each) used in turn, so one step's uploads and the previous step's
-        # downloads overlap the current frame; replays stay in order on
-        # `stream` (they share the workspace)
+        # two buffer sets (scenes, parameters, targets, loss, gradients; one
+        # frame graph each) used in turn, so one step's uploads and the
+        # previous step's downloads overlap the current frame; replays stay
+        # in order on `stream` (they share the workspace)
         handles2 = [B.pr_scene_upload(dev(sc.pos), dev(sc.vel), dev(sc.col), dev(sc.tri)) for sc in wl.scenes]
         hv2 = [handles2[si] for si in wl.scene_of]
-        tgt2 = [torch.empty_like(t) for t in tgt8]
+        tflat2 = torch.empty_like(tflat)
+        tgt2 = [tflat2[int(pix_off[k]):int(pix_off[k + 1])] for k in range(len(views))]
         loss2 = torch.zeros_like(loss)
-        grads2 = [tuple(torch.zeros_like(x) for x in gs) for gs in grads]
+        gflat2 = torch.zeros_like(gflat)
+        grads2 = [scene_slices(gflat2, s) for s in range(len(wl.scenes))]
         rgb2 = [torch.empty_like(r) for r in rgb]
         entries2 = [(hv2[k], v, ids[k], depth[k], rgb2[k], tiles[k]) for k, v in enumerate(views)]
         fgrads2 = [dict(target_u8=tgt2[k], loss=loss2[k:k + 1], dcol=grads2[wl.scene_of[k]][0],
                         dpos=grads2[wl.scene_of[k]][1], dvel=grads2[wl.scene_of[k]][2]) for k in range(len(views))]
         graph2 = B.pr_graph_capture_frame(ws, entries2, fgrads2, params)
-        sets = [dict(h=handles, tgt=tgt8, loss=loss, grads=grads, graph=graph),
-                dict(h=handles2, tgt=tgt2, loss=loss2, grads=grads2, graph=graph2)]
+        sets = [dict(h=handles, par=torch.empty(hpar.numel(), device="cuda"), tf=tflat, loss=loss, g=gflat,
+                     graph=graph),
+                dict(h=handles2, par=torch.empty(hpar.numel(), device="cuda"), tf=tflat2, loss=loss2, g=gflat2,
+                     graph=graph2)]
+        for bs in sets:
+            bs["pv"] = [scene_slices(bs["par"], s) for s in range(len(wl.scenes))]
 
         def upload(bs):
             """Step inputs -> buffer set bs on side_in (the caller has seen the
-            last frame that read bs finish): the scene parameters through
-            pr_scene_update, the targets by copies; returns the event the
-            set's frame waits for."""
+            last frame that read bs finish): parameters and targets, one copy
+            each, then every scene updated from the parameters; returns the
+            event the set's frame waits for."""
             with torch.cuda.stream(side_in):
-                for h, a in zip(bs["h"], hsc):
-                    B.pr_scene_update(h, *a, stream=side_in.cuda_stream)
-                for t, ht in zip(bs["tgt"], htg):
-                    t.copy_(ht, non_blocking=True)
+                bs["par"].copy_(hpar, non_blocking=True)
+                bs["tf"].copy_(htf, non_blocking=True)
+                B.pr_scene_update_batch(bs["h"], [p[0] for p in bs["pv"]], [p[1] for p in bs["pv"]],
+                                        [p[2] for p in bs["pv"]])
                 ev = torch.cuda.Event()
                 ev.record(side_in)
             return ev
 
         def frame(bs):
             bs["loss"].zero_()
-            for gs in bs["grads"]:
-                for x in gs:
-                    x.zero_()
+            bs["g"].zero_()
             B.pr_graph_enqueue(bs["graph"])
             done = torch.cuda.Event()
             done.record(stream)
@@ -482,9 +496,7 @@ def our_arm(args, rank, world):
             with torch.cuda.stream(side_out):
                 side_out.wait_event(done)
                 hloss.copy_(bs["loss"], non_blocking=True)
-                for gs, hgs in zip(bs["grads"], hd):
-                    for x, y in zip(gs, hgs):
-                        y.copy_(x, non_blocking=True)
+                hgrad.copy_(bs["g"], non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(side_out)
             return ev
@@ -525,27 +537,24 @@ def our_arm(args, rank, world):
         # frame's losses and gradients on the device
         last = sets[(k2 - 1) % 2]
         assert torch.equal(last["loss"].cpu(), hloss), "end-to-end losses differ from the device's"
-        for gs, hgs in zip(last["grads"], hd):
-            for x, y in zip(gs, hgs):
-                assert torch.equal(x.cpu(), y), "end-to-end gradients differ from the device's"
+        assert torch.equal(last["g"].cpu(), hgrad), "end-to-end gradients differ from the device's"
         sms = e2e_loop(k2, overlap=False)
         B.pr_graph_free(graph2)
         for h in handles2:
             B.pr_scene_free(h)
-        sv = sum(sc.V for sc in wl.scenes)
-        h2d = 3 * sv * 12 + sum(t.numel() for t in htg)
-        d2h = 3 * sv * 12 + 4 * len(views)
+        h2d = hpar.numel() * 4 + htf.numel()
+        d2h = hgrad.numel() * 4 + hloss.numel() * 4
         e2e = {"value": world * pix / (pms * 1e-3) / 1e6, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": pms,
-               "path": "training loop through the public API: every step the scene parameters (positions, "
-                       "velocities, colours, the host's copy) go up through pr_scene_update from pinned host memory "
-                       "and the step's 8-bit target images by copies, the training-frame graph replays (forward, L2 "
-                       "loss against the targets, adjoint), and the per-view losses and per-vertex gradients come "
-                       "back to pinned host memory; the host reads every replay's pr_graph_status before the step "
-                       "ends; two buffer sets (scenes, targets, loss, gradients, one frame graph each) used in turn, "
-                       "so the next step's uploads (second stream) and this step's downloads (third stream) overlap "
-                       "the frames; L2 flushed before every frame; K steps timed as a whole with CUDA events from "
-                       "the first upload to the last download",
+               "path": "training loop through the public API: every step the parameters of every scene (positions, "
+                       "velocities, colours: the host's copy) and the step's 8-bit target images go up from pinned "
+                       "host memory (one copy each), pr_scene_update_batch steps every scene from them, the "
+                       "training-frame graph replays (forward, L2 loss against the targets, adjoint), and the "
+                       "per-view losses and per-vertex gradients come back to pinned host memory (one copy each); "
+                       "the host reads every replay's pr_graph_status before the step ends; two buffer sets used in "
+                       "turn, so the next step's uploads (second stream) and this step's downloads (third stream) "
+                       "overlap the frames; L2 flushed before every frame; K steps timed as a whole with CUDA "
+                       "events from the first upload to the last download",
                "serial": {"value": world * pix / (sms * 1e-3) / 1e6, "ms_per_step": sms,
                           "path": "the same calls and copies on one buffer set with no overlap across steps: "
                                   "upload, frame, download, wait, status, then the next step's upload"}}

@@ -195,6 +195,18 @@ pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, 
 pr_status pr_scene_update(pr_scene *scene, const float *pos, const float *vel, const float *col,
                           void *stream);
 
+/* pr_scene_update for n scenes in one call (for loops that step many
+ * scenes every iteration): scene k takes pos[k], vel[k], col[k], DEVICE
+ * float32 [V_k][3] arrays (an entry may be NULL to keep that array; pos,
+ * vel or col itself may be NULL for none).  pos, vel, col are HOST arrays of
+ * n pointers.  Two kernel launches for all the scenes (n <= 4096);
+ * asynchronous on `stream`, and a non-finite value is reported by the next
+ * frame that reads the scene, exactly as pr_scene_update.
+ * PR_ERR_INVALID_ARG for a NULL scene, a host data pointer or n out of
+ * range. */
+pr_status pr_scene_update_batch(pr_scene *const *scenes, int32_t n, const float *const *pos,
+                                const float *const *vel, const float *const *col, void *stream);
+
 void pr_scene_free(pr_scene *scene);
 
 /* Stages (a)-(c) for one view: writes id_out uint32 [H][W] (0xFFFFFFFF =

@@ -32,7 +32,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
            "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
            "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status", "pr_measure_fp32_peak",
-           "pr_debug_scan_timeout", "pr_debug_halfplanes")
+           "pr_debug_scan_timeout", "pr_debug_halfplanes", "pr_scene_update_batch")
 
 
 class PrError(RuntimeError):
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
         sig = {
             "pr_scene_upload": ([P, P, P, P, I64, I64, P, C.POINTER(P)], I32),
             "pr_scene_update": ([P, P, P, P, P], I32),
+            "pr_scene_update_batch": ([P, I32, P, P, P, P], I32),
             "pr_scene_free": ([P], None),
             "pr_rasterize": ([P, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
             "pr_shade": ([P, C.POINTER(PrView), P, P, P], I32),
@@ -224,6 +225,26 @@ def pr_scene_upload(pos, vel, col, tri, stream=None) -> int:
 def pr_scene_update(scene, pos=None, vel=None, col=None, stream=None):
     _check(load().pr_scene_update(C.c_void_p(scene), _ptr(pos), _ptr(vel), _ptr(col),
                                   stream if stream is not None else current_stream()), "pr_scene_update")
+
+
+def pr_scene_update_batch(scenes, pos=None, vel=None, col=None, stream=None):
+    """pr_scene_update for several scenes in one call: scenes a list of
+    handles; pos, vel, col lists of CUDA tensors (entries may be None) or
+    None."""
+    n = len(scenes)
+    hs = (C.c_void_p * n)(*[C.c_void_p(h) for h in scenes])
+
+    def arr(lst):
+        if lst is None:
+            return None
+        a = (C.c_void_p * n)()
+        for k, t in enumerate(lst):
+            p = _ptr(t)
+            a[k] = p.value if p is not None else None
+        return a
+    pa, va, ca = arr(pos), arr(vel), arr(col)
+    _check(load().pr_scene_update_batch(hs, n, pa, va, ca, stream if stream is not None else current_stream()),
+           "pr_scene_update_batch")
 
 
 def pr_scene_free(scene):

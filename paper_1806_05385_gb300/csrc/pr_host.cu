@@ -882,6 +882,25 @@ pr_status pr_scene_update(pr_scene *sc, const float *pos, const float *vel, cons
     return PR_OK;
 }
 
+pr_status pr_scene_update_batch(pr_scene *const *scenes, int32_t n, const float *const *pos,
+                                const float *const *vel, const float *const *col, void *stream)
+{
+    if (!scenes || n < 1 || n > 4096)
+        return PR_ERR_INVALID_ARG;
+    std::vector<SceneUpdate> u((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        pr_scene *sc = scenes[k];
+        if (!sc)
+            return PR_ERR_INVALID_ARG;
+        const float *p = pos ? pos[k] : nullptr, *w = vel ? vel[k] : nullptr, *c = col ? col[k] : nullptr;
+        if ((p && !is_device_ptr(p)) || (w && !is_device_ptr(w)) || (c && !is_device_ptr(c)))
+            return PR_ERR_INVALID_ARG;  // device arrays only (no staging)
+        u[k] = SceneUpdate{sc->vtx.as<float4>(), sc->col.as<float4>(), sc->status.as<unsigned>(), p, w, c, sc->V};
+    }
+    PR_TRY(launch_scene_update_batch(u.data(), n, (cudaStream_t)stream));
+    return PR_OK;
+}
+
 pr_status pr_scene_upload(const float *pos, const float *vel, const float *col, const int32_t *tri, int64_t V,
                           int64_t T, void *stream, pr_scene **out)
 {

@@ -15,6 +15,15 @@ cudaError_t launch_scene_pack(const float *pos, const float *vel, const float *c
 cudaError_t launch_scene_idx(const int *tri, long long T, long long V, int4 *tri4, Counters *cnt, cudaStream_t st);
 cudaError_t launch_scene_set(const float *src, int which, long long V, float4 *vtx, float4 *col4, cudaStream_t st);
 cudaError_t launch_scene_check(const float4 *vtx, const float4 *col4, long long V, unsigned *status, cudaStream_t st);
+// one scene of a batched update: its records, status word and new arrays (null: keep)
+struct SceneUpdate {
+    float4 *vtx, *col4;
+    unsigned *status;
+    const float *pos, *vel, *col;
+    long long V;
+};
+constexpr int kSceneUpdateChunk = 64;  // scenes per launch (passed by value)
+cudaError_t launch_scene_update_batch(const SceneUpdate *u, int n, cudaStream_t st);
 
 // stage (a): per-triangle bounds (the tiles' display boxes come with the frame init)
 // binned: the triangles with candidate tiles are appended here (cnt->binned)

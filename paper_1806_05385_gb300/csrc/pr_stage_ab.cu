@@ -8,6 +8,8 @@
 // time strip of the catch-up interval), where it is exact and convex; the
 // foveation warp is applied to the framebuffer tiles instead (their display
 // images), and to the region only to find the range of framebuffer pixels.
+#include <algorithm>
+
 #include "pr_bound.cuh"
 #include "pr_launch.h"
 
@@ -73,6 +75,63 @@ __global__ void k_scene_check(const float4 *__restrict__ vtx, const float4 *__re
                     isfinite(b.y) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
     if (!ok)
         atomicOr(status, ST_NONFINITE);
+}
+
+// Batched scene update: the statuses are cleared, then every vertex of every
+// scene of the chunk takes its new arrays and is checked (blockIdx.y: scene).
+struct SceneUpdateChunk {
+    SceneUpdate u[kSceneUpdateChunk];
+    int n;
+};
+
+__global__ void k_scene_status_clear(const SceneUpdateChunk c)
+{
+    if ((int)threadIdx.x < c.n)
+        *c.u[threadIdx.x].status = 0u;
+}
+
+__global__ void k_scene_update_batch(const SceneUpdateChunk c)
+{
+    const SceneUpdate &u = c.u[blockIdx.y];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= u.V)
+        return;
+    float4 a = u.vtx[2 * k], b = u.vtx[2 * k + 1], cl = u.col4[k];
+    if (u.pos) {
+        a.x = u.pos[3 * k];
+        a.y = u.pos[3 * k + 1];
+        a.z = u.pos[3 * k + 2];
+    }
+    if (u.vel) {
+        a.w = u.vel[3 * k];
+        b = make_float4(u.vel[3 * k + 1], u.vel[3 * k + 2], 0.f, 0.f);
+    }
+    if (u.col)
+        cl = make_float4(u.col[3 * k], u.col[3 * k + 1], u.col[3 * k + 2], 0.f);
+    u.vtx[2 * k] = a;
+    u.vtx[2 * k + 1] = b;
+    u.col4[k] = cl;
+    const bool ok = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w) && isfinite(b.x) &&
+                    isfinite(b.y) && isfinite(cl.x) && isfinite(cl.y) && isfinite(cl.z);
+    if (!ok)
+        atomicOr(u.status, ST_NONFINITE);
+}
+
+cudaError_t launch_scene_update_batch(const SceneUpdate *u, int n, cudaStream_t st)
+{
+    for (int c0 = 0; c0 < n; c0 += kSceneUpdateChunk) {
+        SceneUpdateChunk c;
+        c.n = std::min(kSceneUpdateChunk, n - c0);
+        long long vmax = 0;
+        for (int k = 0; k < c.n; ++k) {
+            c.u[k] = u[c0 + k];
+            vmax = std::max(vmax, c.u[k].V);
+        }
+        k_scene_status_clear<<<1, kSceneUpdateChunk, 0, st>>>(c);
+        if (vmax > 0)
+            k_scene_update_batch<<<dim3((unsigned)((vmax + 255) / 256), (unsigned)c.n), 256, 0, st>>>(c);
+    }
+    return cudaGetLastError();
 }
 
 __global__ void k_scene_idx(const int *__restrict__ tri, long long T, long long V, int4 *__restrict__ tri4,

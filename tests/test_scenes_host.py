@@ -135,3 +135,21 @@ def test_sample_pixels():
     assert np.all(np.diff(idx) > 0) and idx.min() >= 0 and idx.max() < 1440 * 1600
     assert len(idx) >= 4 * 64 * 64  # the windows alone
     assert np.array_equal(idx, S.sample_pixels(1440, 1600, 1 << 16, 4, 64, seed=7))
+
+
+def test_config_batched_span_recipe():
+    """The batch that spans the 64-view workload's extremes: 1k and 500k
+    triangles at its ends (geometric in between), sides 512..2160 (each used
+    once), every mode twice and every tile size, reproducible per seed."""
+    cases = S.config_batched_span(seed=4)
+    assert len(cases) == 8
+    Ts = [sc.T for sc, _, _ in cases]
+    assert Ts[0] == 1000 and Ts[-1] == 500_000 and all(a < b for a, b in zip(Ts, Ts[1:]))
+    sides = sorted(v.W for _, v, _ in cases)
+    assert sides[0] == 512 and sides[-1] == 2160 and len(set(sides)) == 8
+    assert all(v.W == v.H for _, v, _ in cases)
+    assert sorted(v.mode for _, v, _ in cases) == [0, 0, 1, 1, 2, 2, 3, 3]
+    assert {t for _, _, t in cases} == {8, 16, 32}
+    again = S.config_batched_span(seed=4)
+    for (a, va, ta), (b, vb, tb) in zip(cases, again):
+        assert np.array_equal(a.pos, b.pos) and va.W == vb.W and ta == tb

@@ -160,3 +160,49 @@ def test_nonfinite_update_is_reported_by_the_next_frame(pr):
     finally:
         pr.pr_workspace_free(ws)
         pr.pr_scene_free(h)
+
+
+def test_scene_update_batch_equals_fresh_uploads(pr):
+    """pr_scene_update_batch steps several scenes in one call: each frame
+    equals the frame of a scene uploaded with the new arrays; an entry left
+    None keeps that array; a non-finite entry is reported only by the next
+    frame of its own scene."""
+    import torch
+    rng = np.random.default_rng(8)
+    base = [S.random_triangles(300 + 100 * k, 50 + k) for k in range(3)]
+    new = [S.Scene((sc.pos + rng.normal(0, 0.05, sc.pos.shape)).astype(np.float32),
+                   (sc.vel + rng.normal(0, 0.01, sc.vel.shape)).astype(np.float32),
+                   rng.uniform(0, 1, sc.col.shape).astype(np.float32), sc.tri) for sc in base]
+    p0, p1 = S.head_poses(1.5, 0.2)
+    view = S.View(W=80, H=64, tan_x=0.5, tan_y=0.5, pose0=p0, pose1=p1, mode=S.MODE_BOTH, fovea=(0.4, 0.6))
+    hs = [pr.pr_scene_upload(_dev(sc.pos), _dev(sc.vel), _dev(sc.col), _dev(sc.tri)) for sc in base]
+    try:
+        keep_vel = [_dev(nw.vel) for nw in new]
+        keep_vel[1] = None                                   # scene 1 keeps its velocities
+        pr.pr_scene_update_batch(hs, [_dev(nw.pos) for nw in new], keep_vel, [_dev(nw.col) for nw in new])
+        n = view.W * view.H
+        for k, (h, nw, sc) in enumerate(zip(hs, new, base)):
+            ids, dep, rgb = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, device="cuda"),
+                             torch.empty(3 * n, device="cuda"))
+            pr.pr_rasterize(h, view, None, ids, dep)
+            pr.pr_shade(h, view, ids, rgb)
+            want = S.Scene(nw.pos, sc.vel if k == 1 else nw.vel, nw.col, nw.tri)
+            h2 = pr.pr_scene_upload(_dev(want.pos), _dev(want.vel), _dev(want.col), _dev(want.tri))
+            ids2, dep2, rgb2 = torch.empty_like(ids), torch.empty_like(dep), torch.empty_like(rgb)
+            pr.pr_rasterize(h2, view, None, ids2, dep2)
+            pr.pr_shade(h2, view, ids2, rgb2)
+            pr.pr_scene_free(h2)
+            assert torch.equal(ids, ids2) and torch.equal(dep, dep2) and torch.equal(rgb, rgb2), k
+        bad = new[2].col.copy()
+        bad[3, 0] = np.nan
+        pr.pr_scene_update_batch(hs, None, None, [None, None, _dev(bad)])
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        pr.pr_rasterize(hs[0], view, None, ids, None)        # untouched scene: fine
+        with pytest.raises(pr.PrError) as e:
+            pr.pr_rasterize(hs[2], view, None, ids, None)
+        assert e.value.status == pr.PR_ERR_NONFINITE
+        with pytest.raises(pr.PrError):
+            pr.pr_scene_update_batch(hs, [new[0].pos, None, None], None, None)   # a host array
+    finally:
+        for h in hs:
+            pr.pr_scene_free(h)
