@@ -238,7 +238,7 @@ KERNEL_SOURCES = {"k_fragment": "pr_stage_c.cu", "k_shade<1>": "pr_stage_de.cu"}
 def ncu_traffic(workload_kind: str, kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, only
     if it was taken on this workload and on the kernel's current source."""
-    p = os.path.join(ROOT, "profiles", "traffic_hmd.json")
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload_kind}.json")
     try:
         d = json.load(open(p))[kernel]
     except (OSError, ValueError, KeyError):

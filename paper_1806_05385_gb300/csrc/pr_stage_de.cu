@@ -23,6 +23,15 @@ __device__ __forceinline__ float3 cross3_rn(float3 a, float3 b)
 __device__ __forceinline__ float3 scale3(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 
+// An 8-bit value b as b / 255 without the conversion pipe: 2^23 + b is exact
+// in FP32 (its bits are 0x4B000000 | b), so subtracting 2^23 leaves b
+// exactly; the product is the correctly rounded b * (1/255 in FP32), the
+// same as (float)b * (1.f / 255.f).
+__device__ __forceinline__ float u8_unit(unsigned char b)
+{
+    return (__uint_as_float(0x4B000000u | (unsigned)b) - 8388608.f) * (1.f / 255.f);
+}
+
 // Everything shading needs about the visible triangle at one pixel.
 struct PixelHit {
     int ia, ib, ic;     // vertex indices
@@ -456,9 +465,9 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
         float gin[3] = {0.f, 0.f, 0.f};
         if (grad && inside) {
             if (v.target_u8) {
-                gin[0] = (float)v.target_u8[lin] * (1.f / 255.f);
-                gin[1] = (float)v.target_u8[plane + lin] * (1.f / 255.f);
-                gin[2] = (float)v.target_u8[2 * plane + lin] * (1.f / 255.f);
+                gin[0] = u8_unit(v.target_u8[lin]);
+                gin[1] = u8_unit(v.target_u8[plane + lin]);
+                gin[2] = u8_unit(v.target_u8[2 * plane + lin]);
             } else {
                 const float *gsrc = v.grad_in ? v.grad_in : v.target;
                 gin[0] = gsrc[lin];
