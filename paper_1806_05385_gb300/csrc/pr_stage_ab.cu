@@ -569,8 +569,9 @@ __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3
                                    make_float2(bx0, by1)};
         const float4 fb = fov_sector_preimage(corners, 4, f, v.inv_alpha, 2.f * eps, rlo <= 2.f * eps, rlo, v.p_lut,
                                               v.p_n);
-        const float fi0 = ceilf(fb.x * v.W - 0.5f) - 1.f, fi1 = floorf(fb.y * v.W - 0.5f) + 1.f;
-        const float fj0 = ceilf(fb.z * v.H - 0.5f) - 1.f, fj1 = floorf(fb.w * v.H - 0.5f) + 1.f;
+        // pixel centres inside the preimage box, 1/100 pixel of slack (as below)
+        const float fi0 = ceilf(fb.x * v.W - 0.51f), fi1 = floorf(fb.y * v.W - 0.49f);
+        const float fj0 = ceilf(fb.z * v.H - 0.51f), fj1 = floorf(fb.w * v.H - 0.49f);
         if (fmaxf(fi0, 0.f) > fminf(fi1, (float)(v.W - 1)) || fmaxf(fj0, 0.f) > fminf(fj1, (float)(v.H - 1))) {
             B.culled = true;
             return;
@@ -744,9 +745,10 @@ __device__ __forceinline__ void compute_bound(const ViewDev &v, const float3 S[3
         w0 = ymin;
         w1 = ymax;
     }
-    // pixel centres (i + .5)/W inside [u0, u1], one pixel of slack each side
-    const float fi0 = ceilf(u0 * v.W - 0.5f) - 1.f, fi1 = floorf(u1 * v.W - 0.5f) + 1.f;
-    const float fj0 = ceilf(w0 * v.H - 0.5f) - 1.f, fj1 = floorf(w1 * v.H - 0.5f) + 1.f;
+    // pixel centres (i + .5)/W inside [u0, u1]; the slack of 1/100 pixel each
+    // side covers the FP32 rounding of u W (a few ulps of at most 16384)
+    const float fi0 = ceilf(u0 * v.W - 0.51f), fi1 = floorf(u1 * v.W - 0.49f);
+    const float fj0 = ceilf(w0 * v.H - 0.51f), fj1 = floorf(w1 * v.H - 0.49f);
     B.i0 = (int)fmaxf(fi0, 0.f);
     B.i1 = (int)fminf(fi1, (float)(v.W - 1));
     B.j0 = (int)fmaxf(fj0, 0.f);
@@ -874,8 +876,8 @@ __global__ void __launch_bounds__(128) k_paper_fov(const ViewDev *__restrict__ v
         return;  // more edges than half-plane slots: keep the sector bound
     for (int h = 0; h < pf.n; ++h)
         hp[g * kMaxHp + h] = out[h];
-    const float fi0 = ceilf(pf.fb.x * v.W - 0.5f) - 1.f, fi1 = floorf(pf.fb.y * v.W - 0.5f) + 1.f;
-    const float fj0 = ceilf(pf.fb.z * v.H - 0.5f) - 1.f, fj1 = floorf(pf.fb.w * v.H - 0.5f) + 1.f;
+    const float fi0 = ceilf(pf.fb.x * v.W - 0.51f), fi1 = floorf(pf.fb.y * v.W - 0.49f);
+    const float fj0 = ceilf(pf.fb.z * v.H - 0.51f), fj1 = floorf(pf.fb.w * v.H - 0.49f);
     const int i0 = (int)fmaxf(fi0, 0.f), i1 = (int)fminf(fi1, (float)(v.W - 1));
     const int j0 = (int)fmaxf(fj0, 0.f), j1 = (int)fminf(fj1, (float)(v.H - 1));
     if (i0 > i1 || j0 > j1) {
