@@ -205,7 +205,10 @@ __device__ inline Ray64 pixel_ray64(const ViewDev &v, int i, int j)
                 const double t = xk - (double)k;
                 s = ((1.0 - t) * (double)v.p_lut[k] + t * (double)v.p_lut[k + 1]) / r;
             } else {
-                s = pow(r / 1.4142135623730950488, (double)v.alpha - 1.0);
+                // (r / D)^(alpha - 1); the integer exponents of the usual
+                // power maps exactly or by one rounded product
+                const double xr = r / 1.4142135623730950488;
+                s = v.alpha == 2.f ? xr : (v.alpha == 3.f ? xr * xr : pow(xr, (double)v.alpha - 1.0));
             }
             x0 = f0 + e0 * s;
             x1 = f1 + e1 * s;

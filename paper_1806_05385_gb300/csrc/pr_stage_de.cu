@@ -166,17 +166,19 @@ __device__ __noinline__ void pixel_hit64(const ViewDev &v, int i, int j, PixelHi
     }
     const double sw = w[0] + w[1] + w[2];
     if (sw != 0.0) {
-        h.b0 = (float)(w[0] / sw);
-        h.b1 = (float)(w[1] / sw);
-        h.b2 = (float)(w[2] / sw);
+        const double isw = 1.0 / sw;
+        h.b0 = (float)(w[0] * isw);
+        h.b1 = (float)(w[1] * isw);
+        h.b2 = (float)(w[2] * isw);
         h.det = (float)(-sw);  // the watertight edge functions are -w
     }
     const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
     const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
     const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    if (len > 0.0) {
-        const double s = (n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > 0.0 ? -1.0 : 1.0) / len;
+    const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    if (nn > 0.0) {
+        const double il = rsqrt(nn);
+        const double s = n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > 0.0 ? -il : il;
         h.n = make_float3((float)(n[0] * s), (float)(n[1] * s), (float)(n[2] * s));
         h.inl = (float)s;
     }
@@ -578,7 +580,11 @@ static void launch_shade_t(int feat, unsigned g, const ViewDev *views, int nview
                            long long nblocks, const unsigned long long *keys, const Counters *frame_cnt,
                            cudaStream_t st)
 {
-    if (feat & kFeatF64) {  // the precision form: one variant with every path (same bits as the others)
+    if (feat == kFeatF64) {  // the precision form without the specular and sampled-foveation paths
+        k_shade<kAdjoint, kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        return;
+    }
+    if (feat & kFeatF64) {  // the precision form with either: one variant with every path (same bits)
         k_shade<kAdjoint, kFeatSpec | kFeatLut | kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys,
                                                                              frame_cnt);
         return;
