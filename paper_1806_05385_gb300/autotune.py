@@ -2,8 +2,14 @@
 
 For each view class -- mode, resolution bucket and triangle-count bucket --
 it times the view's frame through the C ABI (pr_rasterize, CUDA events on the
-current stream) for each bin tile size in {8, 16, 32} and keeps the fastest;
-choices are cached in a JSON file so that later runs reuse them.  Bin and
+current stream) for each bin tile size in {8, 16, 32}; the timings are cached
+in a JSON file so that later runs reuse them.  A batch then takes one tile
+size for all its views -- the one with the least summed time over them --
+and a view class leaves it only for a tile that is faster by more than
+`margin`: every tile size of a batch is a fragment launch of its own, whose
+start and tail the per-view timings do not see, so near-ties are not worth
+a split (on the 64-view workload, per-class fastest tiles gave a fragment
+stage of 0.96-1.03 ms against 0.85 ms for 16 throughout).  Bin and
 work-item capacities need no tuning: the library sizes them from the counts
 a frame reports and regrows on overflow.
 """
@@ -12,7 +18,6 @@ from __future__ import annotations
 import json
 import math
 import os
-import statistics
 
 from . import binding as B
 
@@ -52,8 +57,9 @@ def _save(path, data):
     os.replace(tmp, path)
 
 
-def time_tile(scene, view, tile: int, reps: int = 5, params=None) -> float:
-    """Median device time (ms) of pr_rasterize for one view at one tile size."""
+def time_tile(scene, view, tile: int, reps: int = 10, params=None) -> float:
+    """Least device time (ms) of pr_rasterize for one view at one tile size
+    over `reps` runs (the least is the run that other work disturbed least)."""
     import torch
     n = int(view.W) * int(view.H)
     ids = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -69,22 +75,46 @@ def time_tile(scene, view, tile: int, reps: int = 5, params=None) -> float:
         e1.record(st)
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
-    return statistics.median(out)
+    return min(out)
 
 
-def tune(cases, cache_path: str | None = None, reps: int = 5, refresh: bool = False):
+def _times(entry):
+    """The cached per-tile times of a class, or None if incomplete."""
+    ms = entry.get("ms")
+    if not isinstance(ms, dict):
+        return None
+    try:
+        out = {t: float(ms[str(t)] if str(t) in ms else ms[t]) for t in TILES}
+    except (KeyError, TypeError, ValueError):
+        return None
+    return out
+
+
+def tune(cases, cache_path: str | None = None, reps: int = 10, refresh: bool = False, margin: float = 0.10):
     """cases: list of (scene_handle, view, T).  Returns one tile size per
-    case (cached classes are not re-timed unless refresh)."""
+    case: the batch's tile (least summed time over the cases), or a class's
+    own fastest where that beats the batch's by more than `margin` (a
+    fraction).  Cached classes are not re-timed unless refresh."""
     path = cache_path or default_cache_path()
     cache = {} if refresh else _load(path)
-    tiles, changed = [], False
+    changed = False
+    per_case = []
     for scene, view, T in cases:
         key = view_class(view, T)
-        if key not in cache:
+        times = _times(cache[key]) if key in cache else None
+        if times is None:
             times = {t: time_tile(scene, view, t, reps) for t in TILES}
             cache[key] = {"tile": min(times, key=times.get), "ms": times}
             changed = True
-        tiles.append(int(cache[key]["tile"]))
+        per_case.append(times)
     if changed:
         _save(path, cache)
+    if not per_case:
+        return []
+    total = {t: sum(ms[t] for ms in per_case) for t in TILES}
+    base = min(TILES, key=lambda t: (total[t], t != 16))
+    tiles = []
+    for ms in per_case:
+        best = min(TILES, key=lambda t: ms[t])
+        tiles.append(best if ms[best] < (1.0 - margin) * ms[base] else base)
     return tiles
