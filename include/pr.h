@@ -336,6 +336,29 @@ typedef struct {
 pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, float *out,
                        const pr_unfoveate_params *params, void *stream);
 
+/* One view of a batched display step. */
+typedef struct {
+    const pr_view *view; /* W, H, mode, fovea, alpha and foveation are used */
+    const float *rgb;    /* DEVICE planar [3][view.H][view.W] f32 */
+    float *out;          /* DEVICE planar [3][Hd][Wd] f32, written */
+    int32_t Wd, Hd;      /* display size, 1..16384 */
+} pr_unfoveate_entry;
+
+/* The display step of n views (Sec. 3.1.1, "Display") in one sequence.
+ * MIP: one launch per pyramid level over every view that has the level and
+ * one over the display pixels of all views, the pyramids side by side in the
+ * workspace.  Projected filter: the single-view kernels view after view,
+ * each view's q table in the same scratch.  Entry k's out equals that of
+ * pr_unfoveate with the same view, rgb, out, Wd, Hd and params->method and
+ * sigma, bit for bit; params->Wd and Hd are ignored.  Scratch grows on
+ * demand.  The view
+ * table goes up through pinned memory of the workspace: a call first waits
+ * for the previous batch call's table copy (not for its kernels).
+ * Asynchronous on `stream`.  PR_ERR_INVALID_ARG, nothing launched, for
+ * n < 0, entries null with n > 0, or any entry that pr_unfoveate refuses. */
+pr_status pr_unfoveate_batch(pr_workspace *ws, const pr_unfoveate_entry *entries, int32_t n,
+                             const pr_unfoveate_params *params, void *stream);
+
 /* Captures the same sequence into a CUDA graph (after one eager run that
  * sizes every buffer) and replays it with pr_graph_launch.  The views and
  * their buffers must stay valid and unchanged in shape while the graph

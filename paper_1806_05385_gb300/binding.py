@@ -32,7 +32,7 @@ EXPORTS = ("pr_scene_upload", "pr_scene_update", "pr_scene_free", "pr_rasterize"
            "pr_debug_catch_interval", "pr_status_string", "pr_version", "pr_rasterize_noalloc",
            "pr_backward_batch", "pr_frame_batch", "pr_graph_capture_frame", "pr_unfoveate", "pr_foveation_create",
            "pr_foveation_free", "pr_graph_enqueue", "pr_graph_status", "pr_measure_fp32_peak",
-           "pr_debug_scan_timeout", "pr_debug_halfplanes", "pr_scene_update_batch")
+           "pr_debug_scan_timeout", "pr_debug_halfplanes", "pr_scene_update_batch", "pr_unfoveate_batch")
 
 
 class PrError(RuntimeError):
@@ -73,6 +73,11 @@ class PrBackwardView(C.Structure):
 
 class PrUnfoveateParams(C.Structure):
     _fields_ = [("method", C.c_int32), ("Wd", C.c_int32), ("Hd", C.c_int32), ("sigma", C.c_float)]
+
+
+class PrUnfoveateEntry(C.Structure):
+    _fields_ = [("view", C.c_void_p), ("rgb", C.c_void_p), ("out", C.c_void_p), ("Wd", C.c_int32),
+                ("Hd", C.c_int32)]
 
 
 UNFOVEATE_METHODS = {"mip": 0, "projected": 1}
@@ -132,6 +137,7 @@ def load(build_if_missing: bool = True):
             "pr_rasterize_noalloc": ([P, P, P, P, I64, I64, C.POINTER(PrView), C.POINTER(PrParams), P, P, P], I32),
             "pr_backward_batch": ([P, C.POINTER(PrBackwardView), I32, P], I32),
             "pr_unfoveate": ([P, C.POINTER(PrView), P, P, C.POINTER(PrUnfoveateParams), P], I32),
+            "pr_unfoveate_batch": ([P, C.POINTER(PrUnfoveateEntry), I32, C.POINTER(PrUnfoveateParams), P], I32),
             "pr_foveation_create": ([P, I32, C.POINTER(P)], I32),
             "pr_foveation_free": ([P], None),
             "pr_frame_batch": ([P, C.POINTER(PrBatchView), I32, C.POINTER(PrParams), C.POINTER(PrFrameGrad), P], I32),
@@ -403,6 +409,19 @@ def pr_unfoveate(ws, view, rgb, out, Wd: int, Hd: int, method: str = "mip", sigm
     v = view if isinstance(view, PrView) else make_view(view)
     _check(load().pr_unfoveate(C.c_void_p(ws), C.byref(v), _ptr(rgb), _ptr(out), C.byref(pp),
                                stream if stream is not None else current_stream()), "pr_unfoveate")
+
+
+def pr_unfoveate_batch(ws, entries, method: str = "mip", sigma: float = 0.5, stream=None):
+    """The display step of many views in one sequence: entries are
+    (view, rgb, out, Wd, Hd) with CUDA tensors rgb [3][H][W] and out
+    [3][Hd][Wd]; out of each equals pr_unfoveate's."""
+    views = [v if isinstance(v, PrView) else make_view(v) for v, *_ in entries]
+    arr = (PrUnfoveateEntry * max(1, len(entries)))()
+    for k, ((_, rgb, out, Wd, Hd), v) in enumerate(zip(entries, views)):
+        arr[k] = PrUnfoveateEntry(C.cast(C.pointer(v), C.c_void_p), _ptr(rgb), _ptr(out), int(Wd), int(Hd))
+    pp = PrUnfoveateParams(UNFOVEATE_METHODS[method] if isinstance(method, str) else int(method), 0, 0, float(sigma))
+    _check(load().pr_unfoveate_batch(C.c_void_p(ws), arr, len(entries), C.byref(pp),
+                                     stream if stream is not None else current_stream()), "pr_unfoveate_batch")
 
 
 def pr_graph_launch(graph, stream=None):

@@ -16,6 +16,7 @@
 //    nearest sample, whose factor cancels, so they cannot all underflow.
 //
 // One thread per display pixel; planar rgb in and out, coalesced along x.
+#include <algorithm>
 #include <cstring>
 
 #include "pr_launch.h"
@@ -42,11 +43,11 @@ struct DisplayView {
     float sigma;         // projected filter width, display pixels
 };
 
-__global__ void k_mip_down(const float *__restrict__ src, int w0, int h0, float *__restrict__ dst, int w1, int h1)
+// Texel (x, y) of a level from the level below (w0 x h0): the 2x2 block's
+// mean, over the texels of the block that exist.
+__device__ __forceinline__ void mip_texel(const float *__restrict__ src, int w0, int h0, float *__restrict__ dst,
+                                          int w1, int h1, int x, int y)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= w1 || y >= h1)
-        return;
     const int x0 = 2 * x, y0 = 2 * y;
     const bool xr = x0 + 1 < w0, yr = y0 + 1 < h0;
     const float n = (float)((1 + xr) * (1 + yr));
@@ -64,14 +65,19 @@ __global__ void k_mip_down(const float *__restrict__ src, int w0, int h0, float 
     }
 }
 
+__global__ void k_mip_down(const float *__restrict__ src, int w0, int h0, float *__restrict__ dst, int w1, int h1)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= w1 || y >= h1)
+        return;
+    mip_texel(src, w0, h0, dst, w1, h1, x, y);
+}
+
 // Display location q(c) of every framebuffer pixel centre c (the offset from
 // the fovea scaled by (|e|/D)^(alpha - 1)), for the projected filter.
-__global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha, const float *__restrict__ p_lut,
-                          int p_n, float2 *__restrict__ table)
+__device__ __forceinline__ float2 q_of(int W, int H, int fov, float fx, float fy, float alpha,
+                                       const float *__restrict__ p_lut, int p_n, int i, int j)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (i >= W)
-        return;
     float q0 = __fdiv_rn((float)i + 0.5f, (float)W), q1 = __fdiv_rn((float)j + 0.5f, (float)H);
     if (fov) {
         const float e0 = q0 - fx, e1 = q1 - fy, r = sqrtf(fmaf(e0, e0, e1 * e1));
@@ -80,7 +86,23 @@ __global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha
         q0 = fmaf(e0, s, fx);
         q1 = fmaf(e1, s, fy);
     }
-    table[(size_t)j * W + i] = make_float2(q0, q1);
+    return make_float2(q0, q1);
+}
+
+__device__ __forceinline__ void q_entry(int W, int H, int fov, float fx, float fy, float alpha,
+                                        const float *__restrict__ p_lut, int p_n, float2 *__restrict__ table, int i,
+                                        int j)
+{
+    table[(size_t)j * W + i] = q_of(W, H, fov, fx, fy, alpha, p_lut, p_n, i, j);
+}
+
+__global__ void k_q_table(int W, int H, int fov, float fx, float fy, float alpha, const float *__restrict__ p_lut,
+                          int p_n, float2 *__restrict__ table)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= W)
+        return;
+    q_entry(W, H, fov, fx, fy, alpha, p_lut, p_n, table, i, j);
 }
 
 __device__ __forceinline__ float bspline3(float x)
@@ -126,13 +148,12 @@ __device__ __forceinline__ void sample3(const float *__restrict__ lev, int w, in
     }
 }
 
+// Display pixel (a, b) of a view.
 template <int kMethod>
-__global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid pyr, const float *__restrict__ rgb,
-                                                  const float2 *__restrict__ qtab, float *__restrict__ out)
+__device__ __forceinline__ void unfoveate_pixel(const DisplayView &dv, const MipPyramid &pyr,
+                                                const float *__restrict__ rgb, const float2 *__restrict__ qtab,
+                                                float *__restrict__ out, int a, int b)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
-    if (a >= dv.Wd)
-        return;
     const float x0 = __fdiv_rn((float)a + 0.5f, (float)dv.Wd), x1 = __fdiv_rn((float)b + 0.5f, (float)dv.Hd);
     // u = q^-1(x): the offset from the fovea scaled by (|e|/D)^(1/alpha - 1)
     float u0 = x0, u1 = x1, tang = 1.f, stretch = 1.f;
@@ -229,6 +250,72 @@ __global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid py
     out[2 * dplane + o] = res[2];
 }
 
+template <int kMethod>
+__global__ void __launch_bounds__(256) k_unfoveate(DisplayView dv, MipPyramid pyr, const float *__restrict__ rgb,
+                                                  const float2 *__restrict__ qtab, float *__restrict__ out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= dv.Wd)
+        return;
+    unfoveate_pixel<kMethod>(dv, pyr, rgb, qtab, out, a, b);
+}
+
+// ---- the batched display step (MIP): many views, one launch per pyramid
+// level and one for the display pixels of all views.  A launch's blocks are
+// numbered view after view (blk[q] = first block of view q, blk[n] = all);
+// a block finds its view by a binary search and runs the same per-texel and
+// per-pixel code as the single-view kernels, so the results are the same.
+struct DisplayBatchView {
+    DisplayView dv;
+    MipPyramid pyr;  // level 0 = rgb
+    const float *rgb;
+    float *out;
+};
+
+__device__ __forceinline__ int block_view(const long long *__restrict__ blk, int n, long long b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Level k of every view that has one (blocks of 256 texels, row-major).
+__global__ void __launch_bounds__(256) k_mip_down_batch(const DisplayBatchView *__restrict__ tab,
+                                                       const long long *__restrict__ blk, int n, int k)
+{
+    const int q = block_view(blk, n, blockIdx.x);
+    const MipPyramid &pyr = tab[q].pyr;
+    const int t = (int)(blockIdx.x - blk[q]) * (int)blockDim.x + (int)threadIdx.x;
+    const int w1 = pyr.w[k], h1 = pyr.h[k];
+    if (t >= w1 * h1)
+        return;
+    const int y = t / w1, x = t - y * w1;
+    mip_texel(pyr.lev[k - 1], pyr.w[k - 1], pyr.h[k - 1], const_cast<float *>(pyr.lev[k]), w1, h1, x, y);
+}
+
+// The display pixels of every view (blocks of 256, row-major; a view has
+// fewer than 2^28 pixels, so its pixel index is 32-bit).  The register cap
+// keeps the single-view kernel's occupancy (5 CTAs per SM): the view's
+// constants, parameters there, are registers here.
+__global__ void __launch_bounds__(256, 5) k_unfoveate_mip_batch(const DisplayBatchView *__restrict__ tab,
+                                                               const long long *__restrict__ blk, int n)
+{
+    const int q = block_view(blk, n, blockIdx.x);
+    const DisplayBatchView &e = tab[q];
+    const DisplayView dv = e.dv;
+    const int t = (int)(blockIdx.x - blk[q]) * (int)blockDim.x + (int)threadIdx.x;
+    if (t >= dv.Wd * dv.Hd)
+        return;
+    const int b = t / dv.Wd, a = t - b * dv.Wd;
+    unfoveate_pixel<PR_UNFOVEATE_MIP_CUBIC>(dv, e.pyr, e.rgb, nullptr, e.out, a, b);
+}
+
 int mip_level_count(int W, int H)
 {
     int L = 1;
@@ -300,6 +387,120 @@ cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float
         k_q_table<<<gq, 256, 0, st>>>(W, H, dv.fov, fx, fy, alpha, p_lut, p_n, qtab);
         k_unfoveate<PR_UNFOVEATE_PROJECTED><<<grd, blk, 0, st>>>(dv, pyr, rgb, qtab, out);
     }
+    return cudaGetLastError();
+}
+
+static size_t view_scratch_floats(int W, int H)
+{
+    return (mip_pyramid_floats(W, H) + 3) & ~(size_t)3;  // 16-byte aligned carve
+}
+
+static size_t qtab_floats(int W, int H)
+{
+    return ((size_t)2 * W * H + 3) & ~(size_t)3;
+}
+
+size_t display_batch_scratch_floats(int method, const DisplayEntry *e, int n)
+{
+    size_t f = 0;
+    for (int q = 0; q < n; ++q) {
+        if (method == PR_UNFOVEATE_MIP_CUBIC)
+            f += view_scratch_floats(e[q].W, e[q].H);  // every view's pyramid, side by side
+        else
+            f = std::max(f, qtab_floats(e[q].W, e[q].H));  // one view's q table at a time
+    }
+    return f;
+}
+
+// Table layout (MIP): n DisplayBatchView, then kMaxMipLevels arrays of n + 1
+// block offsets: the display pixels' at index 0, pyramid level k's at k.
+size_t display_batch_table_bytes(int n)
+{
+    const size_t views = ((sizeof(DisplayBatchView) * (size_t)n) + 15) & ~(size_t)15;
+    return views + sizeof(long long) * (size_t)kMaxMipLevels * (size_t)(n + 1);
+}
+
+cudaError_t launch_unfoveate_batch(int method, float sigma, const DisplayEntry *e, int n, float *scratch,
+                                   void *h_table, void *d_table, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    if (method == PR_UNFOVEATE_PROJECTED) {
+        // view after view with the single-view kernels (q table, then the
+        // filter), each view's q table in the same scratch: the table of all
+        // views at once, or of L2-sized groups, was measured slower
+        for (int q = 0; q < n; ++q) {
+            const cudaError_t err = launch_unfoveate(method, e[q].W, e[q].H, e[q].mode, e[q].fx, e[q].fy, e[q].alpha,
+                                                     e[q].p_lut, e[q].p_n, e[q].Wd, e[q].Hd, sigma, e[q].rgb, scratch,
+                                                     e[q].out, st);
+            if (err != cudaSuccess)
+                return err;
+        }
+        return cudaSuccess;
+    }
+    const size_t views_bytes = ((sizeof(DisplayBatchView) * (size_t)n) + 15) & ~(size_t)15;
+    DisplayBatchView *tab = static_cast<DisplayBatchView *>(h_table);
+    long long *blk = reinterpret_cast<long long *>(static_cast<char *>(h_table) + views_bytes);
+    int Lmax = 1;
+    float *p = scratch;
+    for (int q = 0; q < n; ++q) {
+        DisplayBatchView &t = tab[q];
+        std::memset(&t, 0, sizeof t);
+        DisplayView &dv = t.dv;
+        dv.W = e[q].W;
+        dv.H = e[q].H;
+        dv.Wd = e[q].Wd;
+        dv.Hd = e[q].Hd;
+        dv.fov = e[q].mode == PR_FOVEATED || e[q].mode == PR_BOTH;
+        dv.fx = e[q].fx;
+        dv.fy = e[q].fy;
+        dv.alpha = e[q].alpha;
+        dv.inv_alpha = 1.f / e[q].alpha;
+        dv.p_lut = e[q].p_lut;
+        dv.p_n = e[q].p_n;
+        dv.scale = fmaxf((float)dv.W / (float)dv.Wd, (float)dv.H / (float)dv.Hd);
+        dv.sigma = sigma;
+        t.rgb = e[q].rgb;
+        t.out = e[q].out;
+        // the view's scratch: its pyramid levels 1..
+        float *lp = p;
+        p += view_scratch_floats(dv.W, dv.H);
+        const int L = mip_level_count(dv.W, dv.H);
+        if (L > kMaxMipLevels)
+            return cudaErrorInvalidValue;
+        t.pyr.L = L;
+        t.pyr.lev[0] = e[q].rgb;
+        t.pyr.w[0] = dv.W;
+        t.pyr.h[0] = dv.H;
+        for (int k = 1; k < L; ++k) {
+            t.pyr.w[k] = (t.pyr.w[k - 1] + 1) / 2;
+            t.pyr.h[k] = (t.pyr.h[k - 1] + 1) / 2;
+            t.pyr.lev[k] = lp;
+            lp += (size_t)3 * t.pyr.w[k] * t.pyr.h[k];
+        }
+        Lmax = std::max(Lmax, L);
+    }
+    for (int k = 0; k < kMaxMipLevels; ++k) {
+        long long *o = blk + (size_t)k * (n + 1);
+        o[0] = 0;
+        for (int q = 0; q < n; ++q) {
+            const long long items = k == 0 ? (long long)tab[q].dv.Wd * tab[q].dv.Hd
+                                           : (k < tab[q].pyr.L ? (long long)tab[q].pyr.w[k] * tab[q].pyr.h[k] : 0ll);
+            o[q + 1] = o[q] + (items + 255) / 256;
+        }
+    }
+    cudaError_t err = cudaMemcpyAsync(d_table, h_table, display_batch_table_bytes(n), cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess)
+        return err;
+    const DisplayBatchView *dtab = static_cast<const DisplayBatchView *>(d_table);
+    const long long *dblk = reinterpret_cast<const long long *>(static_cast<const char *>(d_table) + views_bytes);
+    for (int k = 1; k < Lmax; ++k) {
+        const long long nb = blk[(size_t)k * (n + 1) + n];
+        if (nb > 0)
+            k_mip_down_batch<<<(unsigned)nb, 256, 0, st>>>(dtab, dblk + (size_t)k * (n + 1), n, k);
+    }
+    if (blk[n] > 0)
+        k_unfoveate_mip_batch<<<(unsigned)blk[n], 256, 0, st>>>(dtab, dblk, n);
     return cudaGetLastError();
 }
 

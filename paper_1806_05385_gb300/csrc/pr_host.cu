@@ -138,6 +138,10 @@ struct pr_workspace {
     DevBuf views, offs, rec, hp, tbox, tile_box, tile_cnt, scan, fill, sums, pairs, items, keys, counters, heads;
     DevBuf hit_entry, hit_tile;  // (triangle, tile) hits of the binning count pass, before the scatter
     DevBuf mip;                  // display step: MIP pyramid of the framebuffer image
+    DevBuf disp;                 // batched display step: its view and block tables
+    PinnedBuf<char> h_disp;      // ... and their host copy
+    cudaEvent_t disp_ev = nullptr;  // recorded after the table copy of the last batched display call
+    bool disp_ev_pending = false;
     DevBuf cand, cand_off;         // candidate tiles per triangle; prefix sum over the binned triangles
     DevBuf binned;                 // triangles with candidate tiles (listed by the bound pass)
     DevBuf flag_bits, flag_list;   // pixels flagged for the FP64 re-test (bitmap + list)
@@ -157,6 +161,8 @@ struct pr_workspace {
         for (int k = 0; k < kEv; ++k)
             if (ev[k])
                 cudaEventDestroy(ev[k]);
+        if (disp_ev)
+            cudaEventDestroy(disp_ev);
     }
     cudaError_t events()
     {
@@ -1106,24 +1112,39 @@ pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int
     return PR_OK;
 }
 
+namespace {
+
+// The checks of one view of the display step (shared by the single and
+// batched calls).
+bool unfoveate_view_ok(const pr_view *view, const float *rgb, const float *out, int Wd, int Hd, int method,
+                       float sigma)
+{
+    if (!view || !rgb || !out)
+        return false;
+    const pr_view &v = *view;
+    if (v.W < 1 || v.H < 1 || v.W > 16384 || v.H > 16384 || Wd < 1 || Hd < 1 || Wd > 16384 || Hd > 16384)
+        return false;
+    if (v.mode < PR_CLASSIC || v.mode > PR_BOTH || !(v.alpha >= 1.f && v.alpha <= 5.f) ||
+        !(v.fovea[0] >= 0.f && v.fovea[0] <= 1.f && v.fovea[1] >= 0.f && v.fovea[1] <= 1.f))
+        return false;
+    if (method != PR_UNFOVEATE_MIP_CUBIC && method != PR_UNFOVEATE_PROJECTED)
+        return false;
+    if (method == PR_UNFOVEATE_PROJECTED && !(sigma > 0.f && std::isfinite(sigma)))
+        return false;
+    return is_device_ptr(rgb) && is_device_ptr(out);
+}
+
+}  // namespace
+
 pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, float *out,
                        const pr_unfoveate_params *params, void *stream)
 {
-    if (!ws || !view || !rgb || !out || !params)
+    if (!ws || !params)
+        return PR_ERR_INVALID_ARG;
+    const pr_unfoveate_params &p = *params;
+    if (!unfoveate_view_ok(view, rgb, out, p.Wd, p.Hd, p.method, p.sigma))
         return PR_ERR_INVALID_ARG;
     const pr_view &v = *view;
-    const pr_unfoveate_params &p = *params;
-    if (v.W < 1 || v.H < 1 || v.W > 16384 || v.H > 16384 || p.Wd < 1 || p.Hd < 1 || p.Wd > 16384 || p.Hd > 16384)
-        return PR_ERR_INVALID_ARG;
-    if (v.mode < PR_CLASSIC || v.mode > PR_BOTH || !(v.alpha >= 1.f && v.alpha <= 5.f) ||
-        !(v.fovea[0] >= 0.f && v.fovea[0] <= 1.f && v.fovea[1] >= 0.f && v.fovea[1] <= 1.f))
-        return PR_ERR_INVALID_ARG;
-    if (p.method != PR_UNFOVEATE_MIP_CUBIC && p.method != PR_UNFOVEATE_PROJECTED)
-        return PR_ERR_INVALID_ARG;
-    if (p.method == PR_UNFOVEATE_PROJECTED && !(p.sigma > 0.f && std::isfinite(p.sigma)))
-        return PR_ERR_INVALID_ARG;
-    if (!is_device_ptr(rgb) || !is_device_ptr(out))
-        return PR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     // scratch: the MIP pyramid, or the projected filter's table of q (2 floats per pixel)
     PR_TRY(ensure(ws->mip, sizeof(float) * mip_pyramid_floats(v.W, v.H)));
@@ -1131,6 +1152,54 @@ pr_status pr_unfoveate(pr_workspace *ws, const pr_view *view, const float *rgb, 
     PR_TRY(launch_unfoveate(p.method, v.W, v.H, v.mode, v.fovea[0], v.fovea[1], v.alpha,
                             v.foveation ? v.foveation->lut : nullptr, v.foveation ? v.foveation->n : 0, p.Wd, p.Hd,
                             p.sigma, rgb, pyr, out, st));
+    return PR_OK;
+}
+
+pr_status pr_unfoveate_batch(pr_workspace *ws, const pr_unfoveate_entry *entries, int32_t n,
+                             const pr_unfoveate_params *params, void *stream)
+{
+    if (!ws || !params || n < 0 || (n > 0 && !entries))
+        return PR_ERR_INVALID_ARG;
+    const pr_unfoveate_params &p = *params;
+    std::vector<DisplayEntry> e((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const pr_unfoveate_entry &x = entries[k];
+        if (!unfoveate_view_ok(x.view, x.rgb, x.out, x.Wd, x.Hd, p.method, p.sigma))
+            return PR_ERR_INVALID_ARG;
+        const pr_view &v = *x.view;
+        DisplayEntry &d = e[(size_t)k];
+        d.W = v.W;
+        d.H = v.H;
+        d.mode = v.mode;
+        d.fx = v.fovea[0];
+        d.fy = v.fovea[1];
+        d.alpha = v.alpha;
+        d.p_lut = v.foveation ? v.foveation->lut : nullptr;
+        d.p_n = v.foveation ? v.foveation->n : 0;
+        d.Wd = x.Wd;
+        d.Hd = x.Hd;
+        d.rgb = x.rgb;
+        d.out = x.out;
+    }
+    if (n == 0)
+        return PR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the previous batch call's table copy must be done before its pinned
+    // source is rewritten (or freed by a regrowth)
+    if (ws->disp_ev_pending) {
+        PR_TRY(cudaEventSynchronize(ws->disp_ev));
+        ws->disp_ev_pending = false;
+    }
+    const size_t tb = display_batch_table_bytes(n);
+    PR_TRY(ws->h_disp.ensure(tb));
+    PR_TRY(ensure(ws->disp, tb));
+    PR_TRY(ensure(ws->mip, sizeof(float) * std::max<size_t>(display_batch_scratch_floats(p.method, e.data(), n), 1)));
+    if (!ws->disp_ev)
+        PR_TRY(cudaEventCreateWithFlags(&ws->disp_ev, cudaEventDisableTiming));
+    PR_TRY(launch_unfoveate_batch(p.method, p.sigma, e.data(), n, ws->mip.as<float>(), ws->h_disp.p, ws->disp.p,
+                                  st));
+    PR_TRY(cudaEventRecord(ws->disp_ev, st));
+    ws->disp_ev_pending = true;
     return PR_OK;
 }
 

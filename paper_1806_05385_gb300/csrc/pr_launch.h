@@ -110,6 +110,27 @@ size_t mip_pyramid_floats(int W, int H);
 cudaError_t launch_unfoveate(int method, int W, int H, int mode, float fx, float fy, float alpha, const float *p_lut,
                              int p_n, int Wd, int Hd, float sigma, const float *rgb, float *pyramid, float *out,
                              cudaStream_t st);
+// the batched display step: n views, each with its own size, mode and
+// display size, one method and filter width for all
+struct DisplayEntry {
+    int W, H, mode;
+    float fx, fy, alpha;
+    const float *p_lut;  // sampled p (device) or null
+    int p_n;
+    int Wd, Hd;
+    const float *rgb;  // device [3][H][W]
+    float *out;        // device [3][Hd][Wd]
+};
+// scratch floats of the batch (MIP: each view's pyramid, 16-byte aligned;
+// the projected filter needs none)
+size_t display_batch_scratch_floats(int method, const DisplayEntry *e, int n);
+// bytes of the host and device tables of a batch of n views
+size_t display_batch_table_bytes(int n);
+// Fills the table into h_table (pinned host memory, display_batch_table_bytes(n)
+// bytes; the caller makes sure a previous copy out of it has finished), copies
+// it to d_table on st and launches the batch.
+cudaError_t launch_unfoveate_batch(int method, float sigma, const DisplayEntry *e, int n, float *scratch,
+                                   void *h_table, void *d_table, cudaStream_t st);
 // measured FP32 FMA throughput of the current device, TFLOP/s
 cudaError_t measure_fma_peak(cudaStream_t st, double *tflops);
 

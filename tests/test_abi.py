@@ -48,11 +48,12 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pr_view), offsetof(pr_view, pose0),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pr_view), offsetof(pr_view, pose0),
          offsetof(pr_view, light_w), sizeof(pr_params), sizeof(pr_stats), sizeof(pr_batch_view),
          offsetof(pr_batch_view, id_out), offsetof(pr_batch_view, tile), sizeof(pr_frame_grad),
          offsetof(pr_frame_grad, dvel), sizeof(pr_backward_view), offsetof(pr_backward_view, dvel),
-         offsetof(pr_frame_grad, target_u8), offsetof(pr_frame_grad, loss));
+         offsetof(pr_frame_grad, target_u8), offsetof(pr_frame_grad, loss), sizeof(pr_unfoveate_entry),
+         offsetof(pr_unfoveate_entry, Hd));
   return 0;
 }}
 """)
@@ -62,7 +63,8 @@ int main(void) {{
     want = [C.sizeof(B.PrView), B.PrView.pose0.offset, B.PrView.light_w.offset, C.sizeof(B.PrParams),
             C.sizeof(B.PrStats), C.sizeof(B.PrBatchView), B.PrBatchView.id_out.offset, B.PrBatchView.tile.offset,
             C.sizeof(B.PrFrameGrad), B.PrFrameGrad.dvel.offset, C.sizeof(B.PrBackwardView),
-            B.PrBackwardView.dvel.offset, B.PrFrameGrad.target_u8.offset, B.PrFrameGrad.loss.offset]
+            B.PrBackwardView.dvel.offset, B.PrFrameGrad.target_u8.offset, B.PrFrameGrad.loss.offset,
+            C.sizeof(B.PrUnfoveateEntry), B.PrUnfoveateEntry.Hd.offset]
     assert got == want
 
 
@@ -87,6 +89,7 @@ def test_invalid_arguments_are_statuses_not_crashes(lib):
     assert lib.pr_graph_enqueue(None, None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_graph_status(None) == B.PR_ERR_INVALID_ARG
     assert lib.pr_measure_fp32_peak(None, None) == B.PR_ERR_INVALID_ARG
+    assert lib.pr_unfoveate_batch(None, None, 0, None, None) == B.PR_ERR_INVALID_ARG
 
 
 def test_no_device_is_reported(lib):

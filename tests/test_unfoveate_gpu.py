@@ -95,3 +95,104 @@ def test_unfoveate_degenerate_sizes_and_errors(pr, oracle):
             pr.pr_unfoveate(ws, view, torch.zeros(3), out, 2, 2, "mip")  # host input
     finally:
         pr.pr_workspace_free(ws)
+
+
+def _batch_specs():
+    """Views of mixed size, mode and foveation for the batched display step:
+    ragged sizes, a 1x1 framebuffer, a sampled p, enlarged, shrunk and
+    anisotropic displays."""
+    import dataclasses
+    from paper_1806_05385_gb300 import foveation as F
+    lens = F.lens_samples(2.0, 0.22, 0.24, 1024)
+    out = []
+    for (W, H, mode, lut, Wd, Hd) in [(131, 97, S.MODE_FOVEATED, None, 196, 145),
+                                      (64, 200, S.MODE_BOTH, None, 50, 300),
+                                      (257, 129, S.MODE_ROLLING, None, 257, 129),
+                                      (1, 1, S.MODE_CLASSIC, None, 3, 2),
+                                      (160, 128, S.MODE_BOTH, lens, 200, 160),
+                                      (33, 17, S.MODE_FOVEATED, None, 17, 9)]:
+        _, view = small_case(mode, W=W, H=H)
+        if lut is not None:
+            view = dataclasses.replace(view, p_lut=lut)
+        out.append((view, Wd, Hd))
+    return out
+
+
+def _batch_gpu(pr, specs, imgs, method, sigma, ws=None):
+    import torch
+    own = ws is None
+    ws = pr.pr_workspace_create() if own else ws
+    try:
+        rgbs = [torch.from_numpy(np.ascontiguousarray(im, dtype=np.float32).reshape(-1)).cuda() for im in imgs]
+        outs = [torch.full((3 * Wd * Hd,), -7.0, device="cuda") for _, Wd, Hd in specs]
+        pr.pr_unfoveate_batch(ws, [(v, r, o, Wd, Hd) for (v, Wd, Hd), r, o in zip(specs, rgbs, outs)], method, sigma)
+        torch.cuda.synchronize()
+        return [o.cpu().numpy().reshape(3, Hd, Wd) for o, (_, Wd, Hd) in zip(outs, specs)]
+    finally:
+        if own:
+            pr.pr_workspace_free(ws)
+
+
+@pytest.mark.parametrize("method", ["mip", "projected"])
+def test_unfoveate_batch_equals_per_view(pr, method):
+    """The batched display step gives every view the same bits as its own
+    pr_unfoveate call, and a second batch on the same workspace (reusing its
+    pinned table) too."""
+    specs = _batch_specs()
+    rng = np.random.default_rng(17)
+    imgs = [rng.uniform(size=(3, v.H, v.W)).astype(np.float32) for v, _, _ in specs]
+    ws = pr.pr_workspace_create()
+    try:
+        for rnd in range(2):
+            order = list(range(len(specs)))[::(-1 if rnd else 1)]
+            got = _batch_gpu(pr, [specs[k] for k in order], [imgs[k] for k in order], method, 0.7, ws)
+            for k, g in zip(order, got):
+                v, Wd, Hd = specs[k]
+                ref = _unfoveate_gpu(pr, v, imgs[k], Wd, Hd, method, sigma=0.7)
+                assert np.array_equal(g.view(np.uint32), ref.view(np.uint32)), (method, k)
+    finally:
+        pr.pr_workspace_free(ws)
+
+
+@pytest.mark.parametrize("method", ["mip", "projected"])
+def test_unfoveate_batch_matches_oracle(pr, oracle, method):
+    """The batch's outputs against the FP64 oracle, with the tolerances and
+    excusals of the single-view test."""
+    specs = [s for s in _batch_specs() if s[0].W > 1]
+    rng = np.random.default_rng(23)
+    imgs = [rng.uniform(size=(3, v.H, v.W)).astype(np.float32) for v, _, _ in specs]
+    got = _batch_gpu(pr, specs, imgs, method, 0.7)
+    for (v, Wd, Hd), img, g in zip(specs, imgs, got):
+        o, margin = oracle.unfoveate(v, img, Wd, Hd, method, 0.7)
+        err = np.abs(g - o).max(axis=0).reshape(-1)
+        bad = err > np.where(_covered(v, Wd, Hd), TOL, 1e-3)
+        assert not np.any(bad & ~(margin < 1e-3)), (method, v.W, v.H, Wd, Hd)
+
+
+def test_unfoveate_batch_refuses_before_launching(pr):
+    """An empty batch does nothing; a batch with one bad entry (host image,
+    zero display size) is refused whole and writes no output."""
+    import torch
+    specs = _batch_specs()[:2]
+    imgs = [np.zeros((3, v.H, v.W), np.float32) for v, _, _ in specs]
+    ws = pr.pr_workspace_create()
+    try:
+        pr.pr_unfoveate_batch(ws, [], "mip")
+        rgbs = [torch.from_numpy(im.reshape(-1)).cuda() for im in imgs]
+        outs = [torch.full((3 * Wd * Hd,), -7.0, device="cuda") for _, Wd, Hd in specs]
+        good = [(v, r, o, Wd, Hd) for (v, Wd, Hd), r, o in zip(specs, rgbs, outs)]
+        bad_host = good[:1] + [(specs[1][0], imgs[1].reshape(-1), outs[1], specs[1][1], specs[1][2])]
+        bad_size = good[:1] + [(specs[1][0], rgbs[1], outs[1], 0, specs[1][2])]
+        for entries in (bad_host, bad_size):
+            with pytest.raises(pr.PrError) as ei:
+                pr.pr_unfoveate_batch(ws, entries, "mip")
+            assert ei.value.status == pr.PR_ERR_INVALID_ARG
+        with pytest.raises(pr.PrError):
+            pr.pr_unfoveate_batch(ws, good, "projected", sigma=0.0)
+        torch.cuda.synchronize()
+        assert all(bool((o == -7.0).all()) for o in outs)
+        pr.pr_unfoveate_batch(ws, good, "mip")
+        torch.cuda.synchronize()
+        assert all(bool((o == 0.0).all()) for o in outs)
+    finally:
+        pr.pr_workspace_free(ws)
