@@ -1198,8 +1198,10 @@ pr_status pr_unfoveate_batch(pr_workspace *ws, const pr_unfoveate_entry *entries
         PR_TRY(cudaEventCreateWithFlags(&ws->disp_ev, cudaEventDisableTiming));
     PR_TRY(launch_unfoveate_batch(p.method, p.sigma, e.data(), n, ws->mip.as<float>(), ws->h_disp.p, ws->disp.p,
                                   st));
-    PR_TRY(cudaEventRecord(ws->disp_ev, st));
-    ws->disp_ev_pending = true;
+    if (p.method == PR_UNFOVEATE_MIP_CUBIC) {  // the only form that copies the table
+        PR_TRY(cudaEventRecord(ws->disp_ev, st));
+        ws->disp_ev_pending = true;
+    }
     return PR_OK;
 }
 
