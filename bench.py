@@ -411,14 +411,17 @@ def our_arm(args, rank, world):
 
     # every view's framebuffer image unfoveated in one batched call, and the
     # same with one call per view for comparison
-    disp_entries = [(v, rgb[k], disp_out[k], v.W, v.H) for k, v in enumerate(views)]
+    # (the ABI view structs are built once, as a caller that displays every
+    # frame would keep them)
+    pviews = [B.make_view(v) for v in views]
+    disp_entries = [(pviews[k], rgb[k], disp_out[k], v.W, v.H) for k, v in enumerate(views)]
 
     def display(method):
         B.pr_unfoveate_batch(ws_d, disp_entries, method, 0.5)
 
     def display_per_view(method):
         for k, v in enumerate(views):
-            B.pr_unfoveate(ws_d, v, rgb[k], disp_out[k], v.W, v.H, method, 0.5)
+            B.pr_unfoveate(ws_d, pviews[k], rgb[k], disp_out[k], v.W, v.H, method, 0.5)
     display_ms, display_pv_ms = {}, {}
     for m in ("mip", "projected"):
         for _ in range(2):
@@ -441,8 +444,9 @@ def our_arm(args, rank, world):
                         "hbm_frac": disp_bytes[m] / (display_ms[m] * 1e-3) / 1e9 / hbm if hbm else None,
                         "per_view_call_ms": display_pv_ms[m],
                         "basis": "all views in one pr_unfoveate_batch call (per_view_call_ms: one pr_unfoveate "
-                                 "call per view), CUDA events, L2 flushed before each, the two forms "
-                                 "alternating, median"}
+                                 "call per view), CUDA events around the call on an idle stream (the "
+                                 "call's host-side checks included), L2 flushed before each, the two "
+                                 "forms alternating, median"}
                     for m in display_ms}
 
     pix = sum(npx)
