@@ -128,6 +128,9 @@ pr_status from_cuda(cudaError_t e)
     } while (0)
 
 constexpr int kDefaultTile = 16;
+// frames with more key bytes than this have their keys set back to ~0 by the
+// frame's reader instead of cleared at the start of the next frame (L2: 126 MB)
+constexpr long long kKeysInL2Bytes = 96ll << 20;
 constexpr int kDefaultSeg = 256;
 constexpr long long kMaxPairs = 0x7FFFFFFFll;  // bin entries per frame: work items hold 32-bit offsets
 
@@ -148,6 +151,10 @@ struct pr_workspace {
     DevBuf loss_part;              // training frames: kLossSlots partial sums of each view's loss
     DevBuf stage;                  // device copies of host-side outputs
     long long cap_pairs = 0, cap_items = 0;
+    // leading keys known to hold ~0: every frame's reader (the resolve or the
+    // shading) sets the keys it reads back to ~0, so a frame clears only
+    // beyond this count (and after a new allocation)
+    long long keys_clean_n = 0;
     PinnedBuf<ViewDev> h_views;
     PinnedBuf<long long> h_offs;
     PinnedBuf<Counters> h_cnt;
@@ -531,7 +538,10 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
     PR_TRY(ensure(ws->cand, sizeof(unsigned long long) * std::max(P.ttot, 1ll)));
     PR_TRY(ensure(ws->cand_off, sizeof(unsigned long long) * (P.ttot + 1)));
     PR_TRY(ensure(ws->binned, sizeof(int) * std::max(P.ttot, 1ll)));
+    const void *old_keys = ws->keys.p;
     PR_TRY(ensure(ws->keys, sizeof(unsigned long long) * std::max(P.npix, 1ll)));
+    if (ws->keys.p != old_keys)
+        ws->keys_clean_n = 0;
     if (P.any_loss)
         PR_TRY(ensure(ws->loss_part, sizeof(float) * kLossSlots * n));
     if (P.any_fp64) {
@@ -635,13 +645,21 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     unsigned long long *cand = ws->cand.as<unsigned long long>(), *cand_off = ws->cand_off.as<unsigned long long>();
     PR_TRY(mark(0));
     // one launch clears the counters, queue heads, tile counts and cursors,
-    // both scans' tickets and flags, the FP64 flags, sets the keys to ~0 and
-    // computes the tiles' display boxes
+    // both scans' tickets and flags, the FP64 flags, and computes the tiles'
+    // display boxes.  The keys: a frame whose keys fit in L2 clears them
+    // here, where the fragment stage then finds them in L2; a larger frame
+    // has its reader (resolve or shading, which reads every key anyway) set
+    // them back to ~0 for the next frame, and clears here only the keys that
+    // earlier frames' readers have not left so (the state is unknown until
+    // this frame's reader is enqueued)
+    const bool reader_resets = P.npix * (long long)sizeof(unsigned long long) > kKeysInL2Bytes;
+    const long long clean_before = reader_resets ? ws->keys_clean_n : 0;
+    ws->keys_clean_n = 0;
     PR_TRY(launch_frame_init(dv, n, tile_offs, tile_box, cnt, ws->heads.as<int>(), tile_cnt, ws->fill.as<unsigned>(),
                              P.ntiles, state_a, scan_state_words(P.ttot), state_b, scan_state_words(P.ntiles),
                              ws->flag_bits.as<unsigned>(), P.any_fp64 ? (P.npix + 31) / 32 + 1 : 0,
-                             ws->keys.as<unsigned long long>(), P.npix, ws->loss_part.as<float>(),
-                             P.any_loss ? (long long)kLossSlots * n : 0, st));
+                             ws->keys.as<unsigned long long>(), P.npix > clean_before ? P.npix : 0,
+                             ws->loss_part.as<float>(), P.any_loss ? (long long)kLossSlots * n : 0, st));
     int *binned = ws->binned.as<int>();
     PR_TRY(launch_bound(dv, n, tri_offs, P.ttot, rec, hp, tbox, cand, binned, cnt, st));
     if (P.any_paper_fov)
@@ -681,13 +699,17 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
                              ws->flag_list.as<long long>(), ws->keys.as<unsigned long long>(), ws->cap_pairs, cnt, st));
     PR_TRY(mark(4));
     if (!shade)
-        PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), st));
+        PR_TRY(launch_resolve(dv, n, pix_offs, P.npix, ws->keys.as<unsigned long long>(), reader_resets, st));
     PR_TRY(mark(5));
     if (shade)  // resolves the keys too, and in a training frame runs the adjoint
-        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), !P.grads.empty(), cnt,
+        PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), reader_resets,
+                            !P.grads.empty(), cnt,
                             shade_features(P.vd.data(), n), st));
     if (shade && P.any_loss)  // the views' loss partial sums into the callers' losses
         PR_TRY(launch_loss_finalize(dv, n, cnt, st));
+    // the reader has set every key of the frame back to ~0
+    if (reader_resets)
+        ws->keys_clean_n = std::max(clean_before, P.npix);
     PR_TRY(mark(6));
     // host-side outputs
     for (int q = 0; q < n; ++q) {
@@ -1013,8 +1035,8 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
     if (s != PR_OK)
         return s;
     PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, false, nullptr, shade_features(&v, 1),
-                        st));
+                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, false, false, nullptr,
+                        shade_features(&v, 1), st));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
     PR_TRY(cudaStreamSynchronize(st));

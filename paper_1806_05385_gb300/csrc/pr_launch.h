@@ -60,7 +60,8 @@ cudaError_t launch_scan(const unsigned long long *in, unsigned long long *out, u
                         int seg, Counters *cnt, cudaStream_t st, bool state_zeroed = false,
                         const int *gather = nullptr, const unsigned long long *n_dev = nullptr,
                         const ItemsOut *items = nullptr);
-// the start of a frame: clears, keys to ~0, tile display boxes (one launch)
+// the start of a frame: clears, the first npix keys to ~0 (0: none, where the
+// last frames' readers left them so), tile display boxes (one launch)
 cudaError_t launch_frame_init(const ViewDev *views, int nviews, const long long *tile_offs, float4 *tile_box,
                               Counters *cnt, int *heads, unsigned long long *tile_cnt, unsigned *fill, long long ntiles,
                               unsigned long long *state_a, long long nstate_a, unsigned long long *state_b,
@@ -85,16 +86,17 @@ cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix
                           const unsigned long long *tile_cnt, const unsigned long long *pairs, const float4 *rec,
                           const long long *flag_list, unsigned long long *keys, long long cap_pairs, Counters *cnt,
                           cudaStream_t st);
+// id and depth of every pixel from its key (reset_keys: the key set back to ~0)
 cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
-                           const unsigned long long *keys, cudaStream_t st);
+                           unsigned long long *keys, bool reset_keys, cudaStream_t st);
 
 // stages (d) and (e)
-// keys: resolve them too (or null: read id_in); adjoint: a training frame,
+// keys: resolve them too (reset_keys: each set back to ~0), or null: read id_in; adjoint: a training frame,
 // run stage (e) for the views with a gradient from the same pixel hit
 // feat: shade_features of the launch's views (which optional paths to build in)
 int shade_features(const ViewDev *vd, int n);
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, int feat,
+                         unsigned long long *keys, bool reset_keys, bool adjoint, const Counters *frame_cnt, int feat,
                          cudaStream_t st);
 // a training frame's losses: each view's partial sums (loss_part) added into
 // its loss, once (skipped when the frame's forward overflowed)

@@ -238,7 +238,7 @@ extern "C" pr_status pr_rasterize_noalloc(const float *pos, const float *vel, co
     NA_TRY(launch_sort_items(items, scan, nt, cap_items, seg, pairs, cnt, st));
     NA_TRY(launch_fragment(tile, false, dv, items, scan, 0, nt, cap_items, heads, pairs, rec, keys, nullptr,
                            nullptr, cnt, fragment_grid(tile, false), st));
-    NA_TRY(launch_resolve(dv, 1, pix_offs, np, keys, st));
+    NA_TRY(launch_resolve(dv, 1, pix_offs, np, keys, false, st));
     Counters h;
     NA_TRY(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));

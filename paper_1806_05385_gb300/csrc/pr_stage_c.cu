@@ -680,7 +680,7 @@ cudaError_t launch_retest(const ViewDev *views, int nviews, const long long *pix
 // ---------------------------------------------------------------- resolve
 
 __global__ void k_resolve(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ pix_offs,
-                          long long npix, const unsigned long long *__restrict__ keys)
+                          long long npix, unsigned long long *__restrict__ keys, int reset_keys)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= npix)
@@ -689,6 +689,8 @@ __global__ void k_resolve(const ViewDev *__restrict__ views, int nviews, const l
     const long long lin = g - v.pix_off;
     const unsigned long long key = keys[g];
     const bool bg = key == ~0ull;
+    if (!bg && reset_keys)
+        keys[g] = ~0ull;  // left as the next frame wants it
     if (v.id_out)
         v.id_out[lin] = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
     if (v.depth_out)
@@ -696,10 +698,10 @@ __global__ void k_resolve(const ViewDev *__restrict__ views, int nviews, const l
 }
 
 cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pix_offs, long long npix,
-                           const unsigned long long *keys, cudaStream_t st)
+                           unsigned long long *keys, bool reset_keys, cudaStream_t st)
 {
     if (npix > 0)
-        k_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix, keys);
+        k_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(views, nviews, pix_offs, npix, keys, reset_keys);
     return cudaGetLastError();
 }
 

@@ -443,7 +443,7 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 template <bool kAdjoint, int kFeat>
 __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ views, int nviews,
                                               const long long *__restrict__ blk_offs, long long nblocks,
-                                              const unsigned long long *__restrict__ keys,
+                                              unsigned long long *__restrict__ keys, int reset_keys,
                                               const Counters *__restrict__ frame_cnt)
 {
     const long long b0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kShadeBlocks;
@@ -482,6 +482,8 @@ __global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ vi
             if (keys) {
                 const unsigned long long key = keys[v.pix_off + lin];
                 const bool bg = key == ~0ull;
+                if (!bg && reset_keys)
+                    keys[v.pix_off + lin] = ~0ull;  // left as the next frame wants it
                 id = bg ? 0xFFFFFFFFu : (unsigned)(key & 0xFFFFFFFFull);
                 if (v.id_out)
                     v.id_out[lin] = id;
@@ -577,30 +579,30 @@ static unsigned shade_grid(long long nblocks)
 
 template <bool kAdjoint>
 static void launch_shade_t(int feat, unsigned g, const ViewDev *views, int nviews, const long long *blk_offs,
-                           long long nblocks, const unsigned long long *keys, const Counters *frame_cnt,
+                           long long nblocks, unsigned long long *keys, int reset_keys, const Counters *frame_cnt,
                            cudaStream_t st)
 {
     if (feat == kFeatF64) {  // the precision form without the specular and sampled-foveation paths
-        k_shade<kAdjoint, kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        k_shade<kAdjoint, kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         return;
     }
     if (feat & kFeatF64) {  // the precision form with either: one variant with every path (same bits)
         k_shade<kAdjoint, kFeatSpec | kFeatLut | kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys,
-                                                                             frame_cnt);
+                                                                             reset_keys, frame_cnt);
         return;
     }
     switch (feat) {
     case 0:
-        k_shade<kAdjoint, 0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        k_shade<kAdjoint, 0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         break;
     case kFeatSpec:
-        k_shade<kAdjoint, kFeatSpec><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        k_shade<kAdjoint, kFeatSpec><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         break;
     case kFeatLut:
-        k_shade<kAdjoint, kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        k_shade<kAdjoint, kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         break;
     default:
-        k_shade<kAdjoint, kFeatSpec | kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, frame_cnt);
+        k_shade<kAdjoint, kFeatSpec | kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
     }
 }
 
@@ -619,15 +621,15 @@ int shade_features(const ViewDev *vd, int n)
 }
 
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                         const unsigned long long *keys, bool adjoint, const Counters *frame_cnt, int feat,
+                         unsigned long long *keys, bool reset_keys, bool adjoint, const Counters *frame_cnt, int feat,
                          cudaStream_t st)
 {
     if (nblocks > 0) {
         const unsigned g = shade_grid(nblocks);
         if (adjoint)
-            launch_shade_t<true>(feat, g, views, nviews, blk_offs, nblocks, keys, frame_cnt, st);
+            launch_shade_t<true>(feat, g, views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
         else
-            launch_shade_t<false>(feat, g, views, nviews, blk_offs, nblocks, keys, frame_cnt, st);
+            launch_shade_t<false>(feat, g, views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
     }
     return cudaGetLastError();
 }

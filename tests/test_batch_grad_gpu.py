@@ -70,6 +70,71 @@ def test_batched_equals_plain(pr):
             pr.pr_scene_free(h)
 
 
+def test_workspace_reuse_across_frame_sizes(pr):
+    """Keys: a frame whose keys fit in L2 clears them at its start; a larger
+    one has its reader set them back to ~0 and clears only beyond what earlier
+    readers left so.  A sequence of batches that shrink and grow on one
+    workspace, across both forms (frames of 118 MB and of a few MB of keys),
+    with images and without, eager and as graph replays, gives every batch
+    the bits of the same batch on a fresh workspace."""
+    import torch
+    cases = _views_mixed()
+    for k in range(4):  # four 2048 x 1800 views: 14.7 Mpx, 118 MB of keys together
+        sc = S.random_triangles(2000, 60 + k)
+        p0, p1 = S.head_poses(1.5 + k, 0.2 * k, 0.01)
+        cases.append((sc, S.View(W=2048, H=1800, tan_x=0.6, tan_y=0.55, pose0=p0, pose1=p1, mode=k % 4,
+                                 fovea=(0.45, 0.5)), 16))
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+    big = [5, 6, 7, 8]
+
+    def run(ws, picks, with_rgb, graph=False):
+        outs, entries = [], []
+        for k in picks:
+            sc, v, tile = cases[k]
+            n = v.W * v.H
+            o = (torch.full((n,), -5, dtype=torch.int32, device="cuda"), torch.full((n,), -5.0, device="cuda"),
+                 torch.full((3 * n,), -5.0, device="cuda") if with_rgb else None)
+            outs.append(o)
+            entries.append((handles[k], v, o[0], o[1], o[2], tile))
+        if graph:
+            g = pr.pr_graph_capture_batch(ws, entries)
+            for o in outs:
+                o[0].fill_(-5)
+            pr.pr_graph_launch(g)
+            pr.pr_graph_launch(g)
+            pr.pr_graph_free(g)
+        else:
+            pr.pr_rasterize_batch(ws, entries)
+        torch.cuda.synchronize()
+        return [tuple(x.cpu().numpy() if x is not None else None for x in o) for o in outs]
+
+    seq = [(big + [0, 1], True, False), (big, False, False), (big[:2] + [4], True, False), (big + [2], True, True),
+           ([0, 1, 2, 3, 4], False, False), (big[::-1], True, False), ([3, 0], True, True), (big + [4], True, False),
+           (big, True, True), ([4, 2], True, False)]
+    ws = pr.pr_workspace_create()
+    stream = torch.cuda.Stream()  # graphs are captured on a non-default stream
+    try:
+        torch.cuda.set_stream(stream)
+        for picks, with_rgb, graph in seq:
+            got = run(ws, picks, with_rgb, graph)
+            fresh = pr.pr_workspace_create()
+            try:
+                want = run(fresh, picks, with_rgb)
+            finally:
+                pr.pr_workspace_free(fresh)
+            for k, a, b in zip(picks, got, want):
+                assert np.array_equal(a[0], b[0]), (picks, k)
+                assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32)), (picks, k)
+                if with_rgb:
+                    assert np.array_equal(a[2].view(np.uint32), b[2].view(np.uint32)), (picks, k)
+                assert (a[0] != -5).all()
+    finally:
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
 def test_graph_replay_matches_eager(pr):
     import torch
     cases = _views_mixed()[:3]
