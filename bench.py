@@ -492,12 +492,14 @@ def our_arm(args, rank, world):
         for bs in sets:
             bs["pv"] = [scene_slices(bs["par"], s) for s in range(len(wl.scenes))]
 
-        def upload(bs):
-            """Step inputs -> buffer set bs on side_in (the caller has seen the
-            last frame that read bs finish): parameters and targets, one copy
-            each, then every scene updated from the parameters; returns the
-            event the set's frame waits for."""
+        def upload(bs, after=None):
+            """Step inputs -> buffer set bs on side_in, once the event `after`
+            (the last frame that read bs) has passed: parameters and targets,
+            one copy each, then every scene updated from the parameters;
+            returns the event the set's frame waits for."""
             with torch.cuda.stream(side_in):
+                if after is not None:
+                    side_in.wait_event(after)
                 bs["par"].copy_(hpar, non_blocking=True)
                 bs["tf"].copy_(htf, non_blocking=True)
                 B.pr_scene_update_batch(bs["h"], [p[0] for p in bs["pv"]], [p[1] for p in bs["pv"]],
@@ -529,6 +531,7 @@ def our_arm(args, rank, world):
             side_in.wait_event(e0)
             ready = upload(sets[0])
             out_free = [None, None]
+            prev = None  # (done event, graph) of the step whose status the host reads next
             for it in range(k_steps):
                 bs = sets[it % 2 if overlap else 0]
                 stream.wait_event(ready)
@@ -536,16 +539,28 @@ def our_arm(args, rank, world):
                     stream.wait_event(out_free[it % 2])  # step it-2's results have left this set
                 flush.zero_()
                 done = frame(bs)
-                if it + 1 < k_steps and overlap:
-                    # the other set's last frame (step it-1) finished: the
-                    # host saw its status at the end of that step
-                    ready = upload(sets[(it + 1) % 2])
-                out_free[it % 2] = download(bs, done)
-                done.synchronize()
-                B.pr_graph_status(bs["graph"])
-                if it + 1 < k_steps and not overlap:
-                    out_free[it % 2].synchronize()
-                    ready = upload(sets[0])
+                if overlap:
+                    if it + 1 < k_steps:
+                        # the other set's inputs change once its last frame
+                        # (step it-1) has finished: a wait on the device
+                        ready = upload(sets[(it + 1) % 2], prev[0] if prev is not None else None)
+                    out_free[it % 2] = download(bs, done)
+                    if prev is not None:
+                        # step it-1's status, read while step it runs (each
+                        # graph has its own copy of its status words)
+                        prev[0].synchronize()
+                        B.pr_graph_status(prev[1])
+                    prev = (done, bs["graph"])
+                else:
+                    out_free[0] = download(bs, done)
+                    done.synchronize()
+                    B.pr_graph_status(bs["graph"])
+                    if it + 1 < k_steps:
+                        out_free[0].synchronize()
+                        ready = upload(sets[0])
+            if prev is not None:
+                prev[0].synchronize()
+                B.pr_graph_status(prev[1])
             for ev in out_free:
                 if ev is not None:
                     stream.wait_event(ev)
@@ -573,10 +588,12 @@ def our_arm(args, rank, world):
                        "host memory (one copy each), pr_scene_update_batch steps every scene from them, the "
                        "training-frame graph replays (forward, L2 loss against the targets, adjoint), and the "
                        "per-view losses and per-vertex gradients come back to pinned host memory (one copy each); "
-                       "the host reads every replay's pr_graph_status before the step ends; two buffer sets used in "
-                       "turn, so the next step's uploads (second stream) and this step's downloads (third stream) "
-                       "overlap the frames; L2 flushed before every frame; K steps timed as a whole with CUDA "
-                       "events from the first upload to the last download",
+                       "the host reads every replay's pr_graph_status, each while the next replay runs (every "
+                       "graph keeps its own status copy), all before the timed region ends; two buffer sets used "
+                       "in turn, so the next step's uploads (second stream, after the set's last frame on the "
+                       "device) and this step's downloads (third stream) overlap the frames; L2 flushed before "
+                       "every frame; K steps timed as a whole with CUDA events from the first upload to the last "
+                       "download",
                "serial": {"value": world * pix / (sms * 1e-3) / 1e6, "ms_per_step": sms,
                           "path": "the same calls and copies on one buffer set with no overlap across steps: "
                                   "upload, frame, download, wait, status, then the next step's upload"}}

@@ -385,10 +385,14 @@ pr_status pr_graph_launch(pr_graph *g, void *stream);
 /* The two halves of pr_graph_launch, for a frame loop that does not wait on
  * the host after every frame: pr_graph_enqueue launches one replay on
  * stream and returns at once (PR_ERR_INVALID_ARG, nothing launched, for a
- * stale graph); pr_graph_status returns the status of the last replay and
- * fills the workspace statistics, and may be called only once the stream
- * has passed that replay (after a synchronisation the caller makes).
- * Replays of graphs that share a workspace must not overlap on the GPU. */
+ * stale graph); pr_graph_status returns the status of the graph's last
+ * replay and fills the workspace statistics, and may be called only once the
+ * stream has passed that replay (after a synchronisation the caller makes).
+ * Each graph keeps its own copy of its replay's status words, so a loop may
+ * read one graph's status while a replay of another graph on the same
+ * workspace runs (stage times, when captured, are the workspace's and belong
+ * to the last replay).  Replays of graphs that share a workspace must not
+ * overlap on the GPU.  pr_graph_free waits for the device to finish. */
 pr_status pr_graph_enqueue(pr_graph *g, void *stream);
 pr_status pr_graph_status(pr_graph *g);
 void pr_graph_free(pr_graph *g);

@@ -277,6 +277,7 @@ struct pr_graph {
     long long npix = 0;
     bool stage_times = false;           // stage events captured as graph nodes
     DevBuf views, offs;                 // the graph's own view and offset tables
+    PinnedBuf<Counters> h_cnt;          // the graph's own copy of its last replay's counters
     std::vector<const void *> buffers;  // the workspace's buffers at capture
 };
 
@@ -612,7 +613,8 @@ void fill_tables(pr_workspace *ws, BatchPlan &P, bool shade)
 // null to upload the workspace's tables in the same sequence.  marks: record
 // the stage events (always when not capturing).
 pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cudaStream_t st,
-                        const ViewDev *tab_views = nullptr, const long long *tab_offs = nullptr, bool marks = true)
+                        const ViewDev *tab_views = nullptr, const long long *tab_offs = nullptr, bool marks = true,
+                        Counters *h_cnt = nullptr)
 {
     const int n = (int)P.vd.size();
     char *stage = ws->stage.as<char>();
@@ -722,7 +724,10 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
         if (shade && o.rgb_host)
             PR_TRY(cudaMemcpyAsync(o.rgb_user, stage + o.rgb_off, np * 12, cudaMemcpyDeviceToHost, st));
     }
-    PR_TRY(cudaMemcpyAsync(ws->h_cnt.p, ws->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    // the frame's counters to the host: the workspace's copy, or the graph's
+    // own (so a replay's status can be read while the next replay runs)
+    PR_TRY(cudaMemcpyAsync(h_cnt ? h_cnt : ws->h_cnt.p, ws->counters.p, sizeof(Counters), cudaMemcpyDeviceToHost,
+                           st));
     return PR_OK;
 }
 
@@ -1294,6 +1299,10 @@ pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, i
     if (e == cudaSuccess)
         e = ensure(g->offs, sizeof(long long) * 4 * (nv + 1));
     if (e == cudaSuccess)
+        e = g->h_cnt.ensure(1);
+    if (e == cudaSuccess)
+        std::memcpy(g->h_cnt.p, ws->h_cnt.p, sizeof(Counters));  // the eager run's, until the first replay
+    if (e == cudaSuccess)
         e = cudaMemcpy(g->views.p, ws->h_views.p, sizeof(ViewDev) * nv, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(g->offs.p, ws->h_offs.p, sizeof(long long) * 4 * (nv + 1), cudaMemcpyHostToDevice);
@@ -1309,7 +1318,8 @@ pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, i
         return from_cuda(e);
     }
     g->stage_times = prm.graph_stage_times != 0;
-    s = enqueue_batch(ws, P, prm.seg, true, st, g->views.as<ViewDev>(), g->offs.as<long long>(), g->stage_times);
+    s = enqueue_batch(ws, P, prm.seg, true, st, g->views.as<ViewDev>(), g->offs.as<long long>(), g->stage_times,
+                      g->h_cnt.p);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(st, &graph);
     if (s != PR_OK || e != cudaSuccess) {
@@ -1361,7 +1371,7 @@ pr_status pr_graph_status(pr_graph *g)
     if (!g)
         return PR_ERR_INVALID_ARG;
     pr_workspace *ws = g->ws;
-    const Counters &c = *ws->h_cnt.p;
+    const Counters &c = *g->h_cnt.p;
     ws->stats.tests = c.tests;
     ws->stats.hits = c.hits;
     ws->stats.pairs = c.pairs_total;
@@ -1394,6 +1404,7 @@ pr_status pr_graph_status(pr_graph *g)
 void pr_graph_free(pr_graph *g)
 {
     if (g) {
+        cudaDeviceSynchronize();  // a replay in flight still writes the graph's status copy
         if (g->exec)
             cudaGraphExecDestroy(g->exec);
         if (g->graph)

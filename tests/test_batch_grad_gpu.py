@@ -135,6 +135,56 @@ def test_workspace_reuse_across_frame_sizes(pr):
             pr.pr_scene_free(h)
 
 
+def test_each_graph_keeps_its_own_status(pr):
+    """Two graphs on one workspace replayed back to back: the status (and
+    statistics) of the first can be read after the second has run, as a
+    frame loop that reads one replay's status while the next one runs does."""
+    import torch
+    cases = _views_mixed()
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+    ws = pr.pr_workspace_create()
+    stream = torch.cuda.Stream()
+    graphs = []
+    try:
+        torch.cuda.set_stream(stream)
+        # one eager frame of every view first sizes the workspace for both
+        # graphs (a capture that regrew it would make the other graph stale)
+        every = []
+        for k, (sc, v, tile) in enumerate(cases):
+            n = v.W * v.H
+            every.append((handles[k], v, torch.empty(n, dtype=torch.int32, device="cuda"),
+                          torch.empty(n, device="cuda"), None, tile))
+        pr.pr_rasterize_batch(ws, every)
+        stats = []
+        for picks in ([0, 1], [2, 3, 4]):
+            entries = []
+            for k in picks:
+                sc, v, tile = cases[k]
+                n = v.W * v.H
+                entries.append((handles[k], v, torch.empty(n, dtype=torch.int32, device="cuda"),
+                                torch.empty(n, device="cuda"), None, tile))
+            g = pr.pr_graph_capture_batch(ws, entries)
+            graphs.append((g, entries))
+            pr.pr_graph_launch(g)
+            st = pr.pr_workspace_stats(ws)
+            stats.append((st["pixels"], st["pairs"], st["culled"]))
+        assert stats[0] != stats[1]
+        pr.pr_graph_enqueue(graphs[0][0])
+        pr.pr_graph_enqueue(graphs[1][0])
+        stream.synchronize()
+        for (g, _), want in zip(graphs, stats):
+            pr.pr_graph_status(g)
+            st = pr.pr_workspace_stats(ws)
+            assert (st["pixels"], st["pairs"], st["culled"]) == want
+    finally:
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        for g, _ in graphs:
+            pr.pr_graph_free(g)
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
 def test_graph_replay_matches_eager(pr):
     import torch
     cases = _views_mixed()[:3]
