@@ -131,6 +131,7 @@ constexpr int kDefaultTile = 16;
 // frames with more key bytes than this have their keys set back to ~0 by the
 // frame's reader instead of cleared at the start of the next frame (L2: 126 MB)
 constexpr long long kKeysInL2Bytes = 96ll << 20;
+inline bool keys_reset_by_reader(long long npix) { return npix * (long long)sizeof(unsigned long long) > kKeysInL2Bytes; }
 constexpr int kDefaultSeg = 256;
 constexpr long long kMaxPairs = 0x7FFFFFFFll;  // bin entries per frame: work items hold 32-bit offsets
 
@@ -275,6 +276,7 @@ struct pr_graph {
     cudaGraph_t graph = nullptr;
     pr_workspace *ws = nullptr;
     long long npix = 0;
+    bool reader_resets = false;         // the replay's reader sets the keys back to ~0 (and its start clears none)
     bool stage_times = false;           // stage events captured as graph nodes
     DevBuf views, offs;                 // the graph's own view and offset tables
     PinnedBuf<Counters> h_cnt;          // the graph's own copy of its last replay's counters
@@ -654,7 +656,7 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     // them back to ~0 for the next frame, and clears here only the keys that
     // earlier frames' readers have not left so (the state is unknown until
     // this frame's reader is enqueued)
-    const bool reader_resets = P.npix * (long long)sizeof(unsigned long long) > kKeysInL2Bytes;
+    const bool reader_resets = keys_reset_by_reader(P.npix);
     const long long clean_before = reader_resets ? ws->keys_clean_n : 0;
     ws->keys_clean_n = 0;
     PR_TRY(launch_frame_init(dv, n, tile_offs, tile_box, cnt, ws->heads.as<int>(), tile_cnt, ws->fill.as<unsigned>(),
@@ -1318,8 +1320,12 @@ pr_status pr_graph_capture_frame(pr_workspace *ws, const pr_batch_view *views, i
         return from_cuda(e);
     }
     g->stage_times = prm.graph_stage_times != 0;
+    // a capture runs nothing: the keys keep the state the eager run left
+    const long long clean_n = ws->keys_clean_n;
     s = enqueue_batch(ws, P, prm.seg, true, st, g->views.as<ViewDev>(), g->offs.as<long long>(), g->stage_times,
                       g->h_cnt.p);
+    ws->keys_clean_n = clean_n;
+    g->reader_resets = keys_reset_by_reader(P.npix);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(st, &graph);
     if (s != PR_OK || e != cudaSuccess) {
@@ -1351,9 +1357,17 @@ pr_status pr_graph_enqueue(pr_graph *g, void *stream)
 {
     if (!g)
         return PR_ERR_INVALID_ARG;
-    if (g->ws->buffer_set() != g->buffers)
+    pr_workspace *ws = g->ws;
+    if (ws->buffer_set() != g->buffers)
         return PR_ERR_INVALID_ARG;  // a later call regrew the workspace: the graph's pointers are stale
+    // a graph whose reader sets the keys back clears none at its start: if
+    // the work before it (a frame whose keys fit in L2, an interrupted
+    // sequence) left keys in use, they are cleared here first
+    if (g->reader_resets && ws->keys_clean_n < g->npix)
+        PR_TRY(cudaMemsetAsync(ws->keys.p, 0xFF, sizeof(unsigned long long) * (size_t)g->npix,
+                               (cudaStream_t)stream));
     PR_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    ws->keys_clean_n = g->reader_resets ? std::max(ws->keys_clean_n, g->npix) : 0;
     return PR_OK;
 }
 

@@ -135,6 +135,62 @@ def test_workspace_reuse_across_frame_sizes(pr):
             pr.pr_scene_free(h)
 
 
+def test_graph_replay_after_small_frames(pr):
+    """A graph of a frame larger than L2's share for keys (its shading sets
+    the keys back, and its start clears none) replayed after eager frames
+    that leave keys in use -- a small frame, whose keys are cleared at its
+    start instead -- still starts from clean keys: the replay equals the
+    eager frame of the same batch."""
+    import torch
+    big = []
+    for k in range(4):  # 14.7 Mpx, 118 MB of keys
+        sc = S.random_triangles(2000, 80 + k)
+        p0, p1 = S.head_poses(1.0 + k, 0.1 * k, 0.01)
+        big.append((sc, S.View(W=2048, H=1800, tan_x=0.6, tan_y=0.55, pose0=p0, pose1=p1, mode=(k + 1) % 4,
+                               fovea=(0.5, 0.45)), 16))
+    small = _views_mixed()
+    cases = big + small
+    handles = [_upload(pr, sc) for sc, _, _ in cases]
+
+    def entries_of(picks):
+        out = []
+        for k in picks:
+            sc, v, tile = cases[k]
+            n = v.W * v.H
+            out.append((handles[k], v, torch.full((n,), -5, dtype=torch.int32, device="cuda"),
+                        torch.full((n,), -5.0, device="cuda"), torch.full((3 * n,), -5.0, device="cuda"), tile))
+        return out
+
+    ws = pr.pr_workspace_create()
+    stream = torch.cuda.Stream()
+    g = None
+    try:
+        torch.cuda.set_stream(stream)
+        eb = entries_of([0, 1, 2, 3])
+        pr.pr_rasterize_batch(ws, eb)
+        torch.cuda.synchronize()
+        want = [tuple(x.cpu().numpy() for x in e[2:5]) for e in eb]
+        g = pr.pr_graph_capture_batch(ws, eb)
+        for picks in ([4, 5], [6, 7, 8], [4]):  # small frames (keys cleared at their start, left in use)
+            pr.pr_rasterize_batch(ws, entries_of(picks))
+            for e in eb:
+                e[2].fill_(-5)
+            pr.pr_graph_launch(g)
+            torch.cuda.synchronize()
+            for e, w in zip(eb, want):
+                got = tuple(x.cpu().numpy() for x in e[2:5])
+                assert np.array_equal(got[0], w[0])
+                assert np.array_equal(got[1].view(np.uint32), w[1].view(np.uint32))
+                assert np.array_equal(got[2].view(np.uint32), w[2].view(np.uint32))
+    finally:
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        if g is not None:
+            pr.pr_graph_free(g)
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
 def test_each_graph_keeps_its_own_status(pr):
     """Two graphs on one workspace replayed back to back: the status (and
     statistics) of the first can be read after the second has run, as a
