@@ -40,6 +40,7 @@ struct PixelHit {
     float3 A, B, C;     // triangle moved to t (camera space)
     float b0, b1, b2;   // barycentrics of the ray point
     float det;          // U + V + W of the watertight test
+    float inv_det;      // 1 / det (0 if det = 0)
     float3 n;           // unit normal facing the viewer
     float inl;          // flip / |(B-A) x (C-A)| with flip = +-1 the sign applied (0 if degenerate)
     float3 l;           // unit light direction at t
@@ -109,6 +110,7 @@ __device__ __forceinline__ void pixel_hit(const ViewDev &v, int i, int j, unsign
     const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
     h.det = U + V + W;
     const float inv = h.det != 0.f ? 1.f / h.det : 0.f;
+    h.inv_det = inv;
     h.b0 = U * inv;
     h.b1 = V * inv;
     h.b2 = W * inv;
@@ -171,6 +173,7 @@ __device__ __noinline__ void pixel_hit64(const ViewDev &v, int i, int j, PixelHi
         h.b1 = (float)(w[1] * isw);
         h.b2 = (float)(w[2] * isw);
         h.det = (float)(-sw);  // the watertight edge functions are -w
+        h.inv_det = h.det != 0.f ? 1.f / h.det : 0.f;
     }
     const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
     const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
@@ -310,9 +313,8 @@ __device__ __forceinline__ void adjoint_add(const ViewDev &v, const PixelHit &h,
         const float gsig = fmaf(g0, pa.a[0], fmaf(g1, pa.a[1], g2 * pa.a[2]));
         // barycentrics -> moved vertices: with w_0 = D.(B x C) etc.,
         // dL/dA = gw1 (D x C) + gw2 (B x D) = D x (gw1 C - gw2 B), cyclically
-        const float sw = -h.det;
         const float gdotb = fmaf(gb[0], b[0], fmaf(gb[1], b[1], gb[2] * b[2]));
-        const float isw = sw != 0.f ? 1.f / sw : 0.f;
+        const float isw = -h.inv_det;  // 1 / sum w, sum w = -det (exactly the negated reciprocal)
         const float gw0 = (gb[0] - gdotb) * isw, gw1 = (gb[1] - gdotb) * isw, gw2 = (gb[2] - gdotb) * isw;
         const float3 D = h.dir;
         float3 gA = cross3(D, sub3(scale3(h.C, gw1), scale3(h.B, gw2)));
