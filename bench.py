@@ -569,6 +569,23 @@ def our_arm(args, rank, world):
             return e0.elapsed_time(e1) / k_steps
 
         e2e_loop(3)
+        # the step's transfers alone, for reading the overlap: one upload
+        # (copies + scene updates) and one download, each timed by itself
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(side_in)
+        upload(sets[0])
+        a1.record(side_in)
+        a1.synchronize()
+        up_ms = a0.elapsed_time(a1)
+        ev0 = torch.cuda.Event()
+        ev0.record(stream)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(side_out)
+        download(sets[0], ev0)
+        b1.record(side_out)
+        b1.synchronize()
+        down_ms = b0.elapsed_time(b1)
         pms = e2e_loop(k2)
         # the loop's last results reached the host: they equal the last
         # frame's losses and gradients on the device
@@ -583,6 +600,7 @@ def our_arm(args, rank, world):
         d2h = hgrad.numel() * 4 + hloss.numel() * 4
         e2e = {"value": world * pix / (pms * 1e-3) / 1e6, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": pms,
+               "upload_ms_alone": up_ms, "download_ms_alone": down_ms,
                "path": "training loop through the public API: every step the parameters of every scene (positions, "
                        "velocities, colours: the host's copy) and the step's 8-bit target images go up from pinned "
                        "host memory (one copy each), pr_scene_update_batch steps every scene from them, the "
