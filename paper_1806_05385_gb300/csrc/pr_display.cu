@@ -296,6 +296,8 @@ __global__ void __launch_bounds__(256) k_mip_down_batch(const DisplayBatchView *
     if (t >= w1 * h1)
         return;
     const int y = t / w1, x = t - y * w1;
+    // levels k >= 1 live in the call's scratch (only level 0, the caller's
+    // image, is read-only)
     mip_texel(pyr.lev[k - 1], pyr.w[k - 1], pyr.h[k - 1], const_cast<float *>(pyr.lev[k]), w1, h1, x, y);
 }
 
