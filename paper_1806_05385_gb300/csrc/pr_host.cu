@@ -359,6 +359,16 @@ pr_status derive_view(const pr_view &in, int tile, int bound, int fp64, ViewDev 
     v.H = in.H;
     v.mode = in.mode;
     v.S = tile;
+    {
+        // division by the blocks per row as a multiply (the round-up
+        // reciprocal of Granlund and Montgomery, 1994): lb bw_mul / 2^40
+        // exceeds lb / bw by lb e / (bw 2^40), e = bw_mul bw - 2^40 < bw; for
+        // lb < 2^23 and bw <= 2^11 that is below 2^-6 / bw, less than the
+        // 1 / bw from any fraction of lb / bw to the next integer, so the
+        // floor is exact
+        const unsigned long long bw = (unsigned long long)((in.W + 7) / 8);
+        v.bw_mul = ((1ull << 40) + bw - 1) / bw;
+    }
     v.tiles_x = (in.W + tile - 1) / tile;
     v.tiles_y = (in.H + tile - 1) / tile;
     v.bound = bound;

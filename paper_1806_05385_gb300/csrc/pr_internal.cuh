@@ -61,6 +61,7 @@ struct ViewDev {
     const unsigned *scene_status;      // the scene's status word (ST_NONFINITE after an update), or null
     float *dcol, *dpos, *dvel;         // adjoint outputs [V][3]
     const float4 *rec;                 // this frame's stage (a) records (batch-wide index), or null
+    unsigned long long bw_mul;         // ceil(2^40 / bw), bw = 8-pixel blocks per row: lb / bw = (lb * bw_mul) >> 40
 };
 
 struct Counters {

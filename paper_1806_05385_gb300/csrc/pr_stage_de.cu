@@ -206,9 +206,9 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
 {
     q = find_view(blk_offs, nviews, b);
     const ViewDev &v = views[q];
-    const int lb = (int)(b - v.blk_off);  // < 2^23 blocks per view: 32-bit division
+    const int lb = (int)(b - v.blk_off);  // < 2^23 blocks per view
     const int bw = (v.W + 7) >> 3;
-    const int by = lb / bw;
+    const int by = (int)(((unsigned long long)(unsigned)lb * v.bw_mul) >> 40);  // lb / bw
     i = (lb - by * bw) * 8 + (lane & 7);
     j = by * 4 + (lane >> 3);
     lin = (long long)j * v.W + i;
