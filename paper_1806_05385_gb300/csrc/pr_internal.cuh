@@ -91,6 +91,23 @@ __device__ __forceinline__ int find_view(const long long *off, int n, long long 
     return lo;
 }
 
+// The same for a g that every lane of the warp holds: the lanes compare 32
+// offsets at a time (one load each, no chain of dependent loads) and count
+// those at or below g.  Called by the whole warp.
+__device__ __forceinline__ int find_view_warp(const long long *off, int n, long long g)
+{
+    const int lane = threadIdx.x & 31;
+    int q = 0;
+    for (int base = 1; base < n; base += 32) {
+        const int k = base + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, k < n && off[k] <= g);
+        q += __popc(m);
+        if (m != 0xffffffffu)
+            break;  // offsets ascend: none further on is at or below g
+    }
+    return q;
+}
+
 // Camera-space start and end positions of vertex k: S = R0 p + T0 and
 // E = R1 (p + v) + T1 (Sec. 3.2, "Bounding": M_s v_s and M_e v_e).  Every
 // kernel that needs a vertex calls this one function, so the bits agree.

@@ -204,7 +204,7 @@ constexpr int kShadeBlocks = 1;
 __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, const long long *blk_offs, long long b,
                                             int lane, int &q, long long &lin, int &i, int &j)
 {
-    q = find_view(blk_offs, nviews, b);
+    q = find_view_warp(blk_offs, nviews, b);  // b is the warp's
     const ViewDev &v = views[q];
     const int lb = (int)(b - v.blk_off);  // < 2^23 blocks per view
     const int bw = (v.W + 7) >> 3;
