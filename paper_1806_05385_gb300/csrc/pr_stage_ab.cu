@@ -772,9 +772,18 @@ __global__ void __launch_bounds__(128, 6) k_bound(const ViewDev *__restrict__ vi
                                                int *__restrict__ binned, Counters *cnt)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // the view of the warp's first triangle by the whole warp (no chain of
+    // dependent loads), then each lane steps to its own: a warp's 32
+    // triangles meet at most a few view boundaries
+    const long long g0 = g - (threadIdx.x & 31);
+    if (g0 >= ttot)
+        return;  // the whole warp
+    int q = find_view_warp(tri_offs, nviews, g0);
     if (g >= ttot)
         return;
-    const ViewDev &v = views[find_view(tri_offs, nviews, g)];
+    while (q + 1 < nviews && g >= tri_offs[q + 1])
+        ++q;
+    const ViewDev &v = views[q];
     const int k = (int)(g - v.tri_off);
     const int4 tv = v.tri4[k];
     const int ia = tv.x, ib = tv.y, ic = tv.z;
