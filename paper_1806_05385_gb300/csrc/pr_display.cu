@@ -272,17 +272,11 @@ struct DisplayBatchView {
     float *out;
 };
 
+// The view of block b (the same for every lane): the warp compares 32
+// offsets at a time (find_view_warp).  Called by whole warps.
 __device__ __forceinline__ int block_view(const long long *__restrict__ blk, int n, long long b)
 {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (blk[mid] <= b)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
+    return find_view_warp(blk, n, b);
 }
 
 // Level k of every view that has one (blocks of 256 texels, row-major).
