@@ -33,6 +33,11 @@ import time
 
 import numpy as np
 
+# more hardware work queues than the default 8, so that the training loop's
+# streams (frames, uploads, downloads) do not share one and wait on each
+# other's work (a process setting, read when CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -508,12 +513,17 @@ def our_arm(args, rank, world):
                 ev.record(side_in)
             return ev
 
+        marks = []  # (frame start, frame end) events of the timed loop's steps
+
         def frame(bs):
+            f0 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
             bs["loss"].zero_()
             bs["g"].zero_()
             B.pr_graph_enqueue(bs["graph"])
-            done = torch.cuda.Event()
+            done = torch.cuda.Event(enable_timing=True)
             done.record(stream)
+            marks.append((f0, done))
             return done
 
         def download(bs, done):
@@ -586,10 +596,19 @@ def our_arm(args, rank, world):
         b1.record(side_out)
         b1.synchronize()
         down_ms = b0.elapsed_time(b1)
-        pms = e2e_loop(k2)
+        marks.clear()
+        # the timed steps of the overlapped loop: the bench's step count (its
+        # first upload and last download, which nothing overlaps, are spread
+        # over them)
+        ke = max(3, args.steps)
+        pms = e2e_loop(ke)
+        # how the steps lay on the compute stream: each frame's own time, and
+        # the wait before it (its inputs' upload, when that did not overlap)
+        frame_in_loop = statistics.median(a.elapsed_time(b) for a, b in marks)
+        gap_in_loop = statistics.median(marks[k - 1][1].elapsed_time(marks[k][0]) for k in range(1, len(marks)))
         # the loop's last results reached the host: they equal the last
         # frame's losses and gradients on the device
-        last = sets[(k2 - 1) % 2]
+        last = sets[(ke - 1) % 2]
         assert torch.equal(last["loss"].cpu(), hloss), "end-to-end losses differ from the device's"
         assert torch.equal(last["g"].cpu(), hgrad), "end-to-end gradients differ from the device's"
         sms = e2e_loop(k2, overlap=False)
@@ -601,6 +620,7 @@ def our_arm(args, rank, world):
         e2e = {"value": world * pix / (pms * 1e-3) / 1e6, "unit": "Mpix/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": pms,
                "upload_ms_alone": up_ms, "download_ms_alone": down_ms,
+               "frame_ms_in_loop": frame_in_loop, "gap_ms_between_frames": gap_in_loop,
                "path": "training loop through the public API: every step the parameters of every scene (positions, "
                        "velocities, colours: the host's copy) and the step's 8-bit target images go up from pinned "
                        "host memory (one copy each), pr_scene_update_batch steps every scene from them, the "
