@@ -366,7 +366,7 @@ pr_status derive_view(const pr_view &in, int tile, int bound, int fp64, ViewDev 
         // lb < 2^23 and bw <= 2^11 that is below 2^-6 / bw, less than the
         // 1 / bw from any fraction of lb / bw to the next integer, so the
         // floor is exact
-        const unsigned long long bw = (unsigned long long)((in.W + 7) / 8);
+        const unsigned long long bw = (unsigned long long)((in.W + kBlkW - 1) / kBlkW);
         v.bw_mul = ((1ull << 40) + bw - 1) / bw;
     }
     v.tiles_x = (in.W + tile - 1) / tile;
@@ -477,7 +477,7 @@ pr_status plan_batch(const pr_batch_view *views, int n, const pr_params &prm, Ba
         v.tile_off = P.tile_off[q];
         v.pix_off = P.pix_off[q];
         v.blk_off = P.blk_off[q];
-        P.blk_off[q + 1] = P.blk_off[q] + (long long)((v.W + 7) / 8) * ((v.H + 3) / 4);
+        P.blk_off[q + 1] = P.blk_off[q] + pixel_blocks(v.W, v.H);
         P.tri_off[q + 1] = P.tri_off[q] + bv.scene->T;
         P.tile_off[q + 1] = P.tile_off[q] + (long long)v.tiles_x * v.tiles_y;
         P.pix_off[q + 1] = P.pix_off[q] + (long long)v.W * v.H;
@@ -583,7 +583,7 @@ pr_status size_workspace(pr_workspace *ws, const BatchPlan &P, int seg)
 }
 
 // Writes the frame's view and offset tables into the workspace's pinned
-// host copies (h_views: n views; h_offs: triangle, tile, pixel and 8x4
+// host copies (h_views: n views; h_offs: triangle, tile, pixel and warp
 // block offsets, n + 1 each).  shade: views with an rgb output get one.
 void fill_tables(pr_workspace *ws, BatchPlan &P, bool shade)
 {
@@ -832,7 +832,7 @@ pr_status upload_single(pr_scene *sc, const ViewDev &v, cudaStream_t st)
     ws->h_views.p[0] = v;
     long long *o = ws->h_offs.p;
     o[0] = 0;
-    o[1] = (long long)((v.W + 7) / 8) * ((v.H + 3) / 4);  // 8x4 blocks
+    o[1] = pixel_blocks(v.W, v.H);  // warp pixel blocks
     o[2] = o[3] = o[4] = o[5] = 0;
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev), cudaMemcpyHostToDevice, st));
     PR_TRY(cudaMemcpyAsync(ws->offs.p, o, sizeof(long long) * 2, cudaMemcpyHostToDevice, st));
@@ -1052,7 +1052,7 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
     if (s != PR_OK)
         return s;
     PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                        (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, false, false, nullptr,
+                        pixel_blocks(v.W, v.H), nullptr, false, false, nullptr,
                         shade_features(&v, 1), st));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
@@ -1105,7 +1105,7 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     if (s != PR_OK)
         return s;
     PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                           (long long)((v.W + 7) / 8) * ((v.H + 3) / 4), nullptr, shade_features(&v, 1), st));
+                           pixel_blocks(v.W, v.H), nullptr, shade_features(&v, 1), st));
     for (int a = 0; a < 3; ++a)
         if (host[a])
             PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
@@ -1140,7 +1140,7 @@ pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int
         v.dpos = b.dpos;
         v.dvel = b.dvel;
         v.blk_off = blk[k];
-        blk[k + 1] = blk[k] + (long long)((v.W + 7) / 8) * ((v.H + 3) / 4);
+        blk[k + 1] = blk[k] + pixel_blocks(v.W, v.H);
         ws->h_views.p[k] = v;
     }
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));

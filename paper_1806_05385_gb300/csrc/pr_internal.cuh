@@ -15,6 +15,13 @@ constexpr float kEpsDisp = 1e-5f;                  // display-space safety margi
 constexpr float kEpsT = 1e-4f;                     // time margin of every catch-up interval
 constexpr int kMaxHp = 8;                          // half-planes per bound: <= 6 hull edges + 2 time-strip edges
 constexpr int kRecF4 = 6;                          // float4 per fragment record
+// the pixel block of one warp in shading and the adjoint (32 pixels)
+constexpr int kBlkW = 8, kBlkH = 4;
+static_assert(kBlkW * kBlkH == 32, "one pixel per lane");
+__host__ __device__ inline long long pixel_blocks(int W, int H)
+{
+    return (long long)((W + kBlkW - 1) / kBlkW) * ((H + kBlkH - 1) / kBlkH);
+}
 constexpr int kMaxSeg = 1024;                      // longest bin run of one work item (pr_params.seg)
 constexpr int kLossSlots = 256;                    // partial sums per view of a training frame's loss
 
@@ -44,7 +51,7 @@ struct ViewDev {
     int tiles_x, tiles_y, bound, fp64;
     int fov_bound;                     // pr_fov_bound
     long long tri_off, tile_off, pix_off;  // offsets of this view in the batch-wide arrays
-    long long blk_off;                 // offset of its 8x4 pixel blocks (stages d, e)
+    long long blk_off;                 // offset of its warp pixel blocks (stages d, e)
     int T, V;
     const float4 *vtx;                 // scene vertices, two float4 each: (px, py, pz, vx), (vy, vz, 0, 0)
     const float4 *col4;                // per-vertex colour (r, g, b, 0)

@@ -190,11 +190,12 @@ __device__ __noinline__ void pixel_hit64(const ViewDev &v, int i, int j, PixelHi
     h.C = make_float3((float)P[2][0], (float)P[2][1], (float)P[2][2]);
 }
 
-// Stages (d) and (e) run each warp over kShadeBlocks consecutive 8x4 pixel
-// blocks (lane -> column lane % 8, row lane / 8 of each), so the lanes of a
+// Stages (d) and (e) run each warp over kShadeBlocks consecutive pixel
+// blocks of kBlkW x kBlkH (8 x 4; lane -> column lane % kBlkW, row
+// lane / kBlkW of each), so the lanes of a
 // warp mostly see the same triangles: gathers of vertex data coalesce, and
 // the adjoint sums a triangle's contributions over a lane's pixels and then
-// over the warp before touching memory.  blk_offs[q] = first 8x4 block of
+// over the warp before touching memory.  blk_offs[q] = first pixel block of
 // view q in the batch.  One block per warp measured fastest on the stereo
 // HMD frame (0.170 ms against 0.229 ms for two and 0.242 ms for four): the
 // running sums held across pixels push the kernel into register spills
@@ -207,10 +208,10 @@ __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, co
     q = find_view_warp(blk_offs, nviews, b);  // b is the warp's
     const ViewDev &v = views[q];
     const int lb = (int)(b - v.blk_off);  // < 2^23 blocks per view
-    const int bw = (v.W + 7) >> 3;
+    const int bw = (v.W + kBlkW - 1) / kBlkW;
     const int by = (int)(((unsigned long long)(unsigned)lb * v.bw_mul) >> 40);  // lb / bw
-    i = (lb - by * bw) * 8 + (lane & 7);
-    j = by * 4 + (lane >> 3);
+    i = (lb - by * bw) * kBlkW + lane % kBlkW;
+    j = by * kBlkH + lane / kBlkW;
     lin = (long long)j * v.W + i;
     return i < v.W && j < v.H;
 }
