@@ -514,6 +514,7 @@ def our_arm(args, rank, world):
             return ev
 
         marks = []  # (frame start, frame end) events of the timed loop's steps
+        host_t = []  # host clock when each of them was enqueued
 
         def frame(bs):
             f0 = torch.cuda.Event(enable_timing=True)
@@ -524,6 +525,7 @@ def our_arm(args, rank, world):
             done = torch.cuda.Event(enable_timing=True)
             done.record(stream)
             marks.append((f0, done))
+            host_t.append(time.perf_counter())
             return done
 
         def download(bs, done):
@@ -597,6 +599,7 @@ def our_arm(args, rank, world):
         b1.synchronize()
         down_ms = b0.elapsed_time(b1)
         marks.clear()
+        host_t.clear()
         # the timed steps of the overlapped loop: the bench's step count (its
         # first upload and last download, which nothing overlaps, are spread
         # over them)
@@ -604,8 +607,10 @@ def our_arm(args, rank, world):
         pms = e2e_loop(ke)
         # how the steps lay on the compute stream: each frame's own time, and
         # the wait before it (its inputs' upload, when that did not overlap)
-        frame_in_loop = statistics.median(a.elapsed_time(b) for a, b in marks)
-        gap_in_loop = statistics.median(marks[k - 1][1].elapsed_time(marks[k][0]) for k in range(1, len(marks)))
+        frames_in_loop = [a.elapsed_time(b) for a, b in marks]
+        gaps_in_loop = [marks[k - 1][1].elapsed_time(marks[k][0]) for k in range(1, len(marks))]
+        frame_in_loop, gap_in_loop = statistics.median(frames_in_loop), statistics.median(gaps_in_loop)
+        host_gap_max = 1e3 * max(b - a for a, b in zip(host_t, host_t[1:]))
         # the loop's last results reached the host: they equal the last
         # frame's losses and gradients on the device
         last = sets[(ke - 1) % 2]
@@ -621,6 +626,9 @@ def our_arm(args, rank, world):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": pms,
                "upload_ms_alone": up_ms, "download_ms_alone": down_ms,
                "frame_ms_in_loop": frame_in_loop, "gap_ms_between_frames": gap_in_loop,
+               "frame_ms_in_loop_max": max(frames_in_loop), "gap_ms_between_frames_max": max(gaps_in_loop),
+               "gap_ms_between_frames_total": sum(gaps_in_loop),
+               "host_ms_between_enqueues_max": host_gap_max,
                "path": "training loop through the public API: every step the parameters of every scene (positions, "
                        "velocities, colours: the host's copy) and the step's 8-bit target images go up from pinned "
                        "host memory (one copy each), pr_scene_update_batch steps every scene from them, the "
