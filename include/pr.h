@@ -420,7 +420,7 @@ void pr_graph_free(pr_graph *g);
  * is retried.  A bounded device-side wait that ran out returns
  * PR_ERR_TIMEOUT.
  * The first call on a device looks up the array's device address on that
- * device (with it current); make that first call before any stream capture.
+ * device (with it current).
  * Every call waits for its stream before it returns (it reads the frame's
  * status word back).  All calls share the array and it keeps the last
  * call's contents (each call clears what must start at zero); calls that

@@ -15,8 +15,7 @@
 // host thread) race on it: serialise them.  The host-side name of the array
 // is only a stand-in for the device symbol, so its device address is looked
 // up with cudaGetSymbolAddress once per device, on the first call made on
-// that device (with that device current); make that first call before any
-// stream capture.
+// that device (with that device current).
 #include <cuda_runtime.h>
 
 #include <algorithm>
