@@ -202,6 +202,14 @@ __device__ __noinline__ void pixel_hit64(const ViewDev &v, int i, int j, PixelHi
 // that cost more than the warp reductions they save.
 constexpr int kShadeBlocks = 1;
 
+// CTAs of the shading kernels: 64 threads (two warps), 18 resident per SM,
+// which caps them at 56 registers (36 warps per SM).  A CTA's slot frees
+// only when its slowest warp finishes, and the warps of a CTA see different
+// pixel blocks (background, one triangle, several), so small CTAs keep the
+// SM fuller: 64 x 18 measured fastest against 256 x 4, 128 x 8, 128 x 9,
+// 128 x 10, 64 x 16 and 32 x 32.
+constexpr int kShadeThreads = 64, kShadeCtasPerSm = 18;
+
 __device__ __forceinline__ bool block_pixel(const ViewDev *views, int nviews, const long long *blk_offs, long long b,
                                             int lane, int &q, long long &lin, int &i, int &j)
 {
@@ -444,7 +452,7 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 // L2 target, from the colour just computed -- so the frame needs no
 // separate adjoint pass.  Whole warps run (the adjoint's reductions).
 template <bool kAdjoint, int kFeat>
-__global__ void __launch_bounds__(256, 4) k_shade(const ViewDev *__restrict__ views, int nviews,
+__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm) k_shade(const ViewDev *__restrict__ views, int nviews,
                                               const long long *__restrict__ blk_offs, long long nblocks,
                                               unsigned long long *__restrict__ keys, int reset_keys,
                                               const Counters *__restrict__ frame_cnt)
@@ -573,11 +581,11 @@ cudaError_t launch_loss_finalize(const ViewDev *views, int nviews, const Counter
     return cudaGetLastError();
 }
 
-// Warps of kShadeBlocks blocks, 256 threads per CTA.
+// Warps of kShadeBlocks blocks, kShadeThreads threads per CTA.
 static unsigned shade_grid(long long nblocks)
 {
     const long long warps = (nblocks + kShadeBlocks - 1) / kShadeBlocks;
-    return (unsigned)((warps * 32 + 255) / 256);
+    return (unsigned)((warps * 32 + kShadeThreads - 1) / kShadeThreads);
 }
 
 template <bool kAdjoint>
@@ -586,26 +594,26 @@ static void launch_shade_t(int feat, unsigned g, const ViewDev *views, int nview
                            cudaStream_t st)
 {
     if (feat == kFeatF64) {  // the precision form without the specular and sampled-foveation paths
-        k_shade<kAdjoint, kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        k_shade<kAdjoint, kFeatF64><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         return;
     }
     if (feat & kFeatF64) {  // the precision form with either: one variant with every path (same bits)
-        k_shade<kAdjoint, kFeatSpec | kFeatLut | kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys,
+        k_shade<kAdjoint, kFeatSpec | kFeatLut | kFeatF64><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys,
                                                                              reset_keys, frame_cnt);
         return;
     }
     switch (feat) {
     case 0:
-        k_shade<kAdjoint, 0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        k_shade<kAdjoint, 0><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         break;
     case kFeatSpec:
-        k_shade<kAdjoint, kFeatSpec><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        k_shade<kAdjoint, kFeatSpec><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         break;
     case kFeatLut:
-        k_shade<kAdjoint, kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        k_shade<kAdjoint, kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
         break;
     default:
-        k_shade<kAdjoint, kFeatSpec | kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        k_shade<kAdjoint, kFeatSpec | kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
     }
 }
 
@@ -640,7 +648,7 @@ cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_
 // Stage (e) on its own: the adjoint of a shaded frame from its id buffer
 // and an upstream gradient.
 template <int kFeat>
-__global__ void __launch_bounds__(256, 4) k_backward(const ViewDev *__restrict__ views, int nviews,
+__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm) k_backward(const ViewDev *__restrict__ views, int nviews,
                                                  const long long *__restrict__ blk_offs, long long nblocks,
                                                  const Counters *__restrict__ frame_cnt)
 {
@@ -692,21 +700,21 @@ cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *b
     if (nblocks > 0) {
         const unsigned g = shade_grid(nblocks);
         if (feat & kFeatF64) {
-            k_backward<kFeatSpec | kFeatLut | kFeatF64><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            k_backward<kFeatSpec | kFeatLut | kFeatF64><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
             return cudaGetLastError();
         }
         switch (feat) {
         case 0:
-            k_backward<0><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            k_backward<0><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
             break;
         case kFeatSpec:
-            k_backward<kFeatSpec><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            k_backward<kFeatSpec><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
             break;
         case kFeatLut:
-            k_backward<kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            k_backward<kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
             break;
         default:
-            k_backward<kFeatSpec | kFeatLut><<<g, 256, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            k_backward<kFeatSpec | kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
         }
     }
     return cudaGetLastError();
