@@ -717,8 +717,7 @@ pr_status enqueue_batch(pr_workspace *ws, BatchPlan &P, int seg, bool shade, cud
     PR_TRY(mark(5));
     if (shade)  // resolves the keys too, and in a training frame runs the adjoint
         PR_TRY(launch_shade(dv, n, blk_offs, P.nblk, ws->keys.as<unsigned long long>(), reader_resets,
-                            !P.grads.empty(), cnt,
-                            shade_features(P.vd.data(), n), st));
+                            !P.grads.empty(), cnt, shade_features(P.vd.data(), n), st, P.vd.data()));
     if (shade && P.any_loss)  // the views' loss partial sums into the callers' losses
         PR_TRY(launch_loss_finalize(dv, n, cnt, st));
     // the reader has set every key of the frame back to ~0
@@ -1053,7 +1052,7 @@ pr_status pr_shade(pr_scene *sc, const pr_view *view, const uint32_t *id, float 
         return s;
     PR_TRY(launch_shade(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
                         pixel_blocks(v.W, v.H), nullptr, false, false, nullptr,
-                        shade_features(&v, 1), st));
+                        shade_features(&v, 1), st, &v));
     if (host_out)
         PR_TRY(cudaMemcpyAsync(rgb_out, ob->p, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
     PR_TRY(cudaStreamSynchronize(st));
@@ -1105,7 +1104,7 @@ pr_status pr_backward(pr_scene *sc, const pr_view *view, const uint32_t *id, con
     if (s != PR_OK)
         return s;
     PR_TRY(launch_backward(sc->ws.views.as<ViewDev>(), 1, sc->ws.offs.as<long long>(),
-                           pixel_blocks(v.W, v.H), nullptr, shade_features(&v, 1), st));
+                           pixel_blocks(v.W, v.H), nullptr, shade_features(&v, 1), st, &v));
     for (int a = 0; a < 3; ++a)
         if (host[a])
             PR_TRY(cudaMemcpyAsync(outs[a], douts[a], sizeof(float) * 3 * V, cudaMemcpyDeviceToHost, st));
@@ -1146,7 +1145,7 @@ pr_status pr_backward_batch(pr_workspace *ws, const pr_backward_view *views, int
     PR_TRY(cudaMemcpyAsync(ws->views.p, ws->h_views.p, sizeof(ViewDev) * n, cudaMemcpyHostToDevice, st));
     PR_TRY(cudaMemcpyAsync(ws->offs.p, blk, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
     PR_TRY(launch_backward(ws->views.as<ViewDev>(), n, ws->offs.as<long long>(), blk[n], nullptr,
-                           shade_features(ws->h_views.p, n), st));
+                           shade_features(ws->h_views.p, n), st, ws->h_views.p));
     PR_TRY(cudaStreamSynchronize(st));
     return PR_OK;
 }

@@ -71,6 +71,17 @@ struct ViewDev {
     unsigned long long bw_mul;         // ceil(2^40 / bw), bw = 8-pixel blocks per row: lb / bw = (lb * bw_mul) >> 40
 };
 
+// The views of a launch passed by value in the kernel's parameter space, for
+// batches of up to kParamViews views (72 x 416 bytes, within the 32 KB a
+// launch may pass).  A kernel then reads their fields through the constant
+// cache (warp-uniform, off the L1 path) and can re-read one instead of
+// holding it in a register.  Larger batches read the device table.
+constexpr int kParamViews = 72;
+struct ParamViews {
+    ViewDev v[kParamViews];
+};
+static_assert(sizeof(ParamViews) <= 30 * 1024, "the view table must fit the kernel parameter space");
+
 struct Counters {
     unsigned long long tests, hits, culled, flagged, changed;
     unsigned long long pairs_total, items_total;  // copied from the scan for the host

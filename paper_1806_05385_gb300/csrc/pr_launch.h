@@ -95,16 +95,19 @@ cudaError_t launch_resolve(const ViewDev *views, int nviews, const long long *pi
 // run stage (e) for the views with a gradient from the same pixel hit
 // feat: shade_features of the launch's views (which optional paths to build in)
 int shade_features(const ViewDev *vd, int n);
+// host_views: the host copy of the device table `views` (same contents), or
+// null; with one, a launch of up to kParamViews views passes them as a
+// kernel parameter
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                          unsigned long long *keys, bool reset_keys, bool adjoint, const Counters *frame_cnt, int feat,
-                         cudaStream_t st);
+                         cudaStream_t st, const ViewDev *host_views = nullptr);
 // a training frame's losses: each view's partial sums (loss_part) added into
 // its loss, once (skipped when the frame's forward overflowed)
 cudaError_t launch_loss_finalize(const ViewDev *views, int nviews, const Counters *frame_cnt, cudaStream_t st);
 // frame_cnt: the counters of the frame whose forward ran just before in the
 // same sequence (the adjoint is skipped if it overflowed), or null.
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                            const Counters *frame_cnt, int feat, cudaStream_t st);
+                            const Counters *frame_cnt, int feat, cudaStream_t st, const ViewDev *host_views = nullptr);
 
 // display step: unfoveation of a framebuffer image (pyramid: scratch of
 // mip_pyramid_floats(W, H) floats for the MIP method)

@@ -5,6 +5,8 @@
 // barycentrics from the id buffer instead of storing them.
 #include "pr_launch.h"
 
+#include <cstring>
+
 namespace pr {
 
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -451,11 +453,12 @@ __device__ __forceinline__ bool frame_overflowed(const Counters *frame_cnt)
 // stage (e) adjoint of the pixel follows from the same PixelHit -- with an
 // L2 target, from the colour just computed -- so the frame needs no
 // separate adjoint pass.  Whole warps run (the adjoint's reductions).
+// views: the device table, or the kernel's parameter table (k_shade_pv).
 template <bool kAdjoint, int kFeat>
-__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm) k_shade(const ViewDev *__restrict__ views, int nviews,
-                                              const long long *__restrict__ blk_offs, long long nblocks,
-                                              unsigned long long *__restrict__ keys, int reset_keys,
-                                              const Counters *__restrict__ frame_cnt)
+__device__ __forceinline__ void shade_body(const ViewDev *__restrict__ views, int nviews,
+                                           const long long *__restrict__ blk_offs, long long nblocks,
+                                           unsigned long long *__restrict__ keys, int reset_keys,
+                                           const Counters *__restrict__ frame_cnt)
 {
     const long long b0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kShadeBlocks;
     if (b0 >= nblocks)
@@ -550,6 +553,23 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm) k_shade(const 
         adjoint_flush(views, acc);
 }
 
+template <bool kAdjoint, int kFeat>
+__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm)
+    k_shade(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ blk_offs, long long nblocks,
+            unsigned long long *__restrict__ keys, int reset_keys, const Counters *__restrict__ frame_cnt)
+{
+    shade_body<kAdjoint, kFeat>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+}
+
+template <bool kAdjoint, int kFeat>
+__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm)
+    k_shade_pv(const __grid_constant__ ParamViews pv, int nviews, const long long *__restrict__ blk_offs,
+               long long nblocks, unsigned long long *__restrict__ keys, int reset_keys,
+               const Counters *__restrict__ frame_cnt)
+{
+    shade_body<kAdjoint, kFeat>(pv.v, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+}
+
 // A training frame's losses: one block per view sums the view's partial
 // sums and adds them to the caller's loss (views without a loss: nothing).
 __global__ void __launch_bounds__(kLossSlots) k_loss_finalize(const ViewDev *__restrict__ views,
@@ -588,32 +608,57 @@ static unsigned shade_grid(long long nblocks)
     return (unsigned)((warps * 32 + kShadeThreads - 1) / kShadeThreads);
 }
 
+// The parameter table of a launch's views (null: the batch is too large, or
+// the caller has no host copy; the kernels then read the device table).
+static const ParamViews *param_views(const ViewDev *host_views, int nviews)
+{
+    static thread_local ParamViews pv;
+    if (!host_views || nviews < 1 || nviews > kParamViews)
+        return nullptr;
+    std::memcpy(pv.v, host_views, sizeof(ViewDev) * (size_t)nviews);
+    return &pv;
+}
+
+template <bool kAdjoint, int kFeat>
+static void launch_shade_one(unsigned g, const ViewDev *views, const ParamViews *pv, int nviews,
+                             const long long *blk_offs, long long nblocks, unsigned long long *keys, int reset_keys,
+                             const Counters *frame_cnt, cudaStream_t st)
+{
+    if (pv)
+        k_shade_pv<kAdjoint, kFeat><<<g, kShadeThreads, 0, st>>>(*pv, nviews, blk_offs, nblocks, keys, reset_keys,
+                                                                 frame_cnt);
+    else
+        k_shade<kAdjoint, kFeat><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys,
+                                                              frame_cnt);
+}
+
 template <bool kAdjoint>
-static void launch_shade_t(int feat, unsigned g, const ViewDev *views, int nviews, const long long *blk_offs,
-                           long long nblocks, unsigned long long *keys, int reset_keys, const Counters *frame_cnt,
-                           cudaStream_t st)
+static void launch_shade_t(int feat, unsigned g, const ViewDev *views, const ParamViews *pv, int nviews,
+                           const long long *blk_offs, long long nblocks, unsigned long long *keys, int reset_keys,
+                           const Counters *frame_cnt, cudaStream_t st)
 {
     if (feat == kFeatF64) {  // the precision form without the specular and sampled-foveation paths
-        k_shade<kAdjoint, kFeatF64><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        launch_shade_one<kAdjoint, kFeatF64>(g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
         return;
     }
     if (feat & kFeatF64) {  // the precision form with either: one variant with every path (same bits)
-        k_shade<kAdjoint, kFeatSpec | kFeatLut | kFeatF64><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys,
-                                                                             reset_keys, frame_cnt);
+        launch_shade_one<kAdjoint, kFeatSpec | kFeatLut | kFeatF64>(g, views, pv, nviews, blk_offs, nblocks, keys,
+                                                                    reset_keys, frame_cnt, st);
         return;
     }
     switch (feat) {
     case 0:
-        k_shade<kAdjoint, 0><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        launch_shade_one<kAdjoint, 0>(g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
         break;
     case kFeatSpec:
-        k_shade<kAdjoint, kFeatSpec><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        launch_shade_one<kAdjoint, kFeatSpec>(g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
         break;
     case kFeatLut:
-        k_shade<kAdjoint, kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        launch_shade_one<kAdjoint, kFeatLut>(g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
         break;
     default:
-        k_shade<kAdjoint, kFeatSpec | kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt);
+        launch_shade_one<kAdjoint, kFeatSpec | kFeatLut>(g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys,
+                                                         frame_cnt, st);
     }
 }
 
@@ -633,14 +678,15 @@ int shade_features(const ViewDev *vd, int n)
 
 cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
                          unsigned long long *keys, bool reset_keys, bool adjoint, const Counters *frame_cnt, int feat,
-                         cudaStream_t st)
+                         cudaStream_t st, const ViewDev *host_views)
 {
     if (nblocks > 0) {
         const unsigned g = shade_grid(nblocks);
+        const ParamViews *pv = param_views(host_views, nviews);
         if (adjoint)
-            launch_shade_t<true>(feat, g, views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
+            launch_shade_t<true>(feat, g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
         else
-            launch_shade_t<false>(feat, g, views, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
+            launch_shade_t<false>(feat, g, views, pv, nviews, blk_offs, nblocks, keys, reset_keys, frame_cnt, st);
     }
     return cudaGetLastError();
 }
@@ -648,9 +694,9 @@ cudaError_t launch_shade(const ViewDev *views, int nviews, const long long *blk_
 // Stage (e) on its own: the adjoint of a shaded frame from its id buffer
 // and an upstream gradient.
 template <int kFeat>
-__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm) k_backward(const ViewDev *__restrict__ views, int nviews,
-                                                 const long long *__restrict__ blk_offs, long long nblocks,
-                                                 const Counters *__restrict__ frame_cnt)
+__device__ __forceinline__ void backward_body(const ViewDev *__restrict__ views, int nviews,
+                                              const long long *__restrict__ blk_offs, long long nblocks,
+                                              const Counters *__restrict__ frame_cnt)
 {
     const long long b0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kShadeBlocks;
     if (b0 >= nblocks)
@@ -694,27 +740,55 @@ __global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm) k_backward(con
     adjoint_flush(views, acc);
 }
 
+template <int kFeat>
+__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm)
+    k_backward(const ViewDev *__restrict__ views, int nviews, const long long *__restrict__ blk_offs, long long nblocks,
+               const Counters *__restrict__ frame_cnt)
+{
+    backward_body<kFeat>(views, nviews, blk_offs, nblocks, frame_cnt);
+}
+
+template <int kFeat>
+__global__ void __launch_bounds__(kShadeThreads, kShadeCtasPerSm)
+    k_backward_pv(const __grid_constant__ ParamViews pv, int nviews, const long long *__restrict__ blk_offs,
+                  long long nblocks, const Counters *__restrict__ frame_cnt)
+{
+    backward_body<kFeat>(pv.v, nviews, blk_offs, nblocks, frame_cnt);
+}
+
+template <int kFeat>
+static void launch_backward_one(unsigned g, const ViewDev *views, const ParamViews *pv, int nviews,
+                                const long long *blk_offs, long long nblocks, const Counters *frame_cnt,
+                                cudaStream_t st)
+{
+    if (pv)
+        k_backward_pv<kFeat><<<g, kShadeThreads, 0, st>>>(*pv, nviews, blk_offs, nblocks, frame_cnt);
+    else
+        k_backward<kFeat><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+}
+
 cudaError_t launch_backward(const ViewDev *views, int nviews, const long long *blk_offs, long long nblocks,
-                            const Counters *frame_cnt, int feat, cudaStream_t st)
+                            const Counters *frame_cnt, int feat, cudaStream_t st, const ViewDev *host_views)
 {
     if (nblocks > 0) {
         const unsigned g = shade_grid(nblocks);
+        const ParamViews *pv = param_views(host_views, nviews);
         if (feat & kFeatF64) {
-            k_backward<kFeatSpec | kFeatLut | kFeatF64><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            launch_backward_one<kFeatSpec | kFeatLut | kFeatF64>(g, views, pv, nviews, blk_offs, nblocks, frame_cnt, st);
             return cudaGetLastError();
         }
         switch (feat) {
         case 0:
-            k_backward<0><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            launch_backward_one<0>(g, views, pv, nviews, blk_offs, nblocks, frame_cnt, st);
             break;
         case kFeatSpec:
-            k_backward<kFeatSpec><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            launch_backward_one<kFeatSpec>(g, views, pv, nviews, blk_offs, nblocks, frame_cnt, st);
             break;
         case kFeatLut:
-            k_backward<kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            launch_backward_one<kFeatLut>(g, views, pv, nviews, blk_offs, nblocks, frame_cnt, st);
             break;
         default:
-            k_backward<kFeatSpec | kFeatLut><<<g, kShadeThreads, 0, st>>>(views, nviews, blk_offs, nblocks, frame_cnt);
+            launch_backward_one<kFeatSpec | kFeatLut>(g, views, pv, nviews, blk_offs, nblocks, frame_cnt, st);
         }
     }
     return cudaGetLastError();

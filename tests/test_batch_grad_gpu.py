@@ -508,6 +508,69 @@ def test_backward_batch_equals_per_view(pr):
             pr.pr_scene_free(h)
 
 
+def _views_many(n=80):
+    """More views than a launch passes as a kernel parameter (72): the
+    shading and adjoint kernels then read the views from the device table,
+    while one-view calls pass theirs as a parameter."""
+    scenes = [S.random_triangles(300 + 100 * k, 60 + k, offset=0.5 if k % 2 else None) for k in range(5)]
+    out = []
+    for k in range(n):
+        p0, p1 = S.head_poses(0.5 + 0.1 * k, 0.05 * k, 0.002 * k)
+        v = S.View(W=40 + (7 * k) % 50, H=33 + (5 * k) % 40, tan_x=0.55, tan_y=0.5, pose0=p0, pose1=p1, mode=k % 4,
+                   fovea=(0.3 + 0.005 * k, 0.6 - 0.003 * k))
+        out.append((k % 5, v, (8, 16, 32)[k % 3]))
+    return scenes, out
+
+
+def test_batches_beyond_the_parameter_table(pr):
+    """80 views in one batch (the device-table kernels) against one-view
+    calls (the parameter-table kernels): forward bit for bit, the adjoint of
+    the batch and of a training frame up to the order of float atomics."""
+    import torch
+    scenes, cases = _views_many()
+    handles = [_upload(pr, sc) for sc in scenes]
+    ws = pr.pr_workspace_create()
+    try:
+        rng = np.random.default_rng(5)
+        entries, outs, bwd, per, fgrads = [], [], [], [], []
+        for si, v, tile in cases:
+            h, sc, n = handles[si], scenes[si], v.W * v.H
+            o = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, device="cuda"),
+                 torch.empty(3 * n, device="cuda"))
+            outs.append(o)
+            entries.append((h, v, o[0], o[1], o[2], tile))
+        pr.pr_rasterize_batch(ws, entries)
+        for (si, v, tile), o in zip(cases, outs):
+            h, sc, n = handles[si], scenes[si], v.W * v.H
+            ids = torch.empty(n, dtype=torch.int32, device="cuda")
+            dep = torch.empty(n, device="cuda")
+            rgb = torch.empty(3 * n, device="cuda")
+            pr.pr_rasterize(h, v, pr.make_params("zenon", tile), ids, dep)
+            pr.pr_shade(h, v, ids, rgb)
+            assert torch.equal(ids, o[0]) and torch.equal(dep, o[1]) and torch.equal(rgb, o[2])
+            g = _dev(rng.normal(size=3 * n).astype(np.float32))
+            a = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            b = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            f = tuple(torch.zeros(3 * sc.V, device="cuda") for _ in range(3))
+            bwd.append((h, v, ids, g, *a))
+            pr.pr_backward(h, v, ids, g, *b)
+            per.append(b)
+            fgrads.append(dict(grad_rgb=g, dcol=f[0], dpos=f[1], dvel=f[2]))
+        assert sum(float((o[0] >= 0).sum()) for o in outs) > 0
+        pr.pr_backward_batch(ws, bwd)
+        pr.pr_frame_batch(ws, entries, fgrads)
+        for e, b, f in zip(bwd, per, fgrads):
+            for x, y in zip(e[4:], b):
+                assert torch.allclose(x, y, rtol=1e-4, atol=1e-5 * float(y.abs().max()) + 1e-12)
+            for x, y in zip((f["dcol"], f["dpos"], f["dvel"]), b):
+                assert torch.allclose(x, y, rtol=1e-4, atol=1e-5 * float(y.abs().max()) + 1e-12)
+        assert sum(float(b[0].abs().sum()) for b in per) > 0
+    finally:
+        pr.pr_workspace_free(ws)
+        for h in handles:
+            pr.pr_scene_free(h)
+
+
 def _frame_setup(pr, cases):
     import torch
     handles = [_upload(pr, sc) for sc, _, _ in cases]
