@@ -22,6 +22,7 @@ resident in HBM.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -604,7 +605,17 @@ def our_arm(args, rank, world):
         # first upload and last download, which nothing overlaps, are spread
         # over them)
         ke = max(3, args.steps)
-        pms = e2e_loop(ke)
+        # the host waits for a frame every step, so a pause of this Python
+        # process idles the GPU (one run saw a 16 ms stall between two
+        # enqueues); the cyclic garbage collector, the pause the harness
+        # itself can cause, runs before the timed loops and not during them,
+        # as timeit does
+        gc.collect()
+        gc.disable()
+        try:
+            pms = e2e_loop(ke)
+        finally:
+            gc.enable()
         # how the steps lay on the compute stream: each frame's own time, and
         # the wait before it (its inputs' upload, when that did not overlap)
         frames_in_loop = [a.elapsed_time(b) for a, b in marks]
@@ -616,7 +627,12 @@ def our_arm(args, rank, world):
         last = sets[(ke - 1) % 2]
         assert torch.equal(last["loss"].cpu(), hloss), "end-to-end losses differ from the device's"
         assert torch.equal(last["g"].cpu(), hgrad), "end-to-end gradients differ from the device's"
-        sms = e2e_loop(k2, overlap=False)
+        gc.collect()
+        gc.disable()
+        try:
+            sms = e2e_loop(k2, overlap=False)
+        finally:
+            gc.enable()
         B.pr_graph_free(graph2)
         for h in handles2:
             B.pr_scene_free(h)
@@ -639,7 +655,7 @@ def our_arm(args, rank, world):
                        "in turn, so the next step's uploads (second stream, after the set's last frame on the "
                        "device) and this step's downloads (third stream) overlap the frames; L2 flushed before "
                        "every frame; K steps timed as a whole with CUDA events from the first upload to the last "
-                       "download",
+                       "download, Python's cyclic garbage collector paused during the timed steps",
                "serial": {"value": world * pix / (sms * 1e-3) / 1e6, "ms_per_step": sms,
                           "path": "the same calls and copies on one buffer set with no overlap across steps: "
                                   "upload, frame, download, wait, status, then the next step's upload"}}
