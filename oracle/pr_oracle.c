@@ -23,7 +23,7 @@
  *       hit if all barycentrics >= 0 and ray parameter s > z_near
  *     winner = lexicographic minimum of (s, triangle id)  (z-buffering, Sec. 3.2)
  *
- * Readings of the paper taken here (each is also listed in the design notes):
+ * Readings of the paper taken here:
  *  - q maps a framebuffer (foveated-image) location to its display location:
  *    q(u) = x_f + (u - x_f)/|u - x_f| * p(|u - x_f|), p(d) = D (d/D)^alpha,
  *    D = sqrt(2) (the domain of p in Sec. 3.1.1), so p(D) = D and alpha = 1
